@@ -1,0 +1,211 @@
+/*
+ * pt.h -- C ABI of libpt, the GB300 (sm_103a) hot path of the Phylogenetic
+ * Topographer (PT), arXiv 1811.11007.
+ *
+ * PT maps the "high likelihood set": every tree topology whose maximised
+ * log-likelihood lies within a threshold T of the best one found (section
+ * "Methods Overview").  Starting from a set of topologies it repeatedly
+ * visits (fully optimises) topologies, and proposes their NNI neighbours:
+ * each unvisited neighbour is partially optimised and kept for a visit only
+ * if its partial log-likelihood clears lmax - T (section "Phylogenetic
+ * Topographer", the numbered loop).  This library runs one round of that
+ * loop for a whole frontier of topologies on the GPU:
+ *   keys  -> dedup against a device visited table -> proposal optimisation
+ *   (Newton on the five branches the NNI touches) -> threshold ->
+ *   full optimisation of the kept ones -> next frontier.
+ *
+ * Conventions
+ *   - Every call returns pt_status; nothing throws across the ABI.  After an
+ *     error, pt_last_error() holds a one-line description.
+ *   - Host pointers unless the name ends in _dev (device pointers).  The
+ *     library copies every input before returning; outputs are written into
+ *     caller-owned buffers.  Calls with an output capacity report the
+ *     required count and return PT_ERR_BUFFER_TOO_SMALL when it is exceeded.
+ *   - Trees are unrooted binary trees on n taxa: leaves 0..n-1, inner nodes
+ *     n..2n-3, given as 2n-3 edges (int32 pairs) with one length per edge.
+ *     Inner-node labels and edge order are free.  Outputs use the canonical
+ *     edge list: rooted at leaf 0, inner nodes numbered in pre-order with
+ *     children taken in order of their smallest taxon, edge k = (k+1, parent
+ *     of k+1).
+ *   - Lengths and log-likelihoods are FP64 at the boundary in both precision
+ *     modes.  threshold is the magnitude of the paper's negative offset T
+ *     (keep iff lnL >= lmax - threshold); INFINITY keeps everything.
+ *   - A context is used by one host thread at a time; all device work is
+ *     issued on the context's stream (pt_set_stream).
+ */
+#ifndef PT_H
+#define PT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct pt_ctx pt_ctx;
+
+/* Canonical split-set key of a topology: the sum mod 2^128 of a 128-bit hash
+ * of every non-trivial split, each split taken as the side without taxon 0
+ * (replaces the paper's sorted Newick string key, section "Phylogenetic
+ * Topographer").  Zero is reserved for empty table slots and reported as 1. */
+typedef struct { uint64_t lo, hi; } pt_key;
+
+typedef enum {
+    PT_OK = 0,
+    PT_ERR_INVALID_ARG = 1,      /* bad pointer, size, tree or model parameter */
+    PT_ERR_OOM = 2,              /* device allocation failed */
+    PT_ERR_TABLE_FULL = 3,       /* visited table probe limit reached */
+    PT_ERR_BUFFER_TOO_SMALL = 4, /* output capacity below the required count */
+    PT_ERR_CUDA = 5,             /* a CUDA runtime call failed */
+    PT_ERR_TIMEOUT = 6,          /* a bounded device wait ran out */
+    PT_ERR_STATE = 7             /* call out of order (no alignment / model) */
+} pt_status;
+
+enum { PT_PREC_FP64 = 0, PT_PREC_MIXED = 1 };   /* FP64 everywhere / FP32 partials + FP64 reductions */
+enum { PT_SCORE_FIXED = 0, PT_SCORE_FULL = 1 }; /* lnL at the given lengths / after full optimisation */
+enum { PT_PROPOSE_FIVE = 0, PT_PROPOSE_CENTRAL = 1 };
+enum { PT_ST_REJECTED = 1, PT_ST_GOOD = 2, PT_ST_BAD = 3 };
+
+typedef struct {
+    int device;           /* CUDA device ordinal */
+    int precision;        /* PT_PREC_* */
+    int table_log2;       /* visited table of 2^table_log2 slots per alignment (10..30) */
+    int propose_mode;     /* PT_PROPOSE_FIVE (default) or PT_PROPOSE_CENTRAL (the paper's radius 0) */
+    double tmin, tmax;    /* branch-length bounds */
+    double newton_tol;    /* stop when a Newton step moves the length by <= newton_tol */
+    int newton_maxit;     /* evaluations per branch per visit of that branch */
+    double sweep_tol;     /* stop sweeping when a sweep gains < sweep_tol nats */
+    int full_max_sweeps;  /* cap on sweeps of the full optimisation */
+    int prop_max_sweeps;  /* cap on sweeps of the proposal optimisation */
+    int threads;          /* threads per CTA for the site loops (0 = automatic) */
+    size_t mem_budget;    /* device bytes for partial-likelihood buffers per launch group (0 = automatic) */
+} pt_config;
+
+/* Fills cfg with the defaults: device 0, mixed precision, 2^22 slots, five
+ * branches, t in [1e-6, 100], newton_tol 1e-8, 50 evaluations, sweep_tol
+ * 1e-9, 64 full / 8 proposal sweeps. */
+void pt_config_default(pt_config *cfg);
+
+/* Creates a context on cfg->device (NULL cfg = defaults).  *out owns every
+ * device buffer it allocates; pt_destroy frees them. */
+pt_status pt_create(pt_ctx **out, const pt_config *cfg);
+void pt_destroy(pt_ctx *ctx);
+const char *pt_last_error(const pt_ctx *ctx);
+
+/* Issues all further device work on `cuda_stream` (a cudaStream_t owned by
+ * the caller, e.g. PyTorch's current stream; NULL = the legacy stream). */
+pt_status pt_set_stream(pt_ctx *ctx, void *cuda_stream);
+
+/* Copies an alignment, compresses identical columns into site patterns with
+ * integer weights, and uploads it.  codes: [n_taxa][n_sites] bytes, 0..3 =
+ * A C G T, 4 = gap / unknown (contributes an all-ones tip vector, i.e. the
+ * character is summed out).  3 <= n_taxa <= 128.  Writes the new alignment
+ * id.  The data model follows section "Phylogenetic Topographer": PT takes an
+ * alignment plus model parameters. */
+pt_status pt_load_alignment(pt_ctx *ctx, int n_taxa, int n_sites, const uint8_t *codes, int *aln_id);
+
+/* Number of taxa and of unique site patterns of an alignment. */
+pt_status pt_alignment_info(pt_ctx *ctx, int aln_id, int *n_taxa, int *n_patterns);
+
+/* Sets the substitution model of an alignment: GTR with exchangeabilities
+ * exch (order AC AG AT CG CT GT, > 0) and base frequencies freqs (> 0, summing
+ * to 1), normalised to one expected substitution per unit time, with
+ * discrete Gamma(alpha) rate variation over n_cats equal-probability
+ * categories, each represented by its mean rate (n_cats = 1 disables rate
+ * variation; 1, 2, 4 supported).  JC69 = all exch equal, freqs 1/4 (sections
+ * "Phylogenetic Topographer" and "Maximum Likelihood Estimation of Local
+ * Maxima" name JC69+Gamma and GTR). */
+pt_status pt_set_model(pt_ctx *ctx, int aln_id, const double exch[6], const double freqs[4], double alpha,
+                       int n_cats);
+
+/* Host-side view of the model actually used: the n_cats category rates. */
+pt_status pt_model_rates(pt_ctx *ctx, int aln_id, double *rates, int cap);
+
+/* Scores n_trees topologies.  edges: [n_trees][2n-3][2], lengths:
+ * [n_trees][2n-3] (in: starting lengths; out: optimised lengths when mode =
+ * PT_SCORE_FULL, in the caller's edge order).  lnl_out: [n_trees]; keys_out
+ * [n_trees] may be NULL.  FULL = the visit step's full branch optimisation
+ * (loop step 2 of section "Phylogenetic Topographer"): sweeps over all 2n-3
+ * branches in pre-order from leaf 0, one safeguarded Newton solve per branch. */
+pt_status pt_score_topologies(pt_ctx *ctx, int aln_id, int n_trees, const int32_t *edges, double *lengths,
+                              double *lnl_out, pt_key *keys_out, int mode);
+
+/* Round 0 of a search: fully optimises the start trees, enters the first of
+ * each distinct topology into the visited table, sets *lmax_out to the best
+ * lnL, and returns as frontier (canonical edges, lengths, lnL, keys) the
+ * starts with lnL >= lmax - threshold (loop steps 1-5).  Resets the
+ * alignment's visited table and round counter first. */
+pt_status pt_begin(pt_ctx *ctx, int aln_id, int n_start, const int32_t *edges, const double *lengths,
+                   double threshold, double *lmax_out, int cap, int32_t *front_edges, double *front_lengths,
+                   double *front_lnl, pt_key *front_keys, int *n_front);
+
+/* One round of PT on a frontier (loop step 6 for every frontier tree, then
+ * steps 1-5 for every neighbour it keeps).  Every NNI neighbour (2(n-3) per
+ * tree) whose key is not yet visited is proposal-optimised once -- among
+ * equal keys of this round the proposer with the smallest (parent key, edge
+ * split, swap) wins -- and kept iff its proposal lnL >= *lmax_inout -
+ * threshold.  Kept neighbours are fully optimised; *lmax_inout is raised to
+ * the best result; those with lnL >= the new lmax - threshold are GOOD and
+ * returned as the next frontier (cap entries at most, count in *n_kept).
+ * Frontier trees absent from the visited table are entered as GOOD first.
+ * Host buffers: the timed end-to-end path copies in and out. */
+pt_status pt_expand_frontier(pt_ctx *ctx, int aln_id, int n_frontier, const int32_t *edges,
+                             const double *lengths, double threshold, double *lmax_inout, int cap,
+                             int32_t *kept_edges, double *kept_lengths, double *kept_lnl, pt_key *kept_keys,
+                             int *n_kept);
+
+/* pt_expand_frontier on device-resident buffers (same layouts; keys as
+ * [count][2] uint64).  Only *lmax_inout and *n_kept are host values. */
+pt_status pt_expand_frontier_dev(pt_ctx *ctx, int aln_id, int n_frontier, const int32_t *edges_dev,
+                                 const double *lengths_dev, double threshold, double *lmax_inout, int cap,
+                                 int32_t *kept_edges_dev, double *kept_lengths_dev, double *kept_lnl_dev,
+                                 uint64_t *kept_keys_dev, int *n_kept);
+
+/* Dumps the visited table of an alignment (every topology scored so far):
+ * keys, status (PT_ST_*), lnL (full lnL for visited topologies, proposal
+ * lnL for rejected ones).  Writes min(cap, count) entries in table order and
+ * the total in *count. */
+pt_status pt_visited(pt_ctx *ctx, int aln_id, size_t cap, pt_key *keys, uint8_t *status, double *lnl,
+                     size_t *count);
+
+/* Clears the visited table and round counter of an alignment. */
+pt_status pt_reset_visited(pt_ctx *ctx, int aln_id);
+
+/* Counters of the last round (or begin / score call): [0] candidates, [1]
+ * already visited, [2] scored (unique proposals), [3] kept, [4] good,
+ * [5] proposal Newton evaluations, [6] full-optimisation Newton
+ * evaluations, [7] non-converged Newton solves, [8] proposal sweeps,
+ * [9] full-optimisation sweeps. */
+pt_status pt_stats(pt_ctx *ctx, int64_t *out, int cap);
+
+/* Per-neighbour detail of the last round, for parity tests: for each scored
+ * proposal, its key, parent index in the frontier as given, canonical edge
+ * node, swap, proposal lnL and the five optimised lengths (central, A, B, C,
+ * D).  Returns the count in *count. */
+pt_status pt_last_proposals(pt_ctx *ctx, size_t cap, pt_key *keys, int32_t *parent, int32_t *edge_node,
+                            int32_t *swap, double *lnl, double *len5, size_t *count);
+
+/* Device time of the last call's kernels by stage, in milliseconds:
+ * [0] canonicalise+keys, [1] dedup, [2] frontier partials, [3] proposal
+ * Newton, [4] full optimisation, [5] total.  Timed with CUDA events on the
+ * context stream when cfg threads >= 0; zeros if timing is off. */
+pt_status pt_stage_times(pt_ctx *ctx, double *ms, int cap);
+
+/* Library version string. */
+const char *pt_version(void);
+
+/* Host-only helpers (no device, no context), for checking the model set-up:
+ * the discrete-Gamma mean rates of n_cats (1..4) equal-probability
+ * categories of Gamma(alpha, rate alpha), renormalised to mean 1; and the
+ * eigen-decomposition used for P(t): lam[4] and R[16] (R[i*4+k] = component
+ * i of eigenvector k of D^1/2 Q D^-1/2, D = diag(freqs), Q the normalised GTR
+ * matrix).  Return PT_OK or PT_ERR_INVALID_ARG. */
+int pt_discrete_gamma(double alpha, int n_cats, double *rates);
+int pt_model_eigen(const double exch[6], const double freqs[4], double *lam, double *R);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PT_H */

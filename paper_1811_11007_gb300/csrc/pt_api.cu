@@ -1,0 +1,959 @@
+// Host side of libpt: context, ABI entry points, model set-up, pattern
+// compression and the round driver.  Every step of a round runs in the
+// kernels of pt_kernels.cu; this file validates, sizes, launches and copies.
+#include "pt.h"
+#include "pt_internal.h"
+
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <string>
+#include <vector>
+
+using namespace pt;
+
+namespace {
+
+struct DevBuf {
+    void* p = nullptr;
+    size_t n = 0;
+};
+
+struct AlnState {
+    int n = 0, sites = 0, P = 0;
+    uint8_t* tips = nullptr;
+    int32_t* w = nullptr;
+    bool has_model = false;
+    Model M{};
+    Slot* table = nullptr;
+    int log2 = 0;
+    int round = 0;
+};
+
+struct Ctx {
+    pt_config cfg{};
+    cudaStream_t stream = nullptr;
+    std::string err;
+    std::vector<AlnState> alns;
+    std::map<std::string, DevBuf> bufs;
+    int32_t* d_err = nullptr;
+    unsigned long long* d_stats = nullptr;
+    double* d_lmax = nullptr;
+    int64_t stats[kStWords] = {0};
+    int sm_count = 0;
+    size_t smem_optin = 0;
+    size_t budget = 0;
+    cudaEvent_t ev[8] = {};
+    double stage_ms[8] = {0};
+    bool timing = true;
+    // last round's proposals, for pt_last_proposals
+    int last_items = 0;
+};
+
+struct Fail {
+    pt_status st;
+};
+
+void fail(Ctx& c, pt_status st, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    c.err = buf;
+    throw Fail{st};
+}
+
+void ck(Ctx& c, cudaError_t e, const char* what) {
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        fail(c, e == cudaErrorMemoryAllocation ? PT_ERR_OOM : PT_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+    }
+}
+
+// Grow-only named device buffer.  cudaFree synchronises the device, so a
+// buffer still referenced by queued kernels is never released early.
+template <typename T>
+T* buf(Ctx& c, const std::string& name, size_t count) {
+    DevBuf& b = c.bufs[name];
+    size_t bytes = std::max<size_t>(count * sizeof(T), 16);
+    if (b.n < bytes) {
+        if (b.p) cudaFree(b.p);
+        b.p = nullptr;
+        b.n = 0;
+        size_t nb = bytes + bytes / 4;
+        ck(c, cudaMalloc(&b.p, nb), ("allocating " + name).c_str());
+        b.n = nb;
+    }
+    return reinterpret_cast<T*>(b.p);
+}
+
+TreeSet treeset(Ctx& c, const std::string& pre, int n, int cap, bool with_emap) {
+    TreeSet t;
+    const int NN = 2 * n - 2;
+    t.n = n;
+    t.cap = cap;
+    t.up = buf<int32_t>(c, pre + ".up", (size_t)cap * NN);
+    t.ch = buf<int32_t>(c, pre + ".ch", (size_t)cap * NN * 2);
+    t.len = buf<double>(c, pre + ".len", (size_t)cap * NN);
+    t.bits = buf<uint64_t>(c, pre + ".bits", (size_t)cap * NN * 2);
+    t.erank = buf<int32_t>(c, pre + ".erank", (size_t)cap * NN);
+    t.sched = buf<int32_t>(c, pre + ".sched", (size_t)cap * 3 * n);
+    t.key = buf<uint64_t>(c, pre + ".key", (size_t)cap * 2);
+    t.emap = with_emap ? buf<int32_t>(c, pre + ".emap", (size_t)cap * (2 * n - 3)) : nullptr;
+    return t;
+}
+
+AlnState& aln_of(Ctx& c, int id, bool need_model = true) {
+    if (id < 0 || id >= (int)c.alns.size()) fail(c, PT_ERR_INVALID_ARG, "unknown alignment id %d", id);
+    AlnState& a = c.alns[id];
+    if (need_model && !a.has_model) fail(c, PT_ERR_STATE, "alignment %d has no model (call pt_set_model)", id);
+    return a;
+}
+
+Cfg kcfg(const Ctx& c) {
+    Cfg k;
+    k.tmin = c.cfg.tmin;
+    k.tmax = c.cfg.tmax;
+    k.newton_tol = c.cfg.newton_tol;
+    k.sweep_tol = c.cfg.sweep_tol;
+    k.newton_maxit = c.cfg.newton_maxit;
+    k.full_max_sweeps = c.cfg.full_max_sweeps;
+    k.prop_max_sweeps = c.cfg.prop_max_sweeps;
+    k.propose_mode = c.cfg.propose_mode;
+    return k;
+}
+
+int threads_for(const Ctx& c, int P) {
+    if (c.cfg.threads > 0) return c.cfg.threads;
+    return P <= 128 ? 128 : 256;
+}
+
+Aln aln_dev(const AlnState& a) { return Aln{a.n, a.P, a.tips, a.w}; }
+
+size_t rsize(const Ctx& c) { return c.cfg.precision == PT_PREC_FP64 ? 8 : 4; }
+
+// bytes of the partial-likelihood buffers of one tree
+size_t tree_clv_bytes(const Ctx& c, const AlnState& a) {
+    size_t slots = (size_t)(2 * a.n - 5);
+    return slots * a.P * (4 * (size_t)a.M.C * rsize(c) + 4);
+}
+
+ClvGroup clv_group(Ctx& c, const std::string& pre, const AlnState& a, int count) {
+    ClvGroup g;
+    size_t slots = (size_t)(2 * a.n - 5);
+    g.tree_stride = slots * a.P * 4 * a.M.C;
+    g.scl_stride = slots * a.P;
+    g.clv = buf<unsigned char>(c, pre + ".clv", (size_t)count * g.tree_stride * rsize(c));
+    g.scl = buf<int32_t>(c, pre + ".scl", (size_t)count * g.scl_stride);
+    return g;
+}
+
+int chunk_trees(const Ctx& c, const AlnState& a) {
+    size_t per = tree_clv_bytes(c, a) + (size_t)(2 * a.n - 2) * a.M.C * 16 * rsize(c);
+    size_t g = c.budget / std::max<size_t>(per, 1);
+    return (int)std::max<size_t>(1, std::min<size_t>(g, 1 << 20));
+}
+
+void zero_flags(Ctx& c) {
+    ck(c, cudaMemsetAsync(c.d_err, 0, sizeof(int32_t) * kErrWords, c.stream), "memset err");
+}
+
+void check_flags(Ctx& c) {
+    int32_t h[kErrWords];
+    ck(c, cudaMemcpyAsync(h, c.d_err, sizeof h, cudaMemcpyDeviceToHost, c.stream), "read flags");
+    ck(c, cudaStreamSynchronize(c.stream), "stream sync");
+    if (h[kErrTree]) fail(c, PT_ERR_INVALID_ARG, "tree %d is not an unrooted binary tree on leaves 0..n-1", h[kErrTree] - 1);
+    if (h[kErrTable]) fail(c, PT_ERR_TABLE_FULL, "visited table probe limit reached (raise table_log2)");
+    if (h[kErrKey]) fail(c, PT_ERR_STATE, "neighbour key mismatch (internal error)");
+}
+
+void begin_stats(Ctx& c) {
+    ck(c, cudaMemsetAsync(c.d_stats, 0, sizeof(unsigned long long) * kStWords, c.stream), "memset stats");
+    for (double& x : c.stage_ms) x = 0.0;
+}
+
+void end_stats(Ctx& c, const int64_t* host_counts) {
+    unsigned long long h[kStWords];
+    ck(c, cudaMemcpyAsync(h, c.d_stats, sizeof h, cudaMemcpyDeviceToHost, c.stream), "read stats");
+    ck(c, cudaStreamSynchronize(c.stream), "stream sync");
+    for (int i = 0; i < kStWords; ++i) c.stats[i] = (int64_t)h[i];
+    if (host_counts)
+        for (int i : {kStCand, kStScored, kStKept}) c.stats[i] = host_counts[i];
+}
+
+// exclusive scan of N flags; returns the total
+int scan_count(Ctx& c, const int32_t* flag, int32_t* pos, int N) {
+    if (N <= 0) return 0;
+    int32_t* tmp = buf<int32_t>(c, "scan.tmp", (size_t)(N + 1023) / 1024 + 1);
+    launch_scan(c.stream, flag, pos, N, tmp);
+    int32_t last[2];
+    ck(c, cudaMemcpyAsync(&last[0], pos + N - 1, 4, cudaMemcpyDeviceToHost, c.stream), "scan total");
+    ck(c, cudaMemcpyAsync(&last[1], flag + N - 1, 4, cudaMemcpyDeviceToHost, c.stream), "scan total");
+    ck(c, cudaStreamSynchronize(c.stream), "stream sync");
+    return last[0] + last[1];
+}
+
+void mark(Ctx& c, int i) {
+    if (c.timing) cudaEventRecord(c.ev[i], c.stream);
+}
+
+// ---------------------------------------------------------------- model set-up (host)
+// Regularised lower incomplete gamma P(a, x): series for x < a + 1, else
+// 1 - Q(a, x) with Q as a continued fraction (modified Lentz).
+double inc_gamma_p(double a, double x) {
+    if (x <= 0) return 0.0;
+    const double lead = std::exp(a * std::log(x) - x - std::lgamma(a));
+    if (x < a + 1.0) {
+        double sum = 1.0 / a, term = sum;
+        for (int k = 1; k < 10000; ++k) {
+            term *= x / (a + k);
+            sum += term;
+            if (term < sum * 1e-17) break;
+        }
+        return sum * lead;
+    }
+    double f = x + 1.0 - a;
+    if (std::fabs(f) < 1e-300) f = 1e-300;
+    double Cc = f, D = 0.0;
+    for (int k = 1; k < 10000; ++k) {
+        double an = k * (a - k), bn = x + 2.0 * k + 1.0 - a;
+        D = bn + an * D;
+        if (std::fabs(D) < 1e-300) D = 1e-300;
+        Cc = bn + an / Cc;
+        if (std::fabs(Cc) < 1e-300) Cc = 1e-300;
+        D = 1.0 / D;
+        double delta = Cc * D;
+        f *= delta;
+        if (std::fabs(delta - 1.0) < 1e-16) break;
+    }
+    return 1.0 - lead / f;
+}
+
+// y with P(a, y) = q: Newton on P (derivative = Gamma(a) density), kept in a
+// shrinking bracket, bisection when a step leaves it.
+double inc_gamma_inv(double a, double q) {
+    double lo = 0.0, hi = std::max(1.0, a);
+    while (inc_gamma_p(a, hi) < q) hi *= 2.0;
+    double y = 0.5 * (lo + hi);
+    for (int it = 0; it < 200; ++it) {
+        double f = inc_gamma_p(a, y) - q;
+        if (f < 0) lo = y; else hi = y;
+        double dens = std::exp((a - 1.0) * std::log(y) - y - std::lgamma(a));
+        double yn = y - f / dens;
+        if (!(yn > lo && yn < hi)) yn = 0.5 * (lo + hi);
+        if (std::fabs(yn - y) <= 1e-15 * y || hi - lo <= 1e-300) { y = yn; break; }
+        y = yn;
+    }
+    return y;
+}
+
+// Mean rate of each of C equal-probability categories of Gamma(alpha, rate alpha).
+bool discrete_gamma(double alpha, int C, double* rates) {
+    if (C == 1) { rates[0] = 1.0; return true; }
+    if (!(alpha > 0.0) || C < 1 || C > kMaxCat) return false;
+    double prev = 0.0, tot = 0.0;
+    for (int k = 0; k < C; ++k) {
+        double cum = 1.0;
+        if (k + 1 < C) {
+            double b = inc_gamma_inv(alpha, (double)(k + 1) / C) / alpha;  // category bound on the rate scale
+            cum = inc_gamma_p(alpha + 1.0, alpha * b);
+        }
+        rates[k] = (cum - prev) * C;
+        prev = cum;
+        tot += rates[k];
+    }
+    for (int k = 0; k < C; ++k) rates[k] *= C / tot;
+    return true;
+}
+
+// Symmetric 4x4 eigen-decomposition by cyclic Jacobi rotations.
+void jacobi4(double A[16], double V[16], double lam[4]) {
+    for (int i = 0; i < 16; ++i) V[i] = (i % 5 == 0) ? 1.0 : 0.0;
+    for (int sweep = 0; sweep < 100; ++sweep) {
+        double off = 0.0;
+        for (int p = 0; p < 4; ++p)
+            for (int q = p + 1; q < 4; ++q) off += A[p * 4 + q] * A[p * 4 + q];
+        if (off < 1e-34) break;
+        for (int p = 0; p < 4; ++p)
+            for (int q = p + 1; q < 4; ++q) {
+                double apq = A[p * 4 + q];
+                if (std::fabs(apq) < 1e-300) continue;
+                double theta = (A[q * 4 + q] - A[p * 4 + p]) / (2.0 * apq);
+                double t = (theta >= 0 ? 1.0 : -1.0) / (std::fabs(theta) + std::sqrt(theta * theta + 1.0));
+                double cs = 1.0 / std::sqrt(t * t + 1.0), sn = t * cs;
+                for (int k = 0; k < 4; ++k) {  // columns p, q
+                    double akp = A[k * 4 + p], akq = A[k * 4 + q];
+                    A[k * 4 + p] = cs * akp - sn * akq;
+                    A[k * 4 + q] = sn * akp + cs * akq;
+                }
+                for (int k = 0; k < 4; ++k) {  // rows p, q
+                    double apk = A[p * 4 + k], aqk = A[q * 4 + k];
+                    A[p * 4 + k] = cs * apk - sn * aqk;
+                    A[q * 4 + k] = sn * apk + cs * aqk;
+                }
+                for (int k = 0; k < 4; ++k) {
+                    double vkp = V[k * 4 + p], vkq = V[k * 4 + q];
+                    V[k * 4 + p] = cs * vkp - sn * vkq;
+                    V[k * 4 + q] = sn * vkp + cs * vkq;
+                }
+            }
+    }
+    for (int k = 0; k < 4; ++k) lam[k] = A[k * 5];
+}
+
+bool build_model(const double exch[6], const double freqs[4], double alpha, int C, Model& M, std::string& why) {
+    if (C != 1 && C != 4) { why = "n_cats must be 1 or 4"; return false; }
+    double fs = 0.0;
+    for (int i = 0; i < 4; ++i) {
+        if (!(freqs[i] > 0.0) || !std::isfinite(freqs[i])) { why = "frequencies must be positive"; return false; }
+        fs += freqs[i];
+    }
+    if (std::fabs(fs - 1.0) > 1e-6) { why = "frequencies must sum to 1"; return false; }
+    for (int i = 0; i < 6; ++i)
+        if (!(exch[i] > 0.0) || !std::isfinite(exch[i])) { why = "exchangeabilities must be positive"; return false; }
+    double pi[4];
+    for (int i = 0; i < 4; ++i) pi[i] = freqs[i] / fs;
+    const int pairs[6][2] = {{0, 1}, {0, 2}, {0, 3}, {1, 2}, {1, 3}, {2, 3}};
+    double Q[16] = {0};
+    for (int k = 0; k < 6; ++k) {
+        int i = pairs[k][0], j = pairs[k][1];
+        Q[i * 4 + j] = exch[k] * pi[j];
+        Q[j * 4 + i] = exch[k] * pi[i];
+    }
+    double mu = 0.0;
+    for (int i = 0; i < 4; ++i) {
+        double r = 0.0;
+        for (int j = 0; j < 4; ++j) if (j != i) r += Q[i * 4 + j];
+        Q[i * 4 + i] = -r;
+        mu += pi[i] * r;
+    }
+    for (double& q : Q) q /= mu;
+    double B[16];
+    for (int i = 0; i < 4; ++i)
+        for (int j = 0; j < 4; ++j) B[i * 4 + j] = std::sqrt(pi[i]) * Q[i * 4 + j] / std::sqrt(pi[j]);
+    for (int i = 0; i < 4; ++i)  // symmetrise exactly
+        for (int j = i + 1; j < 4; ++j) B[i * 4 + j] = B[j * 4 + i] = 0.5 * (B[i * 4 + j] + B[j * 4 + i]);
+    M.C = C;
+    jacobi4(B, M.R, M.lam);
+    for (int i = 0; i < 4; ++i) {
+        M.pi[i] = pi[i];
+        M.sqpi[i] = std::sqrt(pi[i]);
+        M.isqpi[i] = 1.0 / std::sqrt(pi[i]);
+    }
+    for (int k = 0; k < kMaxCat; ++k) M.rates[k] = 0.0;
+    if (!discrete_gamma(alpha, C, M.rates)) { why = "alpha must be positive"; return false; }
+    return true;
+}
+
+// ---------------------------------------------------------------- validation of host trees
+void validate_trees(Ctx& c, int n, int count, const int32_t* edges, const double* lengths) {
+    const int NN = 2 * n - 2, E = 2 * n - 3;
+    std::vector<int> deg(NN);
+    for (int t = 0; t < count; ++t) {
+        std::fill(deg.begin(), deg.end(), 0);
+        for (int e = 0; e < E; ++e) {
+            int a = edges[(size_t)t * 2 * E + 2 * e], b = edges[(size_t)t * 2 * E + 2 * e + 1];
+            if (a < 0 || b < 0 || a >= NN || b >= NN || a == b)
+                fail(c, PT_ERR_INVALID_ARG, "tree %d edge %d: node out of range", t, e);
+            ++deg[a];
+            ++deg[b];
+            if (lengths) {
+                double l = lengths[(size_t)t * E + e];
+                if (!std::isfinite(l) || l < 0) fail(c, PT_ERR_INVALID_ARG, "tree %d edge %d: bad length", t, e);
+            }
+        }
+        for (int v = 0; v < NN; ++v)
+            if (deg[v] != (v < n ? 1 : 3)) fail(c, PT_ERR_INVALID_ARG, "tree %d: node %d has degree %d", t, v, deg[v]);
+    }
+}
+
+// ---------------------------------------------------------------- drivers
+// Canonicalise + score `count` trees already on the device.  FULL mode runs
+// the full optimisation; lnl_d [count] receives lnL; ts holds the result.
+void score_core(Ctx& c, AlnState& a, int count, const int32_t* edges_d, const double* lens_d, int mode,
+                const std::string& tsname, TreeSet& ts, double* lnl_d) {
+    ts = treeset(c, tsname, a.n, count, true);
+    launch_canon(c.stream, a.n, count, edges_d, lens_d, ts, c.d_err);
+    check_flags(c);
+    const int G = chunk_trees(c, a);
+    const int threads = threads_for(c, a.P);
+    const int prec = c.cfg.precision;
+    bool smem_tab = fullopt_smem_bytes(prec, a.M.C, a.n, a.P, true, threads) <= c.smem_optin;
+    for (int f0 = 0; f0 < count; f0 += G) {
+        int cnt = std::min(G, count - f0);
+        ClvGroup g = clv_group(c, "full", a, cnt);
+        int grid = std::min(cnt, 2 * c.sm_count);
+        void* scratch = nullptr;
+        size_t spc = 0;
+        if (!smem_tab) {
+            spc = (sumtable_bytes(prec, a.M.C, a.P) + 255) & ~size_t(255);
+            scratch = buf<unsigned char>(c, "full.scratch", spc * grid);
+        }
+        launch_fullopt(c.stream, prec, a.M, aln_dev(a), kcfg(c), ts, f0, cnt, g,
+                       mode == PT_SCORE_FULL ? c.cfg.full_max_sweeps : 0, lnl_d + f0, c.d_stats, threads, grid,
+                       scratch, spc);
+        ck(c, cudaGetLastError(), "full optimisation launch");
+    }
+}
+
+// The GOOD set of the last begin/expand: indices into the "kp" tree set.
+struct RoundOut {
+    TreeSet ts;
+    int32_t* idx = nullptr;
+    double* lnl = nullptr;
+    int count = 0;
+};
+
+void begin_core(Ctx& c, AlnState& a, int ns, const int32_t* edges_d, const double* lens_d, double thr,
+                double* lmax_out, RoundOut& out) {
+    if (!a.table || a.log2 != c.cfg.table_log2) {
+        if (a.table) cudaFree(a.table);
+        a.table = nullptr;
+        ck(c, cudaMalloc(&a.table, sizeof(Slot) << c.cfg.table_log2), "allocating visited table");
+        a.log2 = c.cfg.table_log2;
+    }
+    launch_table_init(c.stream, a.table, (size_t)1 << a.log2);
+    a.round = 0;
+    double* lnl = buf<double>(c, "kp.lnl", ns);
+    TreeSet ts;
+    score_core(c, a, ns, edges_d, lens_d, PT_SCORE_FULL, "kp", ts, lnl);
+    int32_t* winner = buf<int32_t>(c, "kp.winner", ns);
+    launch_insert_trees(c.stream, a.table, a.log2, ns, ts, lnl, nullptr, 0, winner, c.d_err);
+    double ninf = -INFINITY;
+    ck(c, cudaMemcpyAsync(c.d_lmax, &ninf, 8, cudaMemcpyHostToDevice, c.stream), "lmax init");
+    launch_lmax(c.stream, ns, lnl, winner, c.d_lmax);
+    int32_t* good = buf<int32_t>(c, "kp.good", ns);
+    launch_finalize_trees(c.stream, a.table, ns, winner, lnl, c.d_lmax, thr, 0, good, c.d_stats);
+    // dedup starts: a start that lost its key is not GOOD
+    std::vector<int32_t> w(ns), gd(ns);
+    ck(c, cudaMemcpyAsync(w.data(), winner, 4 * (size_t)ns, cudaMemcpyDeviceToHost, c.stream), "read winners");
+    ck(c, cudaMemcpyAsync(gd.data(), good, 4 * (size_t)ns, cudaMemcpyDeviceToHost, c.stream), "read good");
+    ck(c, cudaMemcpyAsync(lmax_out, c.d_lmax, 8, cudaMemcpyDeviceToHost, c.stream), "read lmax");
+    check_flags(c);
+    std::vector<int32_t> idx;
+    for (int i = 0; i < ns; ++i) if (w[i] >= 0 && gd[i]) idx.push_back(i);
+    out.ts = ts;
+    out.idx = buf<int32_t>(c, "kp.idx", idx.size() + 1);
+    if (!idx.empty())
+        ck(c, cudaMemcpyAsync(out.idx, idx.data(), 4 * idx.size(), cudaMemcpyHostToDevice, c.stream), "idx");
+    out.lnl = lnl;
+    out.count = (int)idx.size();
+}
+
+void expand_core(Ctx& c, AlnState& a, int F, const int32_t* edges_d, const double* lens_d, double thr,
+                 double* lmax_inout, RoundOut& out) {
+    if (!a.table) fail(c, PT_ERR_STATE, "no visited table: call pt_begin first");
+    const int n = a.n, m = 2 * (n - 3), prec = c.cfg.precision;
+    const int round = ++a.round;
+    int64_t hc[kStWords] = {0};
+    mark(c, 0);
+    // 1. frontier: canonical form, keys; entered as visited if absent
+    TreeSet fr = treeset(c, "fr", n, std::max(F, 1), false);
+    launch_canon(c.stream, n, F, edges_d, lens_d, fr, c.d_err);
+    int32_t* fwin = buf<int32_t>(c, "fr.win", F);
+    launch_insert_trees(c.stream, a.table, a.log2, F, fr, nullptr, nullptr, round - 1, fwin, c.d_err);
+    ck(c, cudaMemcpyAsync(c.d_lmax, lmax_inout, 8, cudaMemcpyHostToDevice, c.stream), "lmax");
+    const int ncand = F * m;
+    hc[kStCand] = ncand;
+    // 2. candidates, dedup, arbitration
+    uint64_t* nkey = buf<uint64_t>(c, "cand.key", (size_t)ncand * 2);
+    int32_t* cinfo = buf<int32_t>(c, "cand.info", (size_t)ncand * 4);
+    int32_t* cslot = buf<int32_t>(c, "cand.slot", ncand);
+    int32_t* flag = buf<int32_t>(c, "cand.flag", ncand);
+    int32_t* pos = buf<int32_t>(c, "cand.pos", ncand);
+    launch_enum(c.stream, n, F, fr, nkey, cinfo);
+    mark(c, 1);
+    launch_cand_insert(c.stream, a.table, a.log2, ncand, nkey, cinfo, fr, round, cslot, flag, c.d_err, c.d_stats);
+    launch_cand_arb(c.stream, 2, a.table, ncand, cinfo, fr, round, cslot, flag);
+    launch_cand_arb(c.stream, 3, a.table, ncand, cinfo, fr, round, cslot, flag);
+    launch_cand_arb(c.stream, 4, a.table, ncand, cinfo, fr, round, cslot, flag);
+    check_flags(c);
+    const int W = scan_count(c, flag, pos, ncand);
+    hc[kStScored] = W;
+    Item* items = buf<Item>(c, "items", W + 1);
+    uint64_t* ikey = buf<uint64_t>(c, "items.key", 2 * (size_t)W + 2);
+    launch_make_items(c.stream, ncand, flag, pos, cinfo, cslot, nkey, items, ikey);
+    // first item of each frontier tree (items are ordered by tree)
+    std::vector<int32_t> tpos(F + 1, W);
+    if (ncand > 0) {
+        std::vector<int32_t> allpos(ncand);
+        ck(c, cudaMemcpyAsync(allpos.data(), pos, 4 * (size_t)ncand, cudaMemcpyDeviceToHost, c.stream), "pos");
+        ck(c, cudaStreamSynchronize(c.stream), "sync");
+        for (int f = 0; f < F; ++f) tpos[f] = allpos[(size_t)f * m];
+    }
+    mark(c, 2);
+    // 3. partials of frontier chunks + proposal optimisation of their items
+    double* plnl = buf<double>(c, "items.lnl", W + 1);
+    double* len5 = buf<double>(c, "items.len5", 5 * (size_t)W + 5);
+    int32_t* kept = buf<int32_t>(c, "items.kept", W + 1);
+    const int G = chunk_trees(c, a);
+    const int threads = threads_for(c, a.P);
+    bool smem_tab = propose_smem_bytes(prec, a.M.C, a.P, true, threads) <= c.smem_optin;
+    float ms_part = 0, ms_prop = 0;
+    for (int f0 = 0; f0 < F && W > 0; f0 += G) {
+        int cnt = std::min(G, F - f0);
+        int i0 = tpos[f0], i1 = (f0 + cnt < F) ? tpos[f0 + cnt] : W;
+        if (i1 <= i0) continue;
+        ClvGroup g = clv_group(c, "fr", a, cnt);
+        void* pm = buf<unsigned char>(c, "fr.pm", pmat_bytes(prec, a.M.C, n, cnt));
+        launch_partials(c.stream, prec, a.M, aln_dev(a), fr, f0, cnt, g, true, threads, pm);
+        ck(c, cudaGetLastError(), "partials launch");
+        int grid = std::min(i1 - i0, 4 * c.sm_count);
+        void* scratch = nullptr;
+        size_t spc = 0;
+        if (!smem_tab) {
+            spc = (sumtable_bytes(prec, a.M.C, a.P) + 255) & ~size_t(255);
+            scratch = buf<unsigned char>(c, "prop.scratch", spc * grid);
+        }
+        launch_propose(c.stream, prec, a.M, aln_dev(a), kcfg(c), fr, f0, g, items, i0, i1, a.table, round, c.d_lmax,
+                       thr, plnl + i0, len5 + (size_t)5 * i0, kept + i0, c.d_stats, threads, grid, scratch, spc, pm);
+        ck(c, cudaGetLastError(), "propose launch");
+    }
+    (void)ms_part; (void)ms_prop;
+    mark(c, 3);
+    c.last_items = W;
+    // 4. kept neighbours: materialise, canonicalise, fully optimise
+    int32_t* kpos = buf<int32_t>(c, "kept.pos", W + 1);
+    const int K = scan_count(c, kept, kpos, W);
+    hc[kStKept] = K;
+    int32_t* kidx = buf<int32_t>(c, "kept.idx", K + 1);
+    launch_compact_idx(c.stream, W, kept, kpos, kidx);
+    int32_t* kedges = buf<int32_t>(c, "kept.edges", (size_t)K * 2 * (2 * n - 3) + 2);
+    double* klens = buf<double>(c, "kept.lens", (size_t)K * (2 * n - 3) + 1);
+    int32_t* kslot = buf<int32_t>(c, "kept.slot", K + 1);
+    launch_materialize(c.stream, n, K, kidx, items, fr, len5, kedges, klens, kslot);
+    double* klnl = buf<double>(c, "kp.lnl", K + 1);
+    TreeSet kp;
+    if (K > 0) score_core(c, a, K, kedges, klens, PT_SCORE_FULL, "kp", kp, klnl);
+    else kp = treeset(c, "kp", n, 1, true);
+    // 5. lmax, GOOD / BAD, next frontier
+    launch_lmax(c.stream, K, klnl, nullptr, c.d_lmax);
+    int32_t* good = buf<int32_t>(c, "kp.good", K + 1);
+    launch_finalize_trees(c.stream, a.table, K, kslot, klnl, c.d_lmax, thr, round, good, c.d_stats);
+    int32_t* gpos = buf<int32_t>(c, "kp.gpos", K + 1);
+    const int Gn = scan_count(c, good, gpos, K);
+    int32_t* gidx = buf<int32_t>(c, "kp.idx", Gn + 1);
+    launch_compact_idx(c.stream, K, good, gpos, gidx);
+    ck(c, cudaMemcpyAsync(lmax_inout, c.d_lmax, 8, cudaMemcpyDeviceToHost, c.stream), "read lmax");
+    check_flags(c);
+    mark(c, 5);
+    out.ts = kp;
+    out.idx = gidx;
+    out.lnl = klnl;
+    out.count = Gn;
+    end_stats(c, hc);
+}
+
+void collect_times(Ctx& c) {
+    if (!c.timing) return;
+    cudaEventSynchronize(c.ev[5]);
+    float ms;
+    auto el = [&](int a, int b) { return cudaEventElapsedTime(&ms, c.ev[a], c.ev[b]) == cudaSuccess ? (double)ms : 0.0; };
+    c.stage_ms[0] = el(0, 1);
+    c.stage_ms[1] = el(1, 2);
+    c.stage_ms[3] = el(2, 3);
+    c.stage_ms[4] = el(3, 5);
+    c.stage_ms[5] = el(0, 5);
+    cudaGetLastError();
+}
+
+void write_out(Ctx& c, const AlnState& a, RoundOut& o, int cap, int32_t* e, double* l, double* lnl, uint64_t* keys,
+               bool host, int* n_out) {
+    *n_out = o.count;
+    if (o.count > cap) fail(c, PT_ERR_BUFFER_TOO_SMALL, "output holds %d trees, %d needed", cap, o.count);
+    if (o.count == 0) return;
+    const int n = a.n, E = 2 * n - 3;
+    if (!host) {
+        launch_gather_out(c.stream, n, o.count, o.idx, o.ts, o.lnl, e, l, lnl, keys);
+        ck(c, cudaGetLastError(), "gather");
+        ck(c, cudaStreamSynchronize(c.stream), "sync");
+        return;
+    }
+    int32_t* de = buf<int32_t>(c, "out.e", (size_t)o.count * 2 * E);
+    double* dl = buf<double>(c, "out.l", (size_t)o.count * E);
+    double* dn = buf<double>(c, "out.lnl", o.count);
+    uint64_t* dk = buf<uint64_t>(c, "out.k", (size_t)o.count * 2);
+    launch_gather_out(c.stream, n, o.count, o.idx, o.ts, o.lnl, de, dl, dn, dk);
+    if (e) ck(c, cudaMemcpyAsync(e, de, 4 * (size_t)o.count * 2 * E, cudaMemcpyDeviceToHost, c.stream), "copy out");
+    if (l) ck(c, cudaMemcpyAsync(l, dl, 8 * (size_t)o.count * E, cudaMemcpyDeviceToHost, c.stream), "copy out");
+    if (lnl) ck(c, cudaMemcpyAsync(lnl, dn, 8 * (size_t)o.count, cudaMemcpyDeviceToHost, c.stream), "copy out");
+    if (keys) ck(c, cudaMemcpyAsync(keys, dk, 16 * (size_t)o.count, cudaMemcpyDeviceToHost, c.stream), "copy out");
+    ck(c, cudaStreamSynchronize(c.stream), "sync");
+}
+
+template <typename F>
+pt_status guarded(pt_ctx* ctx, F&& f);
+
+}  // namespace
+
+struct pt_ctx {
+    Ctx c;
+};
+
+namespace {
+template <typename F>
+pt_status guarded(pt_ctx* ctx, F&& f) {
+    if (!ctx) return PT_ERR_INVALID_ARG;
+    try {
+        ck(ctx->c, cudaSetDevice(ctx->c.cfg.device), "cudaSetDevice");
+        f(ctx->c);
+        ctx->c.err.clear();
+        return PT_OK;
+    } catch (const Fail& e) {
+        return e.st;
+    } catch (...) {
+        ctx->c.err = "unexpected host exception";
+        return PT_ERR_STATE;
+    }
+}
+}  // namespace
+
+extern "C" {
+
+const char* pt_version(void) { return "libpt 0.1 (sm_103a)"; }
+
+void pt_config_default(pt_config* cfg) {
+    if (!cfg) return;
+    std::memset(cfg, 0, sizeof *cfg);
+    cfg->device = 0;
+    cfg->precision = PT_PREC_MIXED;
+    cfg->table_log2 = 22;
+    cfg->propose_mode = PT_PROPOSE_FIVE;
+    cfg->tmin = 1e-6;
+    cfg->tmax = 100.0;
+    cfg->newton_tol = 1e-8;
+    cfg->newton_maxit = 50;
+    cfg->sweep_tol = 1e-9;
+    cfg->full_max_sweeps = 64;
+    cfg->prop_max_sweeps = 8;
+    cfg->threads = 0;
+    cfg->mem_budget = 0;
+}
+
+pt_status pt_create(pt_ctx** out, const pt_config* cfg) {
+    if (!out) return PT_ERR_INVALID_ARG;
+    *out = nullptr;
+    pt_ctx* ctx = new pt_ctx();
+    Ctx& c = ctx->c;
+    if (cfg) c.cfg = *cfg; else pt_config_default(&c.cfg);
+    if (c.cfg.table_log2 < 10 || c.cfg.table_log2 > 30 || c.cfg.precision < 0 || c.cfg.precision > 1 ||
+        !(c.cfg.tmin > 0) || !(c.cfg.tmax > c.cfg.tmin) || c.cfg.newton_maxit < 1 || c.cfg.full_max_sweeps < 0 ||
+        c.cfg.prop_max_sweeps < 1 || (c.cfg.threads != 0 && (c.cfg.threads < 32 || c.cfg.threads > 512 ||
+                                                             c.cfg.threads % 32))) {
+        delete ctx;
+        return PT_ERR_INVALID_ARG;
+    }
+    try {
+        ck(c, cudaSetDevice(c.cfg.device), "cudaSetDevice");
+        cudaDeviceProp prop;
+        ck(c, cudaGetDeviceProperties(&prop, c.cfg.device), "cudaGetDeviceProperties");
+        c.sm_count = prop.multiProcessorCount;
+        c.smem_optin = prop.sharedMemPerBlockOptin;
+        ck(c, cudaMalloc(&c.d_err, sizeof(int32_t) * kErrWords), "alloc");
+        ck(c, cudaMalloc(&c.d_stats, sizeof(unsigned long long) * kStWords), "alloc");
+        ck(c, cudaMalloc(&c.d_lmax, 8), "alloc");
+        ck(c, cudaMemset(c.d_err, 0, sizeof(int32_t) * kErrWords), "memset");
+        for (auto& e : c.ev) ck(c, cudaEventCreate(&e), "event");
+        size_t fr, tot;
+        ck(c, cudaMemGetInfo(&fr, &tot), "cudaMemGetInfo");
+        c.budget = c.cfg.mem_budget ? c.cfg.mem_budget : std::min<size_t>(fr / 4, (size_t)24 << 30);
+    } catch (const Fail& e) {
+        pt_destroy(ctx);
+        return e.st;
+    }
+    *out = ctx;
+    return PT_OK;
+}
+
+void pt_destroy(pt_ctx* ctx) {
+    if (!ctx) return;
+    Ctx& c = ctx->c;
+    cudaSetDevice(c.cfg.device);
+    if (c.stream) cudaStreamSynchronize(c.stream);
+    for (auto& kv : c.bufs) if (kv.second.p) cudaFree(kv.second.p);
+    for (auto& a : c.alns) {
+        if (a.tips) cudaFree(a.tips);
+        if (a.w) cudaFree(a.w);
+        if (a.table) cudaFree(a.table);
+    }
+    if (c.d_err) cudaFree(c.d_err);
+    if (c.d_stats) cudaFree(c.d_stats);
+    if (c.d_lmax) cudaFree(c.d_lmax);
+    for (auto& e : c.ev) if (e) cudaEventDestroy(e);
+    delete ctx;
+}
+
+const char* pt_last_error(const pt_ctx* ctx) { return ctx ? ctx->c.err.c_str() : "null context"; }
+
+pt_status pt_set_stream(pt_ctx* ctx, void* stream) {
+    return guarded(ctx, [&](Ctx& c) { c.stream = reinterpret_cast<cudaStream_t>(stream); });
+}
+
+pt_status pt_load_alignment(pt_ctx* ctx, int n_taxa, int n_sites, const uint8_t* codes, int* aln_id) {
+    return guarded(ctx, [&](Ctx& c) {
+        if (!codes || !aln_id || n_taxa < 3 || n_taxa > kMaxTaxa || n_sites < 1)
+            fail(c, PT_ERR_INVALID_ARG, "need 3..%d taxa, >= 1 site and non-null pointers", kMaxTaxa);
+        for (size_t i = 0; i < (size_t)n_taxa * n_sites; ++i)
+            if (codes[i] > 4) fail(c, PT_ERR_INVALID_ARG, "alignment code %d at %zu (allowed 0..4)", codes[i], i);
+        // columns sorted lexicographically; equal columns merge into one weighted pattern
+        std::vector<int> order(n_sites);
+        for (int i = 0; i < n_sites; ++i) order[i] = i;
+        auto col_less = [&](int x, int y) {
+            for (int t = 0; t < n_taxa; ++t) {
+                uint8_t a = codes[(size_t)t * n_sites + x], b = codes[(size_t)t * n_sites + y];
+                if (a != b) return a < b;
+            }
+            return false;
+        };
+        std::sort(order.begin(), order.end(), col_less);
+        std::vector<int> reps;
+        std::vector<int32_t> w;
+        for (int i = 0; i < n_sites; ++i) {
+            if (i > 0 && !col_less(order[i - 1], order[i])) { ++w.back(); continue; }
+            reps.push_back(order[i]);
+            w.push_back(1);
+        }
+        const int P = (int)reps.size();
+        std::vector<uint8_t> tips((size_t)n_taxa * P);
+        for (int t = 0; t < n_taxa; ++t)
+            for (int p = 0; p < P; ++p) tips[(size_t)t * P + p] = codes[(size_t)t * n_sites + reps[p]];
+        AlnState a;
+        a.n = n_taxa;
+        a.sites = n_sites;
+        a.P = P;
+        ck(c, cudaMalloc(&a.tips, tips.size()), "alloc tips");
+        ck(c, cudaMalloc(&a.w, 4 * (size_t)P), "alloc weights");
+        ck(c, cudaMemcpy(a.tips, tips.data(), tips.size(), cudaMemcpyHostToDevice), "copy tips");
+        ck(c, cudaMemcpy(a.w, w.data(), 4 * (size_t)P, cudaMemcpyHostToDevice), "copy weights");
+        c.alns.push_back(a);
+        *aln_id = (int)c.alns.size() - 1;
+    });
+}
+
+pt_status pt_alignment_info(pt_ctx* ctx, int aln_id, int* n_taxa, int* n_patterns) {
+    return guarded(ctx, [&](Ctx& c) {
+        AlnState& a = aln_of(c, aln_id, false);
+        if (n_taxa) *n_taxa = a.n;
+        if (n_patterns) *n_patterns = a.P;
+    });
+}
+
+pt_status pt_set_model(pt_ctx* ctx, int aln_id, const double exch[6], const double freqs[4], double alpha,
+                       int n_cats) {
+    return guarded(ctx, [&](Ctx& c) {
+        AlnState& a = aln_of(c, aln_id, false);
+        if (!exch || !freqs) fail(c, PT_ERR_INVALID_ARG, "null model parameters");
+        std::string why;
+        Model M;
+        if (!build_model(exch, freqs, alpha, n_cats, M, why)) fail(c, PT_ERR_INVALID_ARG, "%s", why.c_str());
+        a.M = M;
+        a.has_model = true;
+    });
+}
+
+pt_status pt_model_rates(pt_ctx* ctx, int aln_id, double* rates, int cap) {
+    return guarded(ctx, [&](Ctx& c) {
+        AlnState& a = aln_of(c, aln_id);
+        if (!rates || cap < a.M.C) fail(c, PT_ERR_BUFFER_TOO_SMALL, "need %d rates", a.M.C);
+        for (int k = 0; k < a.M.C; ++k) rates[k] = a.M.rates[k];
+    });
+}
+
+pt_status pt_score_topologies(pt_ctx* ctx, int aln_id, int n_trees, const int32_t* edges, double* lengths,
+                              double* lnl_out, pt_key* keys_out, int mode) {
+    return guarded(ctx, [&](Ctx& c) {
+        AlnState& a = aln_of(c, aln_id);
+        if (n_trees < 0 || (n_trees > 0 && (!edges || !lengths || !lnl_out)) ||
+            (mode != PT_SCORE_FULL && mode != PT_SCORE_FIXED))
+            fail(c, PT_ERR_INVALID_ARG, "bad arguments");
+        if (n_trees == 0) return;
+        validate_trees(c, a.n, n_trees, edges, lengths);
+        const int E = 2 * a.n - 3;
+        zero_flags(c);
+        begin_stats(c);
+        mark(c, 0);
+        int32_t* de = buf<int32_t>(c, "in.e", (size_t)n_trees * 2 * E);
+        double* dl = buf<double>(c, "in.l", (size_t)n_trees * E);
+        ck(c, cudaMemcpyAsync(de, edges, 4 * (size_t)n_trees * 2 * E, cudaMemcpyHostToDevice, c.stream), "copy in");
+        ck(c, cudaMemcpyAsync(dl, lengths, 8 * (size_t)n_trees * E, cudaMemcpyHostToDevice, c.stream), "copy in");
+        double* lnl = buf<double>(c, "sc.lnl", n_trees);
+        TreeSet ts;
+        score_core(c, a, n_trees, de, dl, mode, "sc", ts, lnl);
+        launch_lengths_to_input(c.stream, a.n, n_trees, ts, dl);
+        mark(c, 5);
+        ck(c, cudaMemcpyAsync(lengths, dl, 8 * (size_t)n_trees * E, cudaMemcpyDeviceToHost, c.stream), "copy out");
+        ck(c, cudaMemcpyAsync(lnl_out, lnl, 8 * (size_t)n_trees, cudaMemcpyDeviceToHost, c.stream), "copy out");
+        if (keys_out)
+            ck(c, cudaMemcpyAsync(keys_out, ts.key, 16 * (size_t)n_trees, cudaMemcpyDeviceToHost, c.stream), "copy out");
+        check_flags(c);
+        end_stats(c, nullptr);
+        collect_times(c);
+    });
+}
+
+pt_status pt_begin(pt_ctx* ctx, int aln_id, int n_start, const int32_t* edges, const double* lengths,
+                   double threshold, double* lmax_out, int cap, int32_t* front_edges, double* front_lengths,
+                   double* front_lnl, pt_key* front_keys, int* n_front) {
+    return guarded(ctx, [&](Ctx& c) {
+        AlnState& a = aln_of(c, aln_id);
+        if (n_start < 1 || !edges || !lengths || !lmax_out || !n_front || !(threshold >= 0))
+            fail(c, PT_ERR_INVALID_ARG, "bad arguments");
+        validate_trees(c, a.n, n_start, edges, lengths);
+        const int E = 2 * a.n - 3;
+        zero_flags(c);
+        begin_stats(c);
+        mark(c, 0);
+        int32_t* de = buf<int32_t>(c, "in.e", (size_t)n_start * 2 * E);
+        double* dl = buf<double>(c, "in.l", (size_t)n_start * E);
+        ck(c, cudaMemcpyAsync(de, edges, 4 * (size_t)n_start * 2 * E, cudaMemcpyHostToDevice, c.stream), "copy in");
+        ck(c, cudaMemcpyAsync(dl, lengths, 8 * (size_t)n_start * E, cudaMemcpyHostToDevice, c.stream), "copy in");
+        RoundOut o;
+        begin_core(c, a, n_start, de, dl, threshold, lmax_out, o);
+        mark(c, 5);
+        end_stats(c, nullptr);
+        write_out(c, a, o, cap, front_edges, front_lengths, front_lnl, reinterpret_cast<uint64_t*>(front_keys), true,
+                  n_front);
+        collect_times(c);
+    });
+}
+
+pt_status pt_expand_frontier(pt_ctx* ctx, int aln_id, int n_frontier, const int32_t* edges, const double* lengths,
+                             double threshold, double* lmax_inout, int cap, int32_t* kept_edges,
+                             double* kept_lengths, double* kept_lnl, pt_key* kept_keys, int* n_kept) {
+    return guarded(ctx, [&](Ctx& c) {
+        AlnState& a = aln_of(c, aln_id);
+        if (n_frontier < 0 || (n_frontier > 0 && (!edges || !lengths)) || !lmax_inout || !n_kept ||
+            !(threshold >= 0) || std::isnan(*lmax_inout))
+            fail(c, PT_ERR_INVALID_ARG, "bad arguments");
+        validate_trees(c, a.n, n_frontier, edges, lengths);
+        const int E = 2 * a.n - 3;
+        zero_flags(c);
+        begin_stats(c);
+        int32_t* de = buf<int32_t>(c, "in.e", (size_t)std::max(n_frontier, 1) * 2 * E);
+        double* dl = buf<double>(c, "in.l", (size_t)std::max(n_frontier, 1) * E);
+        if (n_frontier > 0) {
+            ck(c, cudaMemcpyAsync(de, edges, 4 * (size_t)n_frontier * 2 * E, cudaMemcpyHostToDevice, c.stream), "copy in");
+            ck(c, cudaMemcpyAsync(dl, lengths, 8 * (size_t)n_frontier * E, cudaMemcpyHostToDevice, c.stream), "copy in");
+        }
+        RoundOut o;
+        expand_core(c, a, n_frontier, de, dl, threshold, lmax_inout, o);
+        write_out(c, a, o, cap, kept_edges, kept_lengths, kept_lnl, reinterpret_cast<uint64_t*>(kept_keys), true,
+                  n_kept);
+        collect_times(c);
+    });
+}
+
+pt_status pt_expand_frontier_dev(pt_ctx* ctx, int aln_id, int n_frontier, const int32_t* edges_dev,
+                                 const double* lengths_dev, double threshold, double* lmax_inout, int cap,
+                                 int32_t* kept_edges_dev, double* kept_lengths_dev, double* kept_lnl_dev,
+                                 uint64_t* kept_keys_dev, int* n_kept) {
+    return guarded(ctx, [&](Ctx& c) {
+        AlnState& a = aln_of(c, aln_id);
+        if (n_frontier < 0 || (n_frontier > 0 && (!edges_dev || !lengths_dev)) || !lmax_inout || !n_kept ||
+            !(threshold >= 0) || std::isnan(*lmax_inout))
+            fail(c, PT_ERR_INVALID_ARG, "bad arguments");
+        zero_flags(c);
+        begin_stats(c);
+        RoundOut o;
+        expand_core(c, a, n_frontier, edges_dev, lengths_dev, threshold, lmax_inout, o);
+        write_out(c, a, o, cap, kept_edges_dev, kept_lengths_dev, kept_lnl_dev, kept_keys_dev, false, n_kept);
+        collect_times(c);
+    });
+}
+
+pt_status pt_visited(pt_ctx* ctx, int aln_id, size_t cap, pt_key* keys, uint8_t* status, double* lnl,
+                     size_t* count) {
+    return guarded(ctx, [&](Ctx& c) {
+        AlnState& a = aln_of(c, aln_id, false);
+        if (!count) fail(c, PT_ERR_INVALID_ARG, "null count");
+        *count = 0;
+        if (!a.table) return;
+        const size_t ns = (size_t)1 << a.log2;
+        if (ns > (size_t)INT32_MAX) fail(c, PT_ERR_INVALID_ARG, "table too large to dump");
+        int32_t* flag = buf<int32_t>(c, "dump.flag", ns);
+        int32_t* pos = buf<int32_t>(c, "dump.pos", ns);
+        launch_dump(c.stream, a.table, ns, flag);
+        const int tot = scan_count(c, flag, pos, (int)ns);
+        *count = (size_t)tot;
+        uint64_t* dk = buf<uint64_t>(c, "dump.k", 2 * (size_t)tot + 2);
+        uint8_t* ds = buf<uint8_t>(c, "dump.s", (size_t)tot + 1);
+        double* dl = buf<double>(c, "dump.l", (size_t)tot + 1);
+        launch_dump_gather(c.stream, a.table, ns, flag, pos, dk, ds, dl);
+        size_t k = std::min(cap, (size_t)tot);
+        if (k) {
+            if (keys) ck(c, cudaMemcpyAsync(keys, dk, 16 * k, cudaMemcpyDeviceToHost, c.stream), "copy");
+            if (status) ck(c, cudaMemcpyAsync(status, ds, k, cudaMemcpyDeviceToHost, c.stream), "copy");
+            if (lnl) ck(c, cudaMemcpyAsync(lnl, dl, 8 * k, cudaMemcpyDeviceToHost, c.stream), "copy");
+        }
+        ck(c, cudaStreamSynchronize(c.stream), "sync");
+        if (cap < (size_t)tot) fail(c, PT_ERR_BUFFER_TOO_SMALL, "visited set has %d entries", tot);
+    });
+}
+
+pt_status pt_reset_visited(pt_ctx* ctx, int aln_id) {
+    return guarded(ctx, [&](Ctx& c) {
+        AlnState& a = aln_of(c, aln_id, false);
+        if (a.table) launch_table_init(c.stream, a.table, (size_t)1 << a.log2);
+        a.round = 0;
+        ck(c, cudaStreamSynchronize(c.stream), "sync");
+    });
+}
+
+pt_status pt_stats(pt_ctx* ctx, int64_t* out, int cap) {
+    return guarded(ctx, [&](Ctx& c) {
+        if (!out) fail(c, PT_ERR_INVALID_ARG, "null");
+        for (int i = 0; i < cap && i < kStWords; ++i) out[i] = c.stats[i];
+    });
+}
+
+pt_status pt_last_proposals(pt_ctx* ctx, size_t cap, pt_key* keys, int32_t* parent, int32_t* edge_node,
+                            int32_t* swap, double* lnl, double* len5, size_t* count) {
+    return guarded(ctx, [&](Ctx& c) {
+        if (!count) fail(c, PT_ERR_INVALID_ARG, "null count");
+        const int W = c.last_items;
+        *count = (size_t)W;
+        size_t k = std::min(cap, (size_t)W);
+        if (k == 0) return;
+        std::vector<Item> it(k);
+        ck(c, cudaMemcpy(it.data(), buf<Item>(c, "items", W + 1), sizeof(Item) * k, cudaMemcpyDeviceToHost), "copy");
+        for (size_t i = 0; i < k; ++i) {
+            if (parent) parent[i] = it[i].tree;
+            if (edge_node) edge_node[i] = it[i].v;
+            if (swap) swap[i] = it[i].swap;
+        }
+        if (keys) ck(c, cudaMemcpy(keys, buf<uint64_t>(c, "items.key", 2 * (size_t)W + 2), 16 * k, cudaMemcpyDeviceToHost), "copy");
+        if (lnl) ck(c, cudaMemcpy(lnl, buf<double>(c, "items.lnl", W + 1), 8 * k, cudaMemcpyDeviceToHost), "copy");
+        if (len5) ck(c, cudaMemcpy(len5, buf<double>(c, "items.len5", 5 * (size_t)W + 5), 40 * k, cudaMemcpyDeviceToHost), "copy");
+        if (cap < (size_t)W) fail(c, PT_ERR_BUFFER_TOO_SMALL, "%d proposals", W);
+    });
+}
+
+pt_status pt_stage_times(pt_ctx* ctx, double* ms, int cap) {
+    return guarded(ctx, [&](Ctx& c) {
+        if (!ms) fail(c, PT_ERR_INVALID_ARG, "null");
+        for (int i = 0; i < cap && i < 6; ++i) ms[i] = c.stage_ms[i];
+    });
+}
+
+int pt_discrete_gamma(double alpha, int n_cats, double* rates) {
+    if (!rates || n_cats < 1 || n_cats > kMaxCat) return PT_ERR_INVALID_ARG;
+    return discrete_gamma(alpha, n_cats, rates) ? PT_OK : PT_ERR_INVALID_ARG;
+}
+
+int pt_model_eigen(const double exch[6], const double freqs[4], double* lam, double* R) {
+    if (!exch || !freqs || !lam || !R) return PT_ERR_INVALID_ARG;
+    Model M;
+    std::string why;
+    if (!build_model(exch, freqs, 1.0, 1, M, why)) return PT_ERR_INVALID_ARG;
+    for (int k = 0; k < 4; ++k) lam[k] = M.lam[k];
+    for (int i = 0; i < 16; ++i) R[i] = M.R[i];
+    return PT_OK;
+}
+
+}  // extern "C"

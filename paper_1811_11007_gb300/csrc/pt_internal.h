@@ -1,0 +1,133 @@
+// Internal interfaces between the host driver (pt_api.cu) and the kernels
+// (pt_kernels.cu).  Nothing here is part of the public ABI.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace pt {
+
+constexpr int kMaxTaxa = 128;
+constexpr int kMaxNode = 2 * kMaxTaxa - 2;
+constexpr int kMaxCat = 4;
+
+// Substitution model on the device, passed by value.  Q is GTR, reversible:
+// with D = diag(pi), B = D^1/2 Q D^-1/2 is symmetric, B = R diag(lam) R^T
+// (R orthonormal), so P(t) = D^-1/2 R exp(lam t) R^T D^1/2.
+struct Model {
+    int C;
+    double pi[4], sqpi[4], isqpi[4];
+    double lam[4];
+    double R[16];      // R[i*4+k]: component i of eigenvector k
+    double rates[kMaxCat];
+};
+
+struct Aln {
+    int n, P;
+    const uint8_t* tips;   // [n][P], 0..3 or 4 = all-ones
+    const int32_t* w;      // [P] pattern weights
+};
+
+struct Cfg {
+    double tmin, tmax, newton_tol, sweep_tol;
+    int newton_maxit, full_max_sweeps, prop_max_sweeps, propose_mode;
+};
+
+// Canonical rooted trees (rooted at leaf 0, inner nodes renumbered n.. in
+// pre-order, children ordered by smallest taxon), structure of arrays with a
+// per-tree stride of NN = 2n-2 nodes.
+struct TreeSet {
+    int n, cap;
+    int32_t* up;      // [cap][NN]   parent (leaf 0: -1)
+    int32_t* ch;      // [cap][NN][2] children of inner nodes
+    double* len;      // [cap][NN]   length of edge (v, up[v])
+    uint64_t* bits;   // [cap][NN][2] leaf set below v
+    int32_t* erank;   // [cap][NN]   rank of internal edge v by split, -1 otherwise
+    int32_t* sched;   // [cap][3n]   full-optimisation schedule: v = visit edge v, v|kUpd = refresh D_v
+    uint64_t* key;    // [cap][2]
+    int32_t* emap;    // [cap][2n-3] input edge e -> canonical child node (edge-list inputs only)
+};
+constexpr int kUpd = 1 << 16;
+
+// Visited-table slot (48 bytes, 16-byte aligned for the 128-bit CAS).
+struct Slot {
+    unsigned long long klo, khi;
+    unsigned long long tag;   // round << 48 | (proposer rank during a round, status after)
+    unsigned long long ahi, alo; // arbitration: smallest parent key of this round's proposers
+    double lnl;
+};
+constexpr unsigned long long kTagEmpty = ~0ull;
+
+// Device error flags (int32 words).
+enum { kErrTree = 0, kErrTable = 1, kErrKey = 2, kErrNumeric = 3, kErrWords = 8 };
+// Device counters (int64 words), match pt_stats.
+enum {
+    kStCand = 0, kStDup = 1, kStScored = 2, kStKept = 3, kStGood = 4, kStPropEvals = 5, kStFullEvals = 6,
+    kStNonconv = 7, kStPropSweeps = 8, kStFullSweeps = 9, kStWords = 16
+};
+
+// A group of trees sharing one partial-likelihood buffer: tree g's vectors
+// start at clv + g * tree_stride (R elements), scalers at scl + g * scl_stride.
+// Slots: D_v (v inner, n-2 of them) then U_v (v inner except the first, n-3).
+struct ClvGroup {
+    void* clv;
+    int32_t* scl;
+    size_t tree_stride, scl_stride;
+};
+
+// Work item of the proposal kernel: frontier tree, internal edge node, swap,
+// visited-table slot.
+struct Item {
+    int32_t tree, v, swap, slot;
+};
+
+// ---- launchers (pt_kernels.cu) ----
+void launch_canon(cudaStream_t s, int n, int count, const int32_t* edges, const double* lengths, TreeSet ts,
+                  int32_t* err);
+void launch_table_init(cudaStream_t s, Slot* tab, size_t nslots);
+void launch_enum(cudaStream_t s, int n, int F, TreeSet fr, uint64_t* nkey, int32_t* cinfo);
+void launch_cand_insert(cudaStream_t s, Slot* tab, int log2, int ncand, const uint64_t* nkey, const int32_t* cinfo,
+                        TreeSet fr, int round, int32_t* cslot, int32_t* flag, int32_t* err,
+                        unsigned long long* stats);
+void launch_cand_arb(cudaStream_t s, int phase, Slot* tab, int ncand, const int32_t* cinfo, TreeSet fr, int round,
+                     const int32_t* cslot, int32_t* flag);
+void launch_scan(cudaStream_t s, const int32_t* in, int32_t* out, int N, int32_t* tmp);
+void launch_make_items(cudaStream_t s, int ncand, const int32_t* flag, const int32_t* pos, const int32_t* cinfo,
+                       const int32_t* cslot, const uint64_t* nkey, Item* items, uint64_t* ikey);
+void launch_compact_idx(cudaStream_t s, int N, const int32_t* flag, const int32_t* pos, int32_t* idx);
+void launch_insert_trees(cudaStream_t s, Slot* tab, int log2, int count, TreeSet ts, const double* lnl,
+                         const int32_t* status, int round, int32_t* winner, int32_t* err);
+void launch_finalize_trees(cudaStream_t s, Slot* tab, int count, const int32_t* slot_of, const double* lnl,
+                           const double* lmax, double thr, int round, int32_t* good, unsigned long long* stats);
+void launch_lmax(cudaStream_t s, int count, const double* lnl, const int32_t* mask, double* lmax);
+void launch_dump(cudaStream_t s, const Slot* tab, size_t nslots, int32_t* flag);
+void launch_dump_gather(cudaStream_t s, const Slot* tab, size_t nslots, const int32_t* flag, const int32_t* pos,
+                        uint64_t* keys, uint8_t* status, double* lnl);
+void launch_materialize(cudaStream_t s, int n, int nk, const int32_t* kidx, const Item* items, TreeSet fr,
+                        const double* len5, int32_t* edges_out, double* lengths_out, int32_t* slot_of);
+void launch_gather_out(cudaStream_t s, int n, int count, const int32_t* idx, TreeSet ts, const double* lnl,
+                       int32_t* edges_out, double* lengths_out, double* lnl_out, uint64_t* keys_out);
+void launch_lengths_to_input(cudaStream_t s, int n, int count, TreeSet ts, double* lengths_out);
+
+// Partials of a group of trees (all D_v, and U_v when with_up).
+// pm: P-matrix buffer of pmat_bytes(prec, C, n, count) bytes; launch_propose reads it for the same group.
+size_t pmat_bytes(int prec, int C, int n, int count);
+void launch_partials(cudaStream_t s, int prec, const Model& M, Aln A, TreeSet ts, int first, int count, ClvGroup g,
+                     bool with_up, int threads, void* pm);
+// Proposal optimisation of work items [i0, i1) whose trees are [first, ...) of g.
+void launch_propose(cudaStream_t s, int prec, const Model& M, Aln A, Cfg cfg, TreeSet fr, int first, ClvGroup g,
+                    const Item* items, int i0, int i1, Slot* tab, int round, const double* lmax, double thr,
+                    double* lnl_out, double* len5_out, int32_t* kept, unsigned long long* stats, int threads,
+                    int grid, void* scratch, size_t scratch_per_cta, const void* pm);
+// Full optimisation (max_sweeps >= 0) of trees [first, first+count) of ts.
+void launch_fullopt(cudaStream_t s, int prec, const Model& M, Aln A, Cfg cfg, TreeSet ts, int first, int count,
+                    ClvGroup g, int max_sweeps, double* lnl_out, unsigned long long* stats, int threads, int grid,
+                    void* scratch, size_t scratch_per_cta);
+
+// Shared-memory sizing helpers for the host.
+size_t propose_smem_bytes(int prec, int C, int P, bool table_in_smem, int threads);
+size_t fullopt_smem_bytes(int prec, int C, int n, int P, bool table_in_smem, int threads);
+size_t sumtable_bytes(int prec, int C, int P);
+
+}  // namespace pt

@@ -1,0 +1,1517 @@
+// CUDA kernels of the PT hot path (sm_103a).
+//
+// Layout in HBM (per group of trees): partial-likelihood vectors
+// [slot][site][category][state] in FP32 (mixed precision) or FP64, one 4C-wide
+// record per site so a thread owning a site reads it with 128-bit loads;
+// per-site power-of-two scaler counts [slot][site] int32.  Slots of a tree:
+// D_v (the subtree below inner node v, at v) for every inner v, then U_v (the
+// rest of the tree, at v's parent) for every inner v but the first.
+//
+// Parallel structure: a thread owns sites; a CTA owns a tree (partials, full
+// optimisation) or one NNI neighbour (proposal optimisation).  Cross-thread
+// traffic is only the per-Newton-iteration reduction of d lnL/dt and
+// d2 lnL/dt2 (FP64) and the per-sweep lnL, so every pass over sites runs
+// without barriers.
+#include "pt_internal.h"
+
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdint>
+
+namespace pt {
+namespace {
+
+constexpr double kLn2 = 0.69314718055994530942;
+
+template <typename R> struct Prec;
+template <> struct Prec<float> {
+    // stored vectors are rescaled by 2^32 when every entry is below 2^-32, so a
+    // product of two stored vectors stays far above the FP32 normal range
+    static constexpr int kScaleExp = 32;
+    __device__ static float thresh() { return 2.3283064365386963e-10f; }   // 2^-32
+    __device__ static float mult() { return 4294967296.0f; }                // 2^32
+    __device__ static float ex(float x) { return expf(x); }
+    __device__ static float lg(float x) { return logf(x); }
+    __device__ static float rcp(float x) { return __frcp_rn(x); }
+};
+template <> struct Prec<double> {
+    static constexpr int kScaleExp = 256;
+    __device__ static double thresh() { return 8.636168555094445e-78; }      // 2^-256
+    __device__ static double mult() { return 1.157920892373162e+77; }        // 2^256
+    __device__ static double ex(double x) { return exp(x); }
+    __device__ static double lg(double x) { return log(x); }
+    __device__ static double rcp(double x) { return 1.0 / x; }
+};
+
+// ---------------------------------------------------------------- hashing
+// Split hash of the key definition: SplitMix64's output function applied as
+//   h.lo = mix(lo ^ mix(hi + 0x9e3779b97f4a7c15)), h.hi = mix(hi ^ mix(lo + 0xd1b54a32d192ed03)).
+__device__ __forceinline__ unsigned long long mix64(unsigned long long z) {
+    z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ull;
+    z = (z ^ (z >> 27)) * 0x94d049bb133111ebull;
+    return z ^ (z >> 31);
+}
+__device__ __forceinline__ unsigned __int128 split_hash(unsigned long long lo, unsigned long long hi) {
+    unsigned long long a = mix64(lo ^ mix64(hi + 0x9e3779b97f4a7c15ull));
+    unsigned long long b = mix64(hi ^ mix64(lo + 0xd1b54a32d192ed03ull));
+    return ((unsigned __int128)b << 64) | a;
+}
+__device__ __forceinline__ bool less128(unsigned long long alo, unsigned long long ahi, unsigned long long blo,
+                                        unsigned long long bhi) {
+    return ahi < bhi || (ahi == bhi && alo < blo);
+}
+
+// ---------------------------------------------------------------- canonicaliser
+// One warp per tree.  Lane 0 builds the adjacency, roots it at leaf 0 and
+// numbers the inner nodes in pre-order (children by smallest taxon); then the
+// lanes hash the n-3 non-trivial splits, reduce the 128-bit key sum, and rank
+// the splits.
+constexpr int kCanonWarps = 4;
+struct CanonSmem {
+    int16_t nbr[kMaxNode][3];
+    int16_t eid[kMaxNode][3];
+    int16_t par[kMaxNode];
+    int16_t canon[kMaxNode];
+    int16_t stack[2 * kMaxNode + 4];
+    int16_t order[kMaxNode];
+    uint8_t deg[kMaxNode];
+    uint8_t mint[kMaxNode];
+};
+
+__global__ void k_canon(int n, int count, const int32_t* __restrict__ edges, const double* __restrict__ lengths,
+                        TreeSet ts, int32_t* err) {
+    __shared__ CanonSmem sm_all[kCanonWarps];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int tree = blockIdx.x * kCanonWarps + warp;
+    if (tree >= count) return;
+    CanonSmem& s = sm_all[warp];
+    const int NN = 2 * n - 2, E = 2 * n - 3;
+    const int32_t* ed = edges + (size_t)tree * 2 * E;
+    int32_t* up = ts.up + (size_t)tree * NN;
+    int32_t* ch = ts.ch + (size_t)tree * NN * 2;
+    double* len = ts.len + (size_t)tree * NN;
+    uint64_t* bits = ts.bits + (size_t)tree * NN * 2;
+    int32_t* erank = ts.erank + (size_t)tree * NN;
+    int32_t* sched = ts.sched + (size_t)tree * 3 * n;
+    int ok = 1;
+    if (lane == 0) {
+        for (int v = 0; v < NN; ++v) s.deg[v] = 0;
+        for (int e = 0; e < E && ok; ++e) {
+            int a = ed[2 * e], b = ed[2 * e + 1];
+            if (a < 0 || b < 0 || a >= NN || b >= NN || a == b || s.deg[a] >= 3 || s.deg[b] >= 3) { ok = 0; break; }
+            s.nbr[a][s.deg[a]] = (int16_t)b; s.eid[a][s.deg[a]++] = (int16_t)e;
+            s.nbr[b][s.deg[b]] = (int16_t)a; s.eid[b][s.deg[b]++] = (int16_t)e;
+        }
+        for (int v = 0; v < NN && ok; ++v) if (s.deg[v] != (v < n ? 1 : 3)) ok = 0;
+        if (ok) {
+            // DFS from leaf 0: parents and a pre-order; min taxon by reverse pre-order
+            for (int v = 0; v < NN; ++v) s.par[v] = -2;
+            int sp = 0, no = 0;
+            s.par[0] = -1;
+            s.stack[sp++] = 0;
+            while (sp) {
+                int v = s.stack[--sp];
+                s.order[no++] = (int16_t)v;
+                for (int k = 0; k < s.deg[v]; ++k) {
+                    int c = s.nbr[v][k];
+                    if (c == s.par[v]) continue;
+                    if (s.par[c] != -2) { ok = 0; break; }
+                    s.par[c] = (int16_t)v;
+                    s.stack[sp++] = (int16_t)c;
+                }
+                if (!ok) break;
+            }
+            if (no != NN) ok = 0;
+            if (ok) {
+                for (int i = NN - 1; i >= 0; --i) {
+                    int v = s.order[i];
+                    if (v < n) { s.mint[v] = (uint8_t)v; continue; }
+                    int m = 255;
+                    for (int k = 0; k < 3; ++k) {
+                        int c = s.nbr[v][k];
+                        if (c != s.par[v] && s.mint[c] < m) m = s.mint[c];
+                    }
+                    s.mint[v] = (uint8_t)m;
+                }
+                // canonical pre-order numbering of inner nodes
+                int next = n;
+                sp = 0;
+                s.stack[sp++] = s.nbr[0][0];
+                for (int v = 0; v < n; ++v) s.canon[v] = (int16_t)v;
+                while (sp) {
+                    int v = s.stack[--sp];
+                    if (v < n) continue;
+                    s.canon[v] = (int16_t)next++;
+                    int c0 = -1, c1 = -1;
+                    for (int k = 0; k < 3; ++k) {
+                        int c = s.nbr[v][k];
+                        if (c == s.par[v]) continue;
+                        if (c0 < 0) c0 = c; else c1 = c;
+                    }
+                    if (s.mint[c1] < s.mint[c0]) { int x = c0; c0 = c1; c1 = x; }
+                    s.stack[sp++] = (int16_t)c1;  // popped second
+                    s.stack[sp++] = (int16_t)c0;  // popped first
+                }
+                // canonical arrays
+                up[0] = -1; ch[0] = ch[1] = -1; len[0] = 0.0;
+                for (int v = 1; v < NN; ++v) {
+                    int c = s.canon[v], p = s.par[v];
+                    up[c] = s.canon[p];
+                    int e = -1;
+                    for (int k = 0; k < s.deg[v]; ++k) if (s.nbr[v][k] == p) e = s.eid[v][k];
+                    len[c] = lengths ? lengths[(size_t)tree * E + e] : 0.1;
+                    if (ts.emap) ts.emap[(size_t)tree * E + e] = c;
+                    if (v >= n) {
+                        int c0 = -1, c1 = -1;
+                        for (int k = 0; k < 3; ++k) {
+                            int x = s.nbr[v][k];
+                            if (x == p) continue;
+                            if (c0 < 0) c0 = x; else c1 = x;
+                        }
+                        if (s.mint[c1] < s.mint[c0]) { int x = c0; c0 = c1; c1 = x; }
+                        ch[2 * c] = s.canon[c0]; ch[2 * c + 1] = s.canon[c1];
+                    } else {
+                        ch[2 * c] = ch[2 * c + 1] = -1;
+                    }
+                }
+                // leaf sets, children before parents (canonical numbers grow downwards)
+                for (int v = 0; v < n; ++v) {
+                    bits[2 * v] = v < 64 ? (1ull << v) : 0ull;
+                    bits[2 * v + 1] = v >= 64 ? (1ull << (v - 64)) : 0ull;
+                }
+                for (int v = NN - 1; v >= n; --v) {
+                    int c0 = ch[2 * v], c1 = ch[2 * v + 1];
+                    bits[2 * v] = bits[2 * c0] | bits[2 * c1];
+                    bits[2 * v + 1] = bits[2 * c0 + 1] | bits[2 * c1 + 1];
+                }
+                // full-optimisation schedule: pre-order visits, refresh of D_v after its subtree
+                int ns = 0;
+                sp = 0;
+                s.stack[sp++] = (int16_t)n;
+                while (sp) {
+                    int x = s.stack[--sp];
+                    if (x < 0) { sched[ns++] = (-x - 1) | kUpd; continue; }
+                    sched[ns++] = x;
+                    if (x >= n) {
+                        s.stack[sp++] = (int16_t)(-x - 1);
+                        s.stack[sp++] = (int16_t)ch[2 * x + 1];
+                        s.stack[sp++] = (int16_t)ch[2 * x];
+                    }
+                }
+                for (; ns < 3 * n; ++ns) sched[ns] = -1;
+            }
+        }
+        if (!ok) atomicCAS(&err[kErrTree], 0, tree + 1);
+    }
+    ok = __shfl_sync(0xffffffffu, ok, 0);
+    __syncwarp();
+    if (!ok) {
+        if (lane == 0) { ts.key[2 * tree] = 0; ts.key[2 * tree + 1] = 0; }
+        return;
+    }
+    // key = sum of split hashes over internal edges (inner nodes except the first)
+    unsigned __int128 acc = 0;
+    for (int v = n + 1 + lane; v < NN; v += 32) acc += split_hash(bits[2 * v], bits[2 * v + 1]);
+    unsigned long long lo = (unsigned long long)acc, hi = (unsigned long long)(acc >> 64);
+    for (int off = 16; off; off >>= 1) {
+        unsigned long long olo = __shfl_down_sync(0xffffffffu, lo, off);
+        unsigned long long ohi = __shfl_down_sync(0xffffffffu, hi, off);
+        unsigned long long nlo = lo + olo;
+        hi = hi + ohi + (nlo < lo);
+        lo = nlo;
+    }
+    if (lane == 0) {
+        if (lo == 0 && hi == 0) lo = 1;
+        ts.key[2 * tree] = lo;
+        ts.key[2 * tree + 1] = hi;
+    }
+    // rank of every internal split among the tree's internal splits
+    for (int v = lane; v < NN; v += 32) {
+        if (v <= n) { erank[v] = -1; continue; }
+        unsigned long long blo = bits[2 * v], bhi = bits[2 * v + 1];
+        int r = 0;
+        for (int w = n + 1; w < NN; ++w)
+            if (less128(bits[2 * w], bits[2 * w + 1], blo, bhi)) ++r;
+        erank[v] = r;
+    }
+}
+
+// ---------------------------------------------------------------- candidates
+// Candidate c = (tree f, internal edge j, swap s): edge node v = n+1+j, its
+// parent u, v's sibling B, v's children C < D.  Swap 0 exchanges B and C
+// (new split B u D), swap 1 exchanges B and D (new split B u C); the key
+// changes by H(new split) - H(C u D).
+__global__ void k_enum(int n, int F, TreeSet fr, uint64_t* __restrict__ nkey, int32_t* __restrict__ cinfo) {
+    const int m = 2 * (n - 3);
+    const long long total = (long long)F * m;
+    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < total;
+         c += (long long)gridDim.x * blockDim.x) {
+        int f = (int)(c / m), r = (int)(c % m), j = r >> 1, sw = r & 1;
+        const int NN = 2 * n - 2;
+        const int32_t* up = fr.up + (size_t)f * NN;
+        const int32_t* ch = fr.ch + (size_t)f * NN * 2;
+        const uint64_t* bits = fr.bits + (size_t)f * NN * 2;
+        int v = n + 1 + j, u = up[v];
+        int sib = ch[2 * u] == v ? ch[2 * u + 1] : ch[2 * u];
+        int keep = sw == 0 ? ch[2 * v + 1] : ch[2 * v];
+        unsigned __int128 key = ((unsigned __int128)fr.key[2 * f + 1] << 64) | fr.key[2 * f];
+        key -= split_hash(bits[2 * v], bits[2 * v + 1]);
+        key += split_hash(bits[2 * sib] | bits[2 * keep], bits[2 * sib + 1] | bits[2 * keep + 1]);
+        unsigned long long lo = (unsigned long long)key, hi = (unsigned long long)(key >> 64);
+        if (!lo && !hi) lo = 1;
+        nkey[2 * c] = lo;
+        nkey[2 * c + 1] = hi;
+        cinfo[4 * c + 0] = f;
+        cinfo[4 * c + 1] = v;
+        cinfo[4 * c + 2] = sw;
+        cinfo[4 * c + 3] = fr.erank[(size_t)f * NN + v];
+    }
+}
+
+// ---------------------------------------------------------------- visited table
+constexpr int kMaxProbe = 1 << 14;
+
+__device__ __forceinline__ size_t slot_hash(unsigned long long lo, unsigned long long hi, unsigned long long mask) {
+    return (size_t)(mix64(lo ^ mix64(hi ^ 0x632be59bd9b4e019ull)) & mask);
+}
+
+// Finds or claims the slot of a key by linear probing with a 128-bit CAS.
+// Returns the slot index and whether this call created it; -1 when the probe
+// limit is reached.
+__device__ long long table_find_or_claim(Slot* tab, int log2, unsigned long long lo, unsigned long long hi,
+                                         bool* created) {
+    const unsigned long long mask = (1ull << log2) - 1;
+    const unsigned __int128 key = ((unsigned __int128)hi << 64) | lo;
+    size_t h = slot_hash(lo, hi, mask);
+    for (int p = 0; p < kMaxProbe; ++p) {
+        size_t i = (h + p) & mask;
+        unsigned __int128* kp = reinterpret_cast<unsigned __int128*>(&tab[i].klo);
+        unsigned __int128 old = atomicCAS(kp, (unsigned __int128)0, key);
+        if (old == 0) { *created = true; return (long long)i; }
+        if (old == key) { *created = false; return (long long)i; }
+    }
+    return -1;
+}
+
+__global__ void k_table_init(Slot* tab, size_t nslots) {
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < nslots; i += (size_t)gridDim.x * blockDim.x) {
+        tab[i].klo = 0; tab[i].khi = 0; tab[i].tag = kTagEmpty; tab[i].ahi = kTagEmpty; tab[i].alo = kTagEmpty;
+        tab[i].lnl = __longlong_as_double(0x7ff8000000000000ll);
+    }
+}
+
+__global__ void k_cand_insert(Slot* tab, int log2, int ncand, const uint64_t* __restrict__ nkey,
+                              const int32_t* __restrict__ cinfo, TreeSet fr, int round, int32_t* cslot,
+                              int32_t* flag, int32_t* err, unsigned long long* stats) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    int dup = 0;
+    if (i < ncand) {
+        bool created;
+        long long s = table_find_or_claim(tab, log2, nkey[2 * i], nkey[2 * i + 1], &created);
+        if (s < 0) {
+            atomicExch(&err[kErrTable], 1);
+            cslot[i] = -1; flag[i] = 0;
+        } else {
+            unsigned long long tag = created ? kTagEmpty : atomicAdd(&tab[s].tag, 0ull);
+            if (tag != kTagEmpty && (int)(tag >> 48) < round) {
+                cslot[i] = -1; flag[i] = 0; dup = 1;
+            } else {
+                int f = cinfo[4 * i];
+                atomicMin(&tab[s].ahi, (unsigned long long)fr.key[2 * f + 1]);
+                cslot[i] = (int32_t)s; flag[i] = 1;
+            }
+        }
+    }
+    unsigned b = __ballot_sync(0xffffffffu, dup);
+    if ((threadIdx.x & 31) == 0 && b) atomicAdd(&stats[kStDup], (unsigned long long)__popc(b));
+}
+
+// phase 2: smallest low word of the parent key among proposers with the smallest high word;
+// phase 3: smallest (edge rank, swap) among proposers with the smallest parent key;
+// phase 4: flag = this candidate is the winner of its slot.
+__global__ void k_cand_arb(int phase, Slot* tab, int ncand, const int32_t* __restrict__ cinfo, TreeSet fr, int round,
+                           const int32_t* __restrict__ cslot, int32_t* flag) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= ncand || !flag[i]) return;
+    Slot* sl = &tab[cslot[i]];
+    int f = cinfo[4 * i];
+    unsigned long long phi = fr.key[2 * f + 1], plo = fr.key[2 * f];
+    unsigned long long me = ((unsigned long long)round << 48) | ((unsigned long long)cinfo[4 * i + 3] << 1) |
+                            (unsigned long long)cinfo[4 * i + 2];
+    if (phase == 2) {
+        if (sl->ahi == phi) atomicMin(&sl->alo, plo);
+    } else if (phase == 3) {
+        if (sl->ahi == phi && sl->alo == plo) atomicMin(&sl->tag, me);
+    } else {
+        flag[i] = (sl->ahi == phi && sl->alo == plo && sl->tag == me) ? 1 : 0;
+    }
+}
+
+__global__ void k_make_items(int ncand, const int32_t* __restrict__ flag, const int32_t* __restrict__ pos,
+                             const int32_t* __restrict__ cinfo, const int32_t* __restrict__ cslot,
+                             const uint64_t* __restrict__ nkey, Item* items, uint64_t* ikey) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= ncand || !flag[i]) return;
+    Item it;
+    it.tree = cinfo[4 * i]; it.v = cinfo[4 * i + 1]; it.swap = cinfo[4 * i + 2]; it.slot = cslot[i];
+    items[pos[i]] = it;
+    ikey[2 * pos[i]] = nkey[2 * i];
+    ikey[2 * pos[i] + 1] = nkey[2 * i + 1];
+}
+
+__global__ void k_compact_idx(int N, const int32_t* __restrict__ flag, const int32_t* __restrict__ pos, int32_t* idx) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < N && flag[i]) idx[pos[i]] = i;
+}
+
+// Enters whole trees (starts, or a caller's frontier) as visited.  Among
+// equal keys the lowest index wins; status/lnl written by the winner.  A key
+// already present from an earlier call is left as it is (winner = -1).
+__global__ void k_insert_trees(Slot* tab, int log2, int count, TreeSet ts, const double* lnl, const int32_t* status,
+                               int round, int32_t* winner, int32_t* err) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= count) return;
+    bool created;
+    long long s = table_find_or_claim(tab, log2, ts.key[2 * i], ts.key[2 * i + 1], &created);
+    if (s < 0) { atomicExch(&err[kErrTable], 1); winner[i] = -1; return; }
+    // only slots claimed by this call (still untagged) take part; a key entered
+    // earlier keeps its record
+    unsigned long long tag = created ? kTagEmpty : atomicAdd(&tab[s].tag, 0ull);
+    if (tag != kTagEmpty) { winner[i] = -1; return; }
+    atomicMin(&tab[s].alo, (unsigned long long)i);
+    winner[i] = (int32_t)s;
+}
+
+__global__ void k_insert_trees_fin(Slot* tab, int count, const double* lnl, const int32_t* status, int round,
+                                   int32_t* winner) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= count || winner[i] < 0) return;
+    Slot* sl = &tab[winner[i]];
+    if (sl->alo != (unsigned long long)i) { winner[i] = -1; return; }
+    sl->lnl = lnl ? lnl[i] : __longlong_as_double(0x7ff8000000000000ll);
+    sl->tag = ((unsigned long long)round << 48) | (unsigned long long)(status ? status[i] : 2);
+}
+
+// lmax = max(lmax, max over masked lnl) (ordered-integer trick on doubles)
+__device__ __forceinline__ long long ord_of(double x) {
+    long long b = __double_as_longlong(x);
+    return b >= 0 ? b : (b ^ 0x7fffffffffffffffll);
+}
+__device__ __forceinline__ double of_ord(long long b) {
+    return __longlong_as_double(b >= 0 ? b : (b ^ 0x7fffffffffffffffll));
+}
+__global__ void k_lmax(int count, const double* lnl, const int32_t* mask, double* lmax) {
+    __shared__ long long best;
+    if (threadIdx.x == 0) best = ord_of(*lmax);
+    __syncthreads();
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < count; i += gridDim.x * blockDim.x)
+        if ((!mask || mask[i] >= 0) && lnl[i] == lnl[i]) atomicMax(&best, ord_of(lnl[i]));
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned long long* p = reinterpret_cast<unsigned long long*>(lmax);
+        unsigned long long cur = *p;
+        while (true) {
+            double c = __longlong_as_double((long long)cur);
+            if (ord_of(c) >= best) break;
+            unsigned long long prev = atomicCAS(p, cur, (unsigned long long)__double_as_longlong(of_ord(best)));
+            if (prev == cur) break;
+            cur = prev;
+        }
+    }
+}
+
+// Visit decision of fully optimised trees: GOOD iff lnl >= lmax - thr.
+__global__ void k_finalize_trees(Slot* tab, int count, const int32_t* slot_of, const double* lnl, const double* lmax,
+                                 double thr, int round, int32_t* good, unsigned long long* stats) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    int g = 0;
+    if (i < count) {
+        g = lnl[i] >= *lmax - thr;
+        good[i] = g;
+        if (slot_of && slot_of[i] >= 0) {
+            Slot* sl = &tab[slot_of[i]];
+            sl->lnl = lnl[i];
+            sl->tag = ((unsigned long long)round << 48) | (unsigned long long)(g ? 2 : 3);
+        }
+    }
+    unsigned b = __ballot_sync(0xffffffffu, g);
+    if ((threadIdx.x & 31) == 0 && b) atomicAdd(&stats[kStGood], (unsigned long long)__popc(b));
+}
+
+__global__ void k_dump_flag(const Slot* tab, size_t nslots, int32_t* flag) {
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < nslots; i += (size_t)gridDim.x * blockDim.x)
+        flag[i] = (tab[i].klo | tab[i].khi) ? 1 : 0;
+}
+__global__ void k_dump_gather(const Slot* tab, size_t nslots, const int32_t* flag, const int32_t* pos, uint64_t* keys,
+                              uint8_t* status, double* lnl) {
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < nslots; i += (size_t)gridDim.x * blockDim.x) {
+        if (!flag[i]) continue;
+        int p = pos[i];
+        keys[2 * p] = tab[i].klo; keys[2 * p + 1] = tab[i].khi;
+        unsigned long long t = tab[i].tag;
+        status[p] = (uint8_t)(t == kTagEmpty ? 0 : (t & 0xff));
+        lnl[p] = tab[i].lnl;
+    }
+}
+
+// ---------------------------------------------------------------- scan
+__global__ void k_scan_block(const int32_t* in, int32_t* out, int N, int32_t* bsum) {
+    __shared__ int32_t ws[32];
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    int x = i < N ? in[i] : 0, lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    int v = x;
+    for (int o = 1; o < 32; o <<= 1) { int y = __shfl_up_sync(0xffffffffu, v, o); if (lane >= o) v += y; }
+    if (lane == 31) ws[w] = v;
+    __syncthreads();
+    if (w == 0) {
+        int s = lane < (blockDim.x >> 5) ? ws[lane] : 0;
+        for (int o = 1; o < 32; o <<= 1) { int y = __shfl_up_sync(0xffffffffu, s, o); if (lane >= o) s += y; }
+        ws[lane] = s;
+    }
+    __syncthreads();
+    int pre = (w ? ws[w - 1] : 0) + v - x;
+    if (i < N) out[i] = pre;
+    if (threadIdx.x == blockDim.x - 1) bsum[blockIdx.x] = ws[(blockDim.x >> 5) - 1];
+}
+__global__ void k_scan_sums(int32_t* bsum, int nb) {
+    __shared__ int32_t ws[32];
+    __shared__ int32_t carry;
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    for (int base = 0; base < nb; base += blockDim.x) {
+        int i = base + threadIdx.x, lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+        int x = i < nb ? bsum[i] : 0, v = x;
+        for (int o = 1; o < 32; o <<= 1) { int y = __shfl_up_sync(0xffffffffu, v, o); if (lane >= o) v += y; }
+        if (lane == 31) ws[w] = v;
+        __syncthreads();
+        if (w == 0) {
+            int s = lane < (blockDim.x >> 5) ? ws[lane] : 0;
+            for (int o = 1; o < 32; o <<= 1) { int y = __shfl_up_sync(0xffffffffu, s, o); if (lane >= o) s += y; }
+            ws[lane] = s;
+        }
+        __syncthreads();
+        int pre = carry + (w ? ws[w - 1] : 0) + v - x;
+        if (i < nb) bsum[i] = pre;
+        __syncthreads();
+        if (threadIdx.x == 0) carry += ws[(blockDim.x >> 5) - 1];
+        __syncthreads();
+    }
+}
+__global__ void k_scan_add(int32_t* out, int N, const int32_t* bsum) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < N) out[i] += bsum[blockIdx.x];
+}
+
+// ---------------------------------------------------------------- tree outputs
+// Materialises NNI neighbours as edge lists in the parent's canonical
+// numbering with the five optimised lengths; the canonicaliser renumbers them.
+__global__ void k_materialize(int n, int nk, const int32_t* kidx, const Item* items, TreeSet fr, const double* len5,
+                              int32_t* edges_out, double* lengths_out, int32_t* slot_of) {
+    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= nk) return;
+    const int NN = 2 * n - 2, E = 2 * n - 3;
+    int ii = kidx[k];
+    Item it = items[ii];
+    const int32_t* up = fr.up + (size_t)it.tree * NN;
+    const int32_t* ch = fr.ch + (size_t)it.tree * NN * 2;
+    const double* len = fr.len + (size_t)it.tree * NN;
+    int v = it.v, u = up[v];
+    int sib = ch[2 * u] == v ? ch[2 * u + 1] : ch[2 * u];
+    int c0 = ch[2 * v], c1 = ch[2 * v + 1];
+    int moved = it.swap == 0 ? c0 : c1;
+    const double* t5 = len5 + (size_t)ii * 5;
+    slot_of[k] = it.slot;
+    int32_t* eo = edges_out + (size_t)k * 2 * E;
+    double* lo = lengths_out + (size_t)k * E;
+    for (int w = 1; w < NN; ++w) {
+        int p = up[w];
+        double l = len[w];
+        if (w == sib) p = v;
+        if (w == moved) p = u;
+        if (w == v) l = t5[0];
+        else if (w == u) l = t5[1];
+        else if (w == sib) l = t5[2];
+        else if (w == c0) l = t5[3];
+        else if (w == c1) l = t5[4];
+        eo[2 * (w - 1)] = w;
+        eo[2 * (w - 1) + 1] = p;
+        lo[w - 1] = l;
+    }
+}
+
+// Gathers trees idx[k] of a set into canonical edge lists + lengths + lnl + keys.
+__global__ void k_gather_out(int n, int count, const int32_t* idx, TreeSet ts, const double* lnl, int32_t* edges_out,
+                             double* lengths_out, double* lnl_out, uint64_t* keys_out) {
+    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= count) return;
+    const int NN = 2 * n - 2, E = 2 * n - 3;
+    int t = idx ? idx[k] : k;
+    const int32_t* up = ts.up + (size_t)t * NN;
+    const double* len = ts.len + (size_t)t * NN;
+    for (int w = 1; w < NN; ++w) {
+        if (edges_out) { edges_out[(size_t)k * 2 * E + 2 * (w - 1)] = w; edges_out[(size_t)k * 2 * E + 2 * (w - 1) + 1] = up[w]; }
+        if (lengths_out) lengths_out[(size_t)k * E + w - 1] = len[w];
+    }
+    if (lnl_out) lnl_out[k] = lnl[t];
+    if (keys_out) { keys_out[2 * k] = ts.key[2 * t]; keys_out[2 * k + 1] = ts.key[2 * t + 1]; }
+}
+
+__global__ void k_lengths_to_input(int n, int count, TreeSet ts, double* lengths_out) {
+    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= count) return;
+    const int NN = 2 * n - 2, E = 2 * n - 3;
+    for (int e = 0; e < E; ++e) lengths_out[(size_t)k * E + e] = ts.len[(size_t)k * NN + ts.emap[(size_t)k * E + e]];
+}
+
+// ---------------------------------------------------------------- likelihood arithmetic
+// P_r(t)[i][j] = isqpi_i * sum_k R_ik exp(lam_k r t) R_jk * sqpi_j, one row
+// (4 entries) per call, exponentials in FP64.
+template <typename R>
+__device__ __forceinline__ void pmat_row(const Model& M, double rt, int i, R* row) {
+    double e[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) e[k] = exp(M.lam[k] * rt);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        double acc = 0.0;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) acc += M.R[i * 4 + k] * e[k] * M.R[j * 4 + k];
+        row[j] = (R)(acc * M.isqpi[i] * M.sqpi[j]);
+    }
+}
+
+// Source of a 4C-wide vector at a site: a tip (code lookup) or a stored slot.
+template <typename R, int C>
+struct Src {
+    const R* clv;      // slot base (nullptr for a tip)
+    const int32_t* scl;
+    const uint8_t* tip;  // tip codes of the leaf (nullptr for a slot)
+};
+
+template <typename R, int C>
+__device__ __forceinline__ void load_raw(const Src<R, C>& s, int p, R* x, int& cnt) {
+    if (s.tip) {
+        int code = s.tip[p];
+#pragma unroll
+        for (int r = 0; r < C; ++r)
+#pragma unroll
+            for (int i = 0; i < 4; ++i) x[r * 4 + i] = (code >= 4 || code == i) ? R(1) : R(0);
+        cnt = 0;
+    } else {
+        const R* src = s.clv + (size_t)p * 4 * C;
+        if constexpr (sizeof(R) == 4) {
+#pragma unroll
+            for (int q = 0; q < C; ++q) {
+                float4 v = reinterpret_cast<const float4*>(src)[q];
+                x[4 * q] = v.x; x[4 * q + 1] = v.y; x[4 * q + 2] = v.z; x[4 * q + 3] = v.w;
+            }
+        } else {
+#pragma unroll
+            for (int q = 0; q < 2 * C; ++q) {
+                double2 v = reinterpret_cast<const double2*>(src)[q];
+                x[2 * q] = v.x; x[2 * q + 1] = v.y;
+            }
+        }
+        cnt = s.scl[p];
+    }
+}
+
+// y_r = P_r x_r (Pm: [C][16] row-major); for a tip the product is a column
+// of P (or all ones for a gap).
+template <typename R, int C>
+__device__ __forceinline__ void apply_p(const R* Pm, const Src<R, C>& s, int p, R* y, int& cnt) {
+    if (s.tip) {
+        int code = s.tip[p];
+        cnt = 0;
+        if (code >= 4) {
+#pragma unroll
+            for (int q = 0; q < 4 * C; ++q) y[q] = R(1);
+        } else {
+#pragma unroll
+            for (int r = 0; r < C; ++r)
+#pragma unroll
+                for (int i = 0; i < 4; ++i) y[r * 4 + i] = Pm[r * 16 + i * 4 + code];
+        }
+        return;
+    }
+    R x[4 * C];
+    load_raw<R, C>(s, p, x, cnt);
+#pragma unroll
+    for (int r = 0; r < C; ++r)
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            R acc = Pm[r * 16 + i * 4] * x[r * 4];
+#pragma unroll
+            for (int j = 1; j < 4; ++j) acc = fma(Pm[r * 16 + i * 4 + j], x[r * 4 + j], acc);
+            y[r * 4 + i] = acc;
+        }
+}
+
+template <typename R, int C>
+__device__ __forceinline__ void apply_p_reg(const R* Pm, const R* x, R* y) {
+#pragma unroll
+    for (int r = 0; r < C; ++r)
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            R acc = Pm[r * 16 + i * 4] * x[r * 4];
+#pragma unroll
+            for (int j = 1; j < 4; ++j) acc = fma(Pm[r * 16 + i * 4 + j], x[r * 4 + j], acc);
+            y[r * 4 + i] = acc;
+        }
+}
+
+template <typename R, int C>
+__device__ __forceinline__ void store_vec(R* dst, int p, const R* y) {
+    R* d = dst + (size_t)p * 4 * C;
+    if constexpr (sizeof(R) == 4) {
+#pragma unroll
+        for (int q = 0; q < C; ++q)
+            reinterpret_cast<float4*>(d)[q] = make_float4(y[4 * q], y[4 * q + 1], y[4 * q + 2], y[4 * q + 3]);
+    } else {
+#pragma unroll
+        for (int q = 0; q < 2 * C; ++q) reinterpret_cast<double2*>(d)[q] = make_double2(y[2 * q], y[2 * q + 1]);
+    }
+}
+
+// threshold rescale of a stored vector
+template <typename R, int C>
+__device__ __forceinline__ int rescale(R* y) {
+    R mx = y[0];
+#pragma unroll
+    for (int q = 1; q < 4 * C; ++q) mx = fmax(mx, y[q]);
+    if (mx < Prec<R>::thresh()) {
+#pragma unroll
+        for (int q = 0; q < 4 * C; ++q) y[q] *= Prec<R>::mult();
+        return 1;
+    }
+    return 0;
+}
+
+// exact power-of-two normalisation to max in [1, 2); returns the exponent removed
+template <typename R, int C>
+__device__ __forceinline__ int normalise(R* y) {
+    R mx = y[0];
+#pragma unroll
+    for (int q = 1; q < 4 * C; ++q) mx = fmax(mx, y[q]);
+    if (!(mx > R(0))) return 0;
+    int e;
+    if constexpr (sizeof(R) == 4) {
+        e = ((__float_as_int(mx) >> 23) & 0xff) - 127;
+        if (e < -125) e = -125;  // keep the multiplier a normal number
+        float m = __int_as_float((127 - e) << 23);
+#pragma unroll
+        for (int q = 0; q < 4 * C; ++q) y[q] *= m;
+    } else {
+        e = (int)((__double_as_longlong(mx) >> 52) & 0x7ff) - 1023;
+        if (e < -1021) e = -1021;
+        double m = __longlong_as_double((long long)(1023 - e) << 52);
+#pragma unroll
+        for (int q = 0; q < 4 * C; ++q) y[q] *= m;
+    }
+    return e;
+}
+
+// Sum-table of one branch at one site: s_{r,k} = (M^T X_r)_k (M^T Y_r)_k with
+// M_ik = sqrt(pi_i) R_ik, so that L(t) = sum_{r,k} exp(lam_k r t)/C s_{r,k}.
+template <typename R, int C>
+__device__ __forceinline__ void sumtable(const R* Mt, const R* X, const R* Y, R* s) {
+#pragma unroll
+    for (int r = 0; r < C; ++r)
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            R x = Mt[k] * X[r * 4], y = Mt[k] * Y[r * 4];
+#pragma unroll
+            for (int i = 1; i < 4; ++i) {
+                x = fma(Mt[i * 4 + k], X[r * 4 + i], x);
+                y = fma(Mt[i * 4 + k], Y[r * 4 + i], y);
+            }
+            s[r * 4 + k] = x * y;
+        }
+}
+
+// Sum-table storage: chunk q (4 values for FP32 / 2 for FP64) of site p at
+// index q * pcap + p, so consecutive threads touch consecutive 16 bytes.
+template <typename R, int C>
+struct STab {
+    R* s;          // [nchunk][pcap] vec
+    R* ew;         // [2][pcap]: exponent, weight
+    int pcap;
+    __device__ __forceinline__ void put(int p, const R* v, R E, R w) const {
+        if constexpr (sizeof(R) == 4) {
+#pragma unroll
+            for (int q = 0; q < C; ++q)
+                reinterpret_cast<float4*>(s)[(size_t)q * pcap + p] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+        } else {
+#pragma unroll
+            for (int q = 0; q < 2 * C; ++q)
+                reinterpret_cast<double2*>(s)[(size_t)q * pcap + p] = make_double2(v[2 * q], v[2 * q + 1]);
+        }
+        ew[p] = E;
+        ew[pcap + p] = w;
+    }
+    __device__ __forceinline__ void get(int p, R* v) const {
+        if constexpr (sizeof(R) == 4) {
+#pragma unroll
+            for (int q = 0; q < C; ++q) {
+                float4 x = reinterpret_cast<const float4*>(s)[(size_t)q * pcap + p];
+                v[4 * q] = x.x; v[4 * q + 1] = x.y; v[4 * q + 2] = x.z; v[4 * q + 3] = x.w;
+            }
+        } else {
+#pragma unroll
+            for (int q = 0; q < 2 * C; ++q) {
+                double2 x = reinterpret_cast<const double2*>(s)[(size_t)q * pcap + p];
+                v[2 * q] = x.x; v[2 * q + 1] = x.y;
+            }
+        }
+    }
+};
+
+// Block-wide context for the Newton machinery.
+template <typename R, int C>
+struct NewtonSmem {
+    R egh[3][4 * C];       // exp(lam r t)/C, times lam r, times (lam r)^2
+    double red[32][2];
+    double fin[2];
+};
+
+__device__ __forceinline__ double warp_sum(double x) {
+    for (int o = 16; o; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    return x;
+}
+
+// e/g/h at branch length t, written by the first 4C threads.
+template <typename R, int C>
+__device__ __forceinline__ void put_egh(const Model& M, double t, NewtonSmem<R, C>& ns) {
+    int q = threadIdx.x;
+    if (q < 4 * C) {
+        int r = q >> 2, k = q & 3;
+        double lr = M.lam[k] * M.rates[r];
+        double e;
+        if constexpr (sizeof(R) == 4) e = (double)expf((float)(lr * t)) / C;
+        else e = exp(lr * t) / C;
+        ns.egh[0][q] = (R)e;
+        ns.egh[1][q] = (R)(lr * e);
+        ns.egh[2][q] = (R)(lr * lr * e);
+    }
+}
+// e at t in FP64 for the log-likelihood evaluation.
+template <typename R, int C>
+__device__ __forceinline__ void put_e_exact(const Model& M, double t, NewtonSmem<R, C>& ns) {
+    int q = threadIdx.x;
+    if (q < 4 * C) {
+        int r = q >> 2, k = q & 3;
+        ns.egh[0][q] = (R)(exp(M.lam[k] * M.rates[r] * t) / C);
+    }
+}
+
+// Safeguarded Newton step (identical in every thread): bracket [lo, hi];
+// Newton point when d2 < 0 and strictly inside, else sqrt(lo*hi).
+__device__ __forceinline__ bool newton_step(double& t, double& lo, double& hi, double d1, double d2, double tol) {
+    if (d1 == 0.0) return true;
+    if (d1 > 0.0) lo = t; else hi = t;
+    double tn = t - d1 / d2;
+    if (!(d2 < 0.0 && tn > lo && tn < hi)) tn = sqrt(lo * hi);
+    bool conv = fabs(tn - t) <= tol;
+    t = tn;
+    return conv;
+}
+
+// lnL of the current sum-table at length t: sum_p w_p (ln L_p + E_p ln 2), FP64 accumulation.
+template <typename R, int C>
+__device__ double eval_lnl(const Model& M, const STab<R, C>& st, int P, double t, NewtonSmem<R, C>& ns) {
+    put_e_exact<R, C>(M, t, ns);
+    __syncthreads();
+    R e[4 * C];
+#pragma unroll
+    for (int q = 0; q < 4 * C; ++q) e[q] = ns.egh[0][q];
+    double acc = 0.0;
+    for (int p = threadIdx.x; p < P; p += blockDim.x) {
+        R s[4 * C];
+        st.get(p, s);
+        R L = e[0] * s[0];
+#pragma unroll
+        for (int q = 1; q < 4 * C; ++q) L = fma(e[q], s[q], L);
+        acc += (double)st.ew[st.pcap + p] * ((double)Prec<R>::lg(L) + (double)st.ew[p] * kLn2);
+    }
+    acc = warp_sum(acc);
+    const int w = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+    if ((threadIdx.x & 31) == 0) ns.red[w][0] = acc;
+    __syncthreads();
+    double tot = 0.0;
+    for (int i = 0; i < nw; ++i) tot += ns.red[i][0];
+    __syncthreads();
+    return tot;
+}
+
+// Newton solve on the current sum-table from t0; returns the final t and the
+// number of evaluations.  Every thread returns the same values.
+template <typename R, int C>
+__device__ double newton_solve(const Model& M, const Cfg& cfg, const STab<R, C>& st, int P, double t0,
+                               NewtonSmem<R, C>& ns, int& evals, bool& converged) {
+    double lo = cfg.tmin, hi = cfg.tmax;
+    double t = fmin(fmax(t0, lo), hi);
+    const int w = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+    put_egh<R, C>(M, t, ns);
+    __syncthreads();
+    converged = false;
+    evals = 0;
+    for (int it = 0; it < cfg.newton_maxit; ++it) {
+        R e[4 * C], g[4 * C], h[4 * C];
+#pragma unroll
+        for (int q = 0; q < 4 * C; ++q) { e[q] = ns.egh[0][q]; g[q] = ns.egh[1][q]; h[q] = ns.egh[2][q]; }
+        R a1 = R(0), a2 = R(0);
+        for (int p = threadIdx.x; p < P; p += blockDim.x) {
+            R s[4 * C];
+            st.get(p, s);
+            R L = e[0] * s[0], L1 = g[0] * s[0], L2 = h[0] * s[0];
+#pragma unroll
+            for (int q = 1; q < 4 * C; ++q) {
+                L = fma(e[q], s[q], L);
+                L1 = fma(g[q], s[q], L1);
+                L2 = fma(h[q], s[q], L2);
+            }
+            R inv = Prec<R>::rcp(L);
+            R a = L1 * inv, b = L2 * inv;
+            R wt = st.ew[st.pcap + p];
+            a1 = fma(wt, a, a1);
+            a2 = fma(wt, b - a * a, a2);
+        }
+        double d1 = warp_sum((double)a1), d2 = warp_sum((double)a2);
+        if ((threadIdx.x & 31) == 0) { ns.red[w][0] = d1; ns.red[w][1] = d2; }
+        __syncthreads();
+        d1 = 0.0; d2 = 0.0;
+        for (int i = 0; i < nw; ++i) { d1 += ns.red[i][0]; d2 += ns.red[i][1]; }
+        ++evals;
+        bool done = newton_step(t, lo, hi, d1, d2, cfg.newton_tol);
+        if (!done) put_egh<R, C>(M, t, ns);
+        __syncthreads();
+        if (done) { converged = true; break; }
+    }
+    return t;
+}
+
+// ---------------------------------------------------------------- P matrices of tree sets
+// Pm[tree][v][r][16] for v = 1..NN-1 (edge (v, up v)); row per thread.
+template <typename R>
+__global__ void k_pmats(Model M, TreeSet ts, int first, int count, R* Pm) {
+    const int n = ts.n, NN = 2 * n - 2, C = M.C;
+    long long total = (long long)count * NN * C * 4;
+    for (long long x = blockIdx.x * (long long)blockDim.x + threadIdx.x; x < total;
+         x += (long long)gridDim.x * blockDim.x) {
+        int i = (int)(x & 3);
+        long long y = x >> 2;
+        int r = (int)(y % C);
+        y /= C;
+        int v = (int)(y % NN);
+        int t = (int)(y / NN);
+        double l = ts.len[(size_t)(first + t) * NN + v];
+        pmat_row<R>(M, l * M.rates[r], i, Pm + ((((size_t)t * NN + v) * C + r) * 16 + i * 4));
+    }
+}
+
+// ---------------------------------------------------------------- partials (K1)
+// grid (tree, site chunk).  All D_v bottom-up, then all U_v top-down.
+template <typename R, int C>
+__global__ void k_partials(Model M, Aln A, TreeSet ts, int first, ClvGroup g, const R* __restrict__ Pm_all,
+                           int with_up) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    R* Pm = reinterpret_cast<R*>(smraw);
+    const int n = ts.n, NN = 2 * n - 2, P = A.P;
+    const int gi = blockIdx.x, tree = first + gi;
+    const R* Psrc = Pm_all + (size_t)gi * NN * C * 16;
+    for (int x = threadIdx.x; x < NN * C * 16; x += blockDim.x) Pm[x] = Psrc[x];
+    __syncthreads();
+    const int p = blockIdx.y * blockDim.x + threadIdx.x;
+    if (p >= P) return;
+    const int32_t* up = ts.up + (size_t)tree * NN;
+    const int32_t* ch = ts.ch + (size_t)tree * NN * 2;
+    R* clv = reinterpret_cast<R*>(g.clv) + (size_t)gi * g.tree_stride;
+    int32_t* scl = g.scl + (size_t)gi * g.scl_stride;
+    const size_t sstride = (size_t)P * 4 * C;
+    auto srcD = [&](int v) {
+        Src<R, C> s;
+        if (v < n) { s.clv = nullptr; s.scl = nullptr; s.tip = A.tips + (size_t)v * P; }
+        else { s.clv = clv + (size_t)(v - n) * sstride; s.scl = scl + (size_t)(v - n) * P; s.tip = nullptr; }
+        return s;
+    };
+    for (int v = NN - 1; v >= n; --v) {
+        R y0[4 * C], y1[4 * C];
+        int c0cnt, c1cnt;
+        int c0 = ch[2 * v], c1 = ch[2 * v + 1];
+        apply_p<R, C>(Pm + (size_t)c0 * C * 16, srcD(c0), p, y0, c0cnt);
+        apply_p<R, C>(Pm + (size_t)c1 * C * 16, srcD(c1), p, y1, c1cnt);
+#pragma unroll
+        for (int q = 0; q < 4 * C; ++q) y0[q] *= y1[q];
+        int sc = rescale<R, C>(y0);
+        store_vec<R, C>(clv + (size_t)(v - n) * sstride, p, y0);
+        scl[(size_t)(v - n) * P + p] = c0cnt + c1cnt + sc;
+    }
+    if (!with_up) return;
+    for (int v = n + 1; v < NN; ++v) {
+        int u = up[v];
+        int sib = ch[2 * u] == v ? ch[2 * u + 1] : ch[2 * u];
+        Src<R, C> a;
+        if (u == n) { a.clv = nullptr; a.scl = nullptr; a.tip = A.tips; }
+        else { a.clv = clv + (size_t)(n - 2 + u - n - 1) * sstride; a.scl = scl + (size_t)(n - 2 + u - n - 1) * P; a.tip = nullptr; }
+        R y0[4 * C], y1[4 * C];
+        int cs, ca;
+        apply_p<R, C>(Pm + (size_t)sib * C * 16, srcD(sib), p, y0, cs);
+        apply_p<R, C>(Pm + (size_t)u * C * 16, a, p, y1, ca);
+#pragma unroll
+        for (int q = 0; q < 4 * C; ++q) y0[q] *= y1[q];
+        int sc = rescale<R, C>(y0);
+        const int slot = n - 2 + (v - n - 1);
+        store_vec<R, C>(clv + (size_t)slot * sstride, p, y0);
+        scl[(size_t)slot * P + p] = cs + ca + sc;
+    }
+}
+
+// ---------------------------------------------------------------- proposal optimisation (K4)
+// One CTA per NNI neighbour (persistent loop).  The quartet around internal
+// edge (u, v): A = the side of u towards leaf 0 (U_u, or leaf 0 itself when u
+// is the first inner node), B = v's sibling, C < D = v's children.  After the
+// swap u holds A and X2, v holds B and Y2 (swap 0: X2 = C, Y2 = D; swap 1:
+// X2 = D, Y2 = C).  Branches 0..4 = central, A, B, C, D, optimised in that
+// order per sweep.
+template <typename R, int C>
+struct ProposeSmem {
+    R Pm[5][C * 16];
+    R Mt[16];
+    double T[5];
+    NewtonSmem<R, C> ns;
+};
+
+template <typename R, int C, bool kSmemTab>
+__global__ void __launch_bounds__(512) k_propose(Model M, Aln A, Cfg cfg, TreeSet fr, int first, ClvGroup g,
+                                                 const R* __restrict__ Pm_all, const Item* __restrict__ items, int i0,
+                                                 int i1, Slot* tab, int round, const double* lmax, double thr,
+                                                 double* lnl_out, double* len5_out, int32_t* kept,
+                                                 unsigned long long* stats, unsigned char* scratch,
+                                                 size_t scratch_per_cta) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    ProposeSmem<R, C>& sm = *reinterpret_cast<ProposeSmem<R, C>*>(smraw);
+    const int n = fr.n, NN = 2 * n - 2, P = A.P;
+    const int pcap = (P + 3) & ~3;
+    STab<R, C> st;
+    {
+        unsigned char* base = kSmemTab ? smraw + ((sizeof(ProposeSmem<R, C>) + 15) & ~size_t(15))
+                                       : scratch + (size_t)blockIdx.x * scratch_per_cta;
+        st.s = reinterpret_cast<R*>(base);
+        st.ew = st.s + (size_t)4 * C * pcap;
+        st.pcap = pcap;
+    }
+    if (threadIdx.x < 16) {
+        int i = threadIdx.x >> 2, k = threadIdx.x & 3;
+        sm.Mt[threadIdx.x] = (R)(M.sqpi[i] * M.R[i * 4 + k]);
+    }
+    const size_t sstride = (size_t)P * 4 * C;
+    const int nb = cfg.propose_mode == 1 ? 1 : 5;
+    unsigned long long evals_total = 0, sweeps_total = 0, nonconv = 0;
+    for (int item = i0 + blockIdx.x; item < i1; item += gridDim.x) {
+        const Item it = items[item];
+        const int gi = it.tree - first;
+        const int32_t* up = fr.up + (size_t)it.tree * NN;
+        const int32_t* ch = fr.ch + (size_t)it.tree * NN * 2;
+        const double* len = fr.len + (size_t)it.tree * NN;
+        const R* clv = reinterpret_cast<const R*>(g.clv) + (size_t)gi * g.tree_stride;
+        const int32_t* scl = g.scl + (size_t)gi * g.scl_stride;
+        const int v = it.v, u = up[v];
+        const int sib = ch[2 * u] == v ? ch[2 * u + 1] : ch[2 * u];
+        const int c0 = ch[2 * v], c1 = ch[2 * v + 1];
+        // members in post-swap position order: m0 = A, m1 = X2 (at u), m2 = B, m3 = Y2 (at v)
+        const int node[4] = {u, it.swap == 0 ? c0 : c1, sib, it.swap == 0 ? c1 : c0};
+        const int brn[4] = {1, it.swap == 0 ? 3 : 4, 2, it.swap == 0 ? 4 : 3};  // branch of each member
+        Src<R, C> src[4];
+        for (int m = 0; m < 4; ++m) {
+            int x = node[m];
+            if (m == 0) {
+                if (u == n) { src[m].clv = nullptr; src[m].scl = nullptr; src[m].tip = A.tips; }
+                else {
+                    int slot = n - 2 + (u - n - 1);
+                    src[m].clv = clv + (size_t)slot * sstride; src[m].scl = scl + (size_t)slot * P; src[m].tip = nullptr;
+                }
+            } else if (x < n) {
+                src[m].clv = nullptr; src[m].scl = nullptr; src[m].tip = A.tips + (size_t)x * P;
+            } else {
+                src[m].clv = clv + (size_t)(x - n) * sstride; src[m].scl = scl + (size_t)(x - n) * P; src[m].tip = nullptr;
+            }
+        }
+        // branch b's node in the parent (its P matrix is the parent's): central v, A u, B sib, C c0, D c1
+        const int bnode[5] = {v, u, sib, c0, c1};
+        const R* Psrc = Pm_all + (size_t)gi * NN * C * 16;
+        __syncthreads();  // previous item done with smem
+        for (int x = threadIdx.x; x < 5 * C * 16; x += blockDim.x) {
+            int b = x / (C * 16), o = x % (C * 16);
+            sm.Pm[b][o] = Psrc[(size_t)bnode[b] * C * 16 + o];
+        }
+        if (threadIdx.x < 5) sm.T[threadIdx.x] = len[bnode[threadIdx.x]];
+        __syncthreads();
+        double f0 = 0.0, f1 = 0.0;
+        int sweeps = 0;
+        for (int sw = 0; sw < cfg.prop_max_sweeps; ++sw) {
+            ++sweeps;
+            for (int b = 0; b < nb; ++b) {
+                // member optimised by branch b (b > 0)
+                int mb = -1;
+                for (int m = 0; m < 4; ++m) if (brn[m] == b) mb = m;
+                for (int p = threadIdx.x; p < P; p += blockDim.x) {
+                    R X[4 * C], Y[4 * C];
+                    int cx = 0, cy = 0;
+                    if (b == 0) {
+                        R t0[4 * C], t1[4 * C];
+                        int k0, k1, k2, k3;
+                        apply_p<R, C>(sm.Pm[brn[0]], src[0], p, t0, k0);
+                        apply_p<R, C>(sm.Pm[brn[1]], src[1], p, t1, k1);
+#pragma unroll
+                        for (int q = 0; q < 4 * C; ++q) X[q] = t0[q] * t1[q];
+                        apply_p<R, C>(sm.Pm[brn[2]], src[2], p, t0, k2);
+                        apply_p<R, C>(sm.Pm[brn[3]], src[3], p, t1, k3);
+#pragma unroll
+                        for (int q = 0; q < 4 * C; ++q) Y[q] = t0[q] * t1[q];
+                        cx = k0 + k1; cy = k2 + k3;
+                    } else {
+                        const int partner = mb ^ 1, o1 = mb < 2 ? 2 : 0, o2 = o1 + 1;
+                        R t0[4 * C], t1[4 * C], far[4 * C];
+                        int k0, k1, k2;
+                        apply_p<R, C>(sm.Pm[brn[o1]], src[o1], p, t0, k0);
+                        apply_p<R, C>(sm.Pm[brn[o2]], src[o2], p, t1, k1);
+#pragma unroll
+                        for (int q = 0; q < 4 * C; ++q) t0[q] *= t1[q];
+                        apply_p_reg<R, C>(sm.Pm[0], t0, far);
+                        apply_p<R, C>(sm.Pm[brn[partner]], src[partner], p, t1, k2);
+#pragma unroll
+                        for (int q = 0; q < 4 * C; ++q) Y[q] = t1[q] * far[q];
+                        load_raw<R, C>(src[mb], p, X, cx);
+                        cy = k0 + k1 + k2;
+                    }
+                    int ex = normalise<R, C>(X), ey = normalise<R, C>(Y);
+                    R s[4 * C];
+                    sumtable<R, C>(sm.Mt, X, Y, s);
+                    st.put(p, s, (R)(ex + ey - Prec<R>::kScaleExp * (cx + cy)), (R)A.w[p]);
+                }
+                if (sw == 0 && b == 0) f0 = eval_lnl<R, C>(M, st, P, sm.T[0], sm.ns);
+                int ev;
+                bool conv;
+                double t = newton_solve<R, C>(M, cfg, st, P, sm.T[b], sm.ns, ev, conv);
+                evals_total += ev;
+                if (!conv) ++nonconv;
+                // new length and P matrices of branch b
+                if (threadIdx.x < 4 * C) {
+                    int r = threadIdx.x >> 2, i = threadIdx.x & 3;
+                    pmat_row<R>(M, t * M.rates[r], i, &sm.Pm[b][r * 16 + i * 4]);
+                }
+                if (threadIdx.x == 0) sm.T[b] = t;
+                __syncthreads();
+            }
+            f1 = eval_lnl<R, C>(M, st, P, sm.T[nb - 1], sm.ns);
+            if (f1 - f0 < cfg.sweep_tol) break;
+            f0 = f1;
+        }
+        sweeps_total += sweeps;
+        if (threadIdx.x == 0) {
+            const int o = item - i0;
+            lnl_out[o] = f1;
+            for (int b = 0; b < 5; ++b) len5_out[(size_t)o * 5 + b] = sm.T[b];
+            int k = f1 >= *lmax - thr;
+            kept[o] = k;
+            Slot* sl = &tab[it.slot];
+            sl->lnl = f1;
+            sl->tag = ((unsigned long long)round << 48) | (unsigned long long)(k ? 4 : 1);
+        }
+    }
+    if (threadIdx.x == 0) {
+        atomicAdd(&stats[kStPropEvals], evals_total);
+        atomicAdd(&stats[kStPropSweeps], sweeps_total);
+        atomicAdd(&stats[kStNonconv], nonconv);
+    }
+}
+
+// ---------------------------------------------------------------- full optimisation (K7)
+// One CTA per tree (persistent loop).  Bottom-up D pass, then sweeps over the
+// schedule: visit edge v = compute U_v (stored for inner v), sum-table of
+// (U_v, D_v), Newton on the length; refresh D_v after its subtree.  With
+// max_sweeps = 0 it only evaluates lnL at the given lengths.
+template <typename R, int C>
+struct FullSmem {
+    R Mt[16];
+    NewtonSmem<R, C> ns;
+};
+
+template <typename R, int C, bool kSmemTab>
+__global__ void __launch_bounds__(512) k_fullopt(Model M, Aln A, Cfg cfg, TreeSet ts, int first, int count,
+                                                 ClvGroup g, int max_sweeps, double* lnl_out,
+                                                 unsigned long long* stats, unsigned char* scratch,
+                                                 size_t scratch_per_cta) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    FullSmem<R, C>& sm = *reinterpret_cast<FullSmem<R, C>*>(smraw);
+    const int n = ts.n, NN = 2 * n - 2, P = A.P;
+    const int pcap = (P + 3) & ~3;
+    size_t off = (sizeof(FullSmem<R, C>) + 15) & ~size_t(15);
+    double* len = reinterpret_cast<double*>(smraw + off);
+    off += ((size_t)NN * sizeof(double) + 15) & ~size_t(15);
+    R* Pm = reinterpret_cast<R*>(smraw + off);
+    off += ((size_t)NN * C * 16 * sizeof(R) + 15) & ~size_t(15);
+    STab<R, C> st;
+    {
+        unsigned char* base = kSmemTab ? smraw + off : scratch + (size_t)blockIdx.x * scratch_per_cta;
+        st.s = reinterpret_cast<R*>(base);
+        st.ew = st.s + (size_t)4 * C * pcap;
+        st.pcap = pcap;
+    }
+    if (threadIdx.x < 16) {
+        int i = threadIdx.x >> 2, k = threadIdx.x & 3;
+        sm.Mt[threadIdx.x] = (R)(M.sqpi[i] * M.R[i * 4 + k]);
+    }
+    const size_t sstride = (size_t)P * 4 * C;
+    unsigned long long evals_total = 0, sweeps_total = 0, nonconv = 0;
+    for (int gi = blockIdx.x; gi < count; gi += gridDim.x) {
+        const int tree = first + gi;
+        const int32_t* up = ts.up + (size_t)tree * NN;
+        const int32_t* ch = ts.ch + (size_t)tree * NN * 2;
+        const int32_t* sched = ts.sched + (size_t)tree * 3 * n;
+        double* glen = ts.len + (size_t)tree * NN;
+        R* clv = reinterpret_cast<R*>(g.clv) + (size_t)gi * g.tree_stride;
+        int32_t* scl = g.scl + (size_t)gi * g.scl_stride;
+        __syncthreads();
+        for (int v = threadIdx.x; v < NN; v += blockDim.x) len[v] = glen[v];
+        __syncthreads();
+        for (int x = threadIdx.x; x < NN * C * 4; x += blockDim.x) {
+            int v = x / (C * 4), r = (x / 4) % C, i = x & 3;
+            if (v > 0) pmat_row<R>(M, len[v] * M.rates[r], i, Pm + ((size_t)v * C + r) * 16 + i * 4);
+        }
+        __syncthreads();
+        auto srcD = [&](int v) {
+            Src<R, C> s;
+            if (v < n) { s.clv = nullptr; s.scl = nullptr; s.tip = A.tips + (size_t)v * P; }
+            else { s.clv = clv + (size_t)(v - n) * sstride; s.scl = scl + (size_t)(v - n) * P; s.tip = nullptr; }
+            return s;
+        };
+        auto srcU = [&](int v) {  // the vector at up[v] without v's subtree, for inner v != n
+            Src<R, C> s;
+            const int slot = n - 2 + (v - n - 1);
+            s.clv = clv + (size_t)slot * sstride; s.scl = scl + (size_t)slot * P; s.tip = nullptr;
+            return s;
+        };
+        auto refreshD = [&](int v) {
+            const int c0 = ch[2 * v], c1 = ch[2 * v + 1];
+            for (int p = threadIdx.x; p < P; p += blockDim.x) {
+                R y0[4 * C], y1[4 * C];
+                int k0, k1;
+                apply_p<R, C>(Pm + (size_t)c0 * C * 16, srcD(c0), p, y0, k0);
+                apply_p<R, C>(Pm + (size_t)c1 * C * 16, srcD(c1), p, y1, k1);
+#pragma unroll
+                for (int q = 0; q < 4 * C; ++q) y0[q] *= y1[q];
+                int sc = rescale<R, C>(y0);
+                store_vec<R, C>(clv + (size_t)(v - n) * sstride, p, y0);
+                scl[(size_t)(v - n) * P + p] = k0 + k1 + sc;
+            }
+        };
+        // builds the sum-table of edge (v, up v), storing U_v for inner v
+        auto visit_build = [&](int v) {
+            const Src<R, C> tip0 = {nullptr, nullptr, A.tips};
+            for (int p = threadIdx.x; p < P; p += blockDim.x) {
+                R X[4 * C], Y[4 * C];
+                int cx, cy;
+                if (v == n) {
+                    load_raw<R, C>(tip0, p, X, cx);
+                } else {
+                    const int u = up[v];
+                    const int sib = ch[2 * u] == v ? ch[2 * u + 1] : ch[2 * u];
+                    R y1[4 * C];
+                    int k0, k1;
+                    apply_p<R, C>(Pm + (size_t)sib * C * 16, srcD(sib), p, X, k0);
+                    apply_p<R, C>(Pm + (size_t)u * C * 16, u == n ? tip0 : srcU(u), p, y1, k1);
+#pragma unroll
+                    for (int q = 0; q < 4 * C; ++q) X[q] *= y1[q];
+                    int sc = rescale<R, C>(X);
+                    cx = k0 + k1 + sc;
+                    if (v >= n) {
+                        const int slot = n - 2 + (v - n - 1);
+                        store_vec<R, C>(clv + (size_t)slot * sstride, p, X);
+                        scl[(size_t)slot * P + p] = cx;
+                    }
+                }
+                load_raw<R, C>(srcD(v), p, Y, cy);
+                int ex = normalise<R, C>(X), ey = normalise<R, C>(Y);
+                R s[4 * C];
+                sumtable<R, C>(sm.Mt, X, Y, s);
+                st.put(p, s, (R)(ex + ey - Prec<R>::kScaleExp * (cx + cy)), (R)A.w[p]);
+            }
+        };
+        // bottom-up D pass
+        for (int v = NN - 1; v >= n; --v) refreshD(v);
+        visit_build(n);
+        double f0 = eval_lnl<R, C>(M, st, P, len[n], sm.ns), f1 = f0;
+        int sweeps = 0;
+        const int nsched = 3 * n - 5;
+        for (int sw = 0; sw < max_sweeps; ++sw) {
+            ++sweeps;
+            int last = n;
+            for (int k = 0; k < nsched; ++k) {
+                const int op = sched[k];
+                if (op & kUpd) { refreshD(op & (kUpd - 1)); continue; }
+                const int v = op;
+                if (!(sw == 0 && k == 0)) visit_build(v);  // the first build is already in place
+                int ev;
+                bool conv;
+                double t = newton_solve<R, C>(M, cfg, st, P, len[v], sm.ns, ev, conv);
+                evals_total += ev;
+                if (!conv) ++nonconv;
+                if (threadIdx.x < 4 * C) {
+                    int r = threadIdx.x >> 2, i = threadIdx.x & 3;
+                    pmat_row<R>(M, t * M.rates[r], i, Pm + ((size_t)v * C + r) * 16 + i * 4);
+                }
+                if (threadIdx.x == 0) len[v] = t;
+                __syncthreads();
+                last = v;
+            }
+            f1 = eval_lnl<R, C>(M, st, P, len[last], sm.ns);
+            if (f1 - f0 < cfg.sweep_tol) break;
+            f0 = f1;
+        }
+        sweeps_total += sweeps;
+        __syncthreads();
+        for (int v = threadIdx.x; v < NN; v += blockDim.x) glen[v] = len[v];
+        if (threadIdx.x == 0) lnl_out[gi] = f1;
+    }
+    if (threadIdx.x == 0) {
+        atomicAdd(&stats[kStFullEvals], evals_total);
+        atomicAdd(&stats[kStFullSweeps], sweeps_total);
+        atomicAdd(&stats[kStNonconv], nonconv);
+    }
+}
+
+inline int blocks_for(long long n, int t) { return (int)((n + t - 1) / t); }
+
+}  // namespace
+
+// ================================================================= launchers
+void launch_canon(cudaStream_t s, int n, int count, const int32_t* edges, const double* lengths, TreeSet ts,
+                  int32_t* err) {
+    if (count <= 0) return;
+    k_canon<<<blocks_for(count, kCanonWarps), 32 * kCanonWarps, 0, s>>>(n, count, edges, lengths, ts, err);
+}
+
+void launch_table_init(cudaStream_t s, Slot* tab, size_t nslots) {
+    k_table_init<<<1024, 256, 0, s>>>(tab, nslots);
+}
+
+void launch_enum(cudaStream_t s, int n, int F, TreeSet fr, uint64_t* nkey, int32_t* cinfo) {
+    long long total = (long long)F * 2 * (n - 3);
+    if (total <= 0) return;
+    k_enum<<<(int)std::min<long long>(blocks_for(total, 256), 65535), 256, 0, s>>>(n, F, fr, nkey, cinfo);
+}
+
+void launch_cand_insert(cudaStream_t s, Slot* tab, int log2, int ncand, const uint64_t* nkey, const int32_t* cinfo,
+                        TreeSet fr, int round, int32_t* cslot, int32_t* flag, int32_t* err,
+                        unsigned long long* stats) {
+    if (ncand <= 0) return;
+    k_cand_insert<<<blocks_for(ncand, 256), 256, 0, s>>>(tab, log2, ncand, nkey, cinfo, fr, round, cslot, flag, err,
+                                                         stats);
+}
+
+void launch_cand_arb(cudaStream_t s, int phase, Slot* tab, int ncand, const int32_t* cinfo, TreeSet fr, int round,
+                     const int32_t* cslot, int32_t* flag) {
+    if (ncand <= 0) return;
+    k_cand_arb<<<blocks_for(ncand, 256), 256, 0, s>>>(phase, tab, ncand, cinfo, fr, round, cslot, flag);
+}
+
+void launch_scan(cudaStream_t s, const int32_t* in, int32_t* out, int N, int32_t* tmp) {
+    if (N <= 0) return;
+    int nb = blocks_for(N, 1024);
+    k_scan_block<<<nb, 1024, 0, s>>>(in, out, N, tmp);
+    k_scan_sums<<<1, 1024, 0, s>>>(tmp, nb);
+    k_scan_add<<<nb, 1024, 0, s>>>(out, N, tmp);
+}
+
+void launch_make_items(cudaStream_t s, int ncand, const int32_t* flag, const int32_t* pos, const int32_t* cinfo,
+                       const int32_t* cslot, const uint64_t* nkey, Item* items, uint64_t* ikey) {
+    if (ncand <= 0) return;
+    k_make_items<<<blocks_for(ncand, 256), 256, 0, s>>>(ncand, flag, pos, cinfo, cslot, nkey, items, ikey);
+}
+
+void launch_compact_idx(cudaStream_t s, int N, const int32_t* flag, const int32_t* pos, int32_t* idx) {
+    if (N <= 0) return;
+    k_compact_idx<<<blocks_for(N, 256), 256, 0, s>>>(N, flag, pos, idx);
+}
+
+void launch_insert_trees(cudaStream_t s, Slot* tab, int log2, int count, TreeSet ts, const double* lnl,
+                         const int32_t* status, int round, int32_t* winner, int32_t* err) {
+    if (count <= 0) return;
+    k_insert_trees<<<blocks_for(count, 256), 256, 0, s>>>(tab, log2, count, ts, lnl, status, round, winner, err);
+    k_insert_trees_fin<<<blocks_for(count, 256), 256, 0, s>>>(tab, count, lnl, status, round, winner);
+}
+
+void launch_finalize_trees(cudaStream_t s, Slot* tab, int count, const int32_t* slot_of, const double* lnl,
+                           const double* lmax, double thr, int round, int32_t* good, unsigned long long* stats) {
+    if (count <= 0) return;
+    k_finalize_trees<<<blocks_for(count, 256), 256, 0, s>>>(tab, count, slot_of, lnl, lmax, thr, round, good, stats);
+}
+
+void launch_lmax(cudaStream_t s, int count, const double* lnl, const int32_t* mask, double* lmax) {
+    if (count <= 0) return;
+    k_lmax<<<std::min(blocks_for(count, 256), 1024), 256, 0, s>>>(count, lnl, mask, lmax);
+}
+
+void launch_dump(cudaStream_t s, const Slot* tab, size_t nslots, int32_t* flag) {
+    k_dump_flag<<<1024, 256, 0, s>>>(tab, nslots, flag);
+}
+
+void launch_dump_gather(cudaStream_t s, const Slot* tab, size_t nslots, const int32_t* flag, const int32_t* pos,
+                        uint64_t* keys, uint8_t* status, double* lnl) {
+    k_dump_gather<<<1024, 256, 0, s>>>(tab, nslots, flag, pos, keys, status, lnl);
+}
+
+void launch_materialize(cudaStream_t s, int n, int nk, const int32_t* kidx, const Item* items, TreeSet fr,
+                        const double* len5, int32_t* edges_out, double* lengths_out, int32_t* slot_of) {
+    if (nk <= 0) return;
+    k_materialize<<<blocks_for(nk, 128), 128, 0, s>>>(n, nk, kidx, items, fr, len5, edges_out, lengths_out, slot_of);
+}
+
+void launch_gather_out(cudaStream_t s, int n, int count, const int32_t* idx, TreeSet ts, const double* lnl,
+                       int32_t* edges_out, double* lengths_out, double* lnl_out, uint64_t* keys_out) {
+    if (count <= 0) return;
+    k_gather_out<<<blocks_for(count, 128), 128, 0, s>>>(n, count, idx, ts, lnl, edges_out, lengths_out, lnl_out,
+                                                         keys_out);
+}
+
+void launch_lengths_to_input(cudaStream_t s, int n, int count, TreeSet ts, double* lengths_out) {
+    if (count <= 0) return;
+    k_lengths_to_input<<<blocks_for(count, 128), 128, 0, s>>>(n, count, ts, lengths_out);
+}
+
+size_t sumtable_bytes(int prec, int C, int P) {
+    size_t rs = prec == 0 ? 8 : 4;
+    size_t pcap = (size_t)((P + 3) & ~3);
+    return (4 * (size_t)C + 2) * rs * pcap + 16;
+}
+
+namespace {
+template <typename R, int C>
+size_t propose_fixed() { return (sizeof(ProposeSmem<R, C>) + 15) & ~size_t(15); }
+template <typename R, int C>
+size_t full_fixed(int n) {
+    const int NN = 2 * n - 2;
+    return ((sizeof(FullSmem<R, C>) + 15) & ~size_t(15)) + (((size_t)NN * 8 + 15) & ~size_t(15)) +
+           (((size_t)NN * C * 16 * sizeof(R) + 15) & ~size_t(15));
+}
+}  // namespace
+
+size_t propose_smem_bytes(int prec, int C, int P, bool table_in_smem, int threads) {
+    (void)threads;
+    size_t f = prec == 0 ? (C == 1 ? propose_fixed<double, 1>() : propose_fixed<double, 4>())
+                         : (C == 1 ? propose_fixed<float, 1>() : propose_fixed<float, 4>());
+    return f + (table_in_smem ? sumtable_bytes(prec, C, P) : 0);
+}
+
+size_t fullopt_smem_bytes(int prec, int C, int n, int P, bool table_in_smem, int threads) {
+    (void)threads;
+    size_t f = prec == 0 ? (C == 1 ? full_fixed<double, 1>(n) : full_fixed<double, 4>(n))
+                         : (C == 1 ? full_fixed<float, 1>(n) : full_fixed<float, 4>(n));
+    return f + (table_in_smem ? sumtable_bytes(prec, C, P) : 0);
+}
+
+namespace {
+template <typename R, int C>
+void partials_t(cudaStream_t s, const Model& M, Aln A, TreeSet ts, int first, int count, ClvGroup g, bool with_up,
+                int threads, R* pm) {
+    const int NN = 2 * ts.n - 2;
+    long long rows = (long long)count * NN * C * 4;
+    k_pmats<R><<<(int)std::min<long long>(blocks_for(rows, 256), 8192), 256, 0, s>>>(M, ts, first, count, pm);
+    size_t smem = (size_t)NN * C * 16 * sizeof(R);
+    cudaFuncSetAttribute(k_partials<R, C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    dim3 grid(count, blocks_for(A.P, threads));
+    k_partials<R, C><<<grid, threads, smem, s>>>(M, A, ts, first, g, pm, with_up ? 1 : 0);
+}
+}  // namespace
+
+size_t pmat_bytes(int prec, int C, int n, int count) {
+    return (size_t)count * (2 * n - 2) * C * 16 * (prec == 0 ? 8 : 4);
+}
+
+void launch_partials(cudaStream_t s, int prec, const Model& M, Aln A, TreeSet ts, int first, int count, ClvGroup g,
+                     bool with_up, int threads, void* pm) {
+    if (count <= 0) return;
+    if (prec == 0) {
+        double* q = reinterpret_cast<double*>(pm);
+        if (M.C == 1) partials_t<double, 1>(s, M, A, ts, first, count, g, with_up, threads, q);
+        else partials_t<double, 4>(s, M, A, ts, first, count, g, with_up, threads, q);
+    } else {
+        float* q = reinterpret_cast<float*>(pm);
+        if (M.C == 1) partials_t<float, 1>(s, M, A, ts, first, count, g, with_up, threads, q);
+        else partials_t<float, 4>(s, M, A, ts, first, count, g, with_up, threads, q);
+    }
+}
+
+namespace {
+template <typename R, int C>
+void propose_t(cudaStream_t s, const Model& M, Aln A, Cfg cfg, TreeSet fr, int first, ClvGroup g, const Item* items,
+               int i0, int i1, Slot* tab, int round, const double* lmax, double thr, double* lnl_out, double* len5_out,
+               int32_t* kept, unsigned long long* stats, int threads, int grid, void* scratch, size_t spc,
+               const void* pmv) {
+    const R* pm = reinterpret_cast<const R*>(pmv);
+    if (scratch) {
+        size_t smem = propose_smem_bytes(sizeof(R) == 8 ? 0 : 1, C, A.P, false, threads);
+        cudaFuncSetAttribute(k_propose<R, C, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        k_propose<R, C, false><<<grid, threads, smem, s>>>(M, A, cfg, fr, first, g, pm, items, i0, i1, tab, round,
+                                                           lmax, thr, lnl_out, len5_out, kept, stats,
+                                                           reinterpret_cast<unsigned char*>(scratch), spc);
+    } else {
+        size_t smem = propose_smem_bytes(sizeof(R) == 8 ? 0 : 1, C, A.P, true, threads);
+        cudaFuncSetAttribute(k_propose<R, C, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        k_propose<R, C, true><<<grid, threads, smem, s>>>(M, A, cfg, fr, first, g, pm, items, i0, i1, tab, round,
+                                                          lmax, thr, lnl_out, len5_out, kept, stats, nullptr, 0);
+    }
+}
+}  // namespace
+
+void launch_propose(cudaStream_t s, int prec, const Model& M, Aln A, Cfg cfg, TreeSet fr, int first, ClvGroup g,
+                    const Item* items, int i0, int i1, Slot* tab, int round, const double* lmax, double thr,
+                    double* lnl_out, double* len5_out, int32_t* kept, unsigned long long* stats, int threads,
+                    int grid, void* scratch, size_t scratch_per_cta, const void* pm) {
+    if (i1 <= i0) return;
+    // pm holds the P matrices of the group's trees, as computed by launch_partials
+    if (prec == 0) {
+        if (M.C == 1) propose_t<double, 1>(s, M, A, cfg, fr, first, g, items, i0, i1, tab, round, lmax, thr, lnl_out, len5_out, kept, stats, threads, grid, scratch, scratch_per_cta, pm);
+        else propose_t<double, 4>(s, M, A, cfg, fr, first, g, items, i0, i1, tab, round, lmax, thr, lnl_out, len5_out, kept, stats, threads, grid, scratch, scratch_per_cta, pm);
+    } else {
+        if (M.C == 1) propose_t<float, 1>(s, M, A, cfg, fr, first, g, items, i0, i1, tab, round, lmax, thr, lnl_out, len5_out, kept, stats, threads, grid, scratch, scratch_per_cta, pm);
+        else propose_t<float, 4>(s, M, A, cfg, fr, first, g, items, i0, i1, tab, round, lmax, thr, lnl_out, len5_out, kept, stats, threads, grid, scratch, scratch_per_cta, pm);
+    }
+}
+
+namespace {
+template <typename R, int C>
+void fullopt_t(cudaStream_t s, const Model& M, Aln A, Cfg cfg, TreeSet ts, int first, int count, ClvGroup g,
+               int max_sweeps, double* lnl_out, unsigned long long* stats, int threads, int grid, void* scratch,
+               size_t spc) {
+    const int prec = sizeof(R) == 8 ? 0 : 1;
+    if (scratch) {
+        size_t smem = fullopt_smem_bytes(prec, C, ts.n, A.P, false, threads);
+        cudaFuncSetAttribute(k_fullopt<R, C, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        k_fullopt<R, C, false><<<grid, threads, smem, s>>>(M, A, cfg, ts, first, count, g, max_sweeps, lnl_out, stats,
+                                                           reinterpret_cast<unsigned char*>(scratch), spc);
+    } else {
+        size_t smem = fullopt_smem_bytes(prec, C, ts.n, A.P, true, threads);
+        cudaFuncSetAttribute(k_fullopt<R, C, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        k_fullopt<R, C, true><<<grid, threads, smem, s>>>(M, A, cfg, ts, first, count, g, max_sweeps, lnl_out, stats,
+                                                          nullptr, 0);
+    }
+}
+}  // namespace
+
+void launch_fullopt(cudaStream_t s, int prec, const Model& M, Aln A, Cfg cfg, TreeSet ts, int first, int count,
+                    ClvGroup g, int max_sweeps, double* lnl_out, unsigned long long* stats, int threads, int grid,
+                    void* scratch, size_t scratch_per_cta) {
+    if (count <= 0) return;
+    if (prec == 0) {
+        if (M.C == 1) fullopt_t<double, 1>(s, M, A, cfg, ts, first, count, g, max_sweeps, lnl_out, stats, threads, grid, scratch, scratch_per_cta);
+        else fullopt_t<double, 4>(s, M, A, cfg, ts, first, count, g, max_sweeps, lnl_out, stats, threads, grid, scratch, scratch_per_cta);
+    } else {
+        if (M.C == 1) fullopt_t<float, 1>(s, M, A, cfg, ts, first, count, g, max_sweeps, lnl_out, stats, threads, grid, scratch, scratch_per_cta);
+        else fullopt_t<float, 4>(s, M, A, cfg, ts, first, count, g, max_sweeps, lnl_out, stats, threads, grid, scratch, scratch_per_cta);
+    }
+}
+
+}  // namespace pt

@@ -1,0 +1,298 @@
+"""Thin ctypes binding of libpt (include/pt.h).
+
+Argument marshalling only: every step of the PT round runs in libpt's CUDA
+kernels.  There is no CPU fallback; loading fails loudly when the library has
+not been built (``paper_1811_11007_gb300.build.build()``).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+import numpy as np
+
+from . import build as _build
+
+PREC_FP64, PREC_MIXED = 0, 1
+SCORE_FIXED, SCORE_FULL = 0, 1
+PROPOSE_FIVE, PROPOSE_CENTRAL = 0, 1
+ST_REJECTED, ST_GOOD, ST_BAD = 1, 2, 3
+STATUS = {0: "OK", 1: "INVALID_ARG", 2: "OOM", 3: "TABLE_FULL", 4: "BUFFER_TOO_SMALL", 5: "CUDA", 6: "TIMEOUT",
+          7: "STATE"}
+EXPORTS = ["pt_config_default", "pt_create", "pt_destroy", "pt_last_error", "pt_set_stream", "pt_load_alignment",
+           "pt_alignment_info", "pt_set_model", "pt_model_rates", "pt_score_topologies", "pt_begin",
+           "pt_expand_frontier", "pt_expand_frontier_dev", "pt_visited", "pt_reset_visited", "pt_stats",
+           "pt_last_proposals", "pt_stage_times", "pt_version", "pt_discrete_gamma", "pt_model_eigen"]
+
+
+class PTError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class Config(C.Structure):
+    _fields_ = [("device", C.c_int), ("precision", C.c_int), ("table_log2", C.c_int), ("propose_mode", C.c_int),
+                ("tmin", C.c_double), ("tmax", C.c_double), ("newton_tol", C.c_double), ("newton_maxit", C.c_int),
+                ("sweep_tol", C.c_double), ("full_max_sweeps", C.c_int), ("prop_max_sweeps", C.c_int),
+                ("threads", C.c_int), ("mem_budget", C.c_size_t)]
+
+
+_lib = None
+_lock = threading.Lock()
+_i32p = np.ctypeslib.ndpointer(np.int32, flags="C_CONTIGUOUS")
+_f64p = np.ctypeslib.ndpointer(np.float64, flags="C_CONTIGUOUS")
+_u64p = np.ctypeslib.ndpointer(np.uint64, flags="C_CONTIGUOUS")
+_u8p = np.ctypeslib.ndpointer(np.uint8, flags="C_CONTIGUOUS")
+_vp = C.c_void_p
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def lib():
+    """Loads libpt.so (raises if it is missing: there is no fallback)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = library_path()
+            if not os.path.exists(path):
+                raise RuntimeError(f"libpt.so not built ({path}); run paper_1811_11007_gb300.build.build()")
+            L = C.CDLL(path)
+            L.pt_config_default.argtypes = [C.POINTER(Config)]
+            L.pt_create.argtypes = [C.POINTER(_vp), C.POINTER(Config)]
+            L.pt_destroy.argtypes = [_vp]
+            L.pt_last_error.restype = C.c_char_p
+            L.pt_last_error.argtypes = [_vp]
+            L.pt_set_stream.argtypes = [_vp, _vp]
+            L.pt_load_alignment.argtypes = [_vp, C.c_int, C.c_int, _u8p, C.POINTER(C.c_int)]
+            L.pt_alignment_info.argtypes = [_vp, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int)]
+            L.pt_set_model.argtypes = [_vp, C.c_int, _f64p, _f64p, C.c_double, C.c_int]
+            L.pt_model_rates.argtypes = [_vp, C.c_int, _f64p, C.c_int]
+            L.pt_score_topologies.argtypes = [_vp, C.c_int, C.c_int, _i32p, _f64p, _f64p, _vp, C.c_int]
+            L.pt_begin.argtypes = [_vp, C.c_int, C.c_int, _i32p, _f64p, C.c_double, C.POINTER(C.c_double), C.c_int,
+                                   _vp, _vp, _vp, _vp, C.POINTER(C.c_int)]
+            L.pt_expand_frontier.argtypes = [_vp, C.c_int, C.c_int, _vp, _vp, C.c_double, C.POINTER(C.c_double),
+                                             C.c_int, _vp, _vp, _vp, _vp, C.POINTER(C.c_int)]
+            L.pt_expand_frontier_dev.argtypes = [_vp, C.c_int, C.c_int, _vp, _vp, C.c_double,
+                                                 C.POINTER(C.c_double), C.c_int, _vp, _vp, _vp, _vp,
+                                                 C.POINTER(C.c_int)]
+            L.pt_visited.argtypes = [_vp, C.c_int, C.c_size_t, _vp, _vp, _vp, C.POINTER(C.c_size_t)]
+            L.pt_reset_visited.argtypes = [_vp, C.c_int]
+            L.pt_stats.argtypes = [_vp, C.POINTER(C.c_int64), C.c_int]
+            L.pt_last_proposals.argtypes = [_vp, C.c_size_t, _vp, _vp, _vp, _vp, _vp, _vp, C.POINTER(C.c_size_t)]
+            L.pt_stage_times.argtypes = [_vp, C.POINTER(C.c_double), C.c_int]
+            L.pt_version.restype = C.c_char_p
+            L.pt_discrete_gamma.argtypes = [C.c_double, C.c_int, _f64p]
+            L.pt_model_eigen.argtypes = [_f64p, _f64p, _f64p, _f64p]
+            _lib = L
+    return _lib
+
+
+def _ptr(a):
+    return None if a is None else a.ctypes.data_as(_vp)
+
+
+def default_config() -> Config:
+    cfg = Config()
+    lib().pt_config_default(C.byref(cfg))
+    return cfg
+
+
+def discrete_gamma(alpha: float, ncat: int) -> np.ndarray:
+    out = np.zeros(ncat, np.float64)
+    st = lib().pt_discrete_gamma(alpha, ncat, out)
+    if st:
+        raise PTError(st, "bad gamma parameters")
+    return out
+
+
+def model_eigen(exch, freqs):
+    lam = np.zeros(4)
+    R = np.zeros(16)
+    st = lib().pt_model_eigen(np.ascontiguousarray(exch, np.float64), np.ascontiguousarray(freqs, np.float64), lam, R)
+    if st:
+        raise PTError(st, "bad model")
+    return lam, R.reshape(4, 4)
+
+
+def keys_to_int(keys: np.ndarray) -> list[int]:
+    k = np.asarray(keys, np.uint64).reshape(-1, 2)
+    return [int(a) | (int(b) << 64) for a, b in k]
+
+
+class Context:
+    """One libpt context (one device, one stream)."""
+
+    def __init__(self, precision: str = "mixed", table_log2: int = 22, propose: str = "five", device: int = 0,
+                 stream=None, **overrides):
+        cfg = default_config()
+        cfg.device = device
+        cfg.precision = {"fp64": PREC_FP64, "mixed": PREC_MIXED}[precision]
+        cfg.table_log2 = table_log2
+        cfg.propose_mode = {"five": PROPOSE_FIVE, "central": PROPOSE_CENTRAL}[propose]
+        for k, v in overrides.items():
+            setattr(cfg, k, v)
+        self.cfg = cfg
+        h = _vp()
+        st = lib().pt_create(C.byref(h), C.byref(cfg))
+        if st:
+            raise PTError(st, "pt_create failed")
+        self._h = h
+        self._n = {}
+        if stream is not None:
+            self.set_stream(stream)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().pt_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        self.close()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def _ck(self, st):
+        if st:
+            raise PTError(st, lib().pt_last_error(self._h).decode())
+
+    def set_stream(self, stream):
+        """stream: a torch.cuda.Stream, an int handle, or None."""
+        handle = getattr(stream, "cuda_stream", stream)
+        self._ck(lib().pt_set_stream(self._h, _vp(handle or 0)))
+
+    def load_alignment(self, codes) -> int:
+        codes = np.ascontiguousarray(codes, np.uint8)
+        aid = C.c_int()
+        self._ck(lib().pt_load_alignment(self._h, codes.shape[0], codes.shape[1], codes.reshape(-1), C.byref(aid)))
+        self._n[aid.value] = codes.shape[0]
+        return aid.value
+
+    def alignment_info(self, aln: int):
+        n, p = C.c_int(), C.c_int()
+        self._ck(lib().pt_alignment_info(self._h, aln, C.byref(n), C.byref(p)))
+        return n.value, p.value
+
+    def set_model(self, aln: int, exch, freqs, alpha: float, ncat: int):
+        self._ck(lib().pt_set_model(self._h, aln, np.ascontiguousarray(exch, np.float64),
+                                    np.ascontiguousarray(freqs, np.float64), float(alpha), int(ncat)))
+
+    def model_rates(self, aln: int, ncat: int):
+        r = np.zeros(ncat, np.float64)
+        self._ck(lib().pt_model_rates(self._h, aln, r, ncat))
+        return r
+
+    def score(self, aln: int, edges, lengths, mode: str = "full"):
+        e = np.ascontiguousarray(edges, np.int32)
+        if e.ndim == 2:
+            e = e[None]
+        t = e.shape[0]
+        lens = np.array(lengths, np.float64, copy=True).reshape(t, -1)
+        lnl = np.zeros(t, np.float64)
+        keys = np.zeros((t, 2), np.uint64)
+        self._ck(lib().pt_score_topologies(self._h, aln, t, e.reshape(-1), lens.reshape(-1), lnl, _ptr(keys),
+                                           SCORE_FULL if mode == "full" else SCORE_FIXED))
+        return lnl, lens, keys
+
+    def _front_buffers(self, n, cap):
+        E = 2 * n - 3
+        return (np.zeros((cap, E, 2), np.int32), np.zeros((cap, E), np.float64), np.zeros(cap, np.float64),
+                np.zeros((cap, 2), np.uint64))
+
+    def begin(self, aln: int, edges, lengths, threshold: float):
+        n = self._n[aln]
+        e = np.ascontiguousarray(edges, np.int32).reshape(-1, 2 * n - 3, 2)
+        l = np.ascontiguousarray(lengths, np.float64).reshape(e.shape[0], -1)
+        cap = e.shape[0]
+        fe, fl, fn, fk = self._front_buffers(n, cap)
+        lmax = C.c_double()
+        cnt = C.c_int()
+        self._ck(lib().pt_begin(self._h, aln, e.shape[0], e.reshape(-1), l.reshape(-1), float(threshold),
+                                C.byref(lmax), cap, _ptr(fe), _ptr(fl), _ptr(fn), _ptr(fk), C.byref(cnt)))
+        k = cnt.value
+        return lmax.value, {"edges": fe[:k], "lengths": fl[:k], "lnl": fn[:k], "keys": fk[:k]}
+
+    def expand(self, aln: int, edges, lengths, threshold: float, lmax: float, cap: int | None = None):
+        """One PT round on a host frontier; returns (lmax, next frontier)."""
+        n = self._n[aln]
+        E = 2 * n - 3
+        e = np.ascontiguousarray(edges, np.int32).reshape(-1, E, 2)
+        l = np.ascontiguousarray(lengths, np.float64).reshape(e.shape[0], E)
+        F = e.shape[0]
+        if cap is None:
+            cap = max(F * 2 * (n - 3), 1)
+        fe, fl, fn, fk = self._front_buffers(n, cap)
+        lm = C.c_double(lmax)
+        cnt = C.c_int()
+        st = lib().pt_expand_frontier(self._h, aln, F, _ptr(e), _ptr(l), float(threshold), C.byref(lm), cap,
+                                      _ptr(fe), _ptr(fl), _ptr(fn), _ptr(fk), C.byref(cnt))
+        self._ck(st)
+        k = cnt.value
+        return lm.value, {"edges": fe[:k], "lengths": fl[:k], "lnl": fn[:k], "keys": fk[:k]}
+
+    def expand_dev(self, aln: int, F: int, edges_ptr: int, lengths_ptr: int, threshold: float, lmax: float,
+                   cap: int, out_edges_ptr: int, out_lengths_ptr: int, out_lnl_ptr: int, out_keys_ptr: int):
+        """One PT round on device buffers (raw device pointers, e.g. tensor.data_ptr())."""
+        lm = C.c_double(lmax)
+        cnt = C.c_int()
+        self._ck(lib().pt_expand_frontier_dev(self._h, aln, F, _vp(edges_ptr), _vp(lengths_ptr), float(threshold),
+                                              C.byref(lm), cap, _vp(out_edges_ptr), _vp(out_lengths_ptr),
+                                              _vp(out_lnl_ptr), _vp(out_keys_ptr), C.byref(cnt)))
+        return lm.value, cnt.value
+
+    def visited(self, aln: int):
+        cnt = C.c_size_t()
+        self._ck(lib().pt_visited(self._h, aln, 0, None, None, None, C.byref(cnt)))
+        k = cnt.value
+        keys = np.zeros((max(k, 1), 2), np.uint64)
+        st = np.zeros(max(k, 1), np.uint8)
+        lnl = np.zeros(max(k, 1), np.float64)
+        self._ck(lib().pt_visited(self._h, aln, k, _ptr(keys), _ptr(st), _ptr(lnl), C.byref(cnt)))
+        return {"keys": keys[:k], "status": st[:k], "lnl": lnl[:k]}
+
+    def reset_visited(self, aln: int):
+        self._ck(lib().pt_reset_visited(self._h, aln))
+
+    def stats(self) -> dict:
+        out = (C.c_int64 * 16)()
+        self._ck(lib().pt_stats(self._h, out, 16))
+        names = ["candidates", "duplicates", "scored", "kept", "good", "prop_evals", "full_evals", "nonconverged",
+                 "prop_sweeps", "full_sweeps"]
+        return {k: int(out[i]) for i, k in enumerate(names)}
+
+    def stage_times(self) -> dict:
+        out = (C.c_double * 6)()
+        self._ck(lib().pt_stage_times(self._h, out, 6))
+        return dict(zip(["canon", "dedup", "partials", "propose", "fullopt", "total"], list(out)))
+
+    def last_proposals(self):
+        cnt = C.c_size_t()
+        self._ck(lib().pt_last_proposals(self._h, 0, None, None, None, None, None, None, C.byref(cnt)))
+        k = cnt.value
+        keys = np.zeros((max(k, 1), 2), np.uint64)
+        par = np.zeros(max(k, 1), np.int32)
+        node = np.zeros(max(k, 1), np.int32)
+        sw = np.zeros(max(k, 1), np.int32)
+        lnl = np.zeros(max(k, 1), np.float64)
+        l5 = np.zeros((max(k, 1), 5), np.float64)
+        self._ck(lib().pt_last_proposals(self._h, k, _ptr(keys), _ptr(par), _ptr(node), _ptr(sw), _ptr(lnl),
+                                         _ptr(l5), C.byref(cnt)))
+        return {"keys": keys[:k], "parent": par[:k], "edge_node": node[:k], "swap": sw[:k], "lnl": lnl[:k],
+                "len5": l5[:k]}
+
+
+def run_search(ctx: Context, aln: int, starts_edges, starts_lengths, threshold: float, max_rounds: int = 1 << 30):
+    """Full round-synchronous PT search driven through the ABI."""
+    lmax, front = ctx.begin(aln, starts_edges, starts_lengths, threshold)
+    rounds = 0
+    while len(front["edges"]) and rounds < max_rounds:
+        lmax, front = ctx.expand(aln, front["edges"], front["lengths"], threshold, lmax)
+        rounds += 1
+    return lmax, rounds
