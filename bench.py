@@ -1,0 +1,374 @@
+#!/usr/bin/env python
+"""Benchmark of the PT hot path: branch-optimised topologies/s.
+
+One step = one PT round on a fixed frontier of F topologies of a 27-taxon,
+2000-site GTR+Gamma4 alignment (exchangeabilities ~ Dirichlet(1^6),
+frequencies ~ Dirichlet(5^4), alpha 0.5, simulated on a random tree with
+Exp(mean 0.05) branches): every NNI neighbour of the frontier is keyed,
+deduplicated against the device visited table (reset at the start of the
+step), proposal-optimised by Newton on its five NNI branches, thresholded at
+lmax - 10, and the kept ones are fully optimised.  The frontier is the one a
+PT search (threshold 10, 8 random starts) reaches on the GPU during set-up.
+Unit: unique neighbours scored to convergence per second, whole job.
+
+value: device-resident inputs (pt_expand_frontier_dev), mixed precision.
+e2e:   the same step through the host-buffer entry point pt_expand_frontier
+       from pinned host memory (frontier in, next frontier out).
+fp64:  the plain FP64 GPU path on the same frontier.
+--impl reference: the FP64 CPU oracle, timed on this host's cores on a
+bounded sample of the same step.
+"""
+from __future__ import annotations
+
+import argparse
+import ctypes as C
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+N_TAXA, N_SITES, THRESH, N_STARTS = 27, 2000, 10.0, 8
+FP32_LANES_PER_SM = 128
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=5)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--frontier", type=int, default=256)
+    p.add_argument("--no-fp64", action="store_true")
+    p.add_argument("--no-cpu", action="store_true")
+    p.add_argument("--cpu-sample", type=int, default=1, help="frontier trees in the CPU baseline sample")
+    return p.parse_args()
+
+
+def peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {}
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, dev):
+        self.dev, self.rows, self.proc = dev, [], None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.dev), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([x.strip() for x in line.split(",")])
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in self.rows:
+            try:
+                sm.append(float(r[1]))
+                mx = float(r[2])
+                for nm, v in zip(names, r[5:9]):
+                    if v.lower() in ("active", "1", "yes"):
+                        reasons.add(nm)
+            except (ValueError, IndexError):
+                continue
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def workload(rank: int):
+    from paper_1811_11007_gb300 import synth
+    seed = synth.SEED_BASE + 2 + 1000 * rank
+    a = synth.simulate(N_TAXA, N_SITES, seed, model="gtr", alpha=0.5, mean_branch=0.05)
+    starts = synth.random_trees(N_TAXA, N_STARTS, seed + 1)
+    return a, starts
+
+
+def build_frontier(ctx, aid, starts, F):
+    """Runs the PT search (threshold 10) until the frontier holds >= F trees;
+    returns the largest frontier seen (first F) and the lmax before it."""
+    lmax, front = ctx.begin(aid, starts[0], starts[1], THRESH)
+    best = (lmax, front)
+    for _ in range(200):
+        if len(front["edges"]) >= F or len(front["edges"]) == 0:
+            break
+        lmax, front = ctx.expand(aid, front["edges"], front["lengths"], THRESH, lmax)
+        if len(front["edges"]) > len(best[1]["edges"]):
+            best = (lmax, front)
+    lmax, front = best if len(front["edges"]) < F else (lmax, front)
+    k = min(F, len(front["edges"]))
+    return lmax, {key: v[:k] for key, v in front.items()}
+
+
+def run_ours(args, rank, world, dev):
+    import torch
+    from paper_1811_11007_gb300 import pt
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.current_stream()
+    a, starts = workload(rank)
+    n, E = N_TAXA, 2 * N_TAXA - 3
+    m = 2 * (n - 3)
+
+    def make(prec):
+        ctx = pt.Context(precision=prec, table_log2=22, stream=stream)
+        aid = ctx.load_alignment(a.codes)
+        ctx.set_model(aid, a.exch, a.freqs, 0.5, 4)
+        return ctx, aid
+
+    ctx, aid = make("mixed")
+    lmax0, front = build_frontier(ctx, aid, starts, args.frontier)
+    F = len(front["edges"])
+    _, P = ctx.alignment_info(aid)
+    d_e = torch.from_numpy(np.ascontiguousarray(front["edges"])).to(dev)
+    d_l = torch.from_numpy(np.ascontiguousarray(front["lengths"])).to(dev)
+    cap = F * m
+    o_e = torch.empty((cap, E, 2), dtype=torch.int32, device=dev)
+    o_l = torch.empty((cap, E), dtype=torch.float64, device=dev)
+    o_n = torch.empty(cap, dtype=torch.float64, device=dev)
+    o_k = torch.empty((cap, 2), dtype=torch.int64, device=dev)
+
+    def step_dev(c, i):
+        c.reset_visited(i)
+        lm, cnt = c.expand_dev(i, F, d_e.data_ptr(), d_l.data_ptr(), THRESH, lmax0, cap, o_e.data_ptr(),
+                               o_l.data_ptr(), o_n.data_ptr(), o_k.data_ptr())
+        st = c.stats()
+        times = c.stage_times()
+        return st["scored"], st["launches"] + 1, times, st, cnt
+
+    def timed(c, i, step, steps, warmup):
+        for _ in range(warmup):
+            step(c, i)
+        torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        units, launches, prop_ms, part_ms, stats, flops, times = 0, 0, 0.0, 0.0, None, 0.0, {}
+        e0.record(stream)
+        for _ in range(steps):
+            w, l, times, st, _ = step(c, i)
+            units += w
+            launches += l
+            prop_ms += times["propose"]
+            part_ms += times["partials"]
+            stats = st
+            nb = 5 if c.cfg.propose_mode == 0 else 1
+            flops += P * (st["prop_sweeps"] * nb * 2 * 272 + st["prop_evals"] * 100)
+        e1.record(stream)
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        if world > 1:
+            t = torch.tensor([ms], device=dev, dtype=torch.float64)
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            u = torch.tensor([units], device=dev, dtype=torch.float64)
+            torch.distributed.all_reduce(u)
+            ms, units = float(t.item()), float(u.item())
+        return {"ms": ms, "units": units, "launches": launches, "prop_ms": prop_ms, "part_ms": part_ms,
+                "stats": stats, "flops": flops, "times": times}
+
+    with ClockSampler(dev) as clk:
+        res = timed(ctx, aid, step_dev, args.steps, args.warmup)
+    clocks = clk.summary()
+
+    # end to end: host buffers (pinned), copies inside every step
+    h_e = torch.from_numpy(np.ascontiguousarray(front["edges"])).pin_memory()
+    h_l = torch.from_numpy(np.ascontiguousarray(front["lengths"])).pin_memory()
+    ho_e = torch.empty((cap, E, 2), dtype=torch.int32).pin_memory()
+    ho_l = torch.empty((cap, E), dtype=torch.float64).pin_memory()
+    ho_n = torch.empty(cap, dtype=torch.float64).pin_memory()
+    ho_k = torch.empty((cap, 2), dtype=torch.int64).pin_memory()
+    bytes_io = {"h2d": 0, "d2h": 0}
+
+    def step_host(c, i):
+        c.reset_visited(i)
+        lm = C.c_double(lmax0)
+        cnt = C.c_int()
+        c._ck(pt.lib().pt_expand_frontier(c._h, i, F, C.c_void_p(h_e.data_ptr()), C.c_void_p(h_l.data_ptr()),
+                                          THRESH, C.byref(lm), cap, C.c_void_p(ho_e.data_ptr()),
+                                          C.c_void_p(ho_l.data_ptr()), C.c_void_p(ho_n.data_ptr()),
+                                          C.c_void_p(ho_k.data_ptr()), C.byref(cnt)))
+        bytes_io["h2d"] = F * E * 2 * 4 + F * E * 8
+        bytes_io["d2h"] = cnt.value * (E * 2 * 4 + E * 8 + 8 + 16)
+        st = c.stats()
+        return st["scored"], st["launches"] + 1, c.stage_times(), st, cnt.value
+
+    e2e = timed(ctx, aid, step_host, args.steps, 1)
+
+    fp64 = None
+    if not args.no_fp64:
+        ctx64, aid64 = make("fp64")
+        fp64 = timed(ctx64, aid64, step_dev, max(1, min(args.steps, 2)), 1)
+        ctx64.close()
+
+    out = None
+    if rank == 0:
+        pk = peaks()
+        value = res["units"] / (res["ms"] / 1e3)
+        sm_max = pk.get("sm_max_mhz", 2070.0)
+        nsm = torch.cuda.get_device_properties(dev).multi_processor_count
+        alu_peak = nsm * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
+        prop_s = res["prop_ms"] / 1e3
+        achieved_tf = res["flops"] / prop_s / 1e12 if prop_s > 0 else None
+        hbm_peak = pk.get("hbm_gbs", 6800.0)
+        alg_bytes = 320.0 * P * res["units"] / max(world, 1)
+        ph_s = (res["prop_ms"] + res["part_ms"]) / 1e3
+        achieved_gb = alg_bytes / ph_s / 1e9 if ph_s > 0 else None
+        st = res["stats"]
+        out = {
+            "metric": "branch-optimised topologies/sec (unique NNI neighbours scored per PT round)",
+            "value": value,
+            "unit": "topologies/s",
+            "n_gpus": world,
+            "steps": args.steps,
+            "warmup": args.warmup,
+            "ms_per_step": res["ms"] / args.steps,
+            "higher_is_better": True,
+            "scaling": "weak",
+            "vs_baseline": None,
+            "dtype": "f32 partials + f64 reductions",
+            "data": "synthetic (seeded simulation; the paper's datasets are not available)",
+            "config": {"workload": f"PT round on a {F}-tree frontier, {N_TAXA} taxa x {N_SITES} sites ({P} patterns), "
+                                   f"GTR+G4, threshold {THRESH}",
+                       "taxa": N_TAXA, "sites": N_SITES, "patterns": P, "frontier": F,
+                       "neighbours_per_step": st["scored"], "kept_per_step": st["kept"],
+                       "threshold": THRESH, "parallelism": f"replicas x{world} (independent alignments)",
+                       "l2": "inputs larger than L2 (frontier partials ~%.2f GB per step)" % (
+                           F * (2 * N_TAXA - 5) * P * 68 / 1e9)},
+            "e2e": {"value": e2e["units"] / (e2e["ms"] / 1e3), "unit": "topologies/s",
+                    "h2d_bytes_per_step": bytes_io["h2d"], "d2h_bytes_per_step": bytes_io["d2h"]},
+            "fp64_gpu": ({"value": fp64["units"] / (fp64["ms"] / 1e3), "unit": "topologies/s",
+                          "ms_per_step": fp64["ms"] / max(1, min(args.steps, 2))} if fp64 else None),
+            "roofline": {"bound": "alu", "kernel": "k_propose (proposal Newton)", "achieved": achieved_tf,
+                         "peak": alu_peak, "unit": "TFLOP/s",
+                         "frac": (achieved_tf / alu_peak) if achieved_tf else None, "traffic": None,
+                         "peak_note": f"FP32 FMA: {nsm} SMs x 128 lanes x 2 flop x {sm_max:.0f} MHz (recipe unit counts)"},
+            "roofline_hbm": {"bound": "hbm", "achieved": achieved_gb, "peak": hbm_peak, "unit": "GB/s",
+                             "frac": (achieved_gb / hbm_peak) if achieved_gb else None,
+                             "note": "algorithmic 320*P bytes per neighbour over partials + proposal kernel time; "
+                                     "peak = measured copy bandwidth"},
+            "stage_ms_per_step": {k: v for k, v in res.get("times", {}).items()},
+            "newton": {"prop_evals_per_neighbour": st["prop_evals"] / max(st["scored"], 1),
+                       "prop_sweeps_per_neighbour": st["prop_sweeps"] / max(st["scored"], 1),
+                       "nonconverged": st["nonconverged"]},
+            "gpu_launches": res["launches"],
+            "clocks": clocks,
+        }
+    return out, (a, front, lmax0)
+
+
+def cpu_baseline(a, front, lmax0, sample):
+    import oracle
+    from paper_1811_11007_gb300 import synth
+    tips, w = synth.compress_patterns(a.codes)
+    pb = oracle.Problem(tips, w, a.exch, a.freqs, 0.5, 4)
+    k = max(1, min(sample, len(front["edges"])))
+    t0 = time.perf_counter()
+    s = oracle.Search(pb, front["edges"][:k], front["lengths"][:k], THRESH, frontier_lmax=lmax0)
+    s.round()
+    dt = time.perf_counter() - t0
+    scored = s.stats()["scored"]
+    return {"value": scored / dt, "unit": "topologies/s", "cores": 1, "kind": "oracle",
+            "sample": f"one PT round on {k} of the frontier trees ({scored} neighbours scored, "
+                      f"{s.stats()['kept']} fully optimised) in {dt:.1f} s, single thread"}
+
+
+def run_reference(args, rank, world):
+    """The oracle as it stands, on the host cores, same metric and config."""
+    if rank != 0:
+        return
+    import torch
+    from paper_1811_11007_gb300 import pt
+    a, starts = workload(0)
+    # the frontier comes from the oracle's own search on the same starts (bounded)
+    import oracle
+    from paper_1811_11007_gb300 import synth
+    tips, w = synth.compress_patterns(a.codes)
+    pb = oracle.Problem(tips, w, a.exch, a.freqs, 0.5, 4)
+    e = np.ascontiguousarray(starts[0][:1])
+    l = np.ascontiguousarray(starts[1][:1])
+    lmax, le = pb.full_optimise(e[0], l[0])[:2]
+    front = {"edges": e, "lengths": le[None]}
+    vals = []
+    for i in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        s = oracle.Search(pb, front["edges"], front["lengths"], THRESH, frontier_lmax=lmax)
+        s.round()
+        dt = time.perf_counter() - t0
+        if i >= args.warmup:
+            vals.append((s.stats()["scored"], dt))
+    units = sum(v[0] for v in vals)
+    secs = sum(v[1] for v in vals)
+    v = units / secs
+    line = {"impl": "reference", "metric": "branch-optimised topologies/sec (unique NNI neighbours scored per PT round)",
+            "value": v, "unit": "topologies/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * secs / len(vals), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"PT round on 1 frontier tree, {N_TAXA} taxa x {N_SITES} sites, GTR+G4, "
+                                   f"threshold {THRESH} (bounded CPU sample)"},
+            "cpu_baseline": {"value": v, "unit": "topologies/s", "cores": 1, "kind": "oracle",
+                             "sample": "one PT round on one hill-start frontier tree per step, single thread"},
+            "e2e": {"value": v, "unit": "topologies/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def main():
+    args = parse()
+    rank = int(os.environ.get("RANK", 0))
+    world = int(os.environ.get("WORLD_SIZE", 1))
+    local = int(os.environ.get("LOCAL_RANK", 0))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    import torch
+    if world > 1:
+        torch.cuda.set_device(local)
+        torch.distributed.init_process_group("nccl", device_id=torch.device("cuda", local))
+    from paper_1811_11007_gb300 import build
+    if rank == 0 or world == 1:
+        build.build()
+    if world > 1:
+        torch.distributed.barrier()
+    out, (a, front, lmax0) = run_ours(args, rank, world, local)
+    if rank == 0:
+        if world == 1 and not args.no_cpu:
+            out["cpu_baseline"] = cpu_baseline(a, front, lmax0, args.cpu_sample)
+        print(json.dumps(out))
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -75,7 +75,7 @@ typedef struct {
     double tmin, tmax;    /* branch-length bounds */
     double newton_tol;    /* stop when a Newton step moves the length by <= newton_tol */
     int newton_maxit;     /* evaluations per branch per visit of that branch */
-    double sweep_tol;     /* stop sweeping when a sweep gains < sweep_tol nats */
+    double sweep_tol;     /* stop sweeping after a sweep that moved no length by more than sweep_tol */
     int full_max_sweeps;  /* cap on sweeps of the full optimisation */
     int prop_max_sweeps;  /* cap on sweeps of the proposal optimisation */
     int threads;          /* threads per CTA for the site loops (0 = automatic) */
@@ -84,7 +84,7 @@ typedef struct {
 
 /* Fills cfg with the defaults: device 0, mixed precision, 2^22 slots, five
  * branches, t in [1e-6, 100], newton_tol 1e-8, 50 evaluations, sweep_tol
- * 1e-9, 64 full / 8 proposal sweeps. */
+ * 1e-6, 64 full / 8 proposal sweeps. */
 void pt_config_default(pt_config *cfg);
 
 /* Creates a context on cfg->device (NULL cfg = defaults).  *out owns every
@@ -165,31 +165,34 @@ pt_status pt_expand_frontier_dev(pt_ctx *ctx, int aln_id, int n_frontier, const 
 /* Dumps the visited table of an alignment (every topology scored so far):
  * keys, status (PT_ST_*), lnL (full lnL for visited topologies, proposal
  * lnL for rejected ones).  Writes min(cap, count) entries in table order and
- * the total in *count. */
+ * the total in *count; with all three output pointers NULL it only reports
+ * the count. */
 pt_status pt_visited(pt_ctx *ctx, int aln_id, size_t cap, pt_key *keys, uint8_t *status, double *lnl,
                      size_t *count);
 
-/* Clears the visited table and round counter of an alignment. */
+/* Clears (allocating on first use) the visited table and round counter of
+ * an alignment. */
 pt_status pt_reset_visited(pt_ctx *ctx, int aln_id);
 
 /* Counters of the last round (or begin / score call): [0] candidates, [1]
  * already visited, [2] scored (unique proposals), [3] kept, [4] good,
  * [5] proposal Newton evaluations, [6] full-optimisation Newton
  * evaluations, [7] non-converged Newton solves, [8] proposal sweeps,
- * [9] full-optimisation sweeps. */
+ * [9] full-optimisation sweeps, [10] kernels launched by the call. */
 pt_status pt_stats(pt_ctx *ctx, int64_t *out, int cap);
 
 /* Per-neighbour detail of the last round, for parity tests: for each scored
  * proposal, its key, parent index in the frontier as given, canonical edge
  * node, swap, proposal lnL and the five optimised lengths (central, A, B, C,
- * D).  Returns the count in *count. */
+ * D).  Returns the count in *count (all outputs NULL = count query). */
 pt_status pt_last_proposals(pt_ctx *ctx, size_t cap, pt_key *keys, int32_t *parent, int32_t *edge_node,
                             int32_t *swap, double *lnl, double *len5, size_t *count);
 
-/* Device time of the last call's kernels by stage, in milliseconds:
- * [0] canonicalise+keys, [1] dedup, [2] frontier partials, [3] proposal
- * Newton, [4] full optimisation, [5] total.  Timed with CUDA events on the
- * context stream when cfg threads >= 0; zeros if timing is off. */
+/* Device time of the last call by stage, in milliseconds, from CUDA events
+ * recorded on the context stream around each stage: [0] canonicalise + keys,
+ * [1] dedup, [2] frontier partials, [3] proposal Newton kernel, [4] visit of
+ * the kept neighbours (canonicalise, full optimisation, decisions), [5]
+ * whole call, [6] full-optimisation kernel alone.  cap entries are written. */
 pt_status pt_stage_times(pt_ctx *ctx, double *ms, int cap);
 
 /* Library version string. */

@@ -75,6 +75,8 @@ def lib():
                                      C.POINTER(C.c_double)]
             L.or_search_new.restype = C.c_void_p
             L.or_search_new.argtypes = [C.c_void_p, C.c_int, _i32p, _f64p, C.c_double]
+            L.or_search_from_frontier.restype = C.c_void_p
+            L.or_search_from_frontier.argtypes = [C.c_void_p, C.c_int, _i32p, _f64p, C.c_double, C.c_double]
             L.or_search_round.argtypes = [C.c_void_p, C.c_void_p]
             L.or_search_run.argtypes = [C.c_void_p, C.c_void_p, C.c_int]
             L.or_search_lmax.restype = C.c_double
@@ -180,7 +182,7 @@ class Problem:
             lib().or_problem_free(p)
             self._p = None
 
-    def settings(self, tmin=1e-6, tmax=100.0, newton_tol=1e-8, newton_maxit=50, sweep_tol=1e-9,
+    def settings(self, tmin=1e-6, tmax=100.0, newton_tol=1e-8, newton_maxit=50, sweep_tol=1e-6,
                  full_max_sweeps=64, prop_max_sweeps=8, prop_mode=0):
         lib().or_problem_settings(self._p, tmin, tmax, newton_tol, newton_maxit, sweep_tol,
                                   full_max_sweeps, prop_max_sweeps, prop_mode)
@@ -246,12 +248,18 @@ class Problem:
 class Search:
     """Round-synchronous PT search on the oracle."""
 
-    def __init__(self, problem: Problem, starts_edges, starts_lengths, threshold: float):
+    def __init__(self, problem: Problem, starts_edges, starts_lengths, threshold: float, frontier_lmax=None):
+        """Round 0 on the starts; or, with frontier_lmax given, a search whose
+        next round() expands the given trees as the frontier with that lmax."""
         self.pb = problem
         se = np.ascontiguousarray(starts_edges, np.int32)
         sl = np.ascontiguousarray(starts_lengths, np.float64)
         self.n_start = se.shape[0]
-        self._s = lib().or_search_new(problem._p, self.n_start, se.reshape(-1), sl.reshape(-1), float(threshold))
+        if frontier_lmax is None:
+            self._s = lib().or_search_new(problem._p, self.n_start, se.reshape(-1), sl.reshape(-1), float(threshold))
+        else:
+            self._s = lib().or_search_from_frontier(problem._p, self.n_start, se.reshape(-1), sl.reshape(-1),
+                                                    float(frontier_lmax), float(threshold))
         if not self._s:
             raise ValueError("bad start trees")
 

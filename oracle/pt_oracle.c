@@ -226,7 +226,7 @@ or_problem *or_problem_new(int n, int P, int C, const uint8_t *tips, const doubl
     }
     pb->tmin = 1e-6; pb->tmax = 100.0;
     pb->newton_tol = 1e-8; pb->newton_maxit = 50;
-    pb->sweep_tol = 1e-9; pb->full_max_sweeps = 64; pb->prop_max_sweeps = 8;
+    pb->sweep_tol = 1e-6; pb->full_max_sweeps = 64; pb->prop_max_sweeps = 8;
     pb->prop_mode = 0;
     return pb;
 }
@@ -490,8 +490,8 @@ static double newton_branch(or_problem *pb, const double *X, const int *sx, cons
 }
 
 /* Newton on edge (u, v) of tree t, with the two subtree vectors recomputed
- * from scratch by pruning. */
-static void optimise_edge(or_problem *pb, or_tree *t, int u, int v)
+ * from scratch by pruning.  Returns |change of the length|. */
+static double optimise_edge(or_problem *pb, or_tree *t, int u, int v)
 {
     const int P = pb->P, S = 4 * pb->C;
     size_t nb = (size_t)(P ? P : 1);
@@ -499,9 +499,11 @@ static void optimise_edge(or_problem *pb, or_tree *t, int u, int v)
     int *sx = (int *)malloc(sizeof(int) * nb), *sy = (int *)malloc(sizeof(int) * nb);
     clv(pb, t, u, v, X, sx);
     clv(pb, t, v, u, Y, sy);
-    double tn = newton_branch(pb, X, sx, Y, sy, tree_len(t, u, v));
+    double t0 = tree_len(t, u, v);
+    double tn = newton_branch(pb, X, sx, Y, sy, t0);
     tree_set_len(t, u, v, tn);
     free(X); free(Y); free(sx); free(sy);
+    return fabs(tn - t0);
 }
 
 static double tree_lnl(const or_problem *pb, const or_tree *t)
@@ -515,9 +517,11 @@ static double tree_lnl(const or_problem *pb, const or_tree *t)
 /* ------------------------------------------------------------------------- */
 /* READING: the sweep visits edges in pre-order from leaf 0: first the edge at
  * leaf 0, then, below each inner node, its two child subtrees in increasing
- * order of their smallest taxon.  Sweeps stop when the exact lnL after a
- * sweep exceeds the lnL before it by less than sweep_tol, or after
- * full_max_sweeps sweeps. */
+ * order of their smallest taxon.  Sweeps stop after the first sweep in which
+ * no branch length moved by more than sweep_tol, or after full_max_sweeps
+ * sweeps; the result is the exact lnL at the final lengths.  (A rule on the
+ * lengths rather than on lnL gains: the lengths converge to within 1e-9 in
+ * FP32 partials too, while lnL gains below ~1e-5 nats do not resolve there.) */
 static int order_edges(const or_tree *t, int p, int q, int (*out)[2], int k)
 {
     out[k][0] = p; out[k][1] = q; ++k;
@@ -537,16 +541,17 @@ static double full_optimise(or_problem *pb, or_tree *t, int *sweeps_out)
 {
     int order[2 * OR_MAXN][2];
     int ne = order_edges(t, 0, t->adj[0][0], order, 0);
-    double f0 = tree_lnl(pb, t), f1 = f0;
     int s;
     for (s = 0; s < pb->full_max_sweeps; ++s) {
-        for (int e = 0; e < ne; ++e) optimise_edge(pb, t, order[e][0], order[e][1]);
-        f1 = tree_lnl(pb, t);
-        if (f1 - f0 < pb->sweep_tol) { ++s; break; }
-        f0 = f1;
+        double moved = 0.0;
+        for (int e = 0; e < ne; ++e) {
+            double d = optimise_edge(pb, t, order[e][0], order[e][1]);
+            if (d > moved) moved = d;
+        }
+        if (moved <= pb->sweep_tol) { ++s; break; }
     }
     if (sweeps_out) *sweeps_out = s;
-    return f1;
+    return tree_lnl(pb, t);
 }
 
 /* ------------------------------------------------------------------------- */
@@ -705,7 +710,8 @@ static void apply_nni(const or_tree *t, const or_quartet *q, int swap, or_tree *
 /* Proposal optimisation of a neighbour: sweeps over the five branches the
  * NNI touches in the order central, A, B, C, D (prop_mode 0), or the central
  * branch only (prop_mode 1, the paper's radius-0 default).  Stop rule as for
- * the full optimisation, capped at prop_max_sweeps. */
+ * the full optimisation (no length moved by more than sweep_tol), capped at
+ * prop_max_sweeps; the result is the exact lnL at the final lengths. */
 static double propose_optimise(or_problem *pb, or_tree *nt, const or_quartet *q, int swap)
 {
     int s = swap == 0 ? q->c : q->d, o = swap == 0 ? q->d : q->c;
@@ -719,14 +725,15 @@ static double propose_optimise(or_problem *pb, or_tree *nt, const or_quartet *q,
     br[4][0] = (q->d == s) ? q->u : q->v; br[4][1] = q->d;
     (void)o;
     int nb = pb->prop_mode == 1 ? 1 : 5;
-    double f0 = tree_lnl(pb, nt), f1 = f0;
     for (int sw = 0; sw < pb->prop_max_sweeps; ++sw) {
-        for (int i = 0; i < nb; ++i) optimise_edge(pb, nt, br[i][0], br[i][1]);
-        f1 = tree_lnl(pb, nt);
-        if (f1 - f0 < pb->sweep_tol) break;
-        f0 = f1;
+        double moved = 0.0;
+        for (int i = 0; i < nb; ++i) {
+            double d = optimise_edge(pb, nt, br[i][0], br[i][1]);
+            if (d > moved) moved = d;
+        }
+        if (moved <= pb->sweep_tol) break;
     }
-    return f1;
+    return tree_lnl(pb, nt);
 }
 
 /* ------------------------------------------------------------------------- */
@@ -977,6 +984,35 @@ or_search *or_search_new(or_problem *pb, int n_start, const int32_t *edges, cons
     }
     qsort(s->front, s->nfront, sizeof(or_tree), tree_cmp_key);
     free(ts); free(l); free(keep);
+    return s;
+}
+
+/* A search positioned just before a round on a given frontier: the trees are
+ * entered as visited GOOD topologies with their given lengths (not
+ * re-optimised) and lmax is taken as given.  The next or_search_round is then
+ * one PT round on that frontier. */
+or_search *or_search_from_frontier(or_problem *pb, int nf, const int32_t *edges, const double *lengths, double lmax,
+                                   double T)
+{
+    int n = pb->n, ne = 2 * n - 3;
+    or_search *s = (or_search *)calloc(1, sizeof *s);
+    s->T = T; s->lmax = lmax;
+    s->vis.n = n;
+    set_grow(&s->vis);
+    s->front = (or_tree *)malloc(sizeof(or_tree) * (size_t)(nf > 0 ? nf : 1));
+    for (int i = 0; i < nf; ++i) {
+        or_tree t;
+        if (tree_from_edges(n, edges + (size_t)i * 2 * ne, lengths + (size_t)i * ne, &t)) {
+            free(s->front); free(s->vis.e); free(s); return NULL;
+        }
+        uint64_t k[2];
+        tree_key(&t, k);
+        if (set_find(&s->vis, k)) continue;
+        or_entry *e = set_insert(&s->vis, k);
+        entry_fill(e, &t, OR_GOOD, NAN, NAN, 0);
+        s->front[s->nfront++] = t;
+    }
+    qsort(s->front, s->nfront, sizeof(or_tree), tree_cmp_key);
     return s;
 }
 

@@ -48,9 +48,13 @@ struct Ctx {
     int sm_count = 0;
     size_t smem_optin = 0;
     size_t budget = 0;
-    cudaEvent_t ev[8] = {};
+    // CUDA-event pairs bracketing the stages of the last call, on the context stream
+    std::vector<cudaEvent_t> evpool;
+    size_t evused = 0;
+    std::vector<std::pair<int, std::pair<size_t, size_t>>> spans;
     double stage_ms[8] = {0};
     bool timing = true;
+    long long launches0 = 0;
     // last round's proposals, for pt_last_proposals
     int last_items = 0;
 };
@@ -176,6 +180,9 @@ void check_flags(Ctx& c) {
 void begin_stats(Ctx& c) {
     ck(c, cudaMemsetAsync(c.d_stats, 0, sizeof(unsigned long long) * kStWords, c.stream), "memset stats");
     for (double& x : c.stage_ms) x = 0.0;
+    c.evused = 0;
+    c.spans.clear();
+    c.launches0 = launch_count();
 }
 
 void end_stats(Ctx& c, const int64_t* host_counts) {
@@ -183,6 +190,7 @@ void end_stats(Ctx& c, const int64_t* host_counts) {
     ck(c, cudaMemcpyAsync(h, c.d_stats, sizeof h, cudaMemcpyDeviceToHost, c.stream), "read stats");
     ck(c, cudaStreamSynchronize(c.stream), "stream sync");
     for (int i = 0; i < kStWords; ++i) c.stats[i] = (int64_t)h[i];
+    c.stats[kStLaunches] = launch_count() - c.launches0;
     if (host_counts)
         for (int i : {kStCand, kStScored, kStKept}) c.stats[i] = host_counts[i];
 }
@@ -199,9 +207,25 @@ int scan_count(Ctx& c, const int32_t* flag, int32_t* pos, int N) {
     return last[0] + last[1];
 }
 
-void mark(Ctx& c, int i) {
-    if (c.timing) cudaEventRecord(c.ev[i], c.stream);
+size_t ev_record(Ctx& c) {
+    if (c.evused == c.evpool.size()) {
+        cudaEvent_t e;
+        ck(c, cudaEventCreate(&e), "event");
+        c.evpool.push_back(e);
+    }
+    ck(c, cudaEventRecord(c.evpool[c.evused], c.stream), "event record");
+    return c.evused++;
 }
+// Stage spans: 0 canonicalise + keys, 1 dedup, 2 partials, 3 proposal Newton, 4 full optimisation, 5 total.
+struct Span {
+    Ctx& c;
+    int stage;
+    size_t start;
+    Span(Ctx& c_, int s) : c(c_), stage(s), start(c_.timing ? ev_record(c_) : 0) {}
+    void end() {
+        if (c.timing) c.spans.push_back({stage, {start, ev_record(c)}});
+    }
+};
 
 // ---------------------------------------------------------------- model set-up (host)
 // Regularised lower incomplete gamma P(a, x): series for x < a + 1, else
@@ -340,7 +364,17 @@ bool build_model(const double exch[6], const double freqs[4], double alpha, int 
     for (int i = 0; i < 4; ++i)  // symmetrise exactly
         for (int j = i + 1; j < 4; ++j) B[i * 4 + j] = B[j * 4 + i] = 0.5 * (B[i * 4 + j] + B[j * 4 + i]);
     M.C = C;
-    jacobi4(B, M.R, M.lam);
+    double V[16], lam[4];
+    jacobi4(B, V, lam);
+    // eigenvector 0 = the stationary one: lam_0 = 0 exactly, R[:,0] = sqrt(pi)
+    int k0 = 0;
+    for (int k = 1; k < 4; ++k) if (std::fabs(lam[k]) < std::fabs(lam[k0])) k0 = k;
+    int ord[4] = {k0, 0, 0, 0};
+    for (int k = 0, j = 1; k < 4; ++k) if (k != k0) ord[j++] = k;
+    for (int j = 0; j < 4; ++j) {
+        M.lam[j] = j == 0 ? 0.0 : lam[ord[j]];
+        for (int i = 0; i < 4; ++i) M.R[i * 4 + j] = j == 0 ? std::sqrt(pi[i]) : V[i * 4 + ord[j]];
+    }
     for (int i = 0; i < 4; ++i) {
         M.pi[i] = pi[i];
         M.sqpi[i] = std::sqrt(pi[i]);
@@ -395,9 +429,11 @@ void score_core(Ctx& c, AlnState& a, int count, const int32_t* edges_d, const do
             spc = (sumtable_bytes(prec, a.M.C, a.P) + 255) & ~size_t(255);
             scratch = buf<unsigned char>(c, "full.scratch", spc * grid);
         }
+        Span sp(c, 6);
         launch_fullopt(c.stream, prec, a.M, aln_dev(a), kcfg(c), ts, f0, cnt, g,
                        mode == PT_SCORE_FULL ? c.cfg.full_max_sweeps : 0, lnl_d + f0, c.d_stats, threads, grid,
                        scratch, spc);
+        sp.end();
         ck(c, cudaGetLastError(), "full optimisation launch");
     }
 }
@@ -410,8 +446,8 @@ struct RoundOut {
     int count = 0;
 };
 
-void begin_core(Ctx& c, AlnState& a, int ns, const int32_t* edges_d, const double* lens_d, double thr,
-                double* lmax_out, RoundOut& out) {
+// Allocates (first use) and clears the visited table of an alignment.
+void reset_table(Ctx& c, AlnState& a) {
     if (!a.table || a.log2 != c.cfg.table_log2) {
         if (a.table) cudaFree(a.table);
         a.table = nullptr;
@@ -420,6 +456,11 @@ void begin_core(Ctx& c, AlnState& a, int ns, const int32_t* edges_d, const doubl
     }
     launch_table_init(c.stream, a.table, (size_t)1 << a.log2);
     a.round = 0;
+}
+
+void begin_core(Ctx& c, AlnState& a, int ns, const int32_t* edges_d, const double* lens_d, double thr,
+                double* lmax_out, RoundOut& out) {
+    reset_table(c, a);
     double* lnl = buf<double>(c, "kp.lnl", ns);
     TreeSet ts;
     score_core(c, a, ns, edges_d, lens_d, PT_SCORE_FULL, "kp", ts, lnl);
@@ -448,11 +489,11 @@ void begin_core(Ctx& c, AlnState& a, int ns, const int32_t* edges_d, const doubl
 
 void expand_core(Ctx& c, AlnState& a, int F, const int32_t* edges_d, const double* lens_d, double thr,
                  double* lmax_inout, RoundOut& out) {
-    if (!a.table) fail(c, PT_ERR_STATE, "no visited table: call pt_begin first");
+    if (!a.table) reset_table(c, a);
     const int n = a.n, m = 2 * (n - 3), prec = c.cfg.precision;
     const int round = ++a.round;
     int64_t hc[kStWords] = {0};
-    mark(c, 0);
+    Span total(c, 5), sp0(c, 0);
     // 1. frontier: canonical form, keys; entered as visited if absent
     TreeSet fr = treeset(c, "fr", n, std::max(F, 1), false);
     launch_canon(c.stream, n, F, edges_d, lens_d, fr, c.d_err);
@@ -468,7 +509,8 @@ void expand_core(Ctx& c, AlnState& a, int F, const int32_t* edges_d, const doubl
     int32_t* flag = buf<int32_t>(c, "cand.flag", ncand);
     int32_t* pos = buf<int32_t>(c, "cand.pos", ncand);
     launch_enum(c.stream, n, F, fr, nkey, cinfo);
-    mark(c, 1);
+    sp0.end();
+    Span sp1(c, 1);
     launch_cand_insert(c.stream, a.table, a.log2, ncand, nkey, cinfo, fr, round, cslot, flag, c.d_err, c.d_stats);
     launch_cand_arb(c.stream, 2, a.table, ncand, cinfo, fr, round, cslot, flag);
     launch_cand_arb(c.stream, 3, a.table, ncand, cinfo, fr, round, cslot, flag);
@@ -487,7 +529,7 @@ void expand_core(Ctx& c, AlnState& a, int F, const int32_t* edges_d, const doubl
         ck(c, cudaStreamSynchronize(c.stream), "sync");
         for (int f = 0; f < F; ++f) tpos[f] = allpos[(size_t)f * m];
     }
-    mark(c, 2);
+    sp1.end();
     // 3. partials of frontier chunks + proposal optimisation of their items
     double* plnl = buf<double>(c, "items.lnl", W + 1);
     double* len5 = buf<double>(c, "items.len5", 5 * (size_t)W + 5);
@@ -502,7 +544,9 @@ void expand_core(Ctx& c, AlnState& a, int F, const int32_t* edges_d, const doubl
         if (i1 <= i0) continue;
         ClvGroup g = clv_group(c, "fr", a, cnt);
         void* pm = buf<unsigned char>(c, "fr.pm", pmat_bytes(prec, a.M.C, n, cnt));
+        Span sp2(c, 2);
         launch_partials(c.stream, prec, a.M, aln_dev(a), fr, f0, cnt, g, true, threads, pm);
+        sp2.end();
         ck(c, cudaGetLastError(), "partials launch");
         int grid = std::min(i1 - i0, 4 * c.sm_count);
         void* scratch = nullptr;
@@ -511,12 +555,14 @@ void expand_core(Ctx& c, AlnState& a, int F, const int32_t* edges_d, const doubl
             spc = (sumtable_bytes(prec, a.M.C, a.P) + 255) & ~size_t(255);
             scratch = buf<unsigned char>(c, "prop.scratch", spc * grid);
         }
+        Span sp3(c, 3);
         launch_propose(c.stream, prec, a.M, aln_dev(a), kcfg(c), fr, f0, g, items, i0, i1, a.table, round, c.d_lmax,
                        thr, plnl + i0, len5 + (size_t)5 * i0, kept + i0, c.d_stats, threads, grid, scratch, spc, pm);
+        sp3.end();
         ck(c, cudaGetLastError(), "propose launch");
     }
     (void)ms_part; (void)ms_prop;
-    mark(c, 3);
+    Span sp4(c, 4);
     c.last_items = W;
     // 4. kept neighbours: materialise, canonicalise, fully optimise
     int32_t* kpos = buf<int32_t>(c, "kept.pos", W + 1);
@@ -540,9 +586,10 @@ void expand_core(Ctx& c, AlnState& a, int F, const int32_t* edges_d, const doubl
     const int Gn = scan_count(c, good, gpos, K);
     int32_t* gidx = buf<int32_t>(c, "kp.idx", Gn + 1);
     launch_compact_idx(c.stream, K, good, gpos, gidx);
+    sp4.end();
+    total.end();
     ck(c, cudaMemcpyAsync(lmax_inout, c.d_lmax, 8, cudaMemcpyDeviceToHost, c.stream), "read lmax");
     check_flags(c);
-    mark(c, 5);
     out.ts = kp;
     out.idx = gidx;
     out.lnl = klnl;
@@ -551,15 +598,13 @@ void expand_core(Ctx& c, AlnState& a, int F, const int32_t* edges_d, const doubl
 }
 
 void collect_times(Ctx& c) {
-    if (!c.timing) return;
-    cudaEventSynchronize(c.ev[5]);
-    float ms;
-    auto el = [&](int a, int b) { return cudaEventElapsedTime(&ms, c.ev[a], c.ev[b]) == cudaSuccess ? (double)ms : 0.0; };
-    c.stage_ms[0] = el(0, 1);
-    c.stage_ms[1] = el(1, 2);
-    c.stage_ms[3] = el(2, 3);
-    c.stage_ms[4] = el(3, 5);
-    c.stage_ms[5] = el(0, 5);
+    if (!c.timing || c.spans.empty()) return;
+    cudaStreamSynchronize(c.stream);
+    for (auto& sp : c.spans) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, c.evpool[sp.second.first], c.evpool[sp.second.second]) == cudaSuccess)
+            c.stage_ms[sp.first] += ms;
+    }
     cudaGetLastError();
 }
 
@@ -629,7 +674,7 @@ void pt_config_default(pt_config* cfg) {
     cfg->tmax = 100.0;
     cfg->newton_tol = 1e-8;
     cfg->newton_maxit = 50;
-    cfg->sweep_tol = 1e-9;
+    cfg->sweep_tol = 1e-6;
     cfg->full_max_sweeps = 64;
     cfg->prop_max_sweeps = 8;
     cfg->threads = 0;
@@ -659,7 +704,6 @@ pt_status pt_create(pt_ctx** out, const pt_config* cfg) {
         ck(c, cudaMalloc(&c.d_stats, sizeof(unsigned long long) * kStWords), "alloc");
         ck(c, cudaMalloc(&c.d_lmax, 8), "alloc");
         ck(c, cudaMemset(c.d_err, 0, sizeof(int32_t) * kErrWords), "memset");
-        for (auto& e : c.ev) ck(c, cudaEventCreate(&e), "event");
         size_t fr, tot;
         ck(c, cudaMemGetInfo(&fr, &tot), "cudaMemGetInfo");
         c.budget = c.cfg.mem_budget ? c.cfg.mem_budget : std::min<size_t>(fr / 4, (size_t)24 << 30);
@@ -685,7 +729,7 @@ void pt_destroy(pt_ctx* ctx) {
     if (c.d_err) cudaFree(c.d_err);
     if (c.d_stats) cudaFree(c.d_stats);
     if (c.d_lmax) cudaFree(c.d_lmax);
-    for (auto& e : c.ev) if (e) cudaEventDestroy(e);
+    for (auto& e : c.evpool) cudaEventDestroy(e);
     delete ctx;
 }
 
@@ -777,7 +821,7 @@ pt_status pt_score_topologies(pt_ctx* ctx, int aln_id, int n_trees, const int32_
         const int E = 2 * a.n - 3;
         zero_flags(c);
         begin_stats(c);
-        mark(c, 0);
+        Span total(c, 5);
         int32_t* de = buf<int32_t>(c, "in.e", (size_t)n_trees * 2 * E);
         double* dl = buf<double>(c, "in.l", (size_t)n_trees * E);
         ck(c, cudaMemcpyAsync(de, edges, 4 * (size_t)n_trees * 2 * E, cudaMemcpyHostToDevice, c.stream), "copy in");
@@ -786,7 +830,7 @@ pt_status pt_score_topologies(pt_ctx* ctx, int aln_id, int n_trees, const int32_
         TreeSet ts;
         score_core(c, a, n_trees, de, dl, mode, "sc", ts, lnl);
         launch_lengths_to_input(c.stream, a.n, n_trees, ts, dl);
-        mark(c, 5);
+        total.end();
         ck(c, cudaMemcpyAsync(lengths, dl, 8 * (size_t)n_trees * E, cudaMemcpyDeviceToHost, c.stream), "copy out");
         ck(c, cudaMemcpyAsync(lnl_out, lnl, 8 * (size_t)n_trees, cudaMemcpyDeviceToHost, c.stream), "copy out");
         if (keys_out)
@@ -808,14 +852,14 @@ pt_status pt_begin(pt_ctx* ctx, int aln_id, int n_start, const int32_t* edges, c
         const int E = 2 * a.n - 3;
         zero_flags(c);
         begin_stats(c);
-        mark(c, 0);
+        Span total(c, 5);
         int32_t* de = buf<int32_t>(c, "in.e", (size_t)n_start * 2 * E);
         double* dl = buf<double>(c, "in.l", (size_t)n_start * E);
         ck(c, cudaMemcpyAsync(de, edges, 4 * (size_t)n_start * 2 * E, cudaMemcpyHostToDevice, c.stream), "copy in");
         ck(c, cudaMemcpyAsync(dl, lengths, 8 * (size_t)n_start * E, cudaMemcpyHostToDevice, c.stream), "copy in");
         RoundOut o;
         begin_core(c, a, n_start, de, dl, threshold, lmax_out, o);
-        mark(c, 5);
+        total.end();
         end_stats(c, nullptr);
         write_out(c, a, o, cap, front_edges, front_lengths, front_lnl, reinterpret_cast<uint64_t*>(front_keys), true,
                   n_front);
@@ -892,15 +936,15 @@ pt_status pt_visited(pt_ctx* ctx, int aln_id, size_t cap, pt_key* keys, uint8_t*
             if (lnl) ck(c, cudaMemcpyAsync(lnl, dl, 8 * k, cudaMemcpyDeviceToHost, c.stream), "copy");
         }
         ck(c, cudaStreamSynchronize(c.stream), "sync");
-        if (cap < (size_t)tot) fail(c, PT_ERR_BUFFER_TOO_SMALL, "visited set has %d entries", tot);
+        const bool query = !keys && !status && !lnl;
+        if (!query && cap < (size_t)tot) fail(c, PT_ERR_BUFFER_TOO_SMALL, "visited set has %d entries", tot);
     });
 }
 
 pt_status pt_reset_visited(pt_ctx* ctx, int aln_id) {
     return guarded(ctx, [&](Ctx& c) {
         AlnState& a = aln_of(c, aln_id, false);
-        if (a.table) launch_table_init(c.stream, a.table, (size_t)1 << a.log2);
-        a.round = 0;
+        reset_table(c, a);
         ck(c, cudaStreamSynchronize(c.stream), "sync");
     });
 }
@@ -919,7 +963,11 @@ pt_status pt_last_proposals(pt_ctx* ctx, size_t cap, pt_key* keys, int32_t* pare
         const int W = c.last_items;
         *count = (size_t)W;
         size_t k = std::min(cap, (size_t)W);
-        if (k == 0) return;
+        if (k == 0) {
+            if (cap == 0 && W > 0 && (keys || parent || edge_node || swap || lnl || len5))
+                fail(c, PT_ERR_BUFFER_TOO_SMALL, "%d proposals", W);
+            return;
+        }
         std::vector<Item> it(k);
         ck(c, cudaMemcpy(it.data(), buf<Item>(c, "items", W + 1), sizeof(Item) * k, cudaMemcpyDeviceToHost), "copy");
         for (size_t i = 0; i < k; ++i) {
@@ -930,14 +978,15 @@ pt_status pt_last_proposals(pt_ctx* ctx, size_t cap, pt_key* keys, int32_t* pare
         if (keys) ck(c, cudaMemcpy(keys, buf<uint64_t>(c, "items.key", 2 * (size_t)W + 2), 16 * k, cudaMemcpyDeviceToHost), "copy");
         if (lnl) ck(c, cudaMemcpy(lnl, buf<double>(c, "items.lnl", W + 1), 8 * k, cudaMemcpyDeviceToHost), "copy");
         if (len5) ck(c, cudaMemcpy(len5, buf<double>(c, "items.len5", 5 * (size_t)W + 5), 40 * k, cudaMemcpyDeviceToHost), "copy");
-        if (cap < (size_t)W) fail(c, PT_ERR_BUFFER_TOO_SMALL, "%d proposals", W);
+        const bool query = !keys && !parent && !edge_node && !swap && !lnl && !len5;
+        if (!query && cap < (size_t)W) fail(c, PT_ERR_BUFFER_TOO_SMALL, "%d proposals", W);
     });
 }
 
 pt_status pt_stage_times(pt_ctx* ctx, double* ms, int cap) {
     return guarded(ctx, [&](Ctx& c) {
         if (!ms) fail(c, PT_ERR_INVALID_ARG, "null");
-        for (int i = 0; i < cap && i < 6; ++i) ms[i] = c.stage_ms[i];
+        for (int i = 0; i < cap && i < 7; ++i) ms[i] = c.stage_ms[i];
     });
 }
 

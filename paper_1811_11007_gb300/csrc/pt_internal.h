@@ -64,7 +64,7 @@ enum { kErrTree = 0, kErrTable = 1, kErrKey = 2, kErrNumeric = 3, kErrWords = 8 
 // Device counters (int64 words), match pt_stats.
 enum {
     kStCand = 0, kStDup = 1, kStScored = 2, kStKept = 3, kStGood = 4, kStPropEvals = 5, kStFullEvals = 6,
-    kStNonconv = 7, kStPropSweeps = 8, kStFullSweeps = 9, kStWords = 16
+    kStNonconv = 7, kStPropSweeps = 8, kStFullSweeps = 9, kStLaunches = 10, kStWords = 16
 };
 
 // A group of trees sharing one partial-likelihood buffer: tree g's vectors
@@ -124,6 +124,9 @@ void launch_propose(cudaStream_t s, int prec, const Model& M, Aln A, Cfg cfg, Tr
 void launch_fullopt(cudaStream_t s, int prec, const Model& M, Aln A, Cfg cfg, TreeSet ts, int first, int count,
                     ClvGroup g, int max_sweeps, double* lnl_out, unsigned long long* stats, int threads, int grid,
                     void* scratch, size_t scratch_per_cta);
+
+// Kernels launched so far by this process (all contexts).
+long long launch_count();
 
 // Shared-memory sizing helpers for the host.
 size_t propose_smem_bytes(int prec, int C, int P, bool table_in_smem, int threads);

@@ -16,10 +16,15 @@
 
 #include <cuda_runtime.h>
 
+#include <atomic>
 #include <cmath>
 #include <cstdint>
 
 namespace pt {
+
+std::atomic<long long> g_launches{0};
+long long launch_count() { return g_launches.load(); }
+
 namespace {
 
 constexpr double kLn2 = 0.69314718055994530942;
@@ -712,14 +717,24 @@ __device__ __forceinline__ int normalise(R* y) {
     return e;
 }
 
-// Sum-table of one branch at one site: s_{r,k} = (M^T X_r)_k (M^T Y_r)_k with
-// M_ik = sqrt(pi_i) R_ik, so that L(t) = sum_{r,k} exp(lam_k r t)/C s_{r,k}.
+// Sum-table of one branch at one site.  With M_ik = sqrt(pi_i) R_ik and
+// x_k = (M^T X_r)_k, y_k = (M^T Y_r)_k, L_r(t) = sum_k exp(lam_k r t) x_k y_k.
+// Eigenvector 0 is the stationary one (lam_0 = 0), and sum_k x_k y_k =
+// sum_i pi_i X_i Y_i, so
+//   L_r(t) = sum_i pi_i X_i Y_i + sum_{k>=1} expm1(lam_k r t) x_k y_k,
+// a form without the cancellation of the plain spectral sum at short branches
+// (which costs FP32 its accuracy).  Stored: s_{r,0} = sum_i pi_i X_i Y_i,
+// s_{r,k} = x_k y_k for k >= 1.
 template <typename R, int C>
-__device__ __forceinline__ void sumtable(const R* Mt, const R* X, const R* Y, R* s) {
+__device__ __forceinline__ void sumtable(const R* Mt, const R* pi, const R* X, const R* Y, R* s) {
 #pragma unroll
-    for (int r = 0; r < C; ++r)
+    for (int r = 0; r < C; ++r) {
+        R s0 = pi[0] * X[r * 4] * Y[r * 4];
 #pragma unroll
-        for (int k = 0; k < 4; ++k) {
+        for (int i = 1; i < 4; ++i) s0 = fma(pi[i] * X[r * 4 + i], Y[r * 4 + i], s0);
+        s[r * 4] = s0;
+#pragma unroll
+        for (int k = 1; k < 4; ++k) {
             R x = Mt[k] * X[r * 4], y = Mt[k] * Y[r * 4];
 #pragma unroll
             for (int i = 1; i < 4; ++i) {
@@ -728,6 +743,7 @@ __device__ __forceinline__ void sumtable(const R* Mt, const R* X, const R* Y, R*
             }
             s[r * 4 + k] = x * y;
         }
+    }
 }
 
 // Sum-table storage: chunk q (4 values for FP32 / 2 for FP64) of site p at
@@ -780,28 +796,28 @@ __device__ __forceinline__ double warp_sum(double x) {
     return x;
 }
 
-// e/g/h at branch length t, written by the first 4C threads.
+// Coefficients at branch length t on the sum-table (see sumtable()):
+// egh[0] gives L (1 for the stationary slot, expm1(lam r t) otherwise),
+// egh[1] and egh[2] give dL/dt and d2L/dt2; all divided by C.  Written by
+// the first 4C threads; FP64 arithmetic rounded once to R.
 template <typename R, int C>
-__device__ __forceinline__ void put_egh(const Model& M, double t, NewtonSmem<R, C>& ns) {
+__device__ __forceinline__ void put_egh(const Model& M, double t, NewtonSmem<R, C>& ns, bool derivs) {
     int q = threadIdx.x;
     if (q < 4 * C) {
         int r = q >> 2, k = q & 3;
-        double lr = M.lam[k] * M.rates[r];
-        double e;
-        if constexpr (sizeof(R) == 4) e = (double)expf((float)(lr * t)) / C;
-        else e = exp(lr * t) / C;
-        ns.egh[0][q] = (R)e;
-        ns.egh[1][q] = (R)(lr * e);
-        ns.egh[2][q] = (R)(lr * lr * e);
-    }
-}
-// e at t in FP64 for the log-likelihood evaluation.
-template <typename R, int C>
-__device__ __forceinline__ void put_e_exact(const Model& M, double t, NewtonSmem<R, C>& ns) {
-    int q = threadIdx.x;
-    if (q < 4 * C) {
-        int r = q >> 2, k = q & 3;
-        ns.egh[0][q] = (R)(exp(M.lam[k] * M.rates[r] * t) / C);
+        if (k == 0) {
+            ns.egh[0][q] = (R)(1.0 / C);
+            ns.egh[1][q] = R(0);
+            ns.egh[2][q] = R(0);
+        } else {
+            double lr = M.lam[k] * M.rates[r];
+            ns.egh[0][q] = (R)(expm1(lr * t) / C);
+            if (derivs) {
+                double e = exp(lr * t) / C;
+                ns.egh[1][q] = (R)(lr * e);
+                ns.egh[2][q] = (R)(lr * lr * e);
+            }
+        }
     }
 }
 
@@ -817,10 +833,22 @@ __device__ __forceinline__ bool newton_step(double& t, double& lo, double& hi, d
     return conv;
 }
 
+// ln x for x > 0: FP32 input as 2^e * m (m in [1, 2)), ln m in FP32 and the
+// exponent part in FP64, so the rounding error is that of ln m (< 0.7) rather
+// than of ln x; FP64 input directly.
+__device__ __forceinline__ double log_split(float x) {
+    int b = __float_as_int(x);
+    int e = ((b >> 23) & 0xff) - 127;
+    if (e == -127) return (double)logf(x);
+    float m = __int_as_float((b & 0x007fffff) | 0x3f800000);
+    return (double)logf(m) + (double)e * kLn2;
+}
+__device__ __forceinline__ double log_split(double x) { return log(x); }
+
 // lnL of the current sum-table at length t: sum_p w_p (ln L_p + E_p ln 2), FP64 accumulation.
 template <typename R, int C>
 __device__ double eval_lnl(const Model& M, const STab<R, C>& st, int P, double t, NewtonSmem<R, C>& ns) {
-    put_e_exact<R, C>(M, t, ns);
+    put_egh<R, C>(M, t, ns, false);
     __syncthreads();
     R e[4 * C];
 #pragma unroll
@@ -832,7 +860,7 @@ __device__ double eval_lnl(const Model& M, const STab<R, C>& st, int P, double t
         R L = e[0] * s[0];
 #pragma unroll
         for (int q = 1; q < 4 * C; ++q) L = fma(e[q], s[q], L);
-        acc += (double)st.ew[st.pcap + p] * ((double)Prec<R>::lg(L) + (double)st.ew[p] * kLn2);
+        acc += (double)st.ew[st.pcap + p] * (log_split(L) + (double)st.ew[p] * kLn2);
     }
     acc = warp_sum(acc);
     const int w = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
@@ -852,7 +880,7 @@ __device__ double newton_solve(const Model& M, const Cfg& cfg, const STab<R, C>&
     double lo = cfg.tmin, hi = cfg.tmax;
     double t = fmin(fmax(t0, lo), hi);
     const int w = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
-    put_egh<R, C>(M, t, ns);
+    put_egh<R, C>(M, t, ns, true);
     __syncthreads();
     converged = false;
     evals = 0;
@@ -884,7 +912,7 @@ __device__ double newton_solve(const Model& M, const Cfg& cfg, const STab<R, C>&
         for (int i = 0; i < nw; ++i) { d1 += ns.red[i][0]; d2 += ns.red[i][1]; }
         ++evals;
         bool done = newton_step(t, lo, hi, d1, d2, cfg.newton_tol);
-        if (!done) put_egh<R, C>(M, t, ns);
+        if (!done) put_egh<R, C>(M, t, ns, true);
         __syncthreads();
         if (done) { converged = true; break; }
     }
@@ -978,6 +1006,7 @@ template <typename R, int C>
 struct ProposeSmem {
     R Pm[5][C * 16];
     R Mt[16];
+    R pi[4];
     double T[5];
     NewtonSmem<R, C> ns;
 };
@@ -1004,6 +1033,7 @@ __global__ void __launch_bounds__(512) k_propose(Model M, Aln A, Cfg cfg, TreeSe
     if (threadIdx.x < 16) {
         int i = threadIdx.x >> 2, k = threadIdx.x & 3;
         sm.Mt[threadIdx.x] = (R)(M.sqpi[i] * M.R[i * 4 + k]);
+        if (threadIdx.x < 4) sm.pi[threadIdx.x] = (R)M.pi[threadIdx.x];
     }
     const size_t sstride = (size_t)P * 4 * C;
     const int nb = cfg.propose_mode == 1 ? 1 : 5;
@@ -1047,10 +1077,11 @@ __global__ void __launch_bounds__(512) k_propose(Model M, Aln A, Cfg cfg, TreeSe
         }
         if (threadIdx.x < 5) sm.T[threadIdx.x] = len[bnode[threadIdx.x]];
         __syncthreads();
-        double f0 = 0.0, f1 = 0.0;
+        double f1 = 0.0;
         int sweeps = 0;
         for (int sw = 0; sw < cfg.prop_max_sweeps; ++sw) {
             ++sweeps;
+            double moved = 0.0;
             for (int b = 0; b < nb; ++b) {
                 // member optimised by branch b (b > 0)
                 int mb = -1;
@@ -1087,13 +1118,14 @@ __global__ void __launch_bounds__(512) k_propose(Model M, Aln A, Cfg cfg, TreeSe
                     }
                     int ex = normalise<R, C>(X), ey = normalise<R, C>(Y);
                     R s[4 * C];
-                    sumtable<R, C>(sm.Mt, X, Y, s);
+                    sumtable<R, C>(sm.Mt, sm.pi, X, Y, s);
                     st.put(p, s, (R)(ex + ey - Prec<R>::kScaleExp * (cx + cy)), (R)A.w[p]);
                 }
-                if (sw == 0 && b == 0) f0 = eval_lnl<R, C>(M, st, P, sm.T[0], sm.ns);
+                const double told = sm.T[b];
                 int ev;
                 bool conv;
-                double t = newton_solve<R, C>(M, cfg, st, P, sm.T[b], sm.ns, ev, conv);
+                double t = newton_solve<R, C>(M, cfg, st, P, told, sm.ns, ev, conv);
+                moved = fmax(moved, fabs(t - told));
                 evals_total += ev;
                 if (!conv) ++nonconv;
                 // new length and P matrices of branch b
@@ -1104,10 +1136,10 @@ __global__ void __launch_bounds__(512) k_propose(Model M, Aln A, Cfg cfg, TreeSe
                 if (threadIdx.x == 0) sm.T[b] = t;
                 __syncthreads();
             }
-            f1 = eval_lnl<R, C>(M, st, P, sm.T[nb - 1], sm.ns);
-            if (f1 - f0 < cfg.sweep_tol) break;
-            f0 = f1;
+            if (moved <= cfg.sweep_tol) break;
         }
+        // exact lnL at the final lengths: the last sum-table at its new length
+        f1 = eval_lnl<R, C>(M, st, P, sm.T[nb - 1], sm.ns);
         sweeps_total += sweeps;
         if (threadIdx.x == 0) {
             const int o = item - i0;
@@ -1135,6 +1167,7 @@ __global__ void __launch_bounds__(512) k_propose(Model M, Aln A, Cfg cfg, TreeSe
 template <typename R, int C>
 struct FullSmem {
     R Mt[16];
+    R pi[4];
     NewtonSmem<R, C> ns;
 };
 
@@ -1162,6 +1195,7 @@ __global__ void __launch_bounds__(512) k_fullopt(Model M, Aln A, Cfg cfg, TreeSe
     if (threadIdx.x < 16) {
         int i = threadIdx.x >> 2, k = threadIdx.x & 3;
         sm.Mt[threadIdx.x] = (R)(M.sqpi[i] * M.R[i * 4 + k]);
+        if (threadIdx.x < 4) sm.pi[threadIdx.x] = (R)M.pi[threadIdx.x];
     }
     const size_t sstride = (size_t)P * 4 * C;
     unsigned long long evals_total = 0, sweeps_total = 0, nonconv = 0;
@@ -1235,27 +1269,28 @@ __global__ void __launch_bounds__(512) k_fullopt(Model M, Aln A, Cfg cfg, TreeSe
                 load_raw<R, C>(srcD(v), p, Y, cy);
                 int ex = normalise<R, C>(X), ey = normalise<R, C>(Y);
                 R s[4 * C];
-                sumtable<R, C>(sm.Mt, X, Y, s);
+                sumtable<R, C>(sm.Mt, sm.pi, X, Y, s);
                 st.put(p, s, (R)(ex + ey - Prec<R>::kScaleExp * (cx + cy)), (R)A.w[p]);
             }
         };
         // bottom-up D pass
         for (int v = NN - 1; v >= n; --v) refreshD(v);
-        visit_build(n);
-        double f0 = eval_lnl<R, C>(M, st, P, len[n], sm.ns), f1 = f0;
-        int sweeps = 0;
+        int sweeps = 0, last = n;
         const int nsched = 3 * n - 5;
+        if (max_sweeps == 0) visit_build(n);
         for (int sw = 0; sw < max_sweeps; ++sw) {
             ++sweeps;
-            int last = n;
+            double moved = 0.0;
             for (int k = 0; k < nsched; ++k) {
                 const int op = sched[k];
                 if (op & kUpd) { refreshD(op & (kUpd - 1)); continue; }
                 const int v = op;
-                if (!(sw == 0 && k == 0)) visit_build(v);  // the first build is already in place
+                visit_build(v);
+                const double told = len[v];
                 int ev;
                 bool conv;
-                double t = newton_solve<R, C>(M, cfg, st, P, len[v], sm.ns, ev, conv);
+                double t = newton_solve<R, C>(M, cfg, st, P, told, sm.ns, ev, conv);
+                moved = fmax(moved, fabs(t - told));
                 evals_total += ev;
                 if (!conv) ++nonconv;
                 if (threadIdx.x < 4 * C) {
@@ -1266,10 +1301,10 @@ __global__ void __launch_bounds__(512) k_fullopt(Model M, Aln A, Cfg cfg, TreeSe
                 __syncthreads();
                 last = v;
             }
-            f1 = eval_lnl<R, C>(M, st, P, len[last], sm.ns);
-            if (f1 - f0 < cfg.sweep_tol) break;
-            f0 = f1;
+            if (moved <= cfg.sweep_tol) break;
         }
+        // exact lnL at the final lengths (the last visited edge's sum-table)
+        const double f1 = eval_lnl<R, C>(M, st, P, len[last], sm.ns);
         sweeps_total += sweeps;
         __syncthreads();
         for (int v = threadIdx.x; v < NN; v += blockDim.x) glen[v] = len[v];
@@ -1291,16 +1326,19 @@ void launch_canon(cudaStream_t s, int n, int count, const int32_t* edges, const 
                   int32_t* err) {
     if (count <= 0) return;
     k_canon<<<blocks_for(count, kCanonWarps), 32 * kCanonWarps, 0, s>>>(n, count, edges, lengths, ts, err);
+    ++g_launches;
 }
 
 void launch_table_init(cudaStream_t s, Slot* tab, size_t nslots) {
     k_table_init<<<1024, 256, 0, s>>>(tab, nslots);
+    ++g_launches;
 }
 
 void launch_enum(cudaStream_t s, int n, int F, TreeSet fr, uint64_t* nkey, int32_t* cinfo) {
     long long total = (long long)F * 2 * (n - 3);
     if (total <= 0) return;
     k_enum<<<(int)std::min<long long>(blocks_for(total, 256), 65535), 256, 0, s>>>(n, F, fr, nkey, cinfo);
+    ++g_launches;
 }
 
 void launch_cand_insert(cudaStream_t s, Slot* tab, int log2, int ncand, const uint64_t* nkey, const int32_t* cinfo,
@@ -1309,64 +1347,78 @@ void launch_cand_insert(cudaStream_t s, Slot* tab, int log2, int ncand, const ui
     if (ncand <= 0) return;
     k_cand_insert<<<blocks_for(ncand, 256), 256, 0, s>>>(tab, log2, ncand, nkey, cinfo, fr, round, cslot, flag, err,
                                                          stats);
+    ++g_launches;
 }
 
 void launch_cand_arb(cudaStream_t s, int phase, Slot* tab, int ncand, const int32_t* cinfo, TreeSet fr, int round,
                      const int32_t* cslot, int32_t* flag) {
     if (ncand <= 0) return;
     k_cand_arb<<<blocks_for(ncand, 256), 256, 0, s>>>(phase, tab, ncand, cinfo, fr, round, cslot, flag);
+    ++g_launches;
 }
 
 void launch_scan(cudaStream_t s, const int32_t* in, int32_t* out, int N, int32_t* tmp) {
     if (N <= 0) return;
     int nb = blocks_for(N, 1024);
     k_scan_block<<<nb, 1024, 0, s>>>(in, out, N, tmp);
+    ++g_launches;
     k_scan_sums<<<1, 1024, 0, s>>>(tmp, nb);
+    ++g_launches;
     k_scan_add<<<nb, 1024, 0, s>>>(out, N, tmp);
+    ++g_launches;
 }
 
 void launch_make_items(cudaStream_t s, int ncand, const int32_t* flag, const int32_t* pos, const int32_t* cinfo,
                        const int32_t* cslot, const uint64_t* nkey, Item* items, uint64_t* ikey) {
     if (ncand <= 0) return;
     k_make_items<<<blocks_for(ncand, 256), 256, 0, s>>>(ncand, flag, pos, cinfo, cslot, nkey, items, ikey);
+    ++g_launches;
 }
 
 void launch_compact_idx(cudaStream_t s, int N, const int32_t* flag, const int32_t* pos, int32_t* idx) {
     if (N <= 0) return;
     k_compact_idx<<<blocks_for(N, 256), 256, 0, s>>>(N, flag, pos, idx);
+    ++g_launches;
 }
 
 void launch_insert_trees(cudaStream_t s, Slot* tab, int log2, int count, TreeSet ts, const double* lnl,
                          const int32_t* status, int round, int32_t* winner, int32_t* err) {
     if (count <= 0) return;
     k_insert_trees<<<blocks_for(count, 256), 256, 0, s>>>(tab, log2, count, ts, lnl, status, round, winner, err);
+    ++g_launches;
     k_insert_trees_fin<<<blocks_for(count, 256), 256, 0, s>>>(tab, count, lnl, status, round, winner);
+    ++g_launches;
 }
 
 void launch_finalize_trees(cudaStream_t s, Slot* tab, int count, const int32_t* slot_of, const double* lnl,
                            const double* lmax, double thr, int round, int32_t* good, unsigned long long* stats) {
     if (count <= 0) return;
     k_finalize_trees<<<blocks_for(count, 256), 256, 0, s>>>(tab, count, slot_of, lnl, lmax, thr, round, good, stats);
+    ++g_launches;
 }
 
 void launch_lmax(cudaStream_t s, int count, const double* lnl, const int32_t* mask, double* lmax) {
     if (count <= 0) return;
     k_lmax<<<std::min(blocks_for(count, 256), 1024), 256, 0, s>>>(count, lnl, mask, lmax);
+    ++g_launches;
 }
 
 void launch_dump(cudaStream_t s, const Slot* tab, size_t nslots, int32_t* flag) {
     k_dump_flag<<<1024, 256, 0, s>>>(tab, nslots, flag);
+    ++g_launches;
 }
 
 void launch_dump_gather(cudaStream_t s, const Slot* tab, size_t nslots, const int32_t* flag, const int32_t* pos,
                         uint64_t* keys, uint8_t* status, double* lnl) {
     k_dump_gather<<<1024, 256, 0, s>>>(tab, nslots, flag, pos, keys, status, lnl);
+    ++g_launches;
 }
 
 void launch_materialize(cudaStream_t s, int n, int nk, const int32_t* kidx, const Item* items, TreeSet fr,
                         const double* len5, int32_t* edges_out, double* lengths_out, int32_t* slot_of) {
     if (nk <= 0) return;
     k_materialize<<<blocks_for(nk, 128), 128, 0, s>>>(n, nk, kidx, items, fr, len5, edges_out, lengths_out, slot_of);
+    ++g_launches;
 }
 
 void launch_gather_out(cudaStream_t s, int n, int count, const int32_t* idx, TreeSet ts, const double* lnl,
@@ -1374,11 +1426,13 @@ void launch_gather_out(cudaStream_t s, int n, int count, const int32_t* idx, Tre
     if (count <= 0) return;
     k_gather_out<<<blocks_for(count, 128), 128, 0, s>>>(n, count, idx, ts, lnl, edges_out, lengths_out, lnl_out,
                                                          keys_out);
+    ++g_launches;
 }
 
 void launch_lengths_to_input(cudaStream_t s, int n, int count, TreeSet ts, double* lengths_out) {
     if (count <= 0) return;
     k_lengths_to_input<<<blocks_for(count, 128), 128, 0, s>>>(n, count, ts, lengths_out);
+    ++g_launches;
 }
 
 size_t sumtable_bytes(int prec, int C, int P) {
@@ -1419,10 +1473,12 @@ void partials_t(cudaStream_t s, const Model& M, Aln A, TreeSet ts, int first, in
     const int NN = 2 * ts.n - 2;
     long long rows = (long long)count * NN * C * 4;
     k_pmats<R><<<(int)std::min<long long>(blocks_for(rows, 256), 8192), 256, 0, s>>>(M, ts, first, count, pm);
+    ++g_launches;
     size_t smem = (size_t)NN * C * 16 * sizeof(R);
     cudaFuncSetAttribute(k_partials<R, C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     dim3 grid(count, blocks_for(A.P, threads));
     k_partials<R, C><<<grid, threads, smem, s>>>(M, A, ts, first, g, pm, with_up ? 1 : 0);
+    ++g_launches;
 }
 }  // namespace
 
@@ -1457,11 +1513,13 @@ void propose_t(cudaStream_t s, const Model& M, Aln A, Cfg cfg, TreeSet fr, int f
         k_propose<R, C, false><<<grid, threads, smem, s>>>(M, A, cfg, fr, first, g, pm, items, i0, i1, tab, round,
                                                            lmax, thr, lnl_out, len5_out, kept, stats,
                                                            reinterpret_cast<unsigned char*>(scratch), spc);
+        ++g_launches;
     } else {
         size_t smem = propose_smem_bytes(sizeof(R) == 8 ? 0 : 1, C, A.P, true, threads);
         cudaFuncSetAttribute(k_propose<R, C, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         k_propose<R, C, true><<<grid, threads, smem, s>>>(M, A, cfg, fr, first, g, pm, items, i0, i1, tab, round,
                                                           lmax, thr, lnl_out, len5_out, kept, stats, nullptr, 0);
+        ++g_launches;
     }
 }
 }  // namespace
@@ -1492,11 +1550,13 @@ void fullopt_t(cudaStream_t s, const Model& M, Aln A, Cfg cfg, TreeSet ts, int f
         cudaFuncSetAttribute(k_fullopt<R, C, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         k_fullopt<R, C, false><<<grid, threads, smem, s>>>(M, A, cfg, ts, first, count, g, max_sweeps, lnl_out, stats,
                                                            reinterpret_cast<unsigned char*>(scratch), spc);
+        ++g_launches;
     } else {
         size_t smem = fullopt_smem_bytes(prec, C, ts.n, A.P, true, threads);
         cudaFuncSetAttribute(k_fullopt<R, C, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         k_fullopt<R, C, true><<<grid, threads, smem, s>>>(M, A, cfg, ts, first, count, g, max_sweeps, lnl_out, stats,
                                                           nullptr, 0);
+        ++g_launches;
     }
 }
 }  // namespace

@@ -264,13 +264,13 @@ class Context:
         out = (C.c_int64 * 16)()
         self._ck(lib().pt_stats(self._h, out, 16))
         names = ["candidates", "duplicates", "scored", "kept", "good", "prop_evals", "full_evals", "nonconverged",
-                 "prop_sweeps", "full_sweeps"]
+                 "prop_sweeps", "full_sweeps", "launches"]
         return {k: int(out[i]) for i, k in enumerate(names)}
 
     def stage_times(self) -> dict:
-        out = (C.c_double * 6)()
-        self._ck(lib().pt_stage_times(self._h, out, 6))
-        return dict(zip(["canon", "dedup", "partials", "propose", "fullopt", "total"], list(out)))
+        out = (C.c_double * 7)()
+        self._ck(lib().pt_stage_times(self._h, out, 7))
+        return dict(zip(["canon", "dedup", "partials", "propose", "visit", "total", "fullopt_kernel"], list(out)))
 
     def last_proposals(self):
         cnt = C.c_size_t()
