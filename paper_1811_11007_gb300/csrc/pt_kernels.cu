@@ -786,9 +786,12 @@ struct STab {
 // Block-wide context for the Newton machinery.
 template <typename R, int C>
 struct NewtonSmem {
-    R egh[3][4 * C];       // exp(lam r t)/C, times lam r, times (lam r)^2
-    double red[32][2];
-    double fin[2];
+    R egh[3][4 * C];       // coefficients on the sum-table for L, dL/dt, d2L/dt2
+    double red[32][2];     // per-warp partial sums
+    double ex[4 * C];      // exp(lam_k r t) for a P-matrix refresh
+    double W[64];          // W[(i*4+j)*4+k] = isqpi_i sqpi_j R_ik R_jk: P_ij = sum_k W_ijk exp(lam_k r t)
+    double tb;             // broadcast of the current length
+    int done;
 };
 
 __device__ __forceinline__ double warp_sum(double x) {
@@ -796,12 +799,38 @@ __device__ __forceinline__ double warp_sum(double x) {
     return x;
 }
 
-// Coefficients at branch length t on the sum-table (see sumtable()):
-// egh[0] gives L (1 for the stationary slot, expm1(lam r t) otherwise),
-// egh[1] and egh[2] give dL/dt and d2L/dt2; all divided by C.  Written by
-// the first 4C threads; FP64 arithmetic rounded once to R.
+// Warp sum of per-lane FP32 partials with a compensated (two-sum) tree, so
+// the cross-lane additions lose nothing beyond FP32 rounding of the running
+// error; FP64 partials are summed directly.
+__device__ __forceinline__ double warp_sum_comp(float x) {
+    float s = x, c = 0.f;
+    for (int o = 16; o; o >>= 1) {
+        float os = __shfl_xor_sync(0xffffffffu, s, o), oc = __shfl_xor_sync(0xffffffffu, c, o);
+        float t = __fadd_rn(s, os);
+        float bp = __fsub_rn(t, s);
+        float err = __fadd_rn(__fsub_rn(s, __fsub_rn(t, bp)), __fsub_rn(os, bp));
+        s = t;
+        c = __fadd_rn(__fadd_rn(c, oc), err);
+    }
+    return (double)s + (double)c;
+}
+__device__ __forceinline__ double warp_sum_comp(double x) { return warp_sum(x); }
+
 template <typename R, int C>
-__device__ __forceinline__ void put_egh(const Model& M, double t, NewtonSmem<R, C>& ns, bool derivs) {
+__device__ __forceinline__ void init_newton_smem(const Model& M, NewtonSmem<R, C>& ns) {
+    for (int x = threadIdx.x; x < 64; x += blockDim.x) {
+        int k = x & 3, ij = x >> 2, i = ij >> 2, j = ij & 3;
+        ns.W[x] = M.isqpi[i] * M.sqpi[j] * M.R[i * 4 + k] * M.R[j * 4 + k];
+    }
+}
+
+// Coefficients at branch length t on the sum-table (see sumtable()): egh[0]
+// gives L (1 for the stationary slot, expm1(lam r t) otherwise), egh[1] and
+// egh[2] give dL/dt and d2L/dt2; all divided by C.  Called by the first 4C
+// threads.  exact = FP64 exponentials rounded once (for lnL), otherwise the
+// working precision's own (for Newton derivatives).
+template <typename R, int C>
+__device__ __forceinline__ void put_egh(const Model& M, double t, NewtonSmem<R, C>& ns, bool exact) {
     int q = threadIdx.x;
     if (q < 4 * C) {
         int r = q >> 2, k = q & 3;
@@ -811,18 +840,41 @@ __device__ __forceinline__ void put_egh(const Model& M, double t, NewtonSmem<R, 
             ns.egh[2][q] = R(0);
         } else {
             double lr = M.lam[k] * M.rates[r];
-            ns.egh[0][q] = (R)(expm1(lr * t) / C);
-            if (derivs) {
+            if (exact || sizeof(R) == 8) {
+                ns.egh[0][q] = (R)(expm1(lr * t) / C);
                 double e = exp(lr * t) / C;
                 ns.egh[1][q] = (R)(lr * e);
                 ns.egh[2][q] = (R)(lr * lr * e);
+            } else {
+                float x = (float)(lr * t), l = (float)lr, e = expf(x) * (1.0f / C);
+                ns.egh[0][q] = (R)(expm1f(x) * (1.0f / C));
+                ns.egh[1][q] = (R)(l * e);
+                ns.egh[2][q] = (R)(l * l * e);
             }
         }
     }
 }
 
-// Safeguarded Newton step (identical in every thread): bracket [lo, hi];
-// Newton point when d2 < 0 and strictly inside, else sqrt(lo*hi).
+// P_r(t) for all categories into Pdst [C][16] (FP64 exponentials, rounded
+// once).  Two phases with a barrier between; the caller syncs after.
+template <typename R, int C>
+__device__ __forceinline__ void refresh_pmat(const Model& M, double t, R* Pdst, NewtonSmem<R, C>& ns) {
+    if (threadIdx.x < 4 * C) {
+        int r = threadIdx.x >> 2, k = threadIdx.x & 3;
+        ns.ex[threadIdx.x] = exp(M.lam[k] * M.rates[r] * t);
+    }
+    __syncthreads();
+    for (int x = threadIdx.x; x < 16 * C; x += blockDim.x) {
+        int r = x >> 4, ij = x & 15;
+        double acc = 0.0;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) acc += ns.W[ij * 4 + k] * ns.ex[r * 4 + k];
+        Pdst[x] = (R)acc;
+    }
+}
+
+// Safeguarded Newton step: bracket [lo, hi]; Newton point when d2 < 0 and
+// strictly inside, else sqrt(lo*hi).  Returns true when converged.
 __device__ __forceinline__ bool newton_step(double& t, double& lo, double& hi, double d1, double d2, double tol) {
     if (d1 == 0.0) return true;
     if (d1 > 0.0) lo = t; else hi = t;
@@ -848,7 +900,7 @@ __device__ __forceinline__ double log_split(double x) { return log(x); }
 // lnL of the current sum-table at length t: sum_p w_p (ln L_p + E_p ln 2), FP64 accumulation.
 template <typename R, int C>
 __device__ double eval_lnl(const Model& M, const STab<R, C>& st, int P, double t, NewtonSmem<R, C>& ns) {
-    put_egh<R, C>(M, t, ns, false);
+    put_egh<R, C>(M, t, ns, true);
     __syncthreads();
     R e[4 * C];
 #pragma unroll
@@ -872,15 +924,18 @@ __device__ double eval_lnl(const Model& M, const STab<R, C>& st, int P, double t
     return tot;
 }
 
-// Newton solve on the current sum-table from t0; returns the final t and the
-// number of evaluations.  Every thread returns the same values.
+// Newton solve on the current sum-table from t0.  Per evaluation: every
+// thread sums w L'/L and w (L''/L - (L'/L)^2) over its sites, the warps
+// reduce, and warp 0 alone takes the FP64 step and writes the coefficients
+// of the next length.  Returns the final length (in every thread).
 template <typename R, int C>
 __device__ double newton_solve(const Model& M, const Cfg& cfg, const STab<R, C>& st, int P, double t0,
                                NewtonSmem<R, C>& ns, int& evals, bool& converged) {
     double lo = cfg.tmin, hi = cfg.tmax;
     double t = fmin(fmax(t0, lo), hi);
-    const int w = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
-    put_egh<R, C>(M, t, ns, true);
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = (blockDim.x + 31) >> 5;
+    put_egh<R, C>(M, t, ns, false);
+    if (threadIdx.x == 0) ns.tb = t;
     __syncthreads();
     converged = false;
     evals = 0;
@@ -905,18 +960,21 @@ __device__ double newton_solve(const Model& M, const Cfg& cfg, const STab<R, C>&
             a1 = fma(wt, a, a1);
             a2 = fma(wt, b - a * a, a2);
         }
-        double d1 = warp_sum((double)a1), d2 = warp_sum((double)a2);
-        if ((threadIdx.x & 31) == 0) { ns.red[w][0] = d1; ns.red[w][1] = d2; }
+        double d1 = warp_sum_comp(a1), d2 = warp_sum_comp(a2);
+        if (lane == 0) { ns.red[w][0] = d1; ns.red[w][1] = d2; }
         __syncthreads();
-        d1 = 0.0; d2 = 0.0;
-        for (int i = 0; i < nw; ++i) { d1 += ns.red[i][0]; d2 += ns.red[i][1]; }
         ++evals;
-        bool done = newton_step(t, lo, hi, d1, d2, cfg.newton_tol);
-        if (!done) put_egh<R, C>(M, t, ns, true);
+        if (w == 0) {
+            double D1 = 0.0, D2 = 0.0;
+            for (int i = 0; i < nw; ++i) { D1 += ns.red[i][0]; D2 += ns.red[i][1]; }
+            bool done = newton_step(t, lo, hi, D1, D2, cfg.newton_tol);
+            if (!done) put_egh<R, C>(M, t, ns, false);
+            if (lane == 0) { ns.tb = t; ns.done = done; }
+        }
         __syncthreads();
-        if (done) { converged = true; break; }
+        if (ns.done) { converged = true; break; }
     }
-    return t;
+    return ns.tb;
 }
 
 // ---------------------------------------------------------------- P matrices of tree sets
@@ -1035,6 +1093,7 @@ __global__ void __launch_bounds__(512) k_propose(Model M, Aln A, Cfg cfg, TreeSe
         sm.Mt[threadIdx.x] = (R)(M.sqpi[i] * M.R[i * 4 + k]);
         if (threadIdx.x < 4) sm.pi[threadIdx.x] = (R)M.pi[threadIdx.x];
     }
+    init_newton_smem<R, C>(M, sm.ns);
     const size_t sstride = (size_t)P * 4 * C;
     const int nb = cfg.propose_mode == 1 ? 1 : 5;
     unsigned long long evals_total = 0, sweeps_total = 0, nonconv = 0;
@@ -1129,10 +1188,7 @@ __global__ void __launch_bounds__(512) k_propose(Model M, Aln A, Cfg cfg, TreeSe
                 evals_total += ev;
                 if (!conv) ++nonconv;
                 // new length and P matrices of branch b
-                if (threadIdx.x < 4 * C) {
-                    int r = threadIdx.x >> 2, i = threadIdx.x & 3;
-                    pmat_row<R>(M, t * M.rates[r], i, &sm.Pm[b][r * 16 + i * 4]);
-                }
+                refresh_pmat<R, C>(M, t, sm.Pm[b], sm.ns);
                 if (threadIdx.x == 0) sm.T[b] = t;
                 __syncthreads();
             }
@@ -1197,6 +1253,7 @@ __global__ void __launch_bounds__(512) k_fullopt(Model M, Aln A, Cfg cfg, TreeSe
         sm.Mt[threadIdx.x] = (R)(M.sqpi[i] * M.R[i * 4 + k]);
         if (threadIdx.x < 4) sm.pi[threadIdx.x] = (R)M.pi[threadIdx.x];
     }
+    init_newton_smem<R, C>(M, sm.ns);
     const size_t sstride = (size_t)P * 4 * C;
     unsigned long long evals_total = 0, sweeps_total = 0, nonconv = 0;
     for (int gi = blockIdx.x; gi < count; gi += gridDim.x) {
@@ -1293,10 +1350,7 @@ __global__ void __launch_bounds__(512) k_fullopt(Model M, Aln A, Cfg cfg, TreeSe
                 moved = fmax(moved, fabs(t - told));
                 evals_total += ev;
                 if (!conv) ++nonconv;
-                if (threadIdx.x < 4 * C) {
-                    int r = threadIdx.x >> 2, i = threadIdx.x & 3;
-                    pmat_row<R>(M, t * M.rates[r], i, Pm + ((size_t)v * C + r) * 16 + i * 4);
-                }
+                refresh_pmat<R, C>(M, t, Pm + (size_t)v * C * 16, sm.ns);
                 if (threadIdx.x == 0) len[v] = t;
                 __syncthreads();
                 last = v;
