@@ -195,6 +195,48 @@ pt_status pt_last_proposals(pt_ctx *ctx, size_t cap, pt_key *keys, int32_t *pare
  * whole call, [6] full-optimisation kernel alone.  cap entries are written. */
 pt_status pt_stage_times(pt_ctx *ctx, double *ms, int cap);
 
+/* Scores n_trees topologies like pt_score_topologies, but allocates no
+ * memory at all: no cudaMalloc, no context, no library allocator.  It is
+ * for callers that must not allocate device memory once they are running:
+ * a process whose device memory is fully reserved up front by another
+ * allocator (a serving process with a fixed pool), code that must not
+ * implicitly synchronise the device the way cudaMalloc/cudaFree can, or a
+ * caller that only holds device buffers handed to it.  The paper has no
+ * counterpart; it is an interface of this library only.
+ *
+ * Inputs and outputs are caller-owned device buffers: tips_dev
+ * [n_taxa][n_patterns] codes 0..4 (already pattern-compressed),
+ * weights_dev [n_patterns] int32 pattern counts, edges_dev
+ * [n_trees][2n-3][2], lengths_dev [n_trees][2n-3] starting lengths;
+ * lengths_out_dev [n_trees][2n-3] receives the lengths in the caller's edge
+ * order (optimised when mode = PT_SCORE_FULL, unchanged for
+ * PT_SCORE_FIXED), lnl_out_dev [n_trees] the log-likelihoods.  The model
+ * arguments are those of pt_set_model; cfg may be NULL (defaults).  Work is
+ * queued on `stream` (a cudaStream_t, NULL = legacy stream); the call waits
+ * once for the canonicaliser's validity flag and returns with the scoring
+ * still queued, so read the outputs after synchronising the stream.
+ *
+ * Working memory is one 32 MiB device array inside the library, held on
+ * every device that loads it until the process exits.  It must hold the
+ * canonical form of all n_trees trees (about 120 * n_taxa bytes each) plus
+ * the partial likelihoods of at least one tree, (2 n_taxa - 5) * n_patterns
+ * * (16 * n_cats + 4) bytes in mixed precision (twice the 16 in FP64), plus
+ * a sum-table when it does not fit in shared memory; e.g. 27 taxa x 2000
+ * patterns x 4 categories is 6.7 MB per tree.  Larger requests return
+ * PT_ERR_INVALID_ARG without touching the device.  All calls share the one
+ * array and it keeps the last call's contents: calls that overlap on the GPU
+ * (different streams or host threads at once) race and must be serialised
+ * by the caller.  The first call on a device looks up the array's device
+ * address (cudaGetSymbolAddress, once per device, with that device current);
+ * make that first call before any stream capture.  Returns PT_OK,
+ * PT_ERR_INVALID_ARG (bad argument, a tree that is not binary on
+ * 0..n_taxa-1, or beyond the size limit) or PT_ERR_CUDA. */
+pt_status pt_score_topologies_noalloc(int n_taxa, int n_patterns, const uint8_t *tips_dev,
+                                      const int32_t *weights_dev, const double exch[6], const double freqs[4],
+                                      double alpha, int n_cats, const pt_config *cfg, int n_trees,
+                                      const int32_t *edges_dev, const double *lengths_dev, double *lengths_out_dev,
+                                      double *lnl_out_dev, int mode, void *stream);
+
 /* Library version string. */
 const char *pt_version(void);
 

@@ -641,6 +641,14 @@ struct pt_ctx {
     Ctx c;
 };
 
+namespace pt {
+// Model set-up for entry points that work without a context.
+bool host_build_model(const double exch[6], const double freqs[4], double alpha, int C, Model& M) {
+    std::string why;
+    return build_model(exch, freqs, alpha, C, M, why);
+}
+}  // namespace pt
+
 namespace {
 template <typename F>
 pt_status guarded(pt_ctx* ctx, F&& f) {

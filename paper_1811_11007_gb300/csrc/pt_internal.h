@@ -125,6 +125,9 @@ void launch_fullopt(cudaStream_t s, int prec, const Model& M, Aln A, Cfg cfg, Tr
                     ClvGroup g, int max_sweeps, double* lnl_out, unsigned long long* stats, int threads, int grid,
                     void* scratch, size_t scratch_per_cta);
 
+// GTR+Gamma model set-up on the host (pt_api.cu); false on invalid parameters.
+bool host_build_model(const double exch[6], const double freqs[4], double alpha, int C, Model& M);
+
 // Kernels launched so far by this process (all contexts).
 long long launch_count();
 

@@ -23,7 +23,8 @@ STATUS = {0: "OK", 1: "INVALID_ARG", 2: "OOM", 3: "TABLE_FULL", 4: "BUFFER_TOO_S
 EXPORTS = ["pt_config_default", "pt_create", "pt_destroy", "pt_last_error", "pt_set_stream", "pt_load_alignment",
            "pt_alignment_info", "pt_set_model", "pt_model_rates", "pt_score_topologies", "pt_begin",
            "pt_expand_frontier", "pt_expand_frontier_dev", "pt_visited", "pt_reset_visited", "pt_stats",
-           "pt_last_proposals", "pt_stage_times", "pt_version", "pt_discrete_gamma", "pt_model_eigen"]
+           "pt_last_proposals", "pt_stage_times", "pt_version", "pt_discrete_gamma", "pt_model_eigen",
+           "pt_score_topologies_noalloc"]
 
 
 class PTError(RuntimeError):
@@ -87,6 +88,8 @@ def lib():
             L.pt_version.restype = C.c_char_p
             L.pt_discrete_gamma.argtypes = [C.c_double, C.c_int, _f64p]
             L.pt_model_eigen.argtypes = [_f64p, _f64p, _f64p, _f64p]
+            L.pt_score_topologies_noalloc.argtypes = [C.c_int, C.c_int, _vp, _vp, _f64p, _f64p, C.c_double, C.c_int,
+                                                      C.POINTER(Config), C.c_int, _vp, _vp, _vp, _vp, C.c_int, _vp]
             _lib = L
     return _lib
 
@@ -116,6 +119,17 @@ def model_eigen(exch, freqs):
     if st:
         raise PTError(st, "bad model")
     return lam, R.reshape(4, 4)
+
+
+def score_noalloc(n_taxa: int, n_patterns: int, tips_ptr: int, weights_ptr: int, exch, freqs, alpha: float,
+                  ncat: int, n_trees: int, edges_ptr: int, lengths_ptr: int, lengths_out_ptr: int, lnl_out_ptr: int,
+                  mode: str = "full", stream: int = 0, cfg: Config | None = None) -> int:
+    """pt_score_topologies_noalloc on raw device pointers; returns the status code."""
+    return lib().pt_score_topologies_noalloc(
+        n_taxa, n_patterns, _vp(tips_ptr), _vp(weights_ptr), np.ascontiguousarray(exch, np.float64),
+        np.ascontiguousarray(freqs, np.float64), float(alpha), int(ncat), C.byref(cfg) if cfg is not None else None,
+        n_trees, _vp(edges_ptr), _vp(lengths_ptr), _vp(lengths_out_ptr), _vp(lnl_out_ptr),
+        SCORE_FULL if mode == "full" else SCORE_FIXED, _vp(stream or 0))
 
 
 def keys_to_int(keys: np.ndarray) -> list[int]:
