@@ -802,17 +802,18 @@ __device__ __forceinline__ double warp_sum(double x) {
 // Warp sum of per-lane FP32 partials with a compensated (two-sum) tree, so
 // the cross-lane additions lose nothing beyond FP32 rounding of the running
 // error; FP64 partials are summed directly.
+// The result is complete in lane 0 only (the FP64 conversion is done there).
 __device__ __forceinline__ double warp_sum_comp(float x) {
     float s = x, c = 0.f;
     for (int o = 16; o; o >>= 1) {
-        float os = __shfl_xor_sync(0xffffffffu, s, o), oc = __shfl_xor_sync(0xffffffffu, c, o);
+        float os = __shfl_down_sync(0xffffffffu, s, o), oc = __shfl_down_sync(0xffffffffu, c, o);
         float t = __fadd_rn(s, os);
         float bp = __fsub_rn(t, s);
         float err = __fadd_rn(__fsub_rn(s, __fsub_rn(t, bp)), __fsub_rn(os, bp));
         s = t;
         c = __fadd_rn(__fadd_rn(c, oc), err);
     }
-    return (double)s + (double)c;
+    return (threadIdx.x & 31) == 0 ? (double)s + (double)c : 0.0;
 }
 __device__ __forceinline__ double warp_sum_comp(double x) { return warp_sum(x); }
 
@@ -906,13 +907,41 @@ __device__ double eval_lnl(const Model& M, const STab<R, C>& st, int P, double t
 #pragma unroll
     for (int q = 0; q < 4 * C; ++q) e[q] = ns.egh[0][q];
     double acc = 0.0;
-    for (int p = threadIdx.x; p < P; p += blockDim.x) {
-        R s[4 * C];
-        st.get(p, s);
-        R L = e[0] * s[0];
+    if constexpr (sizeof(R) == 4) {
+        // sum_p w_p ln L_p = sum_p w_p ln m_p + ln 2 * sum_p w_p (e_p + E_p), L_p = 2^e_p m_p:
+        // the exponent part is an exact integer sum, the mantissa logs a compensated FP32 sum
+        long long ie = 0;
+        float am = 0.f, ac = 0.f;
+        for (int p = threadIdx.x; p < P; p += blockDim.x) {
+            R s[4 * C];
+            st.get(p, s);
+            R L = e[0] * s[0];
 #pragma unroll
-        for (int q = 1; q < 4 * C; ++q) L = fma(e[q], s[q], L);
-        acc += (double)st.ew[st.pcap + p] * (log_split(L) + (double)st.ew[p] * kLn2);
+            for (int q = 1; q < 4 * C; ++q) L = fma(e[q], s[q], L);
+            int b = __float_as_int(L), ex = ((b >> 23) & 0xff) - 127;
+            float m = __int_as_float((b & 0x007fffff) | 0x3f800000);
+            if (ex == -127) {  // subnormal: rescale exactly by 2^23 first
+                const int b2 = __float_as_int(L * 8388608.0f);
+                ex = ((b2 >> 23) & 0xff) - 127 - 23;
+                m = __int_as_float((b2 & 0x007fffff) | 0x3f800000);
+            }
+            const int wi = (int)st.ew[st.pcap + p];
+            ie += (long long)wi * (ex + (int)st.ew[p]);
+            float y = __fsub_rn(__fmul_rn((float)wi, logf(m)), ac);
+            float t = __fadd_rn(am, y);
+            ac = __fsub_rn(__fsub_rn(t, am), y);
+            am = t;
+        }
+        acc = ((double)am - (double)ac) + (double)ie * kLn2;
+    } else {
+        for (int p = threadIdx.x; p < P; p += blockDim.x) {
+            R s[4 * C];
+            st.get(p, s);
+            R L = e[0] * s[0];
+#pragma unroll
+            for (int q = 1; q < 4 * C; ++q) L = fma(e[q], s[q], L);
+            acc += (double)st.ew[st.pcap + p] * (log_split(L) + (double)st.ew[p] * kLn2);
+        }
     }
     acc = warp_sum(acc);
     const int w = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
@@ -1066,6 +1095,9 @@ struct ProposeSmem {
     R Mt[16];
     R pi[4];
     double T[5];
+    Src<R, C> msrc[4];   // members in post-swap position order: A, X2 (at u), B, Y2 (at v)
+    int mbr[4];          // branch of each member
+    int bmem[5];         // member of each branch (-1: central)
     NewtonSmem<R, C> ns;
 };
 
@@ -1108,28 +1140,32 @@ __global__ void __launch_bounds__(512) k_propose(Model M, Aln A, Cfg cfg, TreeSe
         const int v = it.v, u = up[v];
         const int sib = ch[2 * u] == v ? ch[2 * u + 1] : ch[2 * u];
         const int c0 = ch[2 * v], c1 = ch[2 * v + 1];
-        // members in post-swap position order: m0 = A, m1 = X2 (at u), m2 = B, m3 = Y2 (at v)
-        const int node[4] = {u, it.swap == 0 ? c0 : c1, sib, it.swap == 0 ? c1 : c0};
-        const int brn[4] = {1, it.swap == 0 ? 3 : 4, 2, it.swap == 0 ? 4 : 3};  // branch of each member
-        Src<R, C> src[4];
-        for (int m = 0; m < 4; ++m) {
-            int x = node[m];
-            if (m == 0) {
-                if (u == n) { src[m].clv = nullptr; src[m].scl = nullptr; src[m].tip = A.tips; }
-                else {
-                    int slot = n - 2 + (u - n - 1);
-                    src[m].clv = clv + (size_t)slot * sstride; src[m].scl = scl + (size_t)slot * P; src[m].tip = nullptr;
-                }
-            } else if (x < n) {
-                src[m].clv = nullptr; src[m].scl = nullptr; src[m].tip = A.tips + (size_t)x * P;
-            } else {
-                src[m].clv = clv + (size_t)(x - n) * sstride; src[m].scl = scl + (size_t)(x - n) * P; src[m].tip = nullptr;
-            }
-        }
         // branch b's node in the parent (its P matrix is the parent's): central v, A u, B sib, C c0, D c1
         const int bnode[5] = {v, u, sib, c0, c1};
         const R* Psrc = Pm_all + (size_t)gi * NN * C * 16;
         __syncthreads();  // previous item done with smem
+        if (threadIdx.x == 0) {
+            const int node[4] = {u, it.swap == 0 ? c0 : c1, sib, it.swap == 0 ? c1 : c0};
+            const int brn[4] = {1, it.swap == 0 ? 3 : 4, 2, it.swap == 0 ? 4 : 3};
+            sm.bmem[0] = -1;
+            for (int m = 0; m < 4; ++m) {
+                Src<R, C> x;
+                if (m == 0) {
+                    if (u == n) { x.clv = nullptr; x.scl = nullptr; x.tip = A.tips; }
+                    else {
+                        int slot = n - 2 + (u - n - 1);
+                        x.clv = clv + (size_t)slot * sstride; x.scl = scl + (size_t)slot * P; x.tip = nullptr;
+                    }
+                } else if (node[m] < n) {
+                    x.clv = nullptr; x.scl = nullptr; x.tip = A.tips + (size_t)node[m] * P;
+                } else {
+                    x.clv = clv + (size_t)(node[m] - n) * sstride; x.scl = scl + (size_t)(node[m] - n) * P; x.tip = nullptr;
+                }
+                sm.msrc[m] = x;
+                sm.mbr[m] = brn[m];
+                sm.bmem[brn[m]] = m;
+            }
+        }
         for (int x = threadIdx.x; x < 5 * C * 16; x += blockDim.x) {
             int b = x / (C * 16), o = x % (C * 16);
             sm.Pm[b][o] = Psrc[(size_t)bnode[b] * C * 16 + o];
@@ -1142,43 +1178,44 @@ __global__ void __launch_bounds__(512) k_propose(Model M, Aln A, Cfg cfg, TreeSe
             ++sweeps;
             double moved = 0.0;
             for (int b = 0; b < nb; ++b) {
-                // member optimised by branch b (b > 0)
-                int mb = -1;
-                for (int m = 0; m < 4; ++m) if (brn[m] == b) mb = m;
+                // Central branch: X = P0 a0 * P1 a1 (at u), Y = P2 a2 * P3 a3 (at v).
+                // Branch of member mb: X = mb itself; Y = P2 partner * Pcentral (P0 o1 * P1 o2).
+                int i0m, i1m, i2m, i3m;
+                if (b == 0) { i0m = 0; i1m = 1; i2m = 2; i3m = 3; }
+                else {
+                    const int mb = sm.bmem[b];
+                    i3m = mb; i2m = mb ^ 1; i0m = mb < 2 ? 2 : 0; i1m = i0m + 1;
+                }
+                const Src<R, C> a0 = sm.msrc[i0m], a1 = sm.msrc[i1m], a2 = sm.msrc[i2m], a3 = sm.msrc[i3m];
+                const R* P0 = sm.Pm[sm.mbr[i0m]];
+                const R* P1 = sm.Pm[sm.mbr[i1m]];
+                const R* P2 = sm.Pm[sm.mbr[i2m]];
+                const R* P3 = sm.Pm[sm.mbr[i3m]];
                 for (int p = threadIdx.x; p < P; p += blockDim.x) {
-                    R X[4 * C], Y[4 * C];
-                    int cx = 0, cy = 0;
-                    if (b == 0) {
-                        R t0[4 * C], t1[4 * C];
-                        int k0, k1, k2, k3;
-                        apply_p<R, C>(sm.Pm[brn[0]], src[0], p, t0, k0);
-                        apply_p<R, C>(sm.Pm[brn[1]], src[1], p, t1, k1);
+                    R X[4 * C], Y[4 * C], t0[4 * C], t1[4 * C];
+                    int k0, k1, k2, k3;
+                    apply_p<R, C>(P0, a0, p, t0, k0);
+                    apply_p<R, C>(P1, a1, p, t1, k1);
 #pragma unroll
-                        for (int q = 0; q < 4 * C; ++q) X[q] = t0[q] * t1[q];
-                        apply_p<R, C>(sm.Pm[brn[2]], src[2], p, t0, k2);
-                        apply_p<R, C>(sm.Pm[brn[3]], src[3], p, t1, k3);
+                    for (int q = 0; q < 4 * C; ++q) t0[q] *= t1[q];
+                    if (b == 0) {
+#pragma unroll
+                        for (int q = 0; q < 4 * C; ++q) X[q] = t0[q];
+                        apply_p<R, C>(P2, a2, p, t0, k2);
+                        apply_p<R, C>(P3, a3, p, t1, k3);
 #pragma unroll
                         for (int q = 0; q < 4 * C; ++q) Y[q] = t0[q] * t1[q];
-                        cx = k0 + k1; cy = k2 + k3;
                     } else {
-                        const int partner = mb ^ 1, o1 = mb < 2 ? 2 : 0, o2 = o1 + 1;
-                        R t0[4 * C], t1[4 * C], far[4 * C];
-                        int k0, k1, k2;
-                        apply_p<R, C>(sm.Pm[brn[o1]], src[o1], p, t0, k0);
-                        apply_p<R, C>(sm.Pm[brn[o2]], src[o2], p, t1, k1);
+                        apply_p_reg<R, C>(sm.Pm[0], t0, X);  // X used as scratch for the far side
+                        apply_p<R, C>(P2, a2, p, t1, k2);
 #pragma unroll
-                        for (int q = 0; q < 4 * C; ++q) t0[q] *= t1[q];
-                        apply_p_reg<R, C>(sm.Pm[0], t0, far);
-                        apply_p<R, C>(sm.Pm[brn[partner]], src[partner], p, t1, k2);
-#pragma unroll
-                        for (int q = 0; q < 4 * C; ++q) Y[q] = t1[q] * far[q];
-                        load_raw<R, C>(src[mb], p, X, cx);
-                        cy = k0 + k1 + k2;
+                        for (int q = 0; q < 4 * C; ++q) Y[q] = t1[q] * X[q];
+                        load_raw<R, C>(a3, p, X, k3);
                     }
                     int ex = normalise<R, C>(X), ey = normalise<R, C>(Y);
-                    R s[4 * C];
-                    sumtable<R, C>(sm.Mt, sm.pi, X, Y, s);
-                    st.put(p, s, (R)(ex + ey - Prec<R>::kScaleExp * (cx + cy)), (R)A.w[p]);
+                    R s4[4 * C];
+                    sumtable<R, C>(sm.Mt, sm.pi, X, Y, s4);
+                    st.put(p, s4, (R)(ex + ey - Prec<R>::kScaleExp * (k0 + k1 + k2 + k3)), (R)A.w[p]);
                 }
                 const double told = sm.T[b];
                 int ev;
