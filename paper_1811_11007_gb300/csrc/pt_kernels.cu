@@ -788,6 +788,8 @@ template <typename R, int C>
 struct NewtonSmem {
     R egh[3][4 * C];       // coefficients on the sum-table for L, dL/dt, d2L/dt2
     double red[32][2];     // per-warp partial sums
+    float redf[32][4];     // per-warp partial sums as FP32 pairs (hi, lo) x (d1, d2)
+    double lr[4 * C];      // lam_k * rate_r
     double ex[4 * C];      // exp(lam_k r t) for a P-matrix refresh
     double W[64];          // W[(i*4+j)*4+k] = isqpi_i sqpi_j R_ik R_jk: P_ij = sum_k W_ijk exp(lam_k r t)
     double tb;             // broadcast of the current length
@@ -802,8 +804,9 @@ __device__ __forceinline__ double warp_sum(double x) {
 // Warp sum of per-lane FP32 partials with a compensated (two-sum) tree, so
 // the cross-lane additions lose nothing beyond FP32 rounding of the running
 // error; FP64 partials are summed directly.
-// The result is complete in lane 0 only (the FP64 conversion is done there).
-__device__ __forceinline__ double warp_sum_comp(float x) {
+// Compensated warp sum of FP32 partials: lane 0 ends with the sum as an
+// unevaluated pair s + c (no FP64 instruction in the calling warps).
+__device__ __forceinline__ float2 warp_sum_comp(float x) {
     float s = x, c = 0.f;
     for (int o = 16; o; o >>= 1) {
         float os = __shfl_down_sync(0xffffffffu, s, o), oc = __shfl_down_sync(0xffffffffu, c, o);
@@ -813,9 +816,8 @@ __device__ __forceinline__ double warp_sum_comp(float x) {
         s = t;
         c = __fadd_rn(__fadd_rn(c, oc), err);
     }
-    return (threadIdx.x & 31) == 0 ? (double)s + (double)c : 0.0;
+    return make_float2(s, c);
 }
-__device__ __forceinline__ double warp_sum_comp(double x) { return warp_sum(x); }
 
 template <typename R, int C>
 __device__ __forceinline__ void init_newton_smem(const Model& M, NewtonSmem<R, C>& ns) {
@@ -823,6 +825,7 @@ __device__ __forceinline__ void init_newton_smem(const Model& M, NewtonSmem<R, C
         int k = x & 3, ij = x >> 2, i = ij >> 2, j = ij & 3;
         ns.W[x] = M.isqpi[i] * M.sqpi[j] * M.R[i * 4 + k] * M.R[j * 4 + k];
     }
+    for (int q = threadIdx.x; q < 4 * C; q += blockDim.x) ns.lr[q] = M.lam[q & 3] * M.rates[q >> 2];
 }
 
 // Coefficients at branch length t on the sum-table (see sumtable()): egh[0]
@@ -840,7 +843,7 @@ __device__ __forceinline__ void put_egh(const Model& M, double t, NewtonSmem<R, 
             ns.egh[1][q] = R(0);
             ns.egh[2][q] = R(0);
         } else {
-            double lr = M.lam[k] * M.rates[r];
+            const double lr = ns.lr[q];
             if (exact || sizeof(R) == 8) {
                 ns.egh[0][q] = (R)(expm1(lr * t) / C);
                 double e = exp(lr * t) / C;
@@ -989,13 +992,29 @@ __device__ double newton_solve(const Model& M, const Cfg& cfg, const STab<R, C>&
             a1 = fma(wt, a, a1);
             a2 = fma(wt, b - a * a, a2);
         }
-        double d1 = warp_sum_comp(a1), d2 = warp_sum_comp(a2);
-        if (lane == 0) { ns.red[w][0] = d1; ns.red[w][1] = d2; }
+        if constexpr (sizeof(R) == 4) {
+            const float2 d1 = warp_sum_comp(a1), d2 = warp_sum_comp(a2);
+            if (lane == 0) { ns.redf[w][0] = d1.x; ns.redf[w][1] = d1.y; ns.redf[w][2] = d2.x; ns.redf[w][3] = d2.y; }
+        } else {
+            const double d1 = warp_sum(a1), d2 = warp_sum(a2);
+            if (lane == 0) { ns.red[w][0] = d1; ns.red[w][1] = d2; }
+        }
         __syncthreads();
         ++evals;
         if (w == 0) {
+            // lanes 0..nw-1 take one warp's pair each; an FP64 butterfly gives every lane the totals
             double D1 = 0.0, D2 = 0.0;
-            for (int i = 0; i < nw; ++i) { D1 += ns.red[i][0]; D2 += ns.red[i][1]; }
+            if (lane < nw) {
+                if constexpr (sizeof(R) == 4) {
+                    D1 = (double)ns.redf[lane][0] + (double)ns.redf[lane][1];
+                    D2 = (double)ns.redf[lane][2] + (double)ns.redf[lane][3];
+                } else {
+                    D1 = ns.red[lane][0];
+                    D2 = ns.red[lane][1];
+                }
+            }
+            D1 = warp_sum(D1);
+            D2 = warp_sum(D2);
             bool done = newton_step(t, lo, hi, D1, D2, cfg.newton_tol);
             if (!done) put_egh<R, C>(M, t, ns, false);
             if (lane == 0) { ns.tb = t; ns.done = done; }
