@@ -195,6 +195,52 @@ pt_status pt_last_proposals(pt_ctx *ctx, size_t cap, pt_key *keys, int32_t *pare
  * whole call, [6] full-optimisation kernel alone.  cap entries are written. */
 pt_status pt_stage_times(pt_ctx *ctx, double *ms, int cap);
 
+/* ---- Learned warm start of the proposal Newton iterations ----
+ * A small MLP predicts, for each NNI neighbour, how far its five branch
+ * lengths move under optimisation, from the logs of the five inherited lengths and a
+ * 16-value summary of each of the four subtree partial-likelihood vectors
+ * around the NNI edge (pattern-weighted mean of the site vectors divided by
+ * their sum).  69 inputs -> 128 -> 128 -> 5 outputs, GELU, BF16 weights and
+ * activations with FP32 accumulation on the tensor cores.  The prediction is
+ * only Newton's starting point: a non-finite or out-of-bounds prediction is
+ * replaced by the inherited length, and the Newton stop rules are unchanged,
+ * so results agree with the plain start to the Newton tolerance.  (The paper
+ * has no learned component; the proposal optimisation it warm-starts is loop
+ * step 6a of section "Phylogenetic Topographer".)
+ *
+ * Parameters are one flat FP32 array of PT_MLP_PARAMS values: W1 [80][128]
+ * (inputs zero-padded 69 -> 80), b1 [128], W2 [128][128], b2 [128], W3
+ * [128][8] (outputs zero-padded 5 -> 8), b3 [8]; layers compute y = x W + b.
+ * Input row layout [69]: log central, log A, log X2, log B, log Y2 (inherited
+ * lengths; the NNI moves X2 next to A and Y2 next to B), then the 16-value
+ * summaries of A, X2, B, Y2.  Output row [5]: log(optimised / inherited
+ * length) in the same order, so an all-zero network is the plain start. */
+#define PT_MLP_PARAMS 27912
+#define PT_MLP_IN 69
+#define PT_MLP_OUT 5
+
+/* Uploads the FP32 master weights (and resets the Adam state). */
+pt_status pt_mlp_set_weights(pt_ctx *ctx, const float *w, size_t n);
+pt_status pt_mlp_get_weights(pt_ctx *ctx, float *w, size_t n);
+/* Inference on host rows x [n_rows][69] -> y [n_rows][5]. */
+pt_status pt_mlp_forward(pt_ctx *ctx, int n_rows, const float *x, float *y);
+/* Mean squared error over the 5 outputs of n_rows rows against targets t
+ * [n_rows][5], and its gradient with respect to the flat parameters (same
+ * layout as the weights; padding entries are 0). */
+pt_status pt_mlp_loss_grad(pt_ctx *ctx, int n_rows, const float *x, const float *t, double *loss, float *grad);
+/* Trains on the logged pairs: `steps` Adam steps (beta 0.9/0.999) on batches
+ * of `batch` rows (a multiple of 64) drawn with replacement by a
+ * counter-based generator from `seed`; *final_loss = last batch's loss. */
+pt_status pt_mlp_train(pt_ctx *ctx, int steps, int batch, double lr, uint64_t seed, double *final_loss);
+/* Uses (1) or stops using (0) the network as the proposal warm start. */
+pt_status pt_mlp_enable(pt_ctx *ctx, int on);
+/* Logs (features, log(optimised / inherited) lengths) of every proposal of later rounds
+ * into a device buffer of `capacity` pairs (pairs beyond it are dropped);
+ * changing the capacity clears the log. */
+pt_status pt_training_log(pt_ctx *ctx, int on, size_t capacity);
+/* Copies up to cap logged pairs (x [cap][69], t [cap][5]); *count = pairs held. */
+pt_status pt_training_pairs(pt_ctx *ctx, size_t cap, float *x, float *t, size_t *count);
+
 /* Scores n_trees topologies like pt_score_topologies, but allocates no
  * memory at all: no cudaMalloc, no context, no library allocator.  It is
  * for callers that must not allocate device memory once they are running:

@@ -33,6 +33,7 @@ struct AlnState {
     Slot* table = nullptr;
     int log2 = 0;
     int round = 0;
+    float* tip_sum = nullptr;  // [n][16] leaf summaries for the warm-start features
 };
 
 struct Ctx {
@@ -57,6 +58,21 @@ struct Ctx {
     long long launches0 = 0;
     // last round's proposals, for pt_last_proposals
     int last_items = 0;
+    // learned warm start: FP32 master weights, gradients, Adam moments, BF16 copies
+    float* mlp_w = nullptr;
+    float* mlp_g = nullptr;
+    float* mlp_m1 = nullptr;
+    float* mlp_m2 = nullptr;
+    MlpDev mlp{};
+    bool mlp_ready = false;
+    bool mlp_on = false;
+    int adam_t = 0;
+    // (features, optimised log-lengths) pairs logged by rounds
+    bool log_on = false;
+    size_t log_cap = 0;
+    float* log_x = nullptr;
+    float* log_t = nullptr;
+    unsigned long long* log_count = nullptr;
 };
 
 struct Fail {
@@ -555,10 +571,35 @@ void expand_core(Ctx& c, AlnState& a, int F, const int32_t* edges_d, const doubl
             spc = (sumtable_bytes(prec, a.M.C, a.P) + 255) & ~size_t(255);
             scratch = buf<unsigned char>(c, "prop.scratch", spc * grid);
         }
+        // learned warm start and/or training log: features of the chunk's items
+        const double* init = nullptr;
+        float* xf = nullptr;
+        if ((c.mlp_on && c.mlp_ready) || c.log_on) {
+            const int nslot = 2 * n - 5, cnt_items = i1 - i0;
+            if (!a.tip_sum) {
+                ck(c, cudaMalloc(&a.tip_sum, sizeof(float) * 16 * a.n), "alloc tip summaries");
+                launch_tip_summary(c.stream, aln_dev(a), a.M.C, a.tip_sum);
+            }
+            float* ssum = buf<float>(c, "mlp.ssum", (size_t)cnt * nslot * 16);
+            launch_slot_summary(c.stream, prec, a.M.C, aln_dev(a), g, cnt, nslot, ssum);
+            xf = buf<float>(c, "mlp.xf", (size_t)cnt_items * kMlpIn);
+            void* xb = buf<unsigned char>(c, "mlp.xb", (size_t)(cnt_items + 64) * kMlpInPad * 2);
+            launch_item_features(c.stream, n, items, i0, i1, fr, f0, ssum, nslot, a.tip_sum, xf, xb);
+            if (c.mlp_on && c.mlp_ready) {
+                float* yb = buf<float>(c, "mlp.y", (size_t)(cnt_items + 64) * kMlpOutPad);
+                mlp_forward(c.stream, c.mlp, xb, cnt_items, yb, nullptr, nullptr, nullptr, nullptr, false);
+                double* ini = buf<double>(c, "mlp.init", (size_t)cnt_items * 5);
+                launch_item_init(c.stream, items, i0, i1, xf, yb, c.cfg.tmin, c.cfg.tmax, ini);
+                init = ini;
+            }
+        }
         Span sp3(c, 3);
         launch_propose(c.stream, prec, a.M, aln_dev(a), kcfg(c), fr, f0, g, items, i0, i1, a.table, round, c.d_lmax,
-                       thr, plnl + i0, len5 + (size_t)5 * i0, kept + i0, c.d_stats, threads, grid, scratch, spc, pm);
+                       thr, plnl + i0, len5 + (size_t)5 * i0, kept + i0, c.d_stats, threads, grid, scratch, spc, pm,
+                       init);
         sp3.end();
+        if (c.log_on && xf)
+            launch_log_pairs(c.stream, items, i0, i1, xf, len5, c.log_x, c.log_t, c.log_count, c.log_cap);
         ck(c, cudaGetLastError(), "propose launch");
     }
     (void)ms_part; (void)ms_prop;
@@ -733,7 +774,11 @@ void pt_destroy(pt_ctx* ctx) {
         if (a.tips) cudaFree(a.tips);
         if (a.w) cudaFree(a.w);
         if (a.table) cudaFree(a.table);
+        if (a.tip_sum) cudaFree(a.tip_sum);
     }
+    for (void* p : {(void*)c.mlp_w, (void*)c.mlp_g, (void*)c.mlp_m1, (void*)c.mlp_m2, c.mlp.w1t, c.mlp.w2t, c.mlp.w3t,
+                    c.mlp.w2r, c.mlp.w3r, (void*)c.log_x, (void*)c.log_t, (void*)c.log_count})
+        if (p) cudaFree(p);
     if (c.d_err) cudaFree(c.d_err);
     if (c.d_stats) cudaFree(c.d_stats);
     if (c.d_lmax) cudaFree(c.d_lmax);
@@ -806,6 +851,7 @@ pt_status pt_set_model(pt_ctx* ctx, int aln_id, const double exch[6], const doub
         if (!build_model(exch, freqs, alpha, n_cats, M, why)) fail(c, PT_ERR_INVALID_ARG, "%s", why.c_str());
         a.M = M;
         a.has_model = true;
+        if (a.tip_sum) { cudaFree(a.tip_sum); a.tip_sum = nullptr; }
     });
 }
 
@@ -995,6 +1041,178 @@ pt_status pt_stage_times(pt_ctx* ctx, double* ms, int cap) {
     return guarded(ctx, [&](Ctx& c) {
         if (!ms) fail(c, PT_ERR_INVALID_ARG, "null");
         for (int i = 0; i < cap && i < 7; ++i) ms[i] = c.stage_ms[i];
+    });
+}
+
+}  // extern "C"
+
+namespace {
+void mlp_alloc(Ctx& c) {
+    if (c.mlp_w) return;
+    ck(c, cudaMalloc(&c.mlp_w, sizeof(float) * kMlpParams), "alloc mlp");
+    ck(c, cudaMalloc(&c.mlp_g, sizeof(float) * kMlpParams), "alloc mlp");
+    ck(c, cudaMalloc(&c.mlp_m1, sizeof(float) * kMlpParams), "alloc mlp");
+    ck(c, cudaMalloc(&c.mlp_m2, sizeof(float) * kMlpParams), "alloc mlp");
+    ck(c, cudaMalloc(&c.mlp.w1t, 2 * kMlpHidden * kMlpInPad), "alloc mlp");
+    ck(c, cudaMalloc(&c.mlp.w2t, 2 * kMlpHidden * kMlpHidden), "alloc mlp");
+    ck(c, cudaMalloc(&c.mlp.w3t, 2 * kMlpOutPad * kMlpHidden), "alloc mlp");
+    ck(c, cudaMalloc(&c.mlp.w2r, 2 * kMlpHidden * kMlpHidden), "alloc mlp");
+    ck(c, cudaMalloc(&c.mlp.w3r, 2 * kMlpHidden * kMlpOutPad), "alloc mlp");
+    c.mlp.b1 = c.mlp_w + kOffB1;
+    c.mlp.b2 = c.mlp_w + kOffB2;
+    c.mlp.b3 = c.mlp_w + kOffB3;
+}
+
+// Forward + loss + backward on device rows Xb (BF16 [N][80]) and targets T
+// [N][5]; adds the gradients (batch means) to c.mlp_g and the loss to dloss.
+void mlp_step(Ctx& c, const void* Xb, const float* T, int N, double* dloss) {
+    const int Np = (N + 63) / 64 * 64;
+    float* Y = buf<float>(c, "mlpt.y", (size_t)Np * kMlpOutPad);
+    float* Z1 = buf<float>(c, "mlpt.z1", (size_t)Np * kMlpHidden);
+    float* Z2 = buf<float>(c, "mlpt.z2", (size_t)Np * kMlpHidden);
+    void* H1 = buf<unsigned char>(c, "mlpt.h1", (size_t)Np * kMlpHidden * 2);
+    void* H2 = buf<unsigned char>(c, "mlpt.h2", (size_t)Np * kMlpHidden * 2);
+    void* dY = buf<unsigned char>(c, "mlpt.dy", (size_t)Np * kMlpOutPad * 2);
+    mlp_forward(c.stream, c.mlp, Xb, N, Y, Z1, H1, Z2, H2, true);
+    mlp_loss(c.stream, Y, T, N, dY, dloss);
+    mlp_backward(c.stream, c.mlp, Xb, Z1, H1, Z2, H2, dY, N, c.mlp_g);
+}
+
+unsigned long long logged(Ctx& c) {
+    unsigned long long cnt = 0;
+    if (c.log_count) {
+        ck(c, cudaMemcpyAsync(&cnt, c.log_count, 8, cudaMemcpyDeviceToHost, c.stream), "copy count");
+        ck(c, cudaStreamSynchronize(c.stream), "sync");
+    }
+    return std::min<unsigned long long>(cnt, c.log_cap);
+}
+}  // namespace
+
+extern "C" {
+
+pt_status pt_mlp_set_weights(pt_ctx* ctx, const float* w, size_t n) {
+    return guarded(ctx, [&](Ctx& c) {
+        if (!w || n != (size_t)kMlpParams) fail(c, PT_ERR_INVALID_ARG, "expected %d parameters", kMlpParams);
+        for (size_t i = 0; i < n; ++i)
+            if (!std::isfinite(w[i])) fail(c, PT_ERR_INVALID_ARG, "non-finite parameter %zu", i);
+        mlp_alloc(c);
+        ck(c, cudaMemcpyAsync(c.mlp_w, w, sizeof(float) * n, cudaMemcpyHostToDevice, c.stream), "copy weights");
+        ck(c, cudaMemsetAsync(c.mlp_m1, 0, sizeof(float) * n, c.stream), "memset");
+        ck(c, cudaMemsetAsync(c.mlp_m2, 0, sizeof(float) * n, c.stream), "memset");
+        ck(c, cudaMemsetAsync(c.mlp_g, 0, sizeof(float) * n, c.stream), "memset");
+        mlp_cast(c.stream, c.mlp, c.mlp_w);
+        ck(c, cudaStreamSynchronize(c.stream), "sync");
+        c.adam_t = 0;
+        c.mlp_ready = true;
+    });
+}
+
+pt_status pt_mlp_get_weights(pt_ctx* ctx, float* w, size_t n) {
+    return guarded(ctx, [&](Ctx& c) {
+        if (!w || n != (size_t)kMlpParams || !c.mlp_ready) fail(c, PT_ERR_INVALID_ARG, "no weights / bad size");
+        ck(c, cudaMemcpyAsync(w, c.mlp_w, sizeof(float) * n, cudaMemcpyDeviceToHost, c.stream), "copy weights");
+        ck(c, cudaStreamSynchronize(c.stream), "sync");
+    });
+}
+
+pt_status pt_mlp_forward(pt_ctx* ctx, int n_rows, const float* x, float* y) {
+    return guarded(ctx, [&](Ctx& c) {
+        if (!c.mlp_ready) fail(c, PT_ERR_STATE, "no MLP weights (pt_mlp_set_weights)");
+        if (n_rows < 0 || (n_rows > 0 && (!x || !y))) fail(c, PT_ERR_INVALID_ARG, "bad arguments");
+        if (n_rows == 0) return;
+        const int Np = (n_rows + 63) / 64 * 64;
+        float* xf = buf<float>(c, "mlpf.xf", (size_t)n_rows * kMlpIn);
+        void* xb = buf<unsigned char>(c, "mlpf.xb", (size_t)Np * kMlpInPad * 2);
+        float* yd = buf<float>(c, "mlpf.y", (size_t)Np * kMlpOutPad);
+        ck(c, cudaMemcpyAsync(xf, x, sizeof(float) * n_rows * kMlpIn, cudaMemcpyHostToDevice, c.stream), "copy");
+        mlp_pack(c.stream, xf, n_rows, xb);
+        mlp_forward(c.stream, c.mlp, xb, n_rows, yd, nullptr, nullptr, nullptr, nullptr, false);
+        std::vector<float> h((size_t)n_rows * kMlpOutPad);
+        ck(c, cudaMemcpyAsync(h.data(), yd, sizeof(float) * h.size(), cudaMemcpyDeviceToHost, c.stream), "copy");
+        ck(c, cudaStreamSynchronize(c.stream), "sync");
+        for (int r = 0; r < n_rows; ++r)
+            for (int j = 0; j < kMlpOut; ++j) y[(size_t)r * kMlpOut + j] = h[(size_t)r * kMlpOutPad + j];
+    });
+}
+
+pt_status pt_mlp_loss_grad(pt_ctx* ctx, int n_rows, const float* x, const float* t, double* loss, float* grad) {
+    return guarded(ctx, [&](Ctx& c) {
+        if (!c.mlp_ready) fail(c, PT_ERR_STATE, "no MLP weights (pt_mlp_set_weights)");
+        if (n_rows < 1 || !x || !t || !loss || !grad) fail(c, PT_ERR_INVALID_ARG, "bad arguments");
+        const int Np = (n_rows + 63) / 64 * 64;
+        float* xf = buf<float>(c, "mlpf.xf", (size_t)n_rows * kMlpIn);
+        void* xb = buf<unsigned char>(c, "mlpf.xb", (size_t)Np * kMlpInPad * 2);
+        float* td = buf<float>(c, "mlpf.t", (size_t)n_rows * kMlpOut);
+        double* dl = buf<double>(c, "mlpf.loss", 1);
+        ck(c, cudaMemcpyAsync(xf, x, sizeof(float) * n_rows * kMlpIn, cudaMemcpyHostToDevice, c.stream), "copy");
+        ck(c, cudaMemcpyAsync(td, t, sizeof(float) * n_rows * kMlpOut, cudaMemcpyHostToDevice, c.stream), "copy");
+        ck(c, cudaMemsetAsync(dl, 0, 8, c.stream), "memset");
+        ck(c, cudaMemsetAsync(c.mlp_g, 0, sizeof(float) * kMlpParams, c.stream), "memset");
+        mlp_pack(c.stream, xf, n_rows, xb);
+        mlp_step(c, xb, td, n_rows, dl);
+        ck(c, cudaMemcpyAsync(grad, c.mlp_g, sizeof(float) * kMlpParams, cudaMemcpyDeviceToHost, c.stream), "copy");
+        ck(c, cudaMemcpyAsync(loss, dl, 8, cudaMemcpyDeviceToHost, c.stream), "copy");
+        ck(c, cudaMemsetAsync(c.mlp_g, 0, sizeof(float) * kMlpParams, c.stream), "memset");
+        ck(c, cudaStreamSynchronize(c.stream), "sync");
+    });
+}
+
+pt_status pt_mlp_train(pt_ctx* ctx, int steps, int batch, double lr, uint64_t seed, double* final_loss) {
+    return guarded(ctx, [&](Ctx& c) {
+        if (!c.mlp_ready) fail(c, PT_ERR_STATE, "no MLP weights (pt_mlp_set_weights)");
+        if (steps < 0 || batch < 64 || batch % 64 || !(lr > 0)) fail(c, PT_ERR_INVALID_ARG, "bad arguments");
+        const unsigned long long cnt = logged(c);
+        if (cnt == 0) fail(c, PT_ERR_STATE, "no logged training pairs (pt_training_log)");
+        void* xb = buf<unsigned char>(c, "mlpt.xb", (size_t)batch * kMlpInPad * 2);
+        float* tb = buf<float>(c, "mlpt.t", (size_t)batch * kMlpOut);
+        double* dl = buf<double>(c, "mlpt.loss", 1);
+        ck(c, cudaMemsetAsync(c.mlp_g, 0, sizeof(float) * kMlpParams, c.stream), "memset");
+        for (int st = 0; st < steps; ++st) {
+            ck(c, cudaMemsetAsync(dl, 0, 8, c.stream), "memset");
+            mlp_gather(c.stream, c.log_x, c.log_t, cnt, batch, seed, (unsigned long long)st, xb, tb);
+            mlp_step(c, xb, tb, batch, dl);
+            mlp_adam(c.stream, c.mlp_w, c.mlp_g, c.mlp_m1, c.mlp_m2, (float)lr, ++c.adam_t);
+            mlp_cast(c.stream, c.mlp, c.mlp_w);
+        }
+        if (final_loss) ck(c, cudaMemcpyAsync(final_loss, dl, 8, cudaMemcpyDeviceToHost, c.stream), "copy");
+        ck(c, cudaStreamSynchronize(c.stream), "sync");
+    });
+}
+
+pt_status pt_mlp_enable(pt_ctx* ctx, int on) {
+    return guarded(ctx, [&](Ctx& c) {
+        if (on && !c.mlp_ready) fail(c, PT_ERR_STATE, "no MLP weights (pt_mlp_set_weights)");
+        c.mlp_on = on != 0;
+    });
+}
+
+pt_status pt_training_log(pt_ctx* ctx, int on, size_t capacity) {
+    return guarded(ctx, [&](Ctx& c) {
+        if (on && capacity == 0) fail(c, PT_ERR_INVALID_ARG, "zero capacity");
+        if (on && capacity != c.log_cap) {
+            for (void* p : {(void*)c.log_x, (void*)c.log_t}) if (p) cudaFree(p);
+            c.log_x = nullptr;
+            c.log_t = nullptr;
+            c.log_cap = 0;
+            ck(c, cudaMalloc(&c.log_x, sizeof(float) * kMlpIn * capacity), "alloc log");
+            ck(c, cudaMalloc(&c.log_t, sizeof(float) * kMlpOut * capacity), "alloc log");
+            if (!c.log_count) ck(c, cudaMalloc(&c.log_count, 8), "alloc log");
+            ck(c, cudaMemsetAsync(c.log_count, 0, 8, c.stream), "memset");
+            c.log_cap = capacity;
+        }
+        c.log_on = on != 0;
+        ck(c, cudaStreamSynchronize(c.stream), "sync");
+    });
+}
+
+pt_status pt_training_pairs(pt_ctx* ctx, size_t cap, float* x, float* t, size_t* count) {
+    return guarded(ctx, [&](Ctx& c) {
+        if (!count) fail(c, PT_ERR_INVALID_ARG, "null count");
+        const unsigned long long cnt = logged(c);
+        *count = (size_t)cnt;
+        const size_t k = std::min(cap, (size_t)cnt);
+        if (k && x) ck(c, cudaMemcpy(x, c.log_x, sizeof(float) * kMlpIn * k, cudaMemcpyDeviceToHost), "copy");
+        if (k && t) ck(c, cudaMemcpy(t, c.log_t, sizeof(float) * kMlpOut * k, cudaMemcpyDeviceToHost), "copy");
     });
 }
 

@@ -82,6 +82,37 @@ struct Item {
     int32_t tree, v, swap, slot;
 };
 
+// ---- learned warm start (pt_mlp.cu) ----
+// MLP 69 -> 128 -> 128 -> 5 (GELU).  Flat FP32 parameter layout (the ABI's):
+// W1 [80][128] (inputs padded 69 -> 80), b1 [128], W2 [128][128], b2 [128],
+// W3 [128][8] (outputs padded 5 -> 8), b3 [8]; W[in][out], y = x W + b.
+constexpr int kMlpIn = 69, kMlpInPad = 80, kMlpHidden = 128, kMlpOut = 5, kMlpOutPad = 8;
+constexpr int kOffW1 = 0, kOffB1 = kOffW1 + kMlpInPad * kMlpHidden, kOffW2 = kOffB1 + kMlpHidden,
+              kOffB2 = kOffW2 + kMlpHidden * kMlpHidden, kOffW3 = kOffB2 + kMlpHidden,
+              kOffB3 = kOffW3 + kMlpHidden * kMlpOutPad, kMlpParams = kOffB3 + kMlpOutPad;
+struct MlpDev {
+    void* w1t;        // bf16 [128][80]   (n-major, forward)
+    void* w2t;        // bf16 [128][128]
+    void* w3t;        // bf16 [8][128]
+    void* w2r;        // bf16 [128][128]  ([in][out], backward)
+    void* w3r;        // bf16 [128][8]
+    const float* b1;  // FP32 master biases
+    const float* b2;
+    const float* b3;
+};
+size_t mlp_fwd_smem();
+size_t mlp_bwd_smem();
+void mlp_cast(cudaStream_t s, MlpDev m, const float* w);
+void mlp_forward(cudaStream_t s, MlpDev m, const void* Xb, int N, float* Y, float* Z1, void* H1, float* Z2, void* H2,
+                 bool train);
+void mlp_loss(cudaStream_t s, const float* Y, const float* T, int N, void* dY, double* loss);
+void mlp_backward(cudaStream_t s, MlpDev m, const void* Xb, const float* Z1, const void* H1, const float* Z2,
+                  const void* H2, const void* dY, int N, float* grad);
+void mlp_adam(cudaStream_t s, float* w, float* g, float* m1, float* m2, float lr, int t);
+void mlp_gather(cudaStream_t s, const float* LX, const float* LT, size_t count, int B, unsigned long long seed,
+                unsigned long long step, void* Xb, float* T);
+void mlp_pack(cudaStream_t s, const float* Xf, int N, void* Xb);
+
 // ---- launchers (pt_kernels.cu) ----
 void launch_canon(cudaStream_t s, int n, int count, const int32_t* edges, const double* lengths, TreeSet ts,
                   int32_t* err);
@@ -119,7 +150,7 @@ void launch_partials(cudaStream_t s, int prec, const Model& M, Aln A, TreeSet ts
 void launch_propose(cudaStream_t s, int prec, const Model& M, Aln A, Cfg cfg, TreeSet fr, int first, ClvGroup g,
                     const Item* items, int i0, int i1, Slot* tab, int round, const double* lmax, double thr,
                     double* lnl_out, double* len5_out, int32_t* kept, unsigned long long* stats, int threads,
-                    int grid, void* scratch, size_t scratch_per_cta, const void* pm);
+                    int grid, void* scratch, size_t scratch_per_cta, const void* pm, const double* init);
 // Full optimisation (max_sweeps >= 0) of trees [first, first+count) of ts.
 void launch_fullopt(cudaStream_t s, int prec, const Model& M, Aln A, Cfg cfg, TreeSet ts, int first, int count,
                     ClvGroup g, int max_sweeps, double* lnl_out, unsigned long long* stats, int threads, int grid,
@@ -130,6 +161,16 @@ bool host_build_model(const double exch[6], const double freqs[4], double alpha,
 
 // Kernels launched so far by this process (all contexts).
 long long launch_count();
+
+// Feature kernels of the warm start (pt_mlp.cu).
+void launch_slot_summary(cudaStream_t s, int prec, int C, Aln A, ClvGroup g, int ntrees, int nslot, float* out);
+void launch_tip_summary(cudaStream_t s, Aln A, int C, float* out);
+void launch_item_features(cudaStream_t s, int n, const Item* items, int i0, int i1, TreeSet fr, int first,
+                          const float* slot_sum, int nslot, const float* tip_sum, float* Xf, void* Xb);
+void launch_item_init(cudaStream_t s, const Item* items, int i0, int i1, const float* Xf, const float* Y, double tmin,
+                      double tmax, double* init);
+void launch_log_pairs(cudaStream_t s, const Item* items, int i0, int i1, const float* Xf, const double* len5, float* LX,
+                      float* LT, unsigned long long* count, size_t cap);
 
 // Shared-memory sizing helpers for the host.
 size_t propose_smem_bytes(int prec, int C, int P, bool table_in_smem, int threads);

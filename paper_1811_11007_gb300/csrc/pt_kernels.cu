@@ -1117,6 +1117,7 @@ struct ProposeSmem {
     Src<R, C> msrc[4];   // members in post-swap position order: A, X2 (at u), B, Y2 (at v)
     int mbr[4];          // branch of each member
     int bmem[5];         // member of each branch (-1: central)
+    double ex5[5][4 * C];
     NewtonSmem<R, C> ns;
 };
 
@@ -1126,7 +1127,7 @@ __global__ void __launch_bounds__(512) k_propose(Model M, Aln A, Cfg cfg, TreeSe
                                                  int i1, Slot* tab, int round, const double* lmax, double thr,
                                                  double* lnl_out, double* len5_out, int32_t* kept,
                                                  unsigned long long* stats, unsigned char* scratch,
-                                                 size_t scratch_per_cta) {
+                                                 size_t scratch_per_cta, const double* __restrict__ init) {
     extern __shared__ __align__(16) unsigned char smraw[];
     ProposeSmem<R, C>& sm = *reinterpret_cast<ProposeSmem<R, C>*>(smraw);
     const int n = fr.n, NN = 2 * n - 2, P = A.P;
@@ -1189,8 +1190,30 @@ __global__ void __launch_bounds__(512) k_propose(Model M, Aln A, Cfg cfg, TreeSe
             int b = x / (C * 16), o = x % (C * 16);
             sm.Pm[b][o] = Psrc[(size_t)bnode[b] * C * 16 + o];
         }
-        if (threadIdx.x < 5) sm.T[threadIdx.x] = len[bnode[threadIdx.x]];
+        if (threadIdx.x < 5) {
+            double t0 = len[bnode[threadIdx.x]];
+            if (init) {  // learned warm start; NaN = keep the inherited length
+                const double x = init[(size_t)(item - i0) * 5 + threadIdx.x];
+                if (x == x) t0 = x;
+            }
+            sm.T[threadIdx.x] = t0;
+        }
         __syncthreads();
+        if (init) {  // P matrices at the starting lengths
+            for (int x = threadIdx.x; x < 5 * 4 * C; x += blockDim.x) {
+                const int b = x / (4 * C), q = x % (4 * C);
+                sm.ex5[b][q] = exp(M.lam[q & 3] * M.rates[q >> 2] * sm.T[b]);
+            }
+            __syncthreads();
+            for (int x = threadIdx.x; x < 5 * 16 * C; x += blockDim.x) {
+                const int b = x / (16 * C), o = x % (16 * C), r = o >> 4, ij = o & 15;
+                double acc = 0.0;
+#pragma unroll
+                for (int k = 0; k < 4; ++k) acc += sm.ns.W[ij * 4 + k] * sm.ex5[b][r * 4 + k];
+                sm.Pm[b][o] = (R)acc;
+            }
+            __syncthreads();
+        }
         double f1 = 0.0;
         int sweeps = 0;
         for (int sw = 0; sw < cfg.prop_max_sweeps; ++sw) {
@@ -1615,20 +1638,21 @@ template <typename R, int C>
 void propose_t(cudaStream_t s, const Model& M, Aln A, Cfg cfg, TreeSet fr, int first, ClvGroup g, const Item* items,
                int i0, int i1, Slot* tab, int round, const double* lmax, double thr, double* lnl_out, double* len5_out,
                int32_t* kept, unsigned long long* stats, int threads, int grid, void* scratch, size_t spc,
-               const void* pmv) {
+               const void* pmv, const double* init) {
     const R* pm = reinterpret_cast<const R*>(pmv);
     if (scratch) {
         size_t smem = propose_smem_bytes(sizeof(R) == 8 ? 0 : 1, C, A.P, false, threads);
         cudaFuncSetAttribute(k_propose<R, C, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         k_propose<R, C, false><<<grid, threads, smem, s>>>(M, A, cfg, fr, first, g, pm, items, i0, i1, tab, round,
                                                            lmax, thr, lnl_out, len5_out, kept, stats,
-                                                           reinterpret_cast<unsigned char*>(scratch), spc);
+                                                           reinterpret_cast<unsigned char*>(scratch), spc, init);
         ++g_launches;
     } else {
         size_t smem = propose_smem_bytes(sizeof(R) == 8 ? 0 : 1, C, A.P, true, threads);
         cudaFuncSetAttribute(k_propose<R, C, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         k_propose<R, C, true><<<grid, threads, smem, s>>>(M, A, cfg, fr, first, g, pm, items, i0, i1, tab, round,
-                                                          lmax, thr, lnl_out, len5_out, kept, stats, nullptr, 0);
+                                                          lmax, thr, lnl_out, len5_out, kept, stats, nullptr, 0,
+                                                          init);
         ++g_launches;
     }
 }
@@ -1637,15 +1661,15 @@ void propose_t(cudaStream_t s, const Model& M, Aln A, Cfg cfg, TreeSet fr, int f
 void launch_propose(cudaStream_t s, int prec, const Model& M, Aln A, Cfg cfg, TreeSet fr, int first, ClvGroup g,
                     const Item* items, int i0, int i1, Slot* tab, int round, const double* lmax, double thr,
                     double* lnl_out, double* len5_out, int32_t* kept, unsigned long long* stats, int threads,
-                    int grid, void* scratch, size_t scratch_per_cta, const void* pm) {
+                    int grid, void* scratch, size_t scratch_per_cta, const void* pm, const double* init) {
     if (i1 <= i0) return;
     // pm holds the P matrices of the group's trees, as computed by launch_partials
     if (prec == 0) {
-        if (M.C == 1) propose_t<double, 1>(s, M, A, cfg, fr, first, g, items, i0, i1, tab, round, lmax, thr, lnl_out, len5_out, kept, stats, threads, grid, scratch, scratch_per_cta, pm);
-        else propose_t<double, 4>(s, M, A, cfg, fr, first, g, items, i0, i1, tab, round, lmax, thr, lnl_out, len5_out, kept, stats, threads, grid, scratch, scratch_per_cta, pm);
+        if (M.C == 1) propose_t<double, 1>(s, M, A, cfg, fr, first, g, items, i0, i1, tab, round, lmax, thr, lnl_out, len5_out, kept, stats, threads, grid, scratch, scratch_per_cta, pm, init);
+        else propose_t<double, 4>(s, M, A, cfg, fr, first, g, items, i0, i1, tab, round, lmax, thr, lnl_out, len5_out, kept, stats, threads, grid, scratch, scratch_per_cta, pm, init);
     } else {
-        if (M.C == 1) propose_t<float, 1>(s, M, A, cfg, fr, first, g, items, i0, i1, tab, round, lmax, thr, lnl_out, len5_out, kept, stats, threads, grid, scratch, scratch_per_cta, pm);
-        else propose_t<float, 4>(s, M, A, cfg, fr, first, g, items, i0, i1, tab, round, lmax, thr, lnl_out, len5_out, kept, stats, threads, grid, scratch, scratch_per_cta, pm);
+        if (M.C == 1) propose_t<float, 1>(s, M, A, cfg, fr, first, g, items, i0, i1, tab, round, lmax, thr, lnl_out, len5_out, kept, stats, threads, grid, scratch, scratch_per_cta, pm, init);
+        else propose_t<float, 4>(s, M, A, cfg, fr, first, g, items, i0, i1, tab, round, lmax, thr, lnl_out, len5_out, kept, stats, threads, grid, scratch, scratch_per_cta, pm, init);
     }
 }
 

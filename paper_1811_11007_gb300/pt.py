@@ -24,7 +24,10 @@ EXPORTS = ["pt_config_default", "pt_create", "pt_destroy", "pt_last_error", "pt_
            "pt_alignment_info", "pt_set_model", "pt_model_rates", "pt_score_topologies", "pt_begin",
            "pt_expand_frontier", "pt_expand_frontier_dev", "pt_visited", "pt_reset_visited", "pt_stats",
            "pt_last_proposals", "pt_stage_times", "pt_version", "pt_discrete_gamma", "pt_model_eigen",
-           "pt_score_topologies_noalloc"]
+           "pt_score_topologies_noalloc", "pt_mlp_set_weights", "pt_mlp_get_weights", "pt_mlp_forward",
+           "pt_mlp_loss_grad", "pt_mlp_train", "pt_mlp_enable", "pt_training_log", "pt_training_pairs"]
+MLP_PARAMS, MLP_IN, MLP_OUT = 27912, 69, 5
+_f32p = np.ctypeslib.ndpointer(np.float32, flags="C_CONTIGUOUS")
 
 
 class PTError(RuntimeError):
@@ -88,6 +91,14 @@ def lib():
             L.pt_version.restype = C.c_char_p
             L.pt_discrete_gamma.argtypes = [C.c_double, C.c_int, _f64p]
             L.pt_model_eigen.argtypes = [_f64p, _f64p, _f64p, _f64p]
+            L.pt_mlp_set_weights.argtypes = [_vp, _f32p, C.c_size_t]
+            L.pt_mlp_get_weights.argtypes = [_vp, _f32p, C.c_size_t]
+            L.pt_mlp_forward.argtypes = [_vp, C.c_int, _f32p, _f32p]
+            L.pt_mlp_loss_grad.argtypes = [_vp, C.c_int, _f32p, _f32p, C.POINTER(C.c_double), _f32p]
+            L.pt_mlp_train.argtypes = [_vp, C.c_int, C.c_int, C.c_double, C.c_uint64, C.POINTER(C.c_double)]
+            L.pt_mlp_enable.argtypes = [_vp, C.c_int]
+            L.pt_training_log.argtypes = [_vp, C.c_int, C.c_size_t]
+            L.pt_training_pairs.argtypes = [_vp, C.c_size_t, _vp, _vp, C.POINTER(C.c_size_t)]
             L.pt_score_topologies_noalloc.argtypes = [C.c_int, C.c_int, _vp, _vp, _f64p, _f64p, C.c_double, C.c_int,
                                                       C.POINTER(Config), C.c_int, _vp, _vp, _vp, _vp, C.c_int, _vp]
             _lib = L
@@ -285,6 +296,50 @@ class Context:
         out = (C.c_double * 7)()
         self._ck(lib().pt_stage_times(self._h, out, 7))
         return dict(zip(["canon", "dedup", "partials", "propose", "visit", "total", "fullopt_kernel"], list(out)))
+
+    # ---- learned warm start
+    def mlp_set_weights(self, w):
+        w = np.ascontiguousarray(w, np.float32)
+        self._ck(lib().pt_mlp_set_weights(self._h, w, w.size))
+
+    def mlp_get_weights(self):
+        w = np.zeros(MLP_PARAMS, np.float32)
+        self._ck(lib().pt_mlp_get_weights(self._h, w, w.size))
+        return w
+
+    def mlp_forward(self, x):
+        x = np.ascontiguousarray(x, np.float32).reshape(-1, MLP_IN)
+        y = np.zeros((x.shape[0], MLP_OUT), np.float32)
+        self._ck(lib().pt_mlp_forward(self._h, x.shape[0], x, y))
+        return y
+
+    def mlp_loss_grad(self, x, t):
+        x = np.ascontiguousarray(x, np.float32).reshape(-1, MLP_IN)
+        t = np.ascontiguousarray(t, np.float32).reshape(-1, MLP_OUT)
+        g = np.zeros(MLP_PARAMS, np.float32)
+        loss = C.c_double()
+        self._ck(lib().pt_mlp_loss_grad(self._h, x.shape[0], x, t, C.byref(loss), g))
+        return loss.value, g
+
+    def mlp_train(self, steps: int, batch: int = 1024, lr: float = 1e-3, seed: int = 1):
+        loss = C.c_double()
+        self._ck(lib().pt_mlp_train(self._h, steps, batch, lr, seed, C.byref(loss)))
+        return loss.value
+
+    def mlp_enable(self, on: bool = True):
+        self._ck(lib().pt_mlp_enable(self._h, 1 if on else 0))
+
+    def training_log(self, on: bool = True, capacity: int = 1 << 20):
+        self._ck(lib().pt_training_log(self._h, 1 if on else 0, capacity))
+
+    def training_pairs(self):
+        cnt = C.c_size_t()
+        self._ck(lib().pt_training_pairs(self._h, 0, None, None, C.byref(cnt)))
+        k = cnt.value
+        x = np.zeros((max(k, 1), MLP_IN), np.float32)
+        t = np.zeros((max(k, 1), MLP_OUT), np.float32)
+        self._ck(lib().pt_training_pairs(self._h, k, _ptr(x), _ptr(t), C.byref(cnt)))
+        return x[:k], t[:k]
 
     def last_proposals(self):
         cnt = C.c_size_t()
