@@ -162,6 +162,33 @@ pt_status pt_expand_frontier_dev(pt_ctx *ctx, int aln_id, int n_frontier, const 
                                  int32_t *kept_edges_dev, double *kept_lengths_dev, double *kept_lnl_dev,
                                  uint64_t *kept_keys_dev, int *n_kept);
 
+/* One alignment's part of a batched round (pt_expand_batch). */
+typedef struct {
+    int aln_id;
+    int n_frontier;
+    const int32_t *edges;     /* [n_frontier][2n-3][2] */
+    const double *lengths;    /* [n_frontier][2n-3] */
+    double threshold;
+    double lmax;              /* in: lmax at the start of the round; out: raised */
+    int cap;                  /* capacity of the outputs, in trees */
+    int32_t *kept_edges;      /* next frontier, as pt_expand_frontier */
+    double *kept_lengths;
+    double *kept_lnl;
+    pt_key *kept_keys;        /* [cap] (uint64_t pairs on the device variant) */
+    int n_kept;               /* out: size of the next frontier */
+} pt_round;
+
+/* One PT round on the frontiers of n distinct alignments at once: every NNI
+ * neighbour of every frontier is proposal-optimised in one persistent kernel
+ * launch (per memory wave), larger problems first with dynamic scheduling
+ * over uneven alignments, and every kept neighbour is visited in one
+ * full-optimisation launch (per wave).  Results per alignment are those of
+ * pt_expand_frontier on it.  All alignments must share n_cats.  Buffers in
+ * the pt_round entries are host memory; status is for the whole batch. */
+pt_status pt_expand_batch(pt_ctx *ctx, int n, pt_round *rounds);
+/* pt_expand_batch with device-resident frontiers and outputs. */
+pt_status pt_expand_batch_dev(pt_ctx *ctx, int n, pt_round *rounds);
+
 /* Dumps the visited table of an alignment (every topology scored so far):
  * keys, status (PT_ST_*), lnL (full lnL for visited topologies, proposal
  * lnL for rejected ones).  Writes min(cap, count) entries in table order and

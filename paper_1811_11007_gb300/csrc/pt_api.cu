@@ -424,6 +424,117 @@ void validate_trees(Ctx& c, int n, int count, const int32_t* edges, const double
 }
 
 // ---------------------------------------------------------------- drivers
+// Uploads a group table and the prefix sums of the groups' item counts.
+template <typename G>
+const G* upload_groups(Ctx& c, const std::string& name, const std::vector<G>& groups, const std::vector<int>& counts,
+                       const int** gstart_out, int** counter_out) {
+    G* dg = buf<G>(c, name + ".groups", groups.size());
+    int* ds = buf<int>(c, name + ".gstart", groups.size() + 1);
+    int* dc = buf<int>(c, name + ".counter", 1);
+    std::vector<int> pre(groups.size() + 1, 0);
+    for (size_t k = 0; k < groups.size(); ++k) pre[k + 1] = pre[k] + counts[k];
+    ck(c, cudaMemcpyAsync(dg, groups.data(), sizeof(G) * groups.size(), cudaMemcpyHostToDevice, c.stream), "groups");
+    ck(c, cudaMemcpyAsync(ds, pre.data(), sizeof(int) * pre.size(), cudaMemcpyHostToDevice, c.stream), "groups");
+    ck(c, cudaMemsetAsync(dc, 0, sizeof(int), c.stream), "counter");
+    *gstart_out = ds;
+    *counter_out = dc;
+    return dg;
+}
+
+// A full-optimisation job: trees [first, first + count) of ts (alignment a), lnL into lnl_d.
+struct FullJob {
+    AlnState* a;
+    TreeSet ts;
+    int first, count;
+    double* lnl_d;
+    int max_sweeps;
+};
+
+// Runs full-optimisation jobs in waves that fit the memory budget; each wave
+// is one persistent launch over all its groups.
+void run_full_jobs(Ctx& c, std::vector<FullJob> jobs) {
+    const int prec = c.cfg.precision;
+    // split jobs into chunks no larger than one tree group's budget
+    std::vector<FullJob> chunks;
+    for (auto& j : jobs) {
+        const int G = chunk_trees(c, *j.a);
+        for (int f0 = 0; f0 < j.count; f0 += G) {
+            FullJob x = j;
+            x.first = j.first + f0;
+            x.count = std::min(G, j.count - f0);
+            x.lnl_d = j.lnl_d + f0;
+            chunks.push_back(x);
+        }
+    }
+    // larger problems first (dynamic scheduling then balances the tail)
+    std::stable_sort(chunks.begin(), chunks.end(),
+                     [](const FullJob& x, const FullJob& y) { return (size_t)x.a->P * x.a->n > (size_t)y.a->P * y.a->n; });
+    auto group_bytes = [&](const FullJob& j) {
+        const size_t slots = (size_t)(2 * j.a->n - 5);
+        return ((slots * j.a->P * 4 * j.a->M.C * rsize(c) * j.count + 255) & ~size_t(255)) +
+               ((slots * j.a->P * 4 * j.count + 255) & ~size_t(255));
+    };
+    size_t k = 0;
+    while (k < chunks.size()) {
+        size_t used = 0, e = k;
+        while (e < chunks.size()) {
+            const size_t b = group_bytes(chunks[e]);
+            if (e > k && used + b > c.budget) break;
+            used += b;
+            ++e;
+        }
+        unsigned char* clv = buf<unsigned char>(c, "full.clv", used);
+        std::vector<FullGroup> groups;
+        std::vector<int> counts;
+        int maxN = 3, maxP = 1;
+        const int C = chunks[k].a->M.C;
+        size_t off = 0;
+        for (size_t i = k; i < e; ++i) {
+            const FullJob& j = chunks[i];
+            AlnState& a = *j.a;
+            if (a.M.C != C) fail(c, PT_ERR_INVALID_ARG, "alignments of one batch must share the number of categories");
+            FullGroup gp;
+            gp.M = a.M;
+            gp.A = aln_dev(a);
+            gp.ts = j.ts;
+            gp.first = j.first;
+            const size_t slots = (size_t)(2 * a.n - 5);
+            gp.g.tree_stride = slots * a.P * 4 * a.M.C;
+            gp.g.scl_stride = slots * a.P;
+            gp.g.clv = clv + off;
+            off += (gp.g.tree_stride * rsize(c) * j.count + 255) & ~size_t(255);
+            gp.g.scl = reinterpret_cast<int32_t*>(clv + off);
+            off += (gp.g.scl_stride * 4 * j.count + 255) & ~size_t(255);
+            gp.max_sweeps = j.max_sweeps;
+            gp.lnl_out = j.lnl_d;
+            groups.push_back(gp);
+            counts.push_back(j.count);
+            maxN = std::max(maxN, a.n);
+            maxP = std::max(maxP, a.P);
+        }
+        int total = 0;
+        for (int x : counts) total += x;
+        const int threads = threads_for(c, maxP);
+        const bool smem_tab = fullopt_smem_bytes(prec, C, maxN, maxP, true, threads) <= c.smem_optin;
+        const int grid = std::min(total, 2 * c.sm_count);
+        void* scratch = nullptr;
+        size_t spc = 0;
+        if (!smem_tab) {
+            spc = (sumtable_bytes(prec, C, maxP) + 255) & ~size_t(255);
+            scratch = buf<unsigned char>(c, "full.scratch", spc * grid);
+        }
+        const int* gstart;
+        int* counter;
+        const FullGroup* dg = upload_groups(c, "full", groups, counts, &gstart, &counter);
+        Span sp(c, 6);
+        launch_fullopt(c.stream, prec, C, dg, gstart, (int)groups.size(), counter, maxN, maxP, kcfg(c), c.d_stats,
+                       threads, grid, scratch, spc);
+        sp.end();
+        ck(c, cudaGetLastError(), "full optimisation launch");
+        k = e;
+    }
+}
+
 // Canonicalise + score `count` trees already on the device.  FULL mode runs
 // the full optimisation; lnl_d [count] receives lnL; ts holds the result.
 void score_core(Ctx& c, AlnState& a, int count, const int32_t* edges_d, const double* lens_d, int mode,
@@ -431,35 +542,16 @@ void score_core(Ctx& c, AlnState& a, int count, const int32_t* edges_d, const do
     ts = treeset(c, tsname, a.n, count, true);
     launch_canon(c.stream, a.n, count, edges_d, lens_d, ts, c.d_err);
     check_flags(c);
-    const int G = chunk_trees(c, a);
-    const int threads = threads_for(c, a.P);
-    const int prec = c.cfg.precision;
-    bool smem_tab = fullopt_smem_bytes(prec, a.M.C, a.n, a.P, true, threads) <= c.smem_optin;
-    for (int f0 = 0; f0 < count; f0 += G) {
-        int cnt = std::min(G, count - f0);
-        ClvGroup g = clv_group(c, "full", a, cnt);
-        int grid = std::min(cnt, 2 * c.sm_count);
-        void* scratch = nullptr;
-        size_t spc = 0;
-        if (!smem_tab) {
-            spc = (sumtable_bytes(prec, a.M.C, a.P) + 255) & ~size_t(255);
-            scratch = buf<unsigned char>(c, "full.scratch", spc * grid);
-        }
-        Span sp(c, 6);
-        launch_fullopt(c.stream, prec, a.M, aln_dev(a), kcfg(c), ts, f0, cnt, g,
-                       mode == PT_SCORE_FULL ? c.cfg.full_max_sweeps : 0, lnl_d + f0, c.d_stats, threads, grid,
-                       scratch, spc);
-        sp.end();
-        ck(c, cudaGetLastError(), "full optimisation launch");
-    }
+    run_full_jobs(c, {FullJob{&a, ts, 0, count, lnl_d, mode == PT_SCORE_FULL ? c.cfg.full_max_sweeps : 0}});
 }
 
-// The GOOD set of the last begin/expand: indices into the "kp" tree set.
+// The GOOD set of a begin/expand: indices into a tree set.
 struct RoundOut {
     TreeSet ts;
     int32_t* idx = nullptr;
     double* lnl = nullptr;
     int count = 0;
+    double lmax = 0.0;
 };
 
 // Allocates (first use) and clears the visited table of an alignment.
@@ -501,141 +593,299 @@ void begin_core(Ctx& c, AlnState& a, int ns, const int32_t* edges_d, const doubl
         ck(c, cudaMemcpyAsync(out.idx, idx.data(), 4 * idx.size(), cudaMemcpyHostToDevice, c.stream), "idx");
     out.lnl = lnl;
     out.count = (int)idx.size();
+    out.lmax = *lmax_out;
+}
+
+// One alignment's part of a batched round.
+struct RoundIn {
+    int aln;
+    int F;
+    const int32_t* edges_d;
+    const double* lens_d;
+    double thr;
+    double lmax;
+};
+
+// One PT round for several alignments at once: per-alignment keys and dedup,
+// then every NNI neighbour of every frontier in one persistent proposal
+// launch per memory wave, then every kept neighbour in one full-optimisation
+// launch per wave.  The single-alignment round is a batch of one.
+void expand_batch(Ctx& c, const std::vector<RoundIn>& ins, std::vector<RoundOut>& outs) {
+    const int na = (int)ins.size(), prec = c.cfg.precision;
+    struct AR {
+        AlnState* a;
+        int n, m, F, ncand, W, K, G, round, ibase;
+        TreeSet fr, kp;
+        uint64_t* nkey;
+        int32_t *cinfo, *cslot, *flag, *pos, *kpos, *kidx, *kslot, *good, *gpos, *gidx;
+        double *klnl, *lmax;
+        std::vector<int32_t> tpos;
+    };
+    std::vector<AR> ar(na);
+    int64_t hc[kStWords] = {0};
+    double* d_lmax = buf<double>(c, "batch.lmax", na);
+    int C = -1;
+    for (int k = 0; k < na; ++k) {
+        AlnState& a = aln_of(c, ins[k].aln);
+        if (C < 0) C = a.M.C;
+        if (a.M.C != C) fail(c, PT_ERR_INVALID_ARG, "alignments of one batch must share the number of categories");
+        for (int j = 0; j < k; ++j)
+            if (ins[j].aln == ins[k].aln) fail(c, PT_ERR_INVALID_ARG, "alignment %d appears twice in a batch", ins[k].aln);
+    }
+    Span total(c, 5), sp0(c, 0);
+    // ---- A. frontier canonical form and keys; entered as visited if absent
+    for (int k = 0; k < na; ++k) {
+        AR& r = ar[k];
+        r.a = &aln_of(c, ins[k].aln);
+        AlnState& a = *r.a;
+        if (!a.table) reset_table(c, a);
+        const std::string pre = "b" + std::to_string(k) + ".";
+        r.n = a.n;
+        r.m = 2 * (a.n - 3);
+        r.F = ins[k].F;
+        r.round = ++a.round;
+        r.lmax = d_lmax + k;
+        r.fr = treeset(c, pre + "fr", a.n, std::max(r.F, 1), false);
+        launch_canon(c.stream, a.n, r.F, ins[k].edges_d, ins[k].lens_d, r.fr, c.d_err);
+        int32_t* fwin = buf<int32_t>(c, pre + "fr.win", r.F);
+        launch_insert_trees(c.stream, a.table, a.log2, r.F, r.fr, nullptr, nullptr, r.round - 1, fwin, c.d_err);
+        ck(c, cudaMemcpyAsync(r.lmax, &ins[k].lmax, 8, cudaMemcpyHostToDevice, c.stream), "lmax");
+        r.ncand = r.F * r.m;
+        hc[kStCand] += r.ncand;
+        r.nkey = buf<uint64_t>(c, pre + "cand.key", (size_t)r.ncand * 2);
+        r.cinfo = buf<int32_t>(c, pre + "cand.info", (size_t)r.ncand * 4);
+        r.cslot = buf<int32_t>(c, pre + "cand.slot", r.ncand);
+        r.flag = buf<int32_t>(c, pre + "cand.flag", r.ncand);
+        r.pos = buf<int32_t>(c, pre + "cand.pos", r.ncand);
+        launch_enum(c.stream, a.n, r.F, r.fr, r.nkey, r.cinfo);
+    }
+    sp0.end();
+    // ---- dedup and arbitration
+    Span sp1(c, 1);
+    for (int k = 0; k < na; ++k) {
+        AR& r = ar[k];
+        AlnState& a = *r.a;
+        launch_cand_insert(c.stream, a.table, a.log2, r.ncand, r.nkey, r.cinfo, r.fr, r.round, r.cslot, r.flag, c.d_err,
+                           c.d_stats);
+        launch_cand_arb(c.stream, 2, a.table, r.ncand, r.cinfo, r.fr, r.round, r.cslot, r.flag);
+        launch_cand_arb(c.stream, 3, a.table, r.ncand, r.cinfo, r.fr, r.round, r.cslot, r.flag);
+        launch_cand_arb(c.stream, 4, a.table, r.ncand, r.cinfo, r.fr, r.round, r.cslot, r.flag);
+    }
+    check_flags(c);
+    int Wtot = 0;
+    for (int k = 0; k < na; ++k) {
+        AR& r = ar[k];
+        r.W = scan_count(c, r.flag, r.pos, r.ncand);
+        r.ibase = Wtot;
+        Wtot += r.W;
+    }
+    hc[kStScored] = Wtot;
+    Item* items = buf<Item>(c, "items", Wtot + 1);
+    uint64_t* ikey = buf<uint64_t>(c, "items.key", 2 * (size_t)Wtot + 2);
+    for (int k = 0; k < na; ++k) {
+        AR& r = ar[k];
+        launch_make_items(c.stream, r.ncand, r.flag, r.pos, r.cinfo, r.cslot, r.nkey, items + r.ibase,
+                          ikey + 2 * (size_t)r.ibase);
+        // first item of each frontier tree (a tree's items are contiguous)
+        r.tpos.assign(r.F + 1, r.W);
+        if (r.ncand > 0) {
+            std::vector<int32_t> allpos(r.ncand);
+            ck(c, cudaMemcpyAsync(allpos.data(), r.pos, 4 * (size_t)r.ncand, cudaMemcpyDeviceToHost, c.stream), "pos");
+            ck(c, cudaStreamSynchronize(c.stream), "sync");
+            for (int f = 0; f < r.F; ++f) r.tpos[f] = allpos[(size_t)f * r.m];
+        }
+    }
+    sp1.end();
+    // ---- B. partials + (learned start) + one proposal launch per memory wave
+    double* plnl = buf<double>(c, "items.lnl", Wtot + 1);
+    double* len5 = buf<double>(c, "items.len5", 5 * (size_t)Wtot + 5);
+    int32_t* kept = buf<int32_t>(c, "items.kept", Wtot + 1);
+    const bool use_mlp = c.mlp_on && c.mlp_ready;
+    const bool feats = use_mlp || c.log_on;
+    float* xf_all = feats ? buf<float>(c, "mlp.xf", (size_t)(Wtot + 1) * kMlpIn) : nullptr;
+    double* init_all = use_mlp ? buf<double>(c, "mlp.init", (size_t)(Wtot + 1) * 5) : nullptr;
+    struct Chunk {
+        int k, f0, cnt, i0, i1;
+    };
+    std::vector<Chunk> chunks;
+    for (int k = 0; k < na; ++k) {
+        AR& r = ar[k];
+        const int G = chunk_trees(c, *r.a);
+        for (int f0 = 0; f0 < r.F; f0 += G) {
+            const int cnt = std::min(G, r.F - f0);
+            const int i0 = r.tpos[f0], i1 = f0 + cnt < r.F ? r.tpos[f0 + cnt] : r.W;
+            if (i1 > i0) chunks.push_back({k, f0, cnt, i0, i1});
+        }
+    }
+    std::stable_sort(chunks.begin(), chunks.end(), [&](const Chunk& x, const Chunk& y) {
+        return (size_t)ar[x.k].a->P * ar[x.k].n > (size_t)ar[y.k].a->P * ar[y.k].n;
+    });
+    size_t ci = 0;
+    while (ci < chunks.size()) {
+        size_t used = 0, ce = ci;
+        while (ce < chunks.size()) {
+            const AlnState& a = *ar[chunks[ce].k].a;
+            const size_t b = (tree_clv_bytes(c, a) + pmat_bytes(prec, C, a.n, 1) + 1024) * chunks[ce].cnt;
+            if (ce > ci && used + b > c.budget) break;
+            used += b;
+            ++ce;
+        }
+        unsigned char* wave = buf<unsigned char>(c, "wave.buf", used + 4096 * (ce - ci));
+        std::vector<PropGroup> groups;
+        std::vector<int> counts;
+        size_t off = 0;
+        int maxP = 1;
+        Span sp2(c, 2);
+        for (size_t q = ci; q < ce; ++q) {
+            const Chunk& ch = chunks[q];
+            AR& r = ar[ch.k];
+            AlnState& a = *r.a;
+            ClvGroup g;
+            const size_t slots = (size_t)(2 * a.n - 5);
+            g.tree_stride = slots * a.P * 4 * C;
+            g.scl_stride = slots * a.P;
+            g.clv = wave + off;
+            off += ((g.tree_stride * rsize(c) * ch.cnt) + 255) & ~size_t(255);
+            g.scl = reinterpret_cast<int32_t*>(wave + off);
+            off += ((g.scl_stride * 4 * ch.cnt) + 255) & ~size_t(255);
+            void* pm = wave + off;
+            off += (pmat_bytes(prec, C, a.n, ch.cnt) + 255) & ~size_t(255);
+            launch_partials(c.stream, prec, a.M, aln_dev(a), r.fr, ch.f0, ch.cnt, g, true, threads_for(c, a.P), pm);
+            ck(c, cudaGetLastError(), "partials launch");
+            const int gi0 = r.ibase + ch.i0, cnt_items = ch.i1 - ch.i0;
+            const double* init = nullptr;
+            if (feats) {
+                const int nslot = 2 * a.n - 5;
+                if (!a.tip_sum) {
+                    ck(c, cudaMalloc(&a.tip_sum, sizeof(float) * 16 * a.n), "alloc tip summaries");
+                    launch_tip_summary(c.stream, aln_dev(a), C, a.tip_sum);
+                }
+                float* ssum = buf<float>(c, "mlp.ssum", (size_t)ch.cnt * nslot * 16);
+                launch_slot_summary(c.stream, prec, C, aln_dev(a), g, ch.cnt, nslot, ssum);
+                float* xf = xf_all + (size_t)gi0 * kMlpIn;
+                void* xb = buf<unsigned char>(c, "mlp.xb", (size_t)(cnt_items + 64) * kMlpInPad * 2);
+                launch_item_features(c.stream, a.n, items + r.ibase, ch.i0, ch.i1, r.fr, ch.f0, ssum, nslot, a.tip_sum,
+                                     xf, xb);
+                if (use_mlp) {
+                    float* yb = buf<float>(c, "mlp.y", (size_t)(cnt_items + 64) * kMlpOutPad);
+                    mlp_forward(c.stream, c.mlp, xb, cnt_items, yb, nullptr, nullptr, nullptr, nullptr, false);
+                    launch_item_init(c.stream, items + r.ibase, ch.i0, ch.i1, xf, yb, c.cfg.tmin, c.cfg.tmax,
+                                     init_all + (size_t)gi0 * 5);
+                    init = init_all + (size_t)gi0 * 5;
+                }
+            }
+            PropGroup gp;
+            gp.M = a.M;
+            gp.A = aln_dev(a);
+            gp.fr = r.fr;
+            gp.first = ch.f0;
+            gp.g = g;
+            gp.Pm = pm;
+            gp.tab = a.table;
+            gp.round = r.round;
+            gp.lmax = r.lmax;
+            gp.thr = ins[ch.k].thr;
+            gp.items = items + gi0;
+            gp.lnl_out = plnl + gi0;
+            gp.len5_out = len5 + (size_t)5 * gi0;
+            gp.kept = kept + gi0;
+            gp.init = init;
+            groups.push_back(gp);
+            counts.push_back(cnt_items);
+            maxP = std::max(maxP, a.P);
+        }
+        sp2.end();
+        int tot = 0;
+        for (int x : counts) tot += x;
+        const int threads = threads_for(c, maxP);
+        const bool smem_tab = propose_smem_bytes(prec, C, maxP, true, threads) <= c.smem_optin;
+        const int grid = std::min(tot, 4 * c.sm_count);
+        void* scratch = nullptr;
+        size_t spc = 0;
+        if (!smem_tab) {
+            spc = (sumtable_bytes(prec, C, maxP) + 255) & ~size_t(255);
+            scratch = buf<unsigned char>(c, "prop.scratch", spc * grid);
+        }
+        const int* gstart;
+        int* counter;
+        const PropGroup* dg = upload_groups(c, "prop", groups, counts, &gstart, &counter);
+        Span sp3(c, 3);
+        launch_propose(c.stream, prec, C, dg, gstart, (int)groups.size(), counter, kcfg(c), c.d_stats, threads, grid,
+                       scratch, spc, maxP);
+        sp3.end();
+        ck(c, cudaGetLastError(), "propose launch");
+        if (c.log_on)
+            for (size_t q = ci; q < ce; ++q) {
+                const Chunk& ch = chunks[q];
+                AR& r = ar[ch.k];
+                launch_log_pairs(c.stream, items + r.ibase, ch.i0, ch.i1, xf_all + (size_t)(r.ibase + ch.i0) * kMlpIn,
+                                 len5 + (size_t)5 * r.ibase, c.log_x, c.log_t, c.log_count, c.log_cap);
+            }
+        ci = ce;
+    }
+    c.last_items = Wtot;
+    // ---- C. visit the kept neighbours
+    Span sp4(c, 4);
+    std::vector<FullJob> jobs;
+    int Ktot = 0;
+    for (int k = 0; k < na; ++k) {
+        AR& r = ar[k];
+        const std::string pre = "b" + std::to_string(k) + ".";
+        r.kpos = buf<int32_t>(c, pre + "kept.pos", r.W + 1);
+        r.K = scan_count(c, kept + r.ibase, r.kpos, r.W);
+        Ktot += r.K;
+        r.kidx = buf<int32_t>(c, pre + "kept.idx", r.K + 1);
+        launch_compact_idx(c.stream, r.W, kept + r.ibase, r.kpos, r.kidx);
+        int32_t* kedges = buf<int32_t>(c, pre + "kept.edges", (size_t)r.K * 2 * (2 * r.n - 3) + 2);
+        double* klens = buf<double>(c, pre + "kept.lens", (size_t)r.K * (2 * r.n - 3) + 1);
+        r.kslot = buf<int32_t>(c, pre + "kept.slot", r.K + 1);
+        launch_materialize(c.stream, r.n, r.K, r.kidx, items + r.ibase, r.fr, len5 + (size_t)5 * r.ibase, kedges, klens,
+                           r.kslot);
+        r.klnl = buf<double>(c, pre + "kp.lnl", r.K + 1);
+        r.kp = treeset(c, pre + "kp", r.n, std::max(r.K, 1), true);
+        if (r.K > 0) {
+            launch_canon(c.stream, r.n, r.K, kedges, klens, r.kp, c.d_err);
+            jobs.push_back(FullJob{r.a, r.kp, 0, r.K, r.klnl, c.cfg.full_max_sweeps});
+        }
+    }
+    hc[kStKept] = Ktot;
+    check_flags(c);
+    if (!jobs.empty()) run_full_jobs(c, jobs);
+    // ---- lmax, GOOD / BAD, next frontiers
+    outs.assign(na, RoundOut());
+    for (int k = 0; k < na; ++k) {
+        AR& r = ar[k];
+        const std::string pre = "b" + std::to_string(k) + ".";
+        launch_lmax(c.stream, r.K, r.klnl, nullptr, r.lmax);
+        r.good = buf<int32_t>(c, pre + "kp.good", r.K + 1);
+        launch_finalize_trees(c.stream, r.a->table, r.K, r.kslot, r.klnl, r.lmax, ins[k].thr, r.round, r.good,
+                              c.d_stats);
+        r.gpos = buf<int32_t>(c, pre + "kp.gpos", r.K + 1);
+        r.G = scan_count(c, r.good, r.gpos, r.K);
+        r.gidx = buf<int32_t>(c, pre + "kp.idx", r.G + 1);
+        launch_compact_idx(c.stream, r.K, r.good, r.gpos, r.gidx);
+        outs[k].ts = r.kp;
+        outs[k].idx = r.gidx;
+        outs[k].lnl = r.klnl;
+        outs[k].count = r.G;
+    }
+    sp4.end();
+    total.end();
+    std::vector<double> lm(na);
+    ck(c, cudaMemcpyAsync(lm.data(), d_lmax, 8 * (size_t)na, cudaMemcpyDeviceToHost, c.stream), "read lmax");
+    check_flags(c);
+    for (int k = 0; k < na; ++k) outs[k].lmax = lm[k];
+    end_stats(c, hc);
 }
 
 void expand_core(Ctx& c, AlnState& a, int F, const int32_t* edges_d, const double* lens_d, double thr,
                  double* lmax_inout, RoundOut& out) {
-    if (!a.table) reset_table(c, a);
-    const int n = a.n, m = 2 * (n - 3), prec = c.cfg.precision;
-    const int round = ++a.round;
-    int64_t hc[kStWords] = {0};
-    Span total(c, 5), sp0(c, 0);
-    // 1. frontier: canonical form, keys; entered as visited if absent
-    TreeSet fr = treeset(c, "fr", n, std::max(F, 1), false);
-    launch_canon(c.stream, n, F, edges_d, lens_d, fr, c.d_err);
-    int32_t* fwin = buf<int32_t>(c, "fr.win", F);
-    launch_insert_trees(c.stream, a.table, a.log2, F, fr, nullptr, nullptr, round - 1, fwin, c.d_err);
-    ck(c, cudaMemcpyAsync(c.d_lmax, lmax_inout, 8, cudaMemcpyHostToDevice, c.stream), "lmax");
-    const int ncand = F * m;
-    hc[kStCand] = ncand;
-    // 2. candidates, dedup, arbitration
-    uint64_t* nkey = buf<uint64_t>(c, "cand.key", (size_t)ncand * 2);
-    int32_t* cinfo = buf<int32_t>(c, "cand.info", (size_t)ncand * 4);
-    int32_t* cslot = buf<int32_t>(c, "cand.slot", ncand);
-    int32_t* flag = buf<int32_t>(c, "cand.flag", ncand);
-    int32_t* pos = buf<int32_t>(c, "cand.pos", ncand);
-    launch_enum(c.stream, n, F, fr, nkey, cinfo);
-    sp0.end();
-    Span sp1(c, 1);
-    launch_cand_insert(c.stream, a.table, a.log2, ncand, nkey, cinfo, fr, round, cslot, flag, c.d_err, c.d_stats);
-    launch_cand_arb(c.stream, 2, a.table, ncand, cinfo, fr, round, cslot, flag);
-    launch_cand_arb(c.stream, 3, a.table, ncand, cinfo, fr, round, cslot, flag);
-    launch_cand_arb(c.stream, 4, a.table, ncand, cinfo, fr, round, cslot, flag);
-    check_flags(c);
-    const int W = scan_count(c, flag, pos, ncand);
-    hc[kStScored] = W;
-    Item* items = buf<Item>(c, "items", W + 1);
-    uint64_t* ikey = buf<uint64_t>(c, "items.key", 2 * (size_t)W + 2);
-    launch_make_items(c.stream, ncand, flag, pos, cinfo, cslot, nkey, items, ikey);
-    // first item of each frontier tree (items are ordered by tree)
-    std::vector<int32_t> tpos(F + 1, W);
-    if (ncand > 0) {
-        std::vector<int32_t> allpos(ncand);
-        ck(c, cudaMemcpyAsync(allpos.data(), pos, 4 * (size_t)ncand, cudaMemcpyDeviceToHost, c.stream), "pos");
-        ck(c, cudaStreamSynchronize(c.stream), "sync");
-        for (int f = 0; f < F; ++f) tpos[f] = allpos[(size_t)f * m];
-    }
-    sp1.end();
-    // 3. partials of frontier chunks + proposal optimisation of their items
-    double* plnl = buf<double>(c, "items.lnl", W + 1);
-    double* len5 = buf<double>(c, "items.len5", 5 * (size_t)W + 5);
-    int32_t* kept = buf<int32_t>(c, "items.kept", W + 1);
-    const int G = chunk_trees(c, a);
-    const int threads = threads_for(c, a.P);
-    bool smem_tab = propose_smem_bytes(prec, a.M.C, a.P, true, threads) <= c.smem_optin;
-    float ms_part = 0, ms_prop = 0;
-    for (int f0 = 0; f0 < F && W > 0; f0 += G) {
-        int cnt = std::min(G, F - f0);
-        int i0 = tpos[f0], i1 = (f0 + cnt < F) ? tpos[f0 + cnt] : W;
-        if (i1 <= i0) continue;
-        ClvGroup g = clv_group(c, "fr", a, cnt);
-        void* pm = buf<unsigned char>(c, "fr.pm", pmat_bytes(prec, a.M.C, n, cnt));
-        Span sp2(c, 2);
-        launch_partials(c.stream, prec, a.M, aln_dev(a), fr, f0, cnt, g, true, threads, pm);
-        sp2.end();
-        ck(c, cudaGetLastError(), "partials launch");
-        int grid = std::min(i1 - i0, 4 * c.sm_count);
-        void* scratch = nullptr;
-        size_t spc = 0;
-        if (!smem_tab) {
-            spc = (sumtable_bytes(prec, a.M.C, a.P) + 255) & ~size_t(255);
-            scratch = buf<unsigned char>(c, "prop.scratch", spc * grid);
-        }
-        // learned warm start and/or training log: features of the chunk's items
-        const double* init = nullptr;
-        float* xf = nullptr;
-        if ((c.mlp_on && c.mlp_ready) || c.log_on) {
-            const int nslot = 2 * n - 5, cnt_items = i1 - i0;
-            if (!a.tip_sum) {
-                ck(c, cudaMalloc(&a.tip_sum, sizeof(float) * 16 * a.n), "alloc tip summaries");
-                launch_tip_summary(c.stream, aln_dev(a), a.M.C, a.tip_sum);
-            }
-            float* ssum = buf<float>(c, "mlp.ssum", (size_t)cnt * nslot * 16);
-            launch_slot_summary(c.stream, prec, a.M.C, aln_dev(a), g, cnt, nslot, ssum);
-            xf = buf<float>(c, "mlp.xf", (size_t)cnt_items * kMlpIn);
-            void* xb = buf<unsigned char>(c, "mlp.xb", (size_t)(cnt_items + 64) * kMlpInPad * 2);
-            launch_item_features(c.stream, n, items, i0, i1, fr, f0, ssum, nslot, a.tip_sum, xf, xb);
-            if (c.mlp_on && c.mlp_ready) {
-                float* yb = buf<float>(c, "mlp.y", (size_t)(cnt_items + 64) * kMlpOutPad);
-                mlp_forward(c.stream, c.mlp, xb, cnt_items, yb, nullptr, nullptr, nullptr, nullptr, false);
-                double* ini = buf<double>(c, "mlp.init", (size_t)cnt_items * 5);
-                launch_item_init(c.stream, items, i0, i1, xf, yb, c.cfg.tmin, c.cfg.tmax, ini);
-                init = ini;
-            }
-        }
-        Span sp3(c, 3);
-        launch_propose(c.stream, prec, a.M, aln_dev(a), kcfg(c), fr, f0, g, items, i0, i1, a.table, round, c.d_lmax,
-                       thr, plnl + i0, len5 + (size_t)5 * i0, kept + i0, c.d_stats, threads, grid, scratch, spc, pm,
-                       init);
-        sp3.end();
-        if (c.log_on && xf)
-            launch_log_pairs(c.stream, items, i0, i1, xf, len5, c.log_x, c.log_t, c.log_count, c.log_cap);
-        ck(c, cudaGetLastError(), "propose launch");
-    }
-    (void)ms_part; (void)ms_prop;
-    Span sp4(c, 4);
-    c.last_items = W;
-    // 4. kept neighbours: materialise, canonicalise, fully optimise
-    int32_t* kpos = buf<int32_t>(c, "kept.pos", W + 1);
-    const int K = scan_count(c, kept, kpos, W);
-    hc[kStKept] = K;
-    int32_t* kidx = buf<int32_t>(c, "kept.idx", K + 1);
-    launch_compact_idx(c.stream, W, kept, kpos, kidx);
-    int32_t* kedges = buf<int32_t>(c, "kept.edges", (size_t)K * 2 * (2 * n - 3) + 2);
-    double* klens = buf<double>(c, "kept.lens", (size_t)K * (2 * n - 3) + 1);
-    int32_t* kslot = buf<int32_t>(c, "kept.slot", K + 1);
-    launch_materialize(c.stream, n, K, kidx, items, fr, len5, kedges, klens, kslot);
-    double* klnl = buf<double>(c, "kp.lnl", K + 1);
-    TreeSet kp;
-    if (K > 0) score_core(c, a, K, kedges, klens, PT_SCORE_FULL, "kp", kp, klnl);
-    else kp = treeset(c, "kp", n, 1, true);
-    // 5. lmax, GOOD / BAD, next frontier
-    launch_lmax(c.stream, K, klnl, nullptr, c.d_lmax);
-    int32_t* good = buf<int32_t>(c, "kp.good", K + 1);
-    launch_finalize_trees(c.stream, a.table, K, kslot, klnl, c.d_lmax, thr, round, good, c.d_stats);
-    int32_t* gpos = buf<int32_t>(c, "kp.gpos", K + 1);
-    const int Gn = scan_count(c, good, gpos, K);
-    int32_t* gidx = buf<int32_t>(c, "kp.idx", Gn + 1);
-    launch_compact_idx(c.stream, K, good, gpos, gidx);
-    sp4.end();
-    total.end();
-    ck(c, cudaMemcpyAsync(lmax_inout, c.d_lmax, 8, cudaMemcpyDeviceToHost, c.stream), "read lmax");
-    check_flags(c);
-    out.ts = kp;
-    out.idx = gidx;
-    out.lnl = klnl;
-    out.count = Gn;
-    end_stats(c, hc);
+    const int id = (int)(&a - c.alns.data());
+    std::vector<RoundIn> ins{RoundIn{id, F, edges_d, lens_d, thr, *lmax_inout}};
+    std::vector<RoundOut> outs;
+    expand_batch(c, ins, outs);
+    out = outs[0];
+    *lmax_inout = out.lmax;
 }
 
 void collect_times(Ctx& c) {
@@ -964,6 +1214,55 @@ pt_status pt_expand_frontier_dev(pt_ctx* ctx, int aln_id, int n_frontier, const 
         collect_times(c);
     });
 }
+
+static pt_status expand_batch_api(pt_ctx* ctx, int n, pt_round* rounds, bool host) {
+    return guarded(ctx, [&](Ctx& c) {
+        if (n < 1 || !rounds) fail(c, PT_ERR_INVALID_ARG, "bad arguments");
+        std::vector<RoundIn> ins(n);
+        for (int k = 0; k < n; ++k) {
+            pt_round& r = rounds[k];
+            AlnState& a = aln_of(c, r.aln_id);
+            if (r.n_frontier < 0 || (r.n_frontier > 0 && (!r.edges || !r.lengths)) || !(r.threshold >= 0) ||
+                std::isnan(r.lmax))
+                fail(c, PT_ERR_INVALID_ARG, "bad round %d", k);
+            const int E = 2 * a.n - 3;
+            ins[k] = RoundIn{r.aln_id, r.n_frontier, r.edges, r.lengths, r.threshold, r.lmax};
+            if (host) {
+                validate_trees(c, a.n, r.n_frontier, r.edges, r.lengths);
+                const std::string pre = "in" + std::to_string(k);
+                int32_t* de = buf<int32_t>(c, pre + ".e", (size_t)std::max(r.n_frontier, 1) * 2 * E);
+                double* dl = buf<double>(c, pre + ".l", (size_t)std::max(r.n_frontier, 1) * E);
+                if (r.n_frontier > 0) {
+                    ck(c, cudaMemcpyAsync(de, r.edges, 4 * (size_t)r.n_frontier * 2 * E, cudaMemcpyHostToDevice,
+                                          c.stream), "copy in");
+                    ck(c, cudaMemcpyAsync(dl, r.lengths, 8 * (size_t)r.n_frontier * E, cudaMemcpyHostToDevice,
+                                          c.stream), "copy in");
+                }
+                ins[k].edges_d = de;
+                ins[k].lens_d = dl;
+            }
+        }
+        zero_flags(c);
+        begin_stats(c);
+        std::vector<RoundOut> outs;
+        expand_batch(c, ins, outs);
+        pt_status worst = PT_OK;
+        for (int k = 0; k < n; ++k) {
+            pt_round& r = rounds[k];
+            r.lmax = outs[k].lmax;
+            r.n_kept = outs[k].count;
+            if (outs[k].count > r.cap) { worst = PT_ERR_BUFFER_TOO_SMALL; continue; }
+            int nk;
+            write_out(c, c.alns[r.aln_id], outs[k], r.cap, r.kept_edges, r.kept_lengths, r.kept_lnl,
+                      reinterpret_cast<uint64_t*>(r.kept_keys), host, &nk);
+        }
+        collect_times(c);
+        if (worst != PT_OK) fail(c, worst, "an output capacity is below its next frontier's size");
+    });
+}
+
+pt_status pt_expand_batch(pt_ctx* ctx, int n, pt_round* rounds) { return expand_batch_api(ctx, n, rounds, true); }
+pt_status pt_expand_batch_dev(pt_ctx* ctx, int n, pt_round* rounds) { return expand_batch_api(ctx, n, rounds, false); }
 
 pt_status pt_visited(pt_ctx* ctx, int aln_id, size_t cap, pt_key* keys, uint8_t* status, double* lnl,
                      size_t* count) {

@@ -146,14 +146,43 @@ void launch_lengths_to_input(cudaStream_t s, int n, int count, TreeSet ts, doubl
 size_t pmat_bytes(int prec, int C, int n, int count);
 void launch_partials(cudaStream_t s, int prec, const Model& M, Aln A, TreeSet ts, int first, int count, ClvGroup g,
                      bool with_up, int threads, void* pm);
-// Proposal optimisation of work items [i0, i1) whose trees are [first, ...) of g.
-void launch_propose(cudaStream_t s, int prec, const Model& M, Aln A, Cfg cfg, TreeSet fr, int first, ClvGroup g,
-                    const Item* items, int i0, int i1, Slot* tab, int round, const double* lmax, double thr,
-                    double* lnl_out, double* len5_out, int32_t* kept, unsigned long long* stats, int threads,
-                    int grid, void* scratch, size_t scratch_per_cta, const void* pm, const double* init);
-// Full optimisation (max_sweeps >= 0) of trees [first, first+count) of ts.
-void launch_fullopt(cudaStream_t s, int prec, const Model& M, Aln A, Cfg cfg, TreeSet ts, int first, int count,
-                    ClvGroup g, int max_sweeps, double* lnl_out, unsigned long long* stats, int threads, int grid,
+// One group of a batched proposal launch: the work items of one alignment
+// whose frontier trees [first, first + count) have their partials in g.
+struct PropGroup {
+    Model M;
+    Aln A;
+    TreeSet fr;
+    int first;
+    ClvGroup g;
+    const void* Pm;          // P matrices of the group's trees (launch_partials)
+    Slot* tab;
+    int round;
+    const double* lmax;      // lmax at the start of the round (device)
+    double thr;
+    const Item* items;       // the group's items; outputs are indexed like them
+    double* lnl_out;
+    double* len5_out;
+    int32_t* kept;
+    const double* init;      // learned starting lengths [count][5] or nullptr
+};
+// One group of a batched full-optimisation launch: trees [first, first + n) of ts.
+struct FullGroup {
+    Model M;
+    Aln A;
+    TreeSet ts;
+    int first;
+    ClvGroup g;
+    int max_sweeps;
+    double* lnl_out;
+};
+// Batched launches over groups: gstart [ngroups + 1] is the prefix sum of the
+// groups' item (tree) counts (device); counter (device, zeroed) hands out the
+// items dynamically, in order, to the persistent CTAs.
+void launch_propose(cudaStream_t s, int prec, int C, const PropGroup* groups, const int* gstart, int ngroups,
+                    int* counter, Cfg cfg, unsigned long long* stats, int threads, int grid, void* scratch,
+                    size_t scratch_per_cta, int maxP);
+void launch_fullopt(cudaStream_t s, int prec, int C, const FullGroup* groups, const int* gstart, int ngroups,
+                    int* counter, int maxN, int maxP, Cfg cfg, unsigned long long* stats, int threads, int grid,
                     void* scratch, size_t scratch_per_cta);
 
 // GTR+Gamma model set-up on the host (pt_api.cu); false on invalid parameters.

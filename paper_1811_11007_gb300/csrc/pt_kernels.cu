@@ -1118,103 +1118,111 @@ struct ProposeSmem {
     int mbr[4];          // branch of each member
     int bmem[5];         // member of each branch (-1: central)
     double ex5[5][4 * C];
+    int next, grp;       // work item taken from the counter, its group
     NewtonSmem<R, C> ns;
 };
 
 template <typename R, int C, bool kSmemTab>
-__global__ void __launch_bounds__(512) k_propose(Model M, Aln A, Cfg cfg, TreeSet fr, int first, ClvGroup g,
-                                                 const R* __restrict__ Pm_all, const Item* __restrict__ items, int i0,
-                                                 int i1, Slot* tab, int round, const double* lmax, double thr,
-                                                 double* lnl_out, double* len5_out, int32_t* kept,
-                                                 unsigned long long* stats, unsigned char* scratch,
-                                                 size_t scratch_per_cta, const double* __restrict__ init) {
+__global__ void __launch_bounds__(512) k_propose(const PropGroup* __restrict__ groups, const int* __restrict__ gstart,
+                                                 int ngroups, int* counter, Cfg cfg, unsigned long long* stats,
+                                                 unsigned char* scratch, size_t scratch_per_cta) {
     extern __shared__ __align__(16) unsigned char smraw[];
     ProposeSmem<R, C>& sm = *reinterpret_cast<ProposeSmem<R, C>*>(smraw);
-    const int n = fr.n, NN = 2 * n - 2, P = A.P;
-    const int pcap = (P + 3) & ~3;
-    STab<R, C> st;
-    {
-        unsigned char* base = kSmemTab ? smraw + ((sizeof(ProposeSmem<R, C>) + 15) & ~size_t(15))
-                                       : scratch + (size_t)blockIdx.x * scratch_per_cta;
-        st.s = reinterpret_cast<R*>(base);
-        st.ew = st.s + (size_t)4 * C * pcap;
-        st.pcap = pcap;
-    }
-    if (threadIdx.x < 16) {
-        int i = threadIdx.x >> 2, k = threadIdx.x & 3;
-        sm.Mt[threadIdx.x] = (R)(M.sqpi[i] * M.R[i * 4 + k]);
-        if (threadIdx.x < 4) sm.pi[threadIdx.x] = (R)M.pi[threadIdx.x];
-    }
-    init_newton_smem<R, C>(M, sm.ns);
-    const size_t sstride = (size_t)P * 4 * C;
+    unsigned char* const tab_base = kSmemTab ? smraw + ((sizeof(ProposeSmem<R, C>) + 15) & ~size_t(15))
+                                             : scratch + (size_t)blockIdx.x * scratch_per_cta;
+    const int total = gstart[ngroups];
     const int nb = cfg.propose_mode == 1 ? 1 : 5;
     unsigned long long evals_total = 0, sweeps_total = 0, nonconv = 0;
-    for (int item = i0 + blockIdx.x; item < i1; item += gridDim.x) {
-        const Item it = items[item];
-        const int gi = it.tree - first;
-        const int32_t* up = fr.up + (size_t)it.tree * NN;
-        const int32_t* ch = fr.ch + (size_t)it.tree * NN * 2;
-        const double* len = fr.len + (size_t)it.tree * NN;
-        const R* clv = reinterpret_cast<const R*>(g.clv) + (size_t)gi * g.tree_stride;
-        const int32_t* scl = g.scl + (size_t)gi * g.scl_stride;
+    while (true) {
+        __syncthreads();  // previous item done with shared memory
+        if (threadIdx.x == 0) {
+            const int x = atomicAdd(counter, 1);
+            int k = 0;
+            while (k + 1 < ngroups && gstart[k + 1] <= x) ++k;
+            sm.next = x;
+            sm.grp = k;
+        }
+        __syncthreads();
+        const int x = sm.next;
+        if (x >= total) break;
+        const PropGroup& G = groups[sm.grp];
+        const int o = x - gstart[sm.grp];
+        const Model& M = G.M;
+        const int n = G.fr.n, NN = 2 * n - 2, P = G.A.P;
+        STab<R, C> st;
+        st.pcap = (P + 3) & ~3;
+        st.s = reinterpret_cast<R*>(tab_base);
+        st.ew = st.s + (size_t)4 * C * st.pcap;
+        const size_t sstride = (size_t)P * 4 * C;
+        const Item it = G.items[o];
+        const int gi = it.tree - G.first;
+        const int32_t* up = G.fr.up + (size_t)it.tree * NN;
+        const int32_t* ch = G.fr.ch + (size_t)it.tree * NN * 2;
+        const double* len = G.fr.len + (size_t)it.tree * NN;
+        const R* clv = reinterpret_cast<const R*>(G.g.clv) + (size_t)gi * G.g.tree_stride;
+        const int32_t* scl = G.g.scl + (size_t)gi * G.g.scl_stride;
         const int v = it.v, u = up[v];
         const int sib = ch[2 * u] == v ? ch[2 * u + 1] : ch[2 * u];
         const int c0 = ch[2 * v], c1 = ch[2 * v + 1];
         // branch b's node in the parent (its P matrix is the parent's): central v, A u, B sib, C c0, D c1
         const int bnode[5] = {v, u, sib, c0, c1};
-        const R* Psrc = Pm_all + (size_t)gi * NN * C * 16;
-        __syncthreads();  // previous item done with smem
+        const R* Psrc = reinterpret_cast<const R*>(G.Pm) + (size_t)gi * NN * C * 16;
+        if (threadIdx.x < 16) {
+            const int i = threadIdx.x >> 2, k = threadIdx.x & 3;
+            sm.Mt[threadIdx.x] = (R)(M.sqpi[i] * M.R[i * 4 + k]);
+            if (threadIdx.x < 4) sm.pi[threadIdx.x] = (R)M.pi[threadIdx.x];
+        }
+        init_newton_smem<R, C>(M, sm.ns);
         if (threadIdx.x == 0) {
             const int node[4] = {u, it.swap == 0 ? c0 : c1, sib, it.swap == 0 ? c1 : c0};
             const int brn[4] = {1, it.swap == 0 ? 3 : 4, 2, it.swap == 0 ? 4 : 3};
             sm.bmem[0] = -1;
             for (int m = 0; m < 4; ++m) {
-                Src<R, C> x;
+                Src<R, C> y;
                 if (m == 0) {
-                    if (u == n) { x.clv = nullptr; x.scl = nullptr; x.tip = A.tips; }
+                    if (u == n) { y.clv = nullptr; y.scl = nullptr; y.tip = G.A.tips; }
                     else {
-                        int slot = n - 2 + (u - n - 1);
-                        x.clv = clv + (size_t)slot * sstride; x.scl = scl + (size_t)slot * P; x.tip = nullptr;
+                        const int slot = n - 2 + (u - n - 1);
+                        y.clv = clv + (size_t)slot * sstride; y.scl = scl + (size_t)slot * P; y.tip = nullptr;
                     }
                 } else if (node[m] < n) {
-                    x.clv = nullptr; x.scl = nullptr; x.tip = A.tips + (size_t)node[m] * P;
+                    y.clv = nullptr; y.scl = nullptr; y.tip = G.A.tips + (size_t)node[m] * P;
                 } else {
-                    x.clv = clv + (size_t)(node[m] - n) * sstride; x.scl = scl + (size_t)(node[m] - n) * P; x.tip = nullptr;
+                    y.clv = clv + (size_t)(node[m] - n) * sstride; y.scl = scl + (size_t)(node[m] - n) * P; y.tip = nullptr;
                 }
-                sm.msrc[m] = x;
+                sm.msrc[m] = y;
                 sm.mbr[m] = brn[m];
                 sm.bmem[brn[m]] = m;
             }
         }
-        for (int x = threadIdx.x; x < 5 * C * 16; x += blockDim.x) {
-            int b = x / (C * 16), o = x % (C * 16);
-            sm.Pm[b][o] = Psrc[(size_t)bnode[b] * C * 16 + o];
+        for (int z = threadIdx.x; z < 5 * C * 16; z += blockDim.x) {
+            const int b = z / (C * 16), q = z % (C * 16);
+            sm.Pm[b][q] = Psrc[(size_t)bnode[b] * C * 16 + q];
         }
         if (threadIdx.x < 5) {
             double t0 = len[bnode[threadIdx.x]];
-            if (init) {  // learned warm start; NaN = keep the inherited length
-                const double x = init[(size_t)(item - i0) * 5 + threadIdx.x];
-                if (x == x) t0 = x;
+            if (G.init) {  // learned warm start; NaN = keep the inherited length
+                const double y = G.init[(size_t)o * 5 + threadIdx.x];
+                if (y == y) t0 = y;
             }
             sm.T[threadIdx.x] = t0;
         }
         __syncthreads();
-        if (init) {  // P matrices at the starting lengths
-            for (int x = threadIdx.x; x < 5 * 4 * C; x += blockDim.x) {
-                const int b = x / (4 * C), q = x % (4 * C);
+        if (G.init) {  // P matrices at the starting lengths
+            for (int z = threadIdx.x; z < 5 * 4 * C; z += blockDim.x) {
+                const int b = z / (4 * C), q = z % (4 * C);
                 sm.ex5[b][q] = exp(M.lam[q & 3] * M.rates[q >> 2] * sm.T[b]);
             }
             __syncthreads();
-            for (int x = threadIdx.x; x < 5 * 16 * C; x += blockDim.x) {
-                const int b = x / (16 * C), o = x % (16 * C), r = o >> 4, ij = o & 15;
+            for (int z = threadIdx.x; z < 5 * 16 * C; z += blockDim.x) {
+                const int b = z / (16 * C), q = z % (16 * C), r = q >> 4, ij = q & 15;
                 double acc = 0.0;
 #pragma unroll
                 for (int k = 0; k < 4; ++k) acc += sm.ns.W[ij * 4 + k] * sm.ex5[b][r * 4 + k];
-                sm.Pm[b][o] = (R)acc;
+                sm.Pm[b][q] = (R)acc;
             }
             __syncthreads();
         }
-        double f1 = 0.0;
         int sweeps = 0;
         for (int sw = 0; sw < cfg.prop_max_sweeps; ++sw) {
             ++sweeps;
@@ -1257,7 +1265,7 @@ __global__ void __launch_bounds__(512) k_propose(Model M, Aln A, Cfg cfg, TreeSe
                     int ex = normalise<R, C>(X), ey = normalise<R, C>(Y);
                     R s4[4 * C];
                     sumtable<R, C>(sm.Mt, sm.pi, X, Y, s4);
-                    st.put(p, s4, (R)(ex + ey - Prec<R>::kScaleExp * (k0 + k1 + k2 + k3)), (R)A.w[p]);
+                    st.put(p, s4, (R)(ex + ey - Prec<R>::kScaleExp * (k0 + k1 + k2 + k3)), (R)G.A.w[p]);
                 }
                 const double told = sm.T[b];
                 int ev;
@@ -1274,17 +1282,16 @@ __global__ void __launch_bounds__(512) k_propose(Model M, Aln A, Cfg cfg, TreeSe
             if (moved <= cfg.sweep_tol) break;
         }
         // exact lnL at the final lengths: the last sum-table at its new length
-        f1 = eval_lnl<R, C>(M, st, P, sm.T[nb - 1], sm.ns);
+        const double f1 = eval_lnl<R, C>(M, st, P, sm.T[nb - 1], sm.ns);
         sweeps_total += sweeps;
         if (threadIdx.x == 0) {
-            const int o = item - i0;
-            lnl_out[o] = f1;
-            for (int b = 0; b < 5; ++b) len5_out[(size_t)o * 5 + b] = sm.T[b];
-            int k = f1 >= *lmax - thr;
-            kept[o] = k;
-            Slot* sl = &tab[it.slot];
+            G.lnl_out[o] = f1;
+            for (int b = 0; b < 5; ++b) G.len5_out[(size_t)o * 5 + b] = sm.T[b];
+            const int k = f1 >= *G.lmax - G.thr;
+            G.kept[o] = k;
+            Slot* sl = &G.tab[it.slot];
             sl->lnl = f1;
-            sl->tag = ((unsigned long long)round << 48) | (unsigned long long)(k ? 4 : 1);
+            sl->tag = ((unsigned long long)G.round << 48) | (unsigned long long)(k ? 4 : 1);
         }
     }
     if (threadIdx.x == 0) {
@@ -1303,65 +1310,78 @@ template <typename R, int C>
 struct FullSmem {
     R Mt[16];
     R pi[4];
+    int next, grp;
     NewtonSmem<R, C> ns;
 };
 
 template <typename R, int C, bool kSmemTab>
-__global__ void __launch_bounds__(512) k_fullopt(Model M, Aln A, Cfg cfg, TreeSet ts, int first, int count,
-                                                 ClvGroup g, int max_sweeps, double* lnl_out,
+__global__ void __launch_bounds__(512) k_fullopt(const FullGroup* __restrict__ groups, const int* __restrict__ gstart,
+                                                 int ngroups, int* counter, int nn_max, Cfg cfg,
                                                  unsigned long long* stats, unsigned char* scratch,
                                                  size_t scratch_per_cta) {
     extern __shared__ __align__(16) unsigned char smraw[];
     FullSmem<R, C>& sm = *reinterpret_cast<FullSmem<R, C>*>(smraw);
-    const int n = ts.n, NN = 2 * n - 2, P = A.P;
-    const int pcap = (P + 3) & ~3;
     size_t off = (sizeof(FullSmem<R, C>) + 15) & ~size_t(15);
     double* len = reinterpret_cast<double*>(smraw + off);
-    off += ((size_t)NN * sizeof(double) + 15) & ~size_t(15);
+    off += ((size_t)nn_max * sizeof(double) + 15) & ~size_t(15);
     R* Pm = reinterpret_cast<R*>(smraw + off);
-    off += ((size_t)NN * C * 16 * sizeof(R) + 15) & ~size_t(15);
-    STab<R, C> st;
-    {
-        unsigned char* base = kSmemTab ? smraw + off : scratch + (size_t)blockIdx.x * scratch_per_cta;
-        st.s = reinterpret_cast<R*>(base);
-        st.ew = st.s + (size_t)4 * C * pcap;
-        st.pcap = pcap;
-    }
-    if (threadIdx.x < 16) {
-        int i = threadIdx.x >> 2, k = threadIdx.x & 3;
-        sm.Mt[threadIdx.x] = (R)(M.sqpi[i] * M.R[i * 4 + k]);
-        if (threadIdx.x < 4) sm.pi[threadIdx.x] = (R)M.pi[threadIdx.x];
-    }
-    init_newton_smem<R, C>(M, sm.ns);
-    const size_t sstride = (size_t)P * 4 * C;
+    off += ((size_t)nn_max * C * 16 * sizeof(R) + 15) & ~size_t(15);
+    unsigned char* const tab_base = kSmemTab ? smraw + off : scratch + (size_t)blockIdx.x * scratch_per_cta;
+    const int total = gstart[ngroups];
     unsigned long long evals_total = 0, sweeps_total = 0, nonconv = 0;
-    for (int gi = blockIdx.x; gi < count; gi += gridDim.x) {
-        const int tree = first + gi;
-        const int32_t* up = ts.up + (size_t)tree * NN;
-        const int32_t* ch = ts.ch + (size_t)tree * NN * 2;
-        const int32_t* sched = ts.sched + (size_t)tree * 3 * n;
-        double* glen = ts.len + (size_t)tree * NN;
-        R* clv = reinterpret_cast<R*>(g.clv) + (size_t)gi * g.tree_stride;
-        int32_t* scl = g.scl + (size_t)gi * g.scl_stride;
+    while (true) {
         __syncthreads();
+        if (threadIdx.x == 0) {
+            const int x = atomicAdd(counter, 1);
+            int k = 0;
+            while (k + 1 < ngroups && gstart[k + 1] <= x) ++k;
+            sm.next = x;
+            sm.grp = k;
+        }
+        __syncthreads();
+        const int x = sm.next;
+        if (x >= total) break;
+        const FullGroup& G = groups[sm.grp];
+        const int gi = x - gstart[sm.grp];
+        const Model& M = G.M;
+        const Aln& A = G.A;
+        const int n = G.ts.n, NN = 2 * n - 2, P = A.P;
+        STab<R, C> st;
+        st.pcap = (P + 3) & ~3;
+        st.s = reinterpret_cast<R*>(tab_base);
+        st.ew = st.s + (size_t)4 * C * st.pcap;
+        const size_t sstride = (size_t)P * 4 * C;
+        const int tree = G.first + gi;
+        const int32_t* up = G.ts.up + (size_t)tree * NN;
+        const int32_t* ch = G.ts.ch + (size_t)tree * NN * 2;
+        const int32_t* sched = G.ts.sched + (size_t)tree * 3 * n;
+        double* glen = G.ts.len + (size_t)tree * NN;
+        R* clv = reinterpret_cast<R*>(G.g.clv) + (size_t)gi * G.g.tree_stride;
+        int32_t* scl = G.g.scl + (size_t)gi * G.g.scl_stride;
+        if (threadIdx.x < 16) {
+            const int i = threadIdx.x >> 2, k = threadIdx.x & 3;
+            sm.Mt[threadIdx.x] = (R)(M.sqpi[i] * M.R[i * 4 + k]);
+            if (threadIdx.x < 4) sm.pi[threadIdx.x] = (R)M.pi[threadIdx.x];
+        }
+        init_newton_smem<R, C>(M, sm.ns);
         for (int v = threadIdx.x; v < NN; v += blockDim.x) len[v] = glen[v];
         __syncthreads();
-        for (int x = threadIdx.x; x < NN * C * 4; x += blockDim.x) {
-            int v = x / (C * 4), r = (x / 4) % C, i = x & 3;
+        for (int z = threadIdx.x; z < NN * C * 4; z += blockDim.x) {
+            const int v = z / (C * 4), r = (z / 4) % C, i = z & 3;
             if (v > 0) pmat_row<R>(M, len[v] * M.rates[r], i, Pm + ((size_t)v * C + r) * 16 + i * 4);
         }
         __syncthreads();
         auto srcD = [&](int v) {
-            Src<R, C> s;
-            if (v < n) { s.clv = nullptr; s.scl = nullptr; s.tip = A.tips + (size_t)v * P; }
-            else { s.clv = clv + (size_t)(v - n) * sstride; s.scl = scl + (size_t)(v - n) * P; s.tip = nullptr; }
-            return s;
+            Src<R, C> y;
+            if (v < n) { y.clv = nullptr; y.scl = nullptr; y.tip = A.tips + (size_t)v * P; }
+            else { y.clv = clv + (size_t)(v - n) * sstride; y.scl = scl + (size_t)(v - n) * P; y.tip = nullptr; }
+            return y;
         };
         auto srcU = [&](int v) {  // the vector at up[v] without v's subtree, for inner v != n
-            Src<R, C> s;
+            Src<R, C> y;
             const int slot = n - 2 + (v - n - 1);
-            s.clv = clv + (size_t)slot * sstride; s.scl = scl + (size_t)slot * P; s.tip = nullptr;
-            return s;
+            y.clv = clv + (size_t)slot * sstride; y.scl = scl + (size_t)slot * P; y.tip = nullptr;
+            return y;
         };
         auto refreshD = [&](int v) {
             const int c0 = ch[2 * v], c1 = ch[2 * v + 1];
@@ -1372,7 +1392,7 @@ __global__ void __launch_bounds__(512) k_fullopt(Model M, Aln A, Cfg cfg, TreeSe
                 apply_p<R, C>(Pm + (size_t)c1 * C * 16, srcD(c1), p, y1, k1);
 #pragma unroll
                 for (int q = 0; q < 4 * C; ++q) y0[q] *= y1[q];
-                int sc = rescale<R, C>(y0);
+                const int sc = rescale<R, C>(y0);
                 store_vec<R, C>(clv + (size_t)(v - n) * sstride, p, y0);
                 scl[(size_t)(v - n) * P + p] = k0 + k1 + sc;
             }
@@ -1394,7 +1414,7 @@ __global__ void __launch_bounds__(512) k_fullopt(Model M, Aln A, Cfg cfg, TreeSe
                     apply_p<R, C>(Pm + (size_t)u * C * 16, u == n ? tip0 : srcU(u), p, y1, k1);
 #pragma unroll
                     for (int q = 0; q < 4 * C; ++q) X[q] *= y1[q];
-                    int sc = rescale<R, C>(X);
+                    const int sc = rescale<R, C>(X);
                     cx = k0 + k1 + sc;
                     if (v >= n) {
                         const int slot = n - 2 + (v - n - 1);
@@ -1403,18 +1423,18 @@ __global__ void __launch_bounds__(512) k_fullopt(Model M, Aln A, Cfg cfg, TreeSe
                     }
                 }
                 load_raw<R, C>(srcD(v), p, Y, cy);
-                int ex = normalise<R, C>(X), ey = normalise<R, C>(Y);
-                R s[4 * C];
-                sumtable<R, C>(sm.Mt, sm.pi, X, Y, s);
-                st.put(p, s, (R)(ex + ey - Prec<R>::kScaleExp * (cx + cy)), (R)A.w[p]);
+                const int ex = normalise<R, C>(X), ey = normalise<R, C>(Y);
+                R s4[4 * C];
+                sumtable<R, C>(sm.Mt, sm.pi, X, Y, s4);
+                st.put(p, s4, (R)(ex + ey - Prec<R>::kScaleExp * (cx + cy)), (R)A.w[p]);
             }
         };
         // bottom-up D pass
         for (int v = NN - 1; v >= n; --v) refreshD(v);
         int sweeps = 0, last = n;
         const int nsched = 3 * n - 5;
-        if (max_sweeps == 0) visit_build(n);
-        for (int sw = 0; sw < max_sweeps; ++sw) {
+        if (G.max_sweeps == 0) visit_build(n);
+        for (int sw = 0; sw < G.max_sweeps; ++sw) {
             ++sweeps;
             double moved = 0.0;
             for (int k = 0; k < nsched; ++k) {
@@ -1425,7 +1445,7 @@ __global__ void __launch_bounds__(512) k_fullopt(Model M, Aln A, Cfg cfg, TreeSe
                 const double told = len[v];
                 int ev;
                 bool conv;
-                double t = newton_solve<R, C>(M, cfg, st, P, told, sm.ns, ev, conv);
+                const double t = newton_solve<R, C>(M, cfg, st, P, told, sm.ns, ev, conv);
                 moved = fmax(moved, fabs(t - told));
                 evals_total += ev;
                 if (!conv) ++nonconv;
@@ -1441,7 +1461,7 @@ __global__ void __launch_bounds__(512) k_fullopt(Model M, Aln A, Cfg cfg, TreeSe
         sweeps_total += sweeps;
         __syncthreads();
         for (int v = threadIdx.x; v < NN; v += blockDim.x) glen[v] = len[v];
-        if (threadIdx.x == 0) lnl_out[gi] = f1;
+        if (threadIdx.x == 0) G.lnl_out[gi] = f1;
     }
     if (threadIdx.x == 0) {
         atomicAdd(&stats[kStFullEvals], evals_total);
@@ -1635,76 +1655,61 @@ void launch_partials(cudaStream_t s, int prec, const Model& M, Aln A, TreeSet ts
 
 namespace {
 template <typename R, int C>
-void propose_t(cudaStream_t s, const Model& M, Aln A, Cfg cfg, TreeSet fr, int first, ClvGroup g, const Item* items,
-               int i0, int i1, Slot* tab, int round, const double* lmax, double thr, double* lnl_out, double* len5_out,
-               int32_t* kept, unsigned long long* stats, int threads, int grid, void* scratch, size_t spc,
-               const void* pmv, const double* init) {
-    const R* pm = reinterpret_cast<const R*>(pmv);
-    if (scratch) {
-        size_t smem = propose_smem_bytes(sizeof(R) == 8 ? 0 : 1, C, A.P, false, threads);
-        cudaFuncSetAttribute(k_propose<R, C, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        k_propose<R, C, false><<<grid, threads, smem, s>>>(M, A, cfg, fr, first, g, pm, items, i0, i1, tab, round,
-                                                           lmax, thr, lnl_out, len5_out, kept, stats,
-                                                           reinterpret_cast<unsigned char*>(scratch), spc, init);
-        ++g_launches;
-    } else {
-        size_t smem = propose_smem_bytes(sizeof(R) == 8 ? 0 : 1, C, A.P, true, threads);
-        cudaFuncSetAttribute(k_propose<R, C, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        k_propose<R, C, true><<<grid, threads, smem, s>>>(M, A, cfg, fr, first, g, pm, items, i0, i1, tab, round,
-                                                          lmax, thr, lnl_out, len5_out, kept, stats, nullptr, 0,
-                                                          init);
-        ++g_launches;
-    }
-}
-}  // namespace
-
-void launch_propose(cudaStream_t s, int prec, const Model& M, Aln A, Cfg cfg, TreeSet fr, int first, ClvGroup g,
-                    const Item* items, int i0, int i1, Slot* tab, int round, const double* lmax, double thr,
-                    double* lnl_out, double* len5_out, int32_t* kept, unsigned long long* stats, int threads,
-                    int grid, void* scratch, size_t scratch_per_cta, const void* pm, const double* init) {
-    if (i1 <= i0) return;
-    // pm holds the P matrices of the group's trees, as computed by launch_partials
-    if (prec == 0) {
-        if (M.C == 1) propose_t<double, 1>(s, M, A, cfg, fr, first, g, items, i0, i1, tab, round, lmax, thr, lnl_out, len5_out, kept, stats, threads, grid, scratch, scratch_per_cta, pm, init);
-        else propose_t<double, 4>(s, M, A, cfg, fr, first, g, items, i0, i1, tab, round, lmax, thr, lnl_out, len5_out, kept, stats, threads, grid, scratch, scratch_per_cta, pm, init);
-    } else {
-        if (M.C == 1) propose_t<float, 1>(s, M, A, cfg, fr, first, g, items, i0, i1, tab, round, lmax, thr, lnl_out, len5_out, kept, stats, threads, grid, scratch, scratch_per_cta, pm, init);
-        else propose_t<float, 4>(s, M, A, cfg, fr, first, g, items, i0, i1, tab, round, lmax, thr, lnl_out, len5_out, kept, stats, threads, grid, scratch, scratch_per_cta, pm, init);
-    }
-}
-
-namespace {
-template <typename R, int C>
-void fullopt_t(cudaStream_t s, const Model& M, Aln A, Cfg cfg, TreeSet ts, int first, int count, ClvGroup g,
-               int max_sweeps, double* lnl_out, unsigned long long* stats, int threads, int grid, void* scratch,
-               size_t spc) {
+void propose_t(cudaStream_t s, const PropGroup* groups, const int* gstart, int ngroups, int* counter, Cfg cfg,
+               unsigned long long* stats, int threads, int grid, void* scratch, size_t spc, int maxP) {
     const int prec = sizeof(R) == 8 ? 0 : 1;
     if (scratch) {
-        size_t smem = fullopt_smem_bytes(prec, C, ts.n, A.P, false, threads);
-        cudaFuncSetAttribute(k_fullopt<R, C, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        k_fullopt<R, C, false><<<grid, threads, smem, s>>>(M, A, cfg, ts, first, count, g, max_sweeps, lnl_out, stats,
+        const size_t smem = propose_smem_bytes(prec, C, maxP, false, threads);
+        cudaFuncSetAttribute(k_propose<R, C, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        k_propose<R, C, false><<<grid, threads, smem, s>>>(groups, gstart, ngroups, counter, cfg, stats,
                                                            reinterpret_cast<unsigned char*>(scratch), spc);
-        ++g_launches;
     } else {
-        size_t smem = fullopt_smem_bytes(prec, C, ts.n, A.P, true, threads);
-        cudaFuncSetAttribute(k_fullopt<R, C, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        k_fullopt<R, C, true><<<grid, threads, smem, s>>>(M, A, cfg, ts, first, count, g, max_sweeps, lnl_out, stats,
-                                                          nullptr, 0);
-        ++g_launches;
+        const size_t smem = propose_smem_bytes(prec, C, maxP, true, threads);
+        cudaFuncSetAttribute(k_propose<R, C, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        k_propose<R, C, true><<<grid, threads, smem, s>>>(groups, gstart, ngroups, counter, cfg, stats, nullptr, 0);
     }
+    ++g_launches;
+}
+template <typename R, int C>
+void fullopt_t(cudaStream_t s, const FullGroup* groups, const int* gstart, int ngroups, int* counter, int maxN,
+               int maxP, Cfg cfg, unsigned long long* stats, int threads, int grid, void* scratch, size_t spc) {
+    const int prec = sizeof(R) == 8 ? 0 : 1;
+    const int nn = 2 * maxN - 2;
+    if (scratch) {
+        const size_t smem = fullopt_smem_bytes(prec, C, maxN, maxP, false, threads);
+        cudaFuncSetAttribute(k_fullopt<R, C, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        k_fullopt<R, C, false><<<grid, threads, smem, s>>>(groups, gstart, ngroups, counter, nn, cfg, stats,
+                                                           reinterpret_cast<unsigned char*>(scratch), spc);
+    } else {
+        const size_t smem = fullopt_smem_bytes(prec, C, maxN, maxP, true, threads);
+        cudaFuncSetAttribute(k_fullopt<R, C, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        k_fullopt<R, C, true><<<grid, threads, smem, s>>>(groups, gstart, ngroups, counter, nn, cfg, stats, nullptr, 0);
+    }
+    ++g_launches;
 }
 }  // namespace
 
-void launch_fullopt(cudaStream_t s, int prec, const Model& M, Aln A, Cfg cfg, TreeSet ts, int first, int count,
-                    ClvGroup g, int max_sweeps, double* lnl_out, unsigned long long* stats, int threads, int grid,
-                    void* scratch, size_t scratch_per_cta) {
-    if (count <= 0) return;
+void launch_propose(cudaStream_t s, int prec, int C, const PropGroup* groups, const int* gstart, int ngroups,
+                    int* counter, Cfg cfg, unsigned long long* stats, int threads, int grid, void* scratch,
+                    size_t scratch_per_cta, int maxP) {
     if (prec == 0) {
-        if (M.C == 1) fullopt_t<double, 1>(s, M, A, cfg, ts, first, count, g, max_sweeps, lnl_out, stats, threads, grid, scratch, scratch_per_cta);
-        else fullopt_t<double, 4>(s, M, A, cfg, ts, first, count, g, max_sweeps, lnl_out, stats, threads, grid, scratch, scratch_per_cta);
+        if (C == 1) propose_t<double, 1>(s, groups, gstart, ngroups, counter, cfg, stats, threads, grid, scratch, scratch_per_cta, maxP);
+        else propose_t<double, 4>(s, groups, gstart, ngroups, counter, cfg, stats, threads, grid, scratch, scratch_per_cta, maxP);
     } else {
-        if (M.C == 1) fullopt_t<float, 1>(s, M, A, cfg, ts, first, count, g, max_sweeps, lnl_out, stats, threads, grid, scratch, scratch_per_cta);
-        else fullopt_t<float, 4>(s, M, A, cfg, ts, first, count, g, max_sweeps, lnl_out, stats, threads, grid, scratch, scratch_per_cta);
+        if (C == 1) propose_t<float, 1>(s, groups, gstart, ngroups, counter, cfg, stats, threads, grid, scratch, scratch_per_cta, maxP);
+        else propose_t<float, 4>(s, groups, gstart, ngroups, counter, cfg, stats, threads, grid, scratch, scratch_per_cta, maxP);
+    }
+}
+
+void launch_fullopt(cudaStream_t s, int prec, int C, const FullGroup* groups, const int* gstart, int ngroups,
+                    int* counter, int maxN, int maxP, Cfg cfg, unsigned long long* stats, int threads, int grid,
+                    void* scratch, size_t scratch_per_cta) {
+    if (prec == 0) {
+        if (C == 1) fullopt_t<double, 1>(s, groups, gstart, ngroups, counter, maxN, maxP, cfg, stats, threads, grid, scratch, scratch_per_cta);
+        else fullopt_t<double, 4>(s, groups, gstart, ngroups, counter, maxN, maxP, cfg, stats, threads, grid, scratch, scratch_per_cta);
+    } else {
+        if (C == 1) fullopt_t<float, 1>(s, groups, gstart, ngroups, counter, maxN, maxP, cfg, stats, threads, grid, scratch, scratch_per_cta);
+        else fullopt_t<float, 4>(s, groups, gstart, ngroups, counter, maxN, maxP, cfg, stats, threads, grid, scratch, scratch_per_cta);
     }
 }
 

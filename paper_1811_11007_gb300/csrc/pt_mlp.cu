@@ -517,9 +517,10 @@ __global__ void k_log_pairs(const Item* items, int i0, int i1, const float* Xf, 
     const Item it = items[k];
     const int brn[5] = {0, 1, it.swap == 0 ? 3 : 4, 2, it.swap == 0 ? 4 : 3};
     for (int c = threadIdx.x; c < kIn; c += blockDim.x) LX[slot * kIn + c] = Xf[(size_t)(k - i0) * kIn + c];
-    if (threadIdx.x < 5)
-        LT[slot * kMlpOut + threadIdx.x] =
-            (float)(log(len5[(size_t)k * 5 + brn[threadIdx.x]]) - (double)Xf[(size_t)(k - i0) * kIn + threadIdx.x]);
+    if (threadIdx.x < 5) {  // log-ratio target, clipped to +-4 (a factor of ~55) against heavy tails at the bounds
+        const double r = log(len5[(size_t)k * 5 + brn[threadIdx.x]]) - (double)Xf[(size_t)(k - i0) * kIn + threadIdx.x];
+        LT[slot * kMlpOut + threadIdx.x] = (float)fmin(4.0, fmax(-4.0, r));
+    }
 }
 
 inline int nblk(long long n, int t) { return (int)((n + t - 1) / t); }

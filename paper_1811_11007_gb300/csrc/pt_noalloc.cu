@@ -106,6 +106,7 @@ extern "C" pt_status pt_score_topologies_noalloc(int n_taxa, int n_patterns, con
     const size_t o_clv = take(G * up256(slots * P * 4 * M.C * rs));
     const size_t o_scl = take(G * up256(slots * P * 4));
     const size_t o_tab = take(grid_max * spc);
+    const size_t o_grp = take(sizeof(FullGroup) + 3 * sizeof(int));
     if (off > kNoAllocScratchBytes) return PT_ERR_INVALID_ARG;
 
     int32_t* err = reinterpret_cast<int32_t*>(base + o_err);
@@ -151,11 +152,29 @@ extern "C" pt_status pt_score_topologies_noalloc(int n_taxa, int n_patterns, con
     k.prop_max_sweeps = cfg.prop_max_sweeps;
     k.propose_mode = cfg.propose_mode;
     Aln A{n, P, tips_dev, weights_dev};
+    FullGroup* d_group = reinterpret_cast<FullGroup*>(base + o_grp);
+    int* d_gstart = reinterpret_cast<int*>(base + o_grp + sizeof(FullGroup));
+    int* d_counter = d_gstart + 2;
     for (size_t f0 = 0; f0 < T; f0 += G) {
         const int cnt = (int)std::min(G, T - f0);
         const int grid = (int)std::min<size_t>((size_t)cnt, grid_max);
-        launch_fullopt(stream, prec, M, A, k, ts, (int)f0, cnt, g, mode == PT_SCORE_FULL ? cfg.full_max_sweeps : 0,
-                       lnl_out_dev + f0, stats, threads, grid, smem_tab ? nullptr : base + o_tab, spc);
+        FullGroup gp;  // one group per chunk, written into the array (stream-ordered, staged copy)
+        gp.M = M;
+        gp.A = A;
+        gp.ts = ts;
+        gp.first = (int)f0;
+        gp.g = g;
+        gp.max_sweeps = mode == PT_SCORE_FULL ? cfg.full_max_sweeps : 0;
+        gp.lnl_out = lnl_out_dev + f0;
+        const int gs[2] = {0, cnt};
+        if (cudaMemcpyAsync(d_group, &gp, sizeof gp, cudaMemcpyHostToDevice, stream) != cudaSuccess ||
+            cudaMemcpyAsync(d_gstart, gs, sizeof gs, cudaMemcpyHostToDevice, stream) != cudaSuccess ||
+            cudaMemsetAsync(d_counter, 0, sizeof(int), stream) != cudaSuccess) {
+            cudaGetLastError();
+            return PT_ERR_CUDA;
+        }
+        launch_fullopt(stream, prec, M.C, d_group, d_gstart, 1, d_counter, n, P, k, stats, threads, grid,
+                       smem_tab ? nullptr : base + o_tab, spc);
     }
     launch_lengths_to_input(stream, n, n_trees, ts, lengths_out_dev);
     if (cudaGetLastError() != cudaSuccess) return PT_ERR_CUDA;

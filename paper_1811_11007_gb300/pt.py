@@ -25,7 +25,8 @@ EXPORTS = ["pt_config_default", "pt_create", "pt_destroy", "pt_last_error", "pt_
            "pt_expand_frontier", "pt_expand_frontier_dev", "pt_visited", "pt_reset_visited", "pt_stats",
            "pt_last_proposals", "pt_stage_times", "pt_version", "pt_discrete_gamma", "pt_model_eigen",
            "pt_score_topologies_noalloc", "pt_mlp_set_weights", "pt_mlp_get_weights", "pt_mlp_forward",
-           "pt_mlp_loss_grad", "pt_mlp_train", "pt_mlp_enable", "pt_training_log", "pt_training_pairs"]
+           "pt_mlp_loss_grad", "pt_mlp_train", "pt_mlp_enable", "pt_training_log", "pt_training_pairs",
+           "pt_expand_batch", "pt_expand_batch_dev"]
 MLP_PARAMS, MLP_IN, MLP_OUT = 27912, 69, 5
 _f32p = np.ctypeslib.ndpointer(np.float32, flags="C_CONTIGUOUS")
 
@@ -34,6 +35,13 @@ class PTError(RuntimeError):
     def __init__(self, status: int, msg: str):
         super().__init__(f"{STATUS.get(status, status)}: {msg}")
         self.status = status
+
+
+class Round(C.Structure):
+    _fields_ = [("aln_id", C.c_int), ("n_frontier", C.c_int), ("edges", C.c_void_p), ("lengths", C.c_void_p),
+                ("threshold", C.c_double), ("lmax", C.c_double), ("cap", C.c_int), ("kept_edges", C.c_void_p),
+                ("kept_lengths", C.c_void_p), ("kept_lnl", C.c_void_p), ("kept_keys", C.c_void_p),
+                ("n_kept", C.c_int)]
 
 
 class Config(C.Structure):
@@ -91,6 +99,8 @@ def lib():
             L.pt_version.restype = C.c_char_p
             L.pt_discrete_gamma.argtypes = [C.c_double, C.c_int, _f64p]
             L.pt_model_eigen.argtypes = [_f64p, _f64p, _f64p, _f64p]
+            L.pt_expand_batch.argtypes = [_vp, C.c_int, C.POINTER(Round)]
+            L.pt_expand_batch_dev.argtypes = [_vp, C.c_int, C.POINTER(Round)]
             L.pt_mlp_set_weights.argtypes = [_vp, _f32p, C.c_size_t]
             L.pt_mlp_get_weights.argtypes = [_vp, _f32p, C.c_size_t]
             L.pt_mlp_forward.argtypes = [_vp, C.c_int, _f32p, _f32p]
@@ -261,6 +271,29 @@ class Context:
         self._ck(st)
         k = cnt.value
         return lm.value, {"edges": fe[:k], "lengths": fl[:k], "lnl": fn[:k], "keys": fk[:k]}
+
+    def expand_batch(self, parts):
+        """One round on several alignments at once.  parts: list of dicts with
+        aln, edges, lengths, threshold, lmax.  Returns [(lmax, next frontier)]."""
+        keep = []
+        arr = (Round * len(parts))()
+        for k, p in enumerate(parts):
+            n = self._n[p["aln"]]
+            E = 2 * n - 3
+            e = np.ascontiguousarray(p["edges"], np.int32).reshape(-1, E, 2)
+            l = np.ascontiguousarray(p["lengths"], np.float64).reshape(e.shape[0], E)
+            cap = max(e.shape[0] * 2 * (n - 3), 1)
+            fe, fl, fn, fk = self._front_buffers(n, cap)
+            keep += [e, l, fe, fl, fn, fk]
+            arr[k] = Round(p["aln"], e.shape[0], e.ctypes.data, l.ctypes.data, float(p["threshold"]), float(p["lmax"]),
+                           cap, fe.ctypes.data, fl.ctypes.data, fn.ctypes.data, fk.ctypes.data, 0)
+        self._ck(lib().pt_expand_batch(self._h, len(parts), arr))
+        out = []
+        for k in range(len(parts)):
+            fe, fl, fn, fk = keep[6 * k + 2: 6 * k + 6]
+            c = arr[k].n_kept
+            out.append((arr[k].lmax, {"edges": fe[:c], "lengths": fl[:c], "lnl": fn[:c], "keys": fk[:c]}))
+        return out
 
     def expand_dev(self, aln: int, F: int, edges_ptr: int, lengths_ptr: int, threshold: float, lmax: float,
                    cap: int, out_edges_ptr: int, out_lengths_ptr: int, out_lnl_ptr: int, out_keys_ptr: int):
