@@ -134,6 +134,19 @@ def build_frontier(ctx, aid, starts, F):
     return lmax, {key: v[:k] for key, v in front.items()}, rounds
 
 
+def reduce_over_ranks(ms: float, units: float, world: int, device="cuda"):
+    """Whole-job timing: the slowest rank's time and the units of all ranks
+    (each rank runs its own independent alignment; no data-path collective)."""
+    if world <= 1:
+        return ms, units
+    import torch
+    t = torch.tensor([ms], device=device, dtype=torch.float64)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    u = torch.tensor([units], device=device, dtype=torch.float64)
+    torch.distributed.all_reduce(u)
+    return float(t.item()), float(u.item())
+
+
 def train_warm_start(ctx, rank):
     """Trains the warm-start network on proposals logged from PT searches on
     other alignments of the same shape (untimed set-up), then enables it."""
@@ -146,6 +159,7 @@ def train_warm_start(ctx, rank):
         # the same regime as the benchmark frontier: search (threshold 10) until
         # the frontier is large, then log the proposals of the next rounds
         lmax, front, _ = build_frontier(ctx, aid, synth.random_trees(N_TAXA, N_STARTS, seed + 1), 256)
+        ctx.reset_visited(aid)  # score the saved frontier's neighbours afresh, as a benchmark step does
         ctx.training_log(True, 1 << 20)
         for _ in range(3):
             if not len(front["edges"]):
@@ -185,6 +199,7 @@ def run_ours(args, rank, world, dev):
         return ctx, aid
 
     ctx, aid = make("mixed")
+    ctx.autotune(True)  # CTA sizes picked during the untimed set-up rounds
     learned = None
     if not args.no_mlp:
         learned = train_warm_start(ctx, rank)
@@ -233,12 +248,7 @@ def run_ours(args, rank, world, dev):
             torch.distributed.barrier()
         torch.cuda.synchronize()
         ms = e0.elapsed_time(e1)
-        if world > 1:
-            t = torch.tensor([ms], device=dev, dtype=torch.float64)
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            u = torch.tensor([units], device=dev, dtype=torch.float64)
-            torch.distributed.all_reduce(u)
-            ms, units = float(t.item()), float(u.item())
+        ms, units = reduce_over_ranks(ms, units, world, device=f"cuda:{dev}")
         return {"ms": ms, "units": units, "launches": launches, "prop_ms": prop_ms, "part_ms": part_ms,
                 "stats": stats, "flops": flops, "times": times}
 
@@ -337,7 +347,10 @@ def run_ours(args, rank, world, dev):
             "stage_ms_per_step": {k: v for k, v in res.get("times", {}).items()},
             "newton": {"prop_evals_per_neighbour": st["prop_evals"] / max(st["scored"], 1),
                        "prop_sweeps_per_neighbour": st["prop_sweeps"] / max(st["scored"], 1),
+                       "full_evals_per_kept_tree": st["full_evals"] / max(st["kept"], 1),
+                       "full_sweeps_per_kept_tree": st["full_sweeps"] / max(st["kept"], 1),
                        "nonconverged": st["nonconverged"]},
+            "autotune": ctx.autotune_report(),
             "gpu_launches": res["launches"],
             "clocks": clocks,
         }

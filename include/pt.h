@@ -201,6 +201,19 @@ pt_status pt_visited(pt_ctx *ctx, int aln_id, size_t cap, pt_key *keys, uint8_t 
  * an alignment. */
 pt_status pt_reset_visited(pt_ctx *ctx, int aln_id);
 
+/* Autotuning of the persistent kernels' CTA sizes.  When enabled, a launch
+ * of a problem bucket (precision, categories, taxa rounded up to a multiple
+ * of 8, patterns to a multiple of 256) that is large enough to fill the GPU
+ * (>= 4 work items per SM for the proposal kernel, >= 2 trees per SM for the
+ * full optimisation) and not yet tuned -- or 4x larger than the launch it was
+ * tuned on -- is timed at every candidate size (64 ... 512 threads, grid =
+ * resident CTAs x SMs) on the same inputs, and the fastest is kept for the
+ * bucket.  cache_path (may be NULL) is a JSON file read now and rewritten
+ * whenever a bucket is tuned. */
+pt_status pt_autotune(pt_ctx *ctx, int enable, const char *cache_path);
+/* The tuned table as JSON text (NUL-terminated, truncated to cap); *len = full length. */
+pt_status pt_autotune_report(pt_ctx *ctx, char *out, size_t cap, size_t *len);
+
 /* Counters of the last round (or begin / score call): [0] candidates, [1]
  * already visited, [2] scored (unique proposals), [3] kept, [4] good,
  * [5] proposal Newton evaluations, [6] full-optimisation Newton

@@ -58,6 +58,16 @@ struct Ctx {
     long long launches0 = 0;
     // last round's proposals, for pt_last_proposals
     int last_items = 0;
+    // autotuned CTA sizes of the persistent kernels, per problem bucket
+    struct Tune {
+        int prop_threads = 0, full_threads = 0;
+        double prop_ms = 0, full_ms = 0;
+        int prop_items = 0, full_items = 0;  // size of the launch each was tuned on
+        std::vector<std::pair<int, double>> prop_trials, full_trials;  // (threads, ms) of the tuning runs
+    };
+    bool autotune = false;
+    std::string tune_path;
+    std::map<std::string, Tune> tune;
     // learned warm start: FP32 master weights, gradients, Adam moments, BF16 copies
     float* mlp_w = nullptr;
     float* mlp_g = nullptr;
@@ -423,6 +433,79 @@ void validate_trees(Ctx& c, int n, int count, const int32_t* edges, const double
     }
 }
 
+// ---------------------------------------------------------------- autotuner
+// Problems are bucketed by precision, categories, taxa (multiple of 8) and
+// patterns (multiple of 256); per bucket the CTA sizes of the two persistent
+// kernels are picked by timing the first launch of the bucket with every
+// candidate size (grid = resident CTAs per SM x SMs), fastest kept.
+std::string tune_key(int prec, int C, int n, int P) {
+    char b[96];
+    snprintf(b, sizeof b, "prec%d_cat%d_taxa%d_patterns%d", prec, C, (n + 7) / 8 * 8, (P + 255) / 256 * 256);
+    return b;
+}
+
+const int kTuneThreads[] = {64, 96, 128, 192, 256, 384, 512};
+
+void save_tune(Ctx& c) {
+    if (c.tune_path.empty()) return;
+    std::string tmp = c.tune_path + ".tmp";
+    FILE* f = fopen(tmp.c_str(), "w");
+    if (!f) return;
+    fprintf(f, "{\n");
+    size_t i = 0;
+    for (auto& kv : c.tune) {
+        fprintf(f,
+                "  \"%s\": {\"prop_threads\": %d, \"full_threads\": %d, \"prop_ms\": %.4f, \"full_ms\": %.4f, "
+                "\"prop_items\": %d, \"full_items\": %d}%s\n",
+                kv.first.c_str(), kv.second.prop_threads, kv.second.full_threads, kv.second.prop_ms, kv.second.full_ms,
+                kv.second.prop_items, kv.second.full_items, ++i < c.tune.size() ? "," : "");
+    }
+    fprintf(f, "}\n");
+    fclose(f);
+    rename(tmp.c_str(), c.tune_path.c_str());
+}
+
+void load_tune(Ctx& c) {
+    FILE* f = fopen(c.tune_path.c_str(), "r");
+    if (!f) return;
+    std::string txt;
+    char b[4096];
+    size_t k;
+    while ((k = fread(b, 1, sizeof b, f)) > 0) txt.append(b, k);
+    fclose(f);
+    size_t p = 0;
+    while ((p = txt.find('"', p)) != std::string::npos) {
+        size_t q = txt.find('"', p + 1);
+        if (q == std::string::npos) break;
+        std::string key = txt.substr(p + 1, q - p - 1);
+        size_t ob = txt.find('{', q), cb = txt.find('}', q);
+        if (ob == std::string::npos || cb == std::string::npos || ob > cb) { p = q + 1; continue; }
+        std::string body = txt.substr(ob, cb - ob);
+        Ctx::Tune t;
+        auto num = [&](const char* name, double* out) {
+            size_t at = body.find(name);
+            if (at == std::string::npos) return false;
+            at = body.find(':', at);
+            return at != std::string::npos && sscanf(body.c_str() + at + 1, "%lf", out) == 1;
+        };
+        double v;
+        if (num("prop_threads", &v)) t.prop_threads = (int)v;
+        if (num("full_threads", &v)) t.full_threads = (int)v;
+        if (num("prop_ms", &v)) t.prop_ms = v;
+        if (num("full_ms", &v)) t.full_ms = v;
+        if (num("prop_items", &v)) t.prop_items = (int)v;
+        if (num("full_items", &v)) t.full_items = (int)v;
+        bool ok = true;
+        for (int x : {t.prop_threads, t.full_threads}) {
+            bool in = x == 0;
+            for (int cand : kTuneThreads) in = in || x == cand;
+            ok = ok && in;
+        }
+        if (ok && key.rfind("prec", 0) == 0) c.tune[key] = t;
+        p = cb + 1;
+    }
+}
+
 // ---------------------------------------------------------------- drivers
 // Uploads a group table and the prefix sums of the groups' item counts.
 template <typename G>
@@ -514,23 +597,86 @@ void run_full_jobs(Ctx& c, std::vector<FullJob> jobs) {
         }
         int total = 0;
         for (int x : counts) total += x;
-        const int threads = threads_for(c, maxP);
-        const bool smem_tab = fullopt_smem_bytes(prec, C, maxN, maxP, true, threads) <= c.smem_optin;
-        const int grid = std::min(total, 2 * c.sm_count);
-        void* scratch = nullptr;
-        size_t spc = 0;
-        if (!smem_tab) {
-            spc = (sumtable_bytes(prec, C, maxP) + 255) & ~size_t(255);
-            scratch = buf<unsigned char>(c, "full.scratch", spc * grid);
-        }
         const int* gstart;
         int* counter;
         const FullGroup* dg = upload_groups(c, "full", groups, counts, &gstart, &counter);
+        // one launch at a given CTA size; returns its device time when timed
+        auto run = [&](int threads, unsigned long long* stats, bool timed) {
+            const bool smem_tab = fullopt_smem_bytes(prec, C, maxN, maxP, true, threads) <= c.smem_optin;
+            const int bps = std::max(1, fullopt_blocks_per_sm(prec, C, threads, smem_tab, maxN, maxP));
+            const int grid = std::min(total, bps * c.sm_count);
+            void* scratch = nullptr;
+            size_t spc = 0;
+            if (!smem_tab) {
+                spc = (sumtable_bytes(prec, C, maxP) + 255) & ~size_t(255);
+                scratch = buf<unsigned char>(c, "full.scratch", spc * grid);
+            }
+            ck(c, cudaMemsetAsync(counter, 0, sizeof(int), c.stream), "counter");
+            size_t e0 = timed ? ev_record(c) : 0;
+            launch_fullopt(c.stream, prec, C, dg, gstart, (int)groups.size(), counter, maxN, maxP, kcfg(c), stats,
+                           threads, grid, scratch, spc);
+            ck(c, cudaGetLastError(), "full optimisation launch");
+            float ms = 0.f;
+            if (timed) {
+                size_t e1 = ev_record(c);
+                ck(c, cudaEventSynchronize(c.evpool[e1]), "event sync");
+                cudaEventElapsedTime(&ms, c.evpool[e0], c.evpool[e1]);
+            }
+            return (double)ms;
+        };
+        const std::string key = tune_key(prec, C, maxN, maxP);
+        int threads = threads_for(c, maxP);
+        auto it = c.tune.find(key);
+        const bool have = it != c.tune.end() && it->second.full_threads;
+        if (have) threads = it->second.full_threads;
+        // tune on launches with enough trees to fill the GPU, and again when a
+        // launch is much larger than the one the bucket was tuned on
+        const bool big = total >= 2 * c.sm_count && (!have || total >= 4 * it->second.full_items);
+        if (c.autotune && big) {
+            // the kernel writes the optimised lengths back: trials start from a saved copy
+            std::vector<std::pair<double*, size_t>> ranges;
+            size_t nlen = 0;
+            for (size_t g = 0; g < groups.size(); ++g) {
+                const int NN = 2 * groups[g].ts.n - 2;
+                ranges.push_back({groups[g].ts.len + (size_t)groups[g].first * NN, (size_t)counts[g] * NN});
+                nlen += (size_t)counts[g] * NN;
+            }
+            double* saved = buf<double>(c, "tune.len", nlen);
+            auto copy = [&](bool save) {
+                size_t o = 0;
+                for (auto& r : ranges) {
+                    ck(c, cudaMemcpyAsync(save ? saved + o : r.first, save ? r.first : saved + o, 8 * r.second,
+                                          cudaMemcpyDeviceToDevice, c.stream), "lengths copy");
+                    o += r.second;
+                }
+            };
+            copy(true);
+            unsigned long long* tstats = buf<unsigned long long>(c, "tune.stats", kStWords);
+            double best = 1e30;
+            std::vector<std::pair<int, double>> trials;
+            for (int cand : kTuneThreads) {
+                double ms = 1e30;
+                for (int rep = 0; rep < 2; ++rep) {  // best of two: single trials are noisy
+                    const double x = run(cand, tstats, true);
+                    copy(false);
+                    if (x > 0) ms = std::min(ms, x);
+                }
+                trials.push_back({cand, ms});
+                if (ms < best) { best = ms; threads = cand; }
+            }
+            // keep the default unless a candidate is clearly (>= 5%) faster
+            const int dflt = threads_for(c, maxP);
+            for (auto& tr : trials)
+                if (tr.first == dflt && tr.second <= best * 1.05) { threads = dflt; best = tr.second; }
+            c.tune[key].full_trials = trials;
+            c.tune[key].full_threads = threads;
+            c.tune[key].full_ms = best;
+            c.tune[key].full_items = total;
+            save_tune(c);
+        }
         Span sp(c, 6);
-        launch_fullopt(c.stream, prec, C, dg, gstart, (int)groups.size(), counter, maxN, maxP, kcfg(c), c.d_stats,
-                       threads, grid, scratch, spc);
+        run(threads, c.d_stats, false);
         sp.end();
-        ck(c, cudaGetLastError(), "full optimisation launch");
         k = e;
     }
 }
@@ -795,25 +941,66 @@ void expand_batch(Ctx& c, const std::vector<RoundIn>& ins, std::vector<RoundOut>
             maxP = std::max(maxP, a.P);
         }
         sp2.end();
-        int tot = 0;
+        int tot = 0, maxN = 3;
         for (int x : counts) tot += x;
-        const int threads = threads_for(c, maxP);
-        const bool smem_tab = propose_smem_bytes(prec, C, maxP, true, threads) <= c.smem_optin;
-        const int grid = std::min(tot, 4 * c.sm_count);
-        void* scratch = nullptr;
-        size_t spc = 0;
-        if (!smem_tab) {
-            spc = (sumtable_bytes(prec, C, maxP) + 255) & ~size_t(255);
-            scratch = buf<unsigned char>(c, "prop.scratch", spc * grid);
-        }
+        for (size_t q = ci; q < ce; ++q) maxN = std::max(maxN, ar[chunks[q].k].n);
         const int* gstart;
         int* counter;
         const PropGroup* dg = upload_groups(c, "prop", groups, counts, &gstart, &counter);
+        auto run = [&](int threads, unsigned long long* stats, bool timed) {
+            const bool smem_tab = propose_smem_bytes(prec, C, maxP, true, threads) <= c.smem_optin;
+            const int bps = std::max(1, propose_blocks_per_sm(prec, C, threads, smem_tab, maxP));
+            const int grid = std::min(tot, bps * c.sm_count);
+            void* scratch = nullptr;
+            size_t spc = 0;
+            if (!smem_tab) {
+                spc = (sumtable_bytes(prec, C, maxP) + 255) & ~size_t(255);
+                scratch = buf<unsigned char>(c, "prop.scratch", spc * grid);
+            }
+            ck(c, cudaMemsetAsync(counter, 0, sizeof(int), c.stream), "counter");
+            size_t e0 = timed ? ev_record(c) : 0;
+            launch_propose(c.stream, prec, C, dg, gstart, (int)groups.size(), counter, kcfg(c), stats, threads, grid,
+                           scratch, spc, maxP);
+            ck(c, cudaGetLastError(), "propose launch");
+            float ms = 0.f;
+            if (timed) {
+                size_t e1 = ev_record(c);
+                ck(c, cudaEventSynchronize(c.evpool[e1]), "event sync");
+                cudaEventElapsedTime(&ms, c.evpool[e0], c.evpool[e1]);
+            }
+            return (double)ms;
+        };
+        const std::string key = tune_key(prec, C, maxN, maxP);
+        int threads = threads_for(c, maxP);
+        auto tt = c.tune.find(key);
+        const bool have = tt != c.tune.end() && tt->second.prop_threads;
+        if (have) threads = tt->second.prop_threads;
+        const bool big = tot >= 4 * c.sm_count && (!have || tot >= 4 * tt->second.prop_items);
+        if (c.autotune && big) {  // trials rewrite the same outputs; inputs are not modified
+            unsigned long long* tstats = buf<unsigned long long>(c, "tune.stats", kStWords);
+            double best = 1e30;
+            std::vector<std::pair<int, double>> trials;
+            for (int cand : kTuneThreads) {
+                double ms = 1e30;
+                for (int rep = 0; rep < 2; ++rep) {  // best of two: single trials are noisy
+                    const double x = run(cand, tstats, true);
+                    if (x > 0) ms = std::min(ms, x);
+                }
+                trials.push_back({cand, ms});
+                if (ms < best) { best = ms; threads = cand; }
+            }
+            const int dflt = threads_for(c, maxP);
+            for (auto& tr : trials)
+                if (tr.first == dflt && tr.second <= best * 1.05) { threads = dflt; best = tr.second; }
+            c.tune[key].prop_trials = trials;
+            c.tune[key].prop_threads = threads;
+            c.tune[key].prop_ms = best;
+            c.tune[key].prop_items = tot;
+            save_tune(c);
+        }
         Span sp3(c, 3);
-        launch_propose(c.stream, prec, C, dg, gstart, (int)groups.size(), counter, kcfg(c), c.d_stats, threads, grid,
-                       scratch, spc, maxP);
+        run(threads, c.d_stats, false);
         sp3.end();
-        ck(c, cudaGetLastError(), "propose launch");
         if (c.log_on)
             for (size_t q = ci; q < ce; ++q) {
                 const Chunk& ch = chunks[q];
@@ -1299,6 +1486,47 @@ pt_status pt_reset_visited(pt_ctx* ctx, int aln_id) {
         AlnState& a = aln_of(c, aln_id, false);
         reset_table(c, a);
         ck(c, cudaStreamSynchronize(c.stream), "sync");
+    });
+}
+
+pt_status pt_autotune(pt_ctx* ctx, int enable, const char* cache_path) {
+    return guarded(ctx, [&](Ctx& c) {
+        c.autotune = enable != 0;
+        c.tune_path = cache_path ? cache_path : "";
+        if (!c.tune_path.empty()) load_tune(c);
+    });
+}
+
+pt_status pt_autotune_report(pt_ctx* ctx, char* out, size_t cap, size_t* len) {
+    return guarded(ctx, [&](Ctx& c) {
+        std::string txt = "{";
+        size_t i = 0;
+        for (auto& kv : c.tune) {
+            char b[256];
+            snprintf(b, sizeof b,
+                     "\"%s\": {\"prop_threads\": %d, \"full_threads\": %d, \"prop_ms\": %.4f, \"full_ms\": %.4f, "
+                     "\"prop_items\": %d, \"full_items\": %d",
+                     kv.first.c_str(), kv.second.prop_threads, kv.second.full_threads, kv.second.prop_ms,
+                     kv.second.full_ms, kv.second.prop_items, kv.second.full_items);
+            txt += b;
+            for (int w = 0; w < 2; ++w) {
+                const auto& tr = w == 0 ? kv.second.prop_trials : kv.second.full_trials;
+                txt += w == 0 ? ", \"prop_trials\": {" : ", \"full_trials\": {";
+                for (size_t j = 0; j < tr.size(); ++j) {
+                    snprintf(b, sizeof b, "%s\"%d\": %.4f", j ? ", " : "", tr[j].first, tr[j].second);
+                    txt += b;
+                }
+                txt += "}";
+            }
+            txt += ++i < c.tune.size() ? "}, " : "}";
+        }
+        txt += "}";
+        if (len) *len = txt.size();
+        if (out && cap) {
+            size_t k = std::min(cap - 1, txt.size());
+            memcpy(out, txt.data(), k);
+            out[k] = 0;
+        }
     });
 }
 

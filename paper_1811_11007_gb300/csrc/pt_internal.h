@@ -188,6 +188,10 @@ void launch_fullopt(cudaStream_t s, int prec, int C, const FullGroup* groups, co
 // GTR+Gamma model set-up on the host (pt_api.cu); false on invalid parameters.
 bool host_build_model(const double exch[6], const double freqs[4], double alpha, int C, Model& M);
 
+// Resident CTAs per SM of the two persistent kernels at a given CTA size (occupancy API).
+int propose_blocks_per_sm(int prec, int C, int threads, bool smem_tab, int maxP);
+int fullopt_blocks_per_sm(int prec, int C, int threads, bool smem_tab, int maxN, int maxP);
+
 // Kernels launched so far by this process (all contexts).
 long long launch_count();
 

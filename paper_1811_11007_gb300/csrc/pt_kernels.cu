@@ -1689,6 +1689,50 @@ void fullopt_t(cudaStream_t s, const FullGroup* groups, const int* gstart, int n
 }
 }  // namespace
 
+namespace {
+template <typename R, int C>
+int prop_occ(int threads, bool smem_tab, int maxP) {
+    const int prec = sizeof(R) == 8 ? 0 : 1;
+    const size_t smem = propose_smem_bytes(prec, C, maxP, smem_tab, threads);
+    int nb = 0;
+    if (smem_tab) {
+        cudaFuncSetAttribute(k_propose<R, C, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_propose<R, C, true>, threads, smem);
+    } else {
+        cudaFuncSetAttribute(k_propose<R, C, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_propose<R, C, false>, threads, smem);
+    }
+    cudaGetLastError();
+    return nb;
+}
+template <typename R, int C>
+int full_occ(int threads, bool smem_tab, int maxN, int maxP) {
+    const int prec = sizeof(R) == 8 ? 0 : 1;
+    const size_t smem = fullopt_smem_bytes(prec, C, maxN, maxP, smem_tab, threads);
+    int nb = 0;
+    if (smem_tab) {
+        cudaFuncSetAttribute(k_fullopt<R, C, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_fullopt<R, C, true>, threads, smem);
+    } else {
+        cudaFuncSetAttribute(k_fullopt<R, C, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_fullopt<R, C, false>, threads, smem);
+    }
+    cudaGetLastError();
+    return nb;
+}
+}  // namespace
+
+int propose_blocks_per_sm(int prec, int C, int threads, bool smem_tab, int maxP) {
+    if (prec == 0) return C == 1 ? prop_occ<double, 1>(threads, smem_tab, maxP) : prop_occ<double, 4>(threads, smem_tab, maxP);
+    return C == 1 ? prop_occ<float, 1>(threads, smem_tab, maxP) : prop_occ<float, 4>(threads, smem_tab, maxP);
+}
+
+int fullopt_blocks_per_sm(int prec, int C, int threads, bool smem_tab, int maxN, int maxP) {
+    if (prec == 0)
+        return C == 1 ? full_occ<double, 1>(threads, smem_tab, maxN, maxP) : full_occ<double, 4>(threads, smem_tab, maxN, maxP);
+    return C == 1 ? full_occ<float, 1>(threads, smem_tab, maxN, maxP) : full_occ<float, 4>(threads, smem_tab, maxN, maxP);
+}
+
 void launch_propose(cudaStream_t s, int prec, int C, const PropGroup* groups, const int* gstart, int ngroups,
                     int* counter, Cfg cfg, unsigned long long* stats, int threads, int grid, void* scratch,
                     size_t scratch_per_cta, int maxP) {

@@ -26,7 +26,7 @@ EXPORTS = ["pt_config_default", "pt_create", "pt_destroy", "pt_last_error", "pt_
            "pt_last_proposals", "pt_stage_times", "pt_version", "pt_discrete_gamma", "pt_model_eigen",
            "pt_score_topologies_noalloc", "pt_mlp_set_weights", "pt_mlp_get_weights", "pt_mlp_forward",
            "pt_mlp_loss_grad", "pt_mlp_train", "pt_mlp_enable", "pt_training_log", "pt_training_pairs",
-           "pt_expand_batch", "pt_expand_batch_dev"]
+           "pt_expand_batch", "pt_expand_batch_dev", "pt_autotune", "pt_autotune_report"]
 MLP_PARAMS, MLP_IN, MLP_OUT = 27912, 69, 5
 _f32p = np.ctypeslib.ndpointer(np.float32, flags="C_CONTIGUOUS")
 
@@ -99,6 +99,8 @@ def lib():
             L.pt_version.restype = C.c_char_p
             L.pt_discrete_gamma.argtypes = [C.c_double, C.c_int, _f64p]
             L.pt_model_eigen.argtypes = [_f64p, _f64p, _f64p, _f64p]
+            L.pt_autotune.argtypes = [_vp, C.c_int, C.c_char_p]
+            L.pt_autotune_report.argtypes = [_vp, C.c_char_p, C.c_size_t, C.POINTER(C.c_size_t)]
             L.pt_expand_batch.argtypes = [_vp, C.c_int, C.POINTER(Round)]
             L.pt_expand_batch_dev.argtypes = [_vp, C.c_int, C.POINTER(Round)]
             L.pt_mlp_set_weights.argtypes = [_vp, _f32p, C.c_size_t]
@@ -329,6 +331,17 @@ class Context:
         out = (C.c_double * 7)()
         self._ck(lib().pt_stage_times(self._h, out, 7))
         return dict(zip(["canon", "dedup", "partials", "propose", "visit", "total", "fullopt_kernel"], list(out)))
+
+    def autotune(self, enable: bool = True, cache_path: str | None = None):
+        self._ck(lib().pt_autotune(self._h, 1 if enable else 0, cache_path.encode() if cache_path else None))
+
+    def autotune_report(self) -> dict:
+        import json
+        n = C.c_size_t()
+        self._ck(lib().pt_autotune_report(self._h, None, 0, C.byref(n)))
+        b = C.create_string_buffer(n.value + 1)
+        self._ck(lib().pt_autotune_report(self._h, b, n.value + 1, C.byref(n)))
+        return json.loads(b.value.decode())
 
     # ---- learned warm start
     def mlp_set_weights(self, w):
