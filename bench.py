@@ -204,8 +204,10 @@ def run_ours(args, rank, world, dev):
     if not args.no_mlp:
         learned = train_warm_start(ctx, rank)
     lmax0, front, setup_rounds = build_frontier(ctx, aid, starts, args.frontier)
-    # proposal-kernel launches before the first timed step (one per round), for profilers
+    # launches of the two persistent kernels before the first timed step, for profilers
+    # (one proposal and one full-optimisation launch per round; begin adds one of the latter)
     print(f"propose_launches_before_timed={setup_rounds + args.warmup}", file=sys.stderr)
+    print(f"fullopt_launches_before_timed={setup_rounds + args.warmup + 1}", file=sys.stderr)
     F = len(front["edges"])
     _, P = ctx.alignment_info(aid)
     d_e = torch.from_numpy(np.ascontiguousarray(front["edges"])).to(dev)
