@@ -859,24 +859,6 @@ __device__ __forceinline__ void put_egh(const Model& M, double t, NewtonSmem<R, 
     }
 }
 
-// P_r(t) for all categories into Pdst [C][16] (FP64 exponentials, rounded
-// once).  Two phases with a barrier between; the caller syncs after.
-template <typename R, int C>
-__device__ __forceinline__ void refresh_pmat(const Model& M, double t, R* Pdst, NewtonSmem<R, C>& ns) {
-    if (threadIdx.x < 4 * C) {
-        int r = threadIdx.x >> 2, k = threadIdx.x & 3;
-        ns.ex[threadIdx.x] = exp(M.lam[k] * M.rates[r] * t);
-    }
-    __syncthreads();
-    for (int x = threadIdx.x; x < 16 * C; x += blockDim.x) {
-        int r = x >> 4, ij = x & 15;
-        double acc = 0.0;
-#pragma unroll
-        for (int k = 0; k < 4; ++k) acc += ns.W[ij * 4 + k] * ns.ex[r * 4 + k];
-        Pdst[x] = (R)acc;
-    }
-}
-
 // Safeguarded Newton step: bracket [lo, hi]; Newton point when d2 < 0 and
 // strictly inside, else sqrt(lo*hi).  Returns true when converged.
 __device__ __forceinline__ bool newton_step(double& t, double& lo, double& hi, double d1, double d2, double tol) {
@@ -959,10 +941,12 @@ __device__ double eval_lnl(const Model& M, const STab<R, C>& st, int P, double t
 // Newton solve on the current sum-table from t0.  Per evaluation: every
 // thread sums w L'/L and w (L''/L - (L'/L)^2) over its sites, the warps
 // reduce, and warp 0 alone takes the FP64 step and writes the coefficients
-// of the next length.  Returns the final length (in every thread).
+// of the next length; after the last step warp 0 also writes P_r(t) of the
+// final length into Pdst [C][16] (visible when the call returns).  Returns
+// the final length (in every thread).
 template <typename R, int C>
 __device__ double newton_solve(const Model& M, const Cfg& cfg, const STab<R, C>& st, int P, double t0,
-                               NewtonSmem<R, C>& ns, int& evals, bool& converged) {
+                               NewtonSmem<R, C>& ns, int& evals, bool& converged, R* Pdst) {
     double lo = cfg.tmin, hi = cfg.tmax;
     double t = fmin(fmax(t0, lo), hi);
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = (blockDim.x + 31) >> 5;
@@ -1015,12 +999,25 @@ __device__ double newton_solve(const Model& M, const Cfg& cfg, const STab<R, C>&
             }
             D1 = warp_sum(D1);
             D2 = warp_sum(D2);
-            bool done = newton_step(t, lo, hi, D1, D2, cfg.newton_tol);
-            if (!done) put_egh<R, C>(M, t, ns, false);
-            if (lane == 0) { ns.tb = t; ns.done = done; }
+            const bool done = newton_step(t, lo, hi, D1, D2, cfg.newton_tol);
+            const bool last = done || it + 1 == cfg.newton_maxit;
+            if (!last) {
+                put_egh<R, C>(M, t, ns, false);
+            } else {  // P matrices of the final length (FP64 exponentials, rounded once)
+                if (lane < 4 * C) ns.ex[lane] = exp(ns.lr[lane] * t);
+                __syncwarp();
+                for (int x = lane; x < 16 * C; x += 32) {
+                    const int r = x >> 4, ij = x & 15;
+                    double acc = 0.0;
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) acc += ns.W[ij * 4 + k] * ns.ex[r * 4 + k];
+                    Pdst[x] = (R)acc;
+                }
+            }
+            if (lane == 0) { ns.tb = t; ns.done = last ? (done ? 1 : 2) : 0; }
         }
         __syncthreads();
-        if (ns.done) { converged = true; break; }
+        if (ns.done) { converged = ns.done == 1; break; }
     }
     return ns.tb;
 }
@@ -1223,6 +1220,7 @@ __global__ void __launch_bounds__(512) k_propose(const PropGroup* __restrict__ g
             }
             __syncthreads();
         }
+        double tlast = 0.0;  // length of the last branch solved (every thread)
         int sweeps = 0;
         for (int sw = 0; sw < cfg.prop_max_sweeps; ++sw) {
             ++sweeps;
@@ -1270,19 +1268,18 @@ __global__ void __launch_bounds__(512) k_propose(const PropGroup* __restrict__ g
                 const double told = sm.T[b];
                 int ev;
                 bool conv;
-                double t = newton_solve<R, C>(M, cfg, st, P, told, sm.ns, ev, conv);
+                // new length; the solve leaves P matrices of branch b at it in sm.Pm[b]
+                const double t = newton_solve<R, C>(M, cfg, st, P, told, sm.ns, ev, conv, sm.Pm[b]);
                 moved = fmax(moved, fabs(t - told));
                 evals_total += ev;
                 if (!conv) ++nonconv;
-                // new length and P matrices of branch b
-                refresh_pmat<R, C>(M, t, sm.Pm[b], sm.ns);
-                if (threadIdx.x == 0) sm.T[b] = t;
-                __syncthreads();
+                if (threadIdx.x == 0) sm.T[b] = t;  // read again only after later barriers
+                tlast = t;
             }
             if (moved <= cfg.sweep_tol) break;
         }
         // exact lnL at the final lengths: the last sum-table at its new length
-        const double f1 = eval_lnl<R, C>(M, st, P, sm.T[nb - 1], sm.ns);
+        const double f1 = eval_lnl<R, C>(M, st, P, tlast, sm.ns);
         sweeps_total += sweeps;
         if (threadIdx.x == 0) {
             G.lnl_out[o] = f1;
@@ -1432,6 +1429,7 @@ __global__ void __launch_bounds__(512) k_fullopt(const FullGroup* __restrict__ g
         // bottom-up D pass
         for (int v = NN - 1; v >= n; --v) refreshD(v);
         int sweeps = 0, last = n;
+        double tlast = 0.0;
         const int nsched = 3 * n - 5;
         if (G.max_sweeps == 0) visit_build(n);
         for (int sw = 0; sw < G.max_sweeps; ++sw) {
@@ -1445,19 +1443,19 @@ __global__ void __launch_bounds__(512) k_fullopt(const FullGroup* __restrict__ g
                 const double told = len[v];
                 int ev;
                 bool conv;
-                const double t = newton_solve<R, C>(M, cfg, st, P, told, sm.ns, ev, conv);
+                // the solve leaves the P matrices of edge v at its new length in Pm
+                const double t = newton_solve<R, C>(M, cfg, st, P, told, sm.ns, ev, conv, Pm + (size_t)v * C * 16);
                 moved = fmax(moved, fabs(t - told));
                 evals_total += ev;
                 if (!conv) ++nonconv;
-                refresh_pmat<R, C>(M, t, Pm + (size_t)v * C * 16, sm.ns);
-                if (threadIdx.x == 0) len[v] = t;
-                __syncthreads();
+                if (threadIdx.x == 0) len[v] = t;  // read again only after later barriers
                 last = v;
+                tlast = t;
             }
             if (moved <= cfg.sweep_tol) break;
         }
         // exact lnL at the final lengths (the last visited edge's sum-table)
-        const double f1 = eval_lnl<R, C>(M, st, P, len[last], sm.ns);
+        const double f1 = eval_lnl<R, C>(M, st, P, G.max_sweeps == 0 ? len[n] : tlast, sm.ns);
         sweeps_total += sweeps;
         __syncthreads();
         for (int v = threadIdx.x; v < NN; v += blockDim.x) glen[v] = len[v];
