@@ -679,6 +679,14 @@ __device__ __forceinline__ void store_vec(R* dst, int p, const R* y) {
     }
 }
 
+// L2 prefetch hint for [p, p + bytes): the block's threads request its
+// 128-byte lines in turn (every address lies inside the range).
+__device__ __forceinline__ void prefetch_l2(const void* p, size_t bytes) {
+    const char* c = static_cast<const char*>(p);
+    for (size_t o = (size_t)threadIdx.x * 128; o < bytes; o += (size_t)blockDim.x * 128)
+        asm volatile("prefetch.global.L2 [%0];" ::"l"(c + o));
+}
+
 // threshold rescale of a stored vector
 template <typename R, int C>
 __device__ __forceinline__ int rescale(R* y) {
@@ -790,10 +798,12 @@ struct NewtonSmem {
     double red[32][2];     // per-warp partial sums
     float redf[32][4];     // per-warp partial sums as FP32 pairs (hi, lo) x (d1, d2)
     double lr[4 * C];      // lam_k * rate_r
+    float lrf[4 * C];      // the same in FP32 (coefficients of the Newton derivatives)
     double ex[4 * C];      // exp(lam_k r t) for a P-matrix refresh
     double W[64];          // W[(i*4+j)*4+k] = isqpi_i sqpi_j R_ik R_jk: P_ij = sum_k W_ijk exp(lam_k r t)
     double tb;             // broadcast of the current length
     int done;
+    int leader;            // the warp that takes the Newton steps
 };
 
 __device__ __forceinline__ double warp_sum(double x) {
@@ -825,17 +835,34 @@ __device__ __forceinline__ void init_newton_smem(const Model& M, NewtonSmem<R, C
         int k = x & 3, ij = x >> 2, i = ij >> 2, j = ij & 3;
         ns.W[x] = M.isqpi[i] * M.sqpi[j] * M.R[i * 4 + k] * M.R[j * 4 + k];
     }
-    for (int q = threadIdx.x; q < 4 * C; q += blockDim.x) ns.lr[q] = M.lam[q & 3] * M.rates[q >> 2];
+    if (threadIdx.x == 0) {
+        // Leader warp: FP64 instructions issue slowly and only on the issuing warp's
+        // scheduler, so blocks sharing an SM should not all lead from the same one.
+        // Warp slots of a block are taken to be consecutive and schedulers to be
+        // slot mod 4; a wrong guess costs time only.
+        unsigned slot;
+        asm volatile("mov.u32 %0, %%warpid;" : "=r"(slot));
+        const int nw = (blockDim.x + 31) >> 5;
+        const int want = (int)((slot / nw) & 3);
+        int lead = 0;
+        for (int w = 0; w < nw && w < 4; ++w)
+            if ((int)((slot + w) & 3) == want) { lead = w; break; }
+        ns.leader = lead;
+    }
+    for (int q = threadIdx.x; q < 4 * C; q += blockDim.x) {
+        ns.lr[q] = M.lam[q & 3] * M.rates[q >> 2];
+        ns.lrf[q] = (float)ns.lr[q];
+    }
 }
 
 // Coefficients at branch length t on the sum-table (see sumtable()): egh[0]
 // gives L (1 for the stationary slot, expm1(lam r t) otherwise), egh[1] and
 // egh[2] give dL/dt and d2L/dt2; all divided by C.  Called by the first 4C
-// threads.  exact = FP64 exponentials rounded once (for lnL), otherwise the
+// threads (or the lanes q of one warp).  exact = FP64 exponentials rounded once (for lnL), otherwise the
 // working precision's own (for Newton derivatives).
 template <typename R, int C>
-__device__ __forceinline__ void put_egh(const Model& M, double t, NewtonSmem<R, C>& ns, bool exact) {
-    int q = threadIdx.x;
+__device__ __forceinline__ void put_egh(const Model& M, double t, NewtonSmem<R, C>& ns, bool exact,
+                                        int q = threadIdx.x) {
     if (q < 4 * C) {
         int r = q >> 2, k = q & 3;
         if (k == 0) {
@@ -850,7 +877,7 @@ __device__ __forceinline__ void put_egh(const Model& M, double t, NewtonSmem<R, 
                 ns.egh[1][q] = (R)(lr * e);
                 ns.egh[2][q] = (R)(lr * lr * e);
             } else {
-                float x = (float)(lr * t), l = (float)lr, e = expf(x) * (1.0f / C);
+                const float l = ns.lrf[q], x = l * (float)t, e = expf(x) * (1.0f / C);
                 ns.egh[0][q] = (R)(expm1f(x) * (1.0f / C));
                 ns.egh[1][q] = (R)(l * e);
                 ns.egh[2][q] = (R)(l * l * e);
@@ -861,13 +888,51 @@ __device__ __forceinline__ void put_egh(const Model& M, double t, NewtonSmem<R, 
 
 // Safeguarded Newton step: bracket [lo, hi]; Newton point when d2 < 0 and
 // strictly inside, else sqrt(lo*hi).  Returns true when converged.
-__device__ __forceinline__ bool newton_step(double& t, double& lo, double& hi, double d1, double d2, double tol) {
-    if (d1 == 0.0) return true;
-    if (d1 > 0.0) lo = t; else hi = t;
-    double tn = t - d1 / d2;
-    if (!(d2 < 0.0 && tn > lo && tn < hi)) tn = sqrt(lo * hi);
-    bool conv = fabs(tn - t) <= tol;
-    t = tn;
+//
+// Written for the one warp that takes the step while the rest of the block
+// waits: FP64 instructions issue at a small fraction of the FP32 rate, so the
+// comparisons are done on the IEEE bit patterns with integer instructions
+// (t, lo, hi are positive and finite, so their patterns order like the
+// values), and d1/d2 is a reciprocal seed refined by one Newton-Raphson
+// correction of the quotient (Markstein's scheme: q = q0 + r (d1 - d2 q0)),
+// accurate to about 2^-46 relative; NaN and infinite quotients fail the
+// bracket test and fall back to the midpoint, as in plain IEEE arithmetic.
+__device__ __forceinline__ bool dbl_pos(double x) {  // x > 0 (false for NaN)
+    const long long b = __double_as_longlong(x);
+    return b > 0 && b <= 0x7ff0000000000000LL;
+}
+__device__ __forceinline__ bool dbl_neg(double x) {  // x < 0 (false for NaN, -0)
+    const long long a = __double_as_longlong(x) & 0x7fffffffffffffffLL;
+    return __double_as_longlong(x) < 0 && a != 0 && a <= 0x7ff0000000000000LL;
+}
+// d2f: an FP32 estimate of d2, available before d2 itself (the reciprocal
+// seed then stays off the FP64 dependency chain); on the Newton branch the
+// convergence test uses the increment itself.
+__device__ __forceinline__ bool newton_step(double& t, double& lo, double& hi, double d1, double d2, float d2f,
+                                            double tol) {
+    const long long b1 = __double_as_longlong(d1);
+    if ((b1 & 0x7fffffffffffffffLL) == 0) return true;  // d1 == 0
+    if (dbl_pos(d1)) lo = t; else hi = t;
+    double r = (double)__frcp_rn(d2f);
+    double q0 = d1 * r;
+    double e = fma(-d2, q0, d1);
+    // a seed off by more than ~2^-10 (d2f lost to cancellation): reseed from d2 (rare)
+    const int xe = (int)((__double_as_longlong(e) >> 52) & 0x7ff), x1 = (int)((b1 >> 52) & 0x7ff);
+    if (xe > x1 - 10) {
+        r = (double)__frcp_rn(__double2float_rn(d2));
+        q0 = d1 * r;
+        e = fma(-d2, q0, d1);
+    }
+    const double q = fma(e, r, q0);
+    const double tn = t - q;
+    const long long bt = __double_as_longlong(tn);
+    if (dbl_neg(d2) && bt > __double_as_longlong(lo) && bt < __double_as_longlong(hi)) {
+        t = tn;
+        return (__double_as_longlong(q) & 0x7fffffffffffffffLL) <= __double_as_longlong(tol);
+    }
+    const double tm = sqrt(lo * hi);
+    const bool conv = (__double_as_longlong(tm - t) & 0x7fffffffffffffffLL) <= __double_as_longlong(tol);
+    t = tm;
     return conv;
 }
 
@@ -950,9 +1015,11 @@ __device__ double newton_solve(const Model& M, const Cfg& cfg, const STab<R, C>&
     double lo = cfg.tmin, hi = cfg.tmax;
     double t = fmin(fmax(t0, lo), hi);
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = (blockDim.x + 31) >> 5;
+    const int top = nw > 8 ? 8 : nw > 4 ? 4 : nw > 2 ? 2 : 1;  // first butterfly offset
     put_egh<R, C>(M, t, ns, false);
     if (threadIdx.x == 0) ns.tb = t;
     __syncthreads();
+    const int ld = ns.leader;
     converged = false;
     evals = 0;
     for (int it = 0; it < cfg.newton_maxit; ++it) {
@@ -985,39 +1052,50 @@ __device__ double newton_solve(const Model& M, const Cfg& cfg, const STab<R, C>&
         }
         __syncthreads();
         ++evals;
-        if (w == 0) {
-            // lanes 0..nw-1 take one warp's pair each; an FP64 butterfly gives every lane the totals
-            double D1 = 0.0, D2 = 0.0;
-            if (lane < nw) {
+        if (w == ld) {
+            // Both derivative sums in one FP64 butterfly: lane j < nw holds warp j's
+            // d1 partial, lane 16 + j its d2 partial; offsets below 16 keep the halves
+            // apart.  An FP32 sum of the same words runs alongside (reciprocal seed).
+            const int src = lane & 15, half = lane >> 4;
+            double D = 0.0;
+            float Df = 0.f;
+            if (src < nw) {
                 if constexpr (sizeof(R) == 4) {
-                    D1 = (double)ns.redf[lane][0] + (double)ns.redf[lane][1];
-                    D2 = (double)ns.redf[lane][2] + (double)ns.redf[lane][3];
+                    const float h = ns.redf[src][2 * half], l = ns.redf[src][2 * half + 1];
+                    D = (double)h + (double)l;
+                    Df = h;
                 } else {
-                    D1 = ns.red[lane][0];
-                    D2 = ns.red[lane][1];
+                    D = ns.red[src][half];
+                    Df = (float)D;
                 }
             }
-            D1 = warp_sum(D1);
-            D2 = warp_sum(D2);
-            const bool done = newton_step(t, lo, hi, D1, D2, cfg.newton_tol);
+            for (int o = top; o; o >>= 1) {
+                D += __shfl_xor_sync(0xffffffffu, D, o);
+                Df += __shfl_xor_sync(0xffffffffu, Df, o);
+            }
+            const double D1 = __shfl_sync(0xffffffffu, D, 0), D2 = __shfl_sync(0xffffffffu, D, 16);
+            const float D2f = __shfl_sync(0xffffffffu, Df, 16);
+            const bool done = newton_step(t, lo, hi, D1, D2, D2f, cfg.newton_tol);
             const bool last = done || it + 1 == cfg.newton_maxit;
-            if (!last) {
-                put_egh<R, C>(M, t, ns, false);
-            } else {  // P matrices of the final length (FP64 exponentials, rounded once)
-                if (lane < 4 * C) ns.ex[lane] = exp(ns.lr[lane] * t);
-                __syncwarp();
-                for (int x = lane; x < 16 * C; x += 32) {
-                    const int r = x >> 4, ij = x & 15;
-                    double acc = 0.0;
-#pragma unroll
-                    for (int k = 0; k < 4; ++k) acc += ns.W[ij * 4 + k] * ns.ex[r * 4 + k];
-                    Pdst[x] = (R)acc;
-                }
-            }
+            if (!last) put_egh<R, C>(M, t, ns, false, lane);
+            else if (lane < 4 * C) ns.ex[lane] = exp(ns.lr[lane] * t);  // for the P matrices below
             if (lane == 0) { ns.tb = t; ns.done = last ? (done ? 1 : 2) : 0; }
         }
         __syncthreads();
-        if (ns.done) { converged = ns.done == 1; break; }
+        if (ns.done) {
+            // P matrices of the final length (FP64 exponentials, rounded once), spread
+            // over the first warps so their FP64 work runs on several schedulers
+            converged = ns.done == 1;
+            for (int x = threadIdx.x; x < 16 * C; x += blockDim.x) {
+                const int r = x >> 4, ij = x & 15;
+                double acc = 0.0;
+#pragma unroll
+                for (int k = 0; k < 4; ++k) acc += ns.W[ij * 4 + k] * ns.ex[r * 4 + k];
+                Pdst[x] = (R)acc;
+            }
+            __syncthreads();
+            break;
+        }
     }
     return ns.tb;
 }
@@ -1426,6 +1504,28 @@ __global__ void __launch_bounds__(512) k_fullopt(const FullGroup* __restrict__ g
                 st.put(p, s4, (R)(ex + ey - Prec<R>::kScaleExp * (cx + cy)), (R)A.w[p]);
             }
         };
+        // the stored vectors an operation of the schedule reads, requested into L2
+        // while the operation before it runs (its Newton iterations touch no HBM)
+        auto prefetch_op = [&](int op) {
+            const size_t vb = (size_t)P * 4 * C * sizeof(R);
+            auto slot = [&](int sl) {
+                prefetch_l2(clv + (size_t)sl * sstride, vb);
+                prefetch_l2(scl + (size_t)sl * P, (size_t)P * 4);
+            };
+            if (op & kUpd) {
+                const int w = op & (kUpd - 1);
+                if (ch[2 * w] >= n) slot(ch[2 * w] - n);
+                if (ch[2 * w + 1] >= n) slot(ch[2 * w + 1] - n);
+                return;
+            }
+            if (op != n) {
+                const int u = up[op];
+                const int sib = ch[2 * u] == op ? ch[2 * u + 1] : ch[2 * u];
+                if (sib >= n) slot(sib - n);
+                if (u != n) slot(n - 2 + (u - n - 1));
+            }
+            if (op >= n) slot(op - n);
+        };
         // bottom-up D pass
         for (int v = NN - 1; v >= n; --v) refreshD(v);
         int sweeps = 0, last = n;
@@ -1437,9 +1537,14 @@ __global__ void __launch_bounds__(512) k_fullopt(const FullGroup* __restrict__ g
             double moved = 0.0;
             for (int k = 0; k < nsched; ++k) {
                 const int op = sched[k];
-                if (op & kUpd) { refreshD(op & (kUpd - 1)); continue; }
+                if (op & kUpd) {
+                    if (k + 1 < nsched) prefetch_op(sched[k + 1]);
+                    refreshD(op & (kUpd - 1));
+                    continue;
+                }
                 const int v = op;
                 visit_build(v);
+                if (k + 1 < nsched) prefetch_op(sched[k + 1]);
                 const double told = len[v];
                 int ev;
                 bool conv;
