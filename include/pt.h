@@ -189,6 +189,60 @@ pt_status pt_expand_batch(pt_ctx *ctx, int n, pt_round *rounds);
 /* pt_expand_batch with device-resident frontiers and outputs. */
 pt_status pt_expand_batch_dev(pt_ctx *ctx, int n, pt_round *rounds);
 
+/* ---- graph rounds (batching; no counterpart in the paper, whose rounds are
+ * the asynchronous steps of its PT loop, "Phylogenetic Topographer").
+ *
+ * The round of pt_expand_batch over a fixed set of alignments, recorded once
+ * as a CUDA graph and replayed for every later round.  Inside a replay all
+ * counts (candidates, unique proposals, kept, good) stay on the device and
+ * every buffer has its capacity, so the host neither waits nor copies
+ * between the steps of a round.  Results equal pt_expand_batch's on the same
+ * frontiers (same visited tables, lnL, next frontiers).
+ *
+ * The graph owns its buffers (one device allocation, sized from the frontier
+ * capacities: partials for frontier_caps[k] trees, and 2(n-3) x that many
+ * proposals, kept and next-frontier trees per alignment).  It records the
+ * alignments' visited tables, models, thresholds, CUDA settings, learned warm
+ * start (on or off, as at creation; weights are read at run time) and the
+ * autotuned CTA sizes known at creation.  It must not outlive its context and
+ * is used from the context's stream only. */
+typedef struct pt_graph pt_graph;
+
+/* Records the graph round for n distinct alignments (same n_cats) with
+ * frontier capacity frontier_caps[k] >= 1 (trees) and threshold
+ * thresholds[k] >= 0.  Errors: PT_ERR_INVALID_ARG (ids, capacities,
+ * thresholds), PT_ERR_OOM, PT_ERR_CUDA (capture or instantiation). */
+pt_status pt_graph_create(pt_ctx *ctx, int n, const int *aln_ids, const int *frontier_caps,
+                          const double *thresholds, pt_graph **out);
+/* Device input buffers of alignment k (index into aln_ids): edges
+ * [cap][2n-3][2] int32 and lengths [cap][2n-3] float64, owned by the graph,
+ * in pt_expand_frontier's layout.  The caller writes the frontier there
+ * (stream-ordered before pt_graph_run). */
+pt_status pt_graph_frontier_dev(pt_ctx *ctx, pt_graph *g, int k, int32_t **edges_dev, double **lengths_dev);
+/* Copies a host frontier of n_frontier <= cap trees into alignment k's input
+ * buffers (validated like pt_expand_frontier's input). */
+pt_status pt_graph_set_frontier(pt_ctx *ctx, pt_graph *g, int k, int n_frontier, const int32_t *edges,
+                                const double *lengths);
+/* Replays the round.  n_frontier[k]: trees in alignment k's input buffers
+ * (0..cap); lmax_inout[k]: lmax at the start of the round, raised on return;
+ * n_next[k] (out): size of alignment k's next frontier.  Synchronises the
+ * context stream.  pt_stats reports the round (launch count = kernel nodes). */
+pt_status pt_graph_run(pt_ctx *ctx, pt_graph *g, const int *n_frontier, double *lmax_inout, int *n_next);
+/* Device pointers to alignment k's next frontier of the last run (canonical
+ * edge lists, lengths, lnL, keys as uint64 pairs); valid until the next run. */
+pt_status pt_graph_next_dev(pt_ctx *ctx, pt_graph *g, int k, const int32_t **edges_dev, const double **lengths_dev,
+                            const double **lnl_dev, const uint64_t **keys_dev);
+/* Host copy of alignment k's next frontier (any output may be NULL); *n =
+ * its size; PT_ERR_BUFFER_TOO_SMALL when it exceeds cap. */
+pt_status pt_graph_get_next(pt_ctx *ctx, pt_graph *g, int k, int cap, int32_t *edges, double *lengths, double *lnl,
+                            pt_key *keys, int *n);
+/* Makes every alignment's next frontier its input (device copy) and writes
+ * the sizes to n_frontier[k]; PT_ERR_BUFFER_TOO_SMALL when one exceeds its
+ * capacity (nothing is copied then). */
+pt_status pt_graph_advance(pt_ctx *ctx, pt_graph *g, int *n_frontier);
+/* Releases the graph (NULL is a no-op); pt_destroy releases the graphs left. */
+pt_status pt_graph_destroy(pt_ctx *ctx, pt_graph *g);
+
 /* Dumps the visited table of an alignment (every topology scored so far):
  * keys, status (PT_ST_*), lnL (full lnL for visited topologies, proposal
  * lnL for rejected ones).  Writes min(cap, count) entries in table order and

@@ -11,7 +11,9 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <functional>
 #include <map>
+#include <memory>
 #include <string>
 #include <vector>
 
@@ -36,8 +38,11 @@ struct AlnState {
     float* tip_sum = nullptr;  // [n][16] leaf summaries for the warm-start features
 };
 
+struct GraphRound;
+
 struct Ctx {
     pt_config cfg{};
+    std::vector<GraphRound*> graphs;  // graph rounds recorded on this context
     cudaStream_t stream = nullptr;
     std::string err;
     std::vector<AlnState> alns;
@@ -172,16 +177,6 @@ size_t rsize(const Ctx& c) { return c.cfg.precision == PT_PREC_FP64 ? 8 : 4; }
 size_t tree_clv_bytes(const Ctx& c, const AlnState& a) {
     size_t slots = (size_t)(2 * a.n - 5);
     return slots * a.P * (4 * (size_t)a.M.C * rsize(c) + 4);
-}
-
-ClvGroup clv_group(Ctx& c, const std::string& pre, const AlnState& a, int count) {
-    ClvGroup g;
-    size_t slots = (size_t)(2 * a.n - 5);
-    g.tree_stride = slots * a.P * 4 * a.M.C;
-    g.scl_stride = slots * a.P;
-    g.clv = buf<unsigned char>(c, pre + ".clv", (size_t)count * g.tree_stride * rsize(c));
-    g.scl = buf<int32_t>(c, pre + ".scl", (size_t)count * g.scl_stride);
-    return g;
 }
 
 int chunk_trees(const Ctx& c, const AlnState& a) {
@@ -533,47 +528,23 @@ struct FullJob {
     int max_sweeps;
 };
 
-// Runs full-optimisation jobs in waves that fit the memory budget; each wave
-// is one persistent launch over all its groups.
+// Runs full-optimisation jobs in one persistent launch over all of them.  The
+// partials live in per-CTA slabs (a CTA reuses its slab tree after tree), so
+// memory grows with the grid, not with the number of trees.
 void run_full_jobs(Ctx& c, std::vector<FullJob> jobs) {
     const int prec = c.cfg.precision;
-    // split jobs into chunks no larger than one tree group's budget
-    std::vector<FullJob> chunks;
-    for (auto& j : jobs) {
-        const int G = chunk_trees(c, *j.a);
-        for (int f0 = 0; f0 < j.count; f0 += G) {
-            FullJob x = j;
-            x.first = j.first + f0;
-            x.count = std::min(G, j.count - f0);
-            x.lnl_d = j.lnl_d + f0;
-            chunks.push_back(x);
-        }
-    }
+    jobs.erase(std::remove_if(jobs.begin(), jobs.end(), [](const FullJob& j) { return j.count <= 0; }), jobs.end());
+    if (jobs.empty()) return;
     // larger problems first (dynamic scheduling then balances the tail)
-    std::stable_sort(chunks.begin(), chunks.end(),
+    std::stable_sort(jobs.begin(), jobs.end(),
                      [](const FullJob& x, const FullJob& y) { return (size_t)x.a->P * x.a->n > (size_t)y.a->P * y.a->n; });
-    auto group_bytes = [&](const FullJob& j) {
-        const size_t slots = (size_t)(2 * j.a->n - 5);
-        return ((slots * j.a->P * 4 * j.a->M.C * rsize(c) * j.count + 255) & ~size_t(255)) +
-               ((slots * j.a->P * 4 * j.count + 255) & ~size_t(255));
-    };
-    size_t k = 0;
-    while (k < chunks.size()) {
-        size_t used = 0, e = k;
-        while (e < chunks.size()) {
-            const size_t b = group_bytes(chunks[e]);
-            if (e > k && used + b > c.budget) break;
-            used += b;
-            ++e;
-        }
-        unsigned char* clv = buf<unsigned char>(c, "full.clv", used);
+    {
         std::vector<FullGroup> groups;
         std::vector<int> counts;
         int maxN = 3, maxP = 1;
-        const int C = chunks[k].a->M.C;
-        size_t off = 0;
-        for (size_t i = k; i < e; ++i) {
-            const FullJob& j = chunks[i];
+        const int C = jobs[0].a->M.C;
+        size_t slab_stride = 0;
+        for (const FullJob& j : jobs) {
             AlnState& a = *j.a;
             if (a.M.C != C) fail(c, PT_ERR_INVALID_ARG, "alignments of one batch must share the number of categories");
             FullGroup gp;
@@ -581,19 +552,14 @@ void run_full_jobs(Ctx& c, std::vector<FullJob> jobs) {
             gp.A = aln_dev(a);
             gp.ts = j.ts;
             gp.first = j.first;
-            const size_t slots = (size_t)(2 * a.n - 5);
-            gp.g.tree_stride = slots * a.P * 4 * a.M.C;
-            gp.g.scl_stride = slots * a.P;
-            gp.g.clv = clv + off;
-            off += (gp.g.tree_stride * rsize(c) * j.count + 255) & ~size_t(255);
-            gp.g.scl = reinterpret_cast<int32_t*>(clv + off);
-            off += (gp.g.scl_stride * 4 * j.count + 255) & ~size_t(255);
+            gp.g = ClvGroup{nullptr, nullptr, 0, 0};
             gp.max_sweeps = j.max_sweeps;
             gp.lnl_out = j.lnl_d;
             groups.push_back(gp);
             counts.push_back(j.count);
             maxN = std::max(maxN, a.n);
             maxP = std::max(maxP, a.P);
+            slab_stride = std::max(slab_stride, fullopt_slab_bytes(prec, C, a.n, a.P));
         }
         int total = 0;
         for (int x : counts) total += x;
@@ -611,10 +577,11 @@ void run_full_jobs(Ctx& c, std::vector<FullJob> jobs) {
                 spc = (sumtable_bytes(prec, C, maxP) + 255) & ~size_t(255);
                 scratch = buf<unsigned char>(c, "full.scratch", spc * grid);
             }
+            unsigned char* slab = buf<unsigned char>(c, "full.slab", slab_stride * grid);
             ck(c, cudaMemsetAsync(counter, 0, sizeof(int), c.stream), "counter");
             size_t e0 = timed ? ev_record(c) : 0;
             launch_fullopt(c.stream, prec, C, dg, gstart, (int)groups.size(), counter, maxN, maxP, kcfg(c), stats,
-                           threads, grid, scratch, spc);
+                           threads, grid, scratch, spc, slab, slab_stride);
             ck(c, cudaGetLastError(), "full optimisation launch");
             float ms = 0.f;
             if (timed) {
@@ -677,7 +644,6 @@ void run_full_jobs(Ctx& c, std::vector<FullJob> jobs) {
         Span sp(c, 6);
         run(threads, c.d_stats, false);
         sp.end();
-        k = e;
     }
 }
 
@@ -719,12 +685,12 @@ void begin_core(Ctx& c, AlnState& a, int ns, const int32_t* edges_d, const doubl
     TreeSet ts;
     score_core(c, a, ns, edges_d, lens_d, PT_SCORE_FULL, "kp", ts, lnl);
     int32_t* winner = buf<int32_t>(c, "kp.winner", ns);
-    launch_insert_trees(c.stream, a.table, a.log2, ns, ts, lnl, nullptr, 0, winner, c.d_err);
+    launch_insert_trees(c.stream, a.table, a.log2, hcount(ns), ts, lnl, nullptr, hround(0), winner, c.d_err);
     double ninf = -INFINITY;
     ck(c, cudaMemcpyAsync(c.d_lmax, &ninf, 8, cudaMemcpyHostToDevice, c.stream), "lmax init");
-    launch_lmax(c.stream, ns, lnl, winner, c.d_lmax);
+    launch_lmax(c.stream, hcount(ns), lnl, winner, c.d_lmax);
     int32_t* good = buf<int32_t>(c, "kp.good", ns);
-    launch_finalize_trees(c.stream, a.table, ns, winner, lnl, c.d_lmax, thr, 0, good, c.d_stats);
+    launch_finalize_trees(c.stream, a.table, hcount(ns), winner, lnl, c.d_lmax, thr, hround(0), good, c.d_stats);
     // dedup starts: a start that lost its key is not GOOD
     std::vector<int32_t> w(ns), gd(ns);
     ck(c, cudaMemcpyAsync(w.data(), winner, 4 * (size_t)ns, cudaMemcpyDeviceToHost, c.stream), "read winners");
@@ -794,7 +760,8 @@ void expand_batch(Ctx& c, const std::vector<RoundIn>& ins, std::vector<RoundOut>
         r.fr = treeset(c, pre + "fr", a.n, std::max(r.F, 1), false);
         launch_canon(c.stream, a.n, r.F, ins[k].edges_d, ins[k].lens_d, r.fr, c.d_err);
         int32_t* fwin = buf<int32_t>(c, pre + "fr.win", r.F);
-        launch_insert_trees(c.stream, a.table, a.log2, r.F, r.fr, nullptr, nullptr, r.round - 1, fwin, c.d_err);
+        launch_insert_trees(c.stream, a.table, a.log2, hcount(r.F), r.fr, nullptr, nullptr, hround(r.round - 1), fwin,
+                            c.d_err);
         ck(c, cudaMemcpyAsync(r.lmax, &ins[k].lmax, 8, cudaMemcpyHostToDevice, c.stream), "lmax");
         r.ncand = r.F * r.m;
         hc[kStCand] += r.ncand;
@@ -803,7 +770,7 @@ void expand_batch(Ctx& c, const std::vector<RoundIn>& ins, std::vector<RoundOut>
         r.cslot = buf<int32_t>(c, pre + "cand.slot", r.ncand);
         r.flag = buf<int32_t>(c, pre + "cand.flag", r.ncand);
         r.pos = buf<int32_t>(c, pre + "cand.pos", r.ncand);
-        launch_enum(c.stream, a.n, r.F, r.fr, r.nkey, r.cinfo);
+        launch_enum(c.stream, a.n, hcount(r.F), r.fr, r.nkey, r.cinfo);
     }
     sp0.end();
     // ---- dedup and arbitration
@@ -811,11 +778,10 @@ void expand_batch(Ctx& c, const std::vector<RoundIn>& ins, std::vector<RoundOut>
     for (int k = 0; k < na; ++k) {
         AR& r = ar[k];
         AlnState& a = *r.a;
-        launch_cand_insert(c.stream, a.table, a.log2, r.ncand, r.nkey, r.cinfo, r.fr, r.round, r.cslot, r.flag, c.d_err,
-                           c.d_stats);
-        launch_cand_arb(c.stream, 2, a.table, r.ncand, r.cinfo, r.fr, r.round, r.cslot, r.flag);
-        launch_cand_arb(c.stream, 3, a.table, r.ncand, r.cinfo, r.fr, r.round, r.cslot, r.flag);
-        launch_cand_arb(c.stream, 4, a.table, r.ncand, r.cinfo, r.fr, r.round, r.cslot, r.flag);
+        launch_cand_insert(c.stream, a.table, a.log2, hcount(r.ncand), r.nkey, r.cinfo, r.fr, hround(r.round), r.cslot,
+                           r.flag, c.d_err, c.d_stats);
+        for (int ph = 2; ph <= 4; ++ph)
+            launch_cand_arb(c.stream, ph, a.table, hcount(r.ncand), r.cinfo, r.fr, hround(r.round), r.cslot, r.flag);
     }
     check_flags(c);
     int Wtot = 0;
@@ -896,7 +862,8 @@ void expand_batch(Ctx& c, const std::vector<RoundIn>& ins, std::vector<RoundOut>
             off += ((g.scl_stride * 4 * ch.cnt) + 255) & ~size_t(255);
             void* pm = wave + off;
             off += (pmat_bytes(prec, C, a.n, ch.cnt) + 255) & ~size_t(255);
-            launch_partials(c.stream, prec, a.M, aln_dev(a), r.fr, ch.f0, ch.cnt, g, true, threads_for(c, a.P), pm);
+            launch_partials(c.stream, prec, a.M, aln_dev(a), r.fr, ch.f0, hcount(ch.cnt), g, true, threads_for(c, a.P),
+                            pm);
             ck(c, cudaGetLastError(), "partials launch");
             const int gi0 = r.ibase + ch.i0, cnt_items = ch.i1 - ch.i0;
             const double* init = nullptr;
@@ -907,15 +874,15 @@ void expand_batch(Ctx& c, const std::vector<RoundIn>& ins, std::vector<RoundOut>
                     launch_tip_summary(c.stream, aln_dev(a), C, a.tip_sum);
                 }
                 float* ssum = buf<float>(c, "mlp.ssum", (size_t)ch.cnt * nslot * 16);
-                launch_slot_summary(c.stream, prec, C, aln_dev(a), g, ch.cnt, nslot, ssum);
+                launch_slot_summary(c.stream, prec, C, aln_dev(a), g, hcount(ch.cnt), nslot, ssum);
                 float* xf = xf_all + (size_t)gi0 * kMlpIn;
                 void* xb = buf<unsigned char>(c, "mlp.xb", (size_t)(cnt_items + 64) * kMlpInPad * 2);
-                launch_item_features(c.stream, a.n, items + r.ibase, ch.i0, ch.i1, r.fr, ch.f0, ssum, nslot, a.tip_sum,
+                launch_item_features(c.stream, a.n, items + r.ibase, ch.i0, hcount(ch.i1), r.fr, ch.f0, ssum, nslot, a.tip_sum,
                                      xf, xb);
                 if (use_mlp) {
                     float* yb = buf<float>(c, "mlp.y", (size_t)(cnt_items + 64) * kMlpOutPad);
                     mlp_forward(c.stream, c.mlp, xb, cnt_items, yb, nullptr, nullptr, nullptr, nullptr, false);
-                    launch_item_init(c.stream, items + r.ibase, ch.i0, ch.i1, xf, yb, c.cfg.tmin, c.cfg.tmax,
+                    launch_item_init(c.stream, items + r.ibase, ch.i0, hcount(ch.i1), xf, yb, c.cfg.tmin, c.cfg.tmax,
                                      init_all + (size_t)gi0 * 5);
                     init = init_all + (size_t)gi0 * 5;
                 }
@@ -928,7 +895,7 @@ void expand_batch(Ctx& c, const std::vector<RoundIn>& ins, std::vector<RoundOut>
             gp.g = g;
             gp.Pm = pm;
             gp.tab = a.table;
-            gp.round = r.round;
+            gp.round = hround(r.round);
             gp.lmax = r.lmax;
             gp.thr = ins[ch.k].thr;
             gp.items = items + gi0;
@@ -1026,7 +993,7 @@ void expand_batch(Ctx& c, const std::vector<RoundIn>& ins, std::vector<RoundOut>
         int32_t* kedges = buf<int32_t>(c, pre + "kept.edges", (size_t)r.K * 2 * (2 * r.n - 3) + 2);
         double* klens = buf<double>(c, pre + "kept.lens", (size_t)r.K * (2 * r.n - 3) + 1);
         r.kslot = buf<int32_t>(c, pre + "kept.slot", r.K + 1);
-        launch_materialize(c.stream, r.n, r.K, r.kidx, items + r.ibase, r.fr, len5 + (size_t)5 * r.ibase, kedges, klens,
+        launch_materialize(c.stream, r.n, hcount(r.K), r.kidx, items + r.ibase, r.fr, len5 + (size_t)5 * r.ibase, kedges, klens,
                            r.kslot);
         r.klnl = buf<double>(c, pre + "kp.lnl", r.K + 1);
         r.kp = treeset(c, pre + "kp", r.n, std::max(r.K, 1), true);
@@ -1043,9 +1010,9 @@ void expand_batch(Ctx& c, const std::vector<RoundIn>& ins, std::vector<RoundOut>
     for (int k = 0; k < na; ++k) {
         AR& r = ar[k];
         const std::string pre = "b" + std::to_string(k) + ".";
-        launch_lmax(c.stream, r.K, r.klnl, nullptr, r.lmax);
+        launch_lmax(c.stream, hcount(r.K), r.klnl, nullptr, r.lmax);
         r.good = buf<int32_t>(c, pre + "kp.good", r.K + 1);
-        launch_finalize_trees(c.stream, r.a->table, r.K, r.kslot, r.klnl, r.lmax, ins[k].thr, r.round, r.good,
+        launch_finalize_trees(c.stream, r.a->table, hcount(r.K), r.kslot, r.klnl, r.lmax, ins[k].thr, hround(r.round), r.good,
                               c.d_stats);
         r.gpos = buf<int32_t>(c, pre + "kp.gpos", r.K + 1);
         r.G = scan_count(c, r.good, r.gpos, r.K);
@@ -1093,7 +1060,7 @@ void write_out(Ctx& c, const AlnState& a, RoundOut& o, int cap, int32_t* e, doub
     if (o.count == 0) return;
     const int n = a.n, E = 2 * n - 3;
     if (!host) {
-        launch_gather_out(c.stream, n, o.count, o.idx, o.ts, o.lnl, e, l, lnl, keys);
+        launch_gather_out(c.stream, n, hcount(o.count), o.idx, o.ts, o.lnl, e, l, lnl, keys);
         ck(c, cudaGetLastError(), "gather");
         ck(c, cudaStreamSynchronize(c.stream), "sync");
         return;
@@ -1102,12 +1069,393 @@ void write_out(Ctx& c, const AlnState& a, RoundOut& o, int cap, int32_t* e, doub
     double* dl = buf<double>(c, "out.l", (size_t)o.count * E);
     double* dn = buf<double>(c, "out.lnl", o.count);
     uint64_t* dk = buf<uint64_t>(c, "out.k", (size_t)o.count * 2);
-    launch_gather_out(c.stream, n, o.count, o.idx, o.ts, o.lnl, de, dl, dn, dk);
+    launch_gather_out(c.stream, n, hcount(o.count), o.idx, o.ts, o.lnl, de, dl, dn, dk);
     if (e) ck(c, cudaMemcpyAsync(e, de, 4 * (size_t)o.count * 2 * E, cudaMemcpyDeviceToHost, c.stream), "copy out");
     if (l) ck(c, cudaMemcpyAsync(l, dl, 8 * (size_t)o.count * E, cudaMemcpyDeviceToHost, c.stream), "copy out");
     if (lnl) ck(c, cudaMemcpyAsync(lnl, dn, 8 * (size_t)o.count, cudaMemcpyDeviceToHost, c.stream), "copy out");
     if (keys) ck(c, cudaMemcpyAsync(keys, dk, 16 * (size_t)o.count, cudaMemcpyDeviceToHost, c.stream), "copy out");
     ck(c, cudaStreamSynchronize(c.stream), "sync");
+}
+
+// ---------------------------------------------------------------- graph rounds
+// A batched PT round (the work of expand_batch) captured once as a CUDA graph
+// and replayed round after round.  Every count the round produces (candidates,
+// items, kept, good) stays on the device and every buffer is allocated at its
+// capacity, so nothing is read back inside the round: the host writes the
+// frontier sizes, round numbers and lmax before a replay and reads the
+// next-frontier sizes after it.  All buffers are owned by the graph (one
+// allocation), so other calls on the context cannot move them.
+struct GraphAln {
+    int aln, n, m, E, NN, P, F_cap, cap;  // cap = F_cap * m (candidates, items, kept trees)
+    double thr;
+    int32_t* in_edges;
+    double* in_lens;
+    TreeSet fr, kp;
+    int32_t *fwin, *cinfo, *cslot, *flag, *pos, *kept, *kpos, *kidx, *kslot, *good, *gpos, *gidx, *kedges;
+    uint64_t *nkey, *ikey;
+    Item* items;
+    double *plnl, *len5, *klens, *klnl;
+    ClvGroup g;
+    void* pm;
+    float *ssum, *xf, *yb;
+    void* xb;
+    double* init;
+    int32_t* out_edges;
+    double *out_lens, *out_lnl;
+    uint64_t* out_keys;
+};
+
+struct GraphRound {
+    int na = 0;
+    std::vector<GraphAln> a;
+    unsigned char* mem = nullptr;
+    int* di = nullptr;          // device counts, layout below
+    double* dlmax = nullptr;    // [na]
+    int* hi = nullptr;          // pinned mirror of di
+    double* hl = nullptr;       // pinned mirror of dlmax
+    PropGroup* dpg = nullptr;
+    FullGroup* dfg = nullptr;
+    int32_t* scan_tmp = nullptr;
+    void* prop_scratch = nullptr;
+    void* full_scratch = nullptr;
+    unsigned char* slab = nullptr;
+    cudaStream_t cs = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    long long kernels = 0;      // kernel nodes per replay
+    bool mlp = false;
+    int prop_threads = 0, full_threads = 0;
+    // di layout: F [na], m [na], ncand [na], W [na], K [na], G [na], round [na],
+    // gstart (proposal) [na + 1], gstart (full optimisation) [na + 1], two counters
+    int oF() const { return 0; }
+    int oM() const { return na; }
+    int oNC() const { return 2 * na; }
+    int oW() const { return 3 * na; }
+    int oK() const { return 4 * na; }
+    int oG() const { return 5 * na; }
+    int oRD() const { return 6 * na; }
+    int oGSP() const { return 7 * na; }
+    int oGSF() const { return 8 * na + 1; }
+    int oCP() const { return 9 * na + 2; }
+    int oCF() const { return 9 * na + 3; }
+    int nints() const { return 9 * na + 4; }
+};
+
+// Lays buffers out in one allocation: add() records a request, carve() assigns.
+struct Arena {
+    std::vector<std::pair<size_t, std::function<void(unsigned char*)>>> req;
+    template <typename T>
+    void add(T*& p, size_t count) {
+        req.push_back({std::max<size_t>(count * sizeof(T), 16), [&p](unsigned char* b) { p = reinterpret_cast<T*>(b); }});
+    }
+    void addv(void*& p, size_t bytes) {
+        req.push_back({std::max<size_t>(bytes, 16), [&p](unsigned char* b) { p = b; }});
+    }
+    size_t total() const {
+        size_t t = 0;
+        for (auto& r : req) t += (r.first + 255) & ~size_t(255);
+        return t;
+    }
+    void carve(unsigned char* base) {
+        size_t o = 0;
+        for (auto& r : req) {
+            r.second(base + o);
+            o += (r.first + 255) & ~size_t(255);
+        }
+    }
+};
+
+void arena_treeset(Arena& ar, TreeSet& t, int n, int cap, bool with_emap) {
+    const int NN = 2 * n - 2;
+    t.n = n;
+    t.cap = cap;
+    ar.add(t.up, (size_t)cap * NN);
+    ar.add(t.ch, (size_t)cap * NN * 2);
+    ar.add(t.len, (size_t)cap * NN);
+    ar.add(t.bits, (size_t)cap * NN * 2);
+    ar.add(t.erank, (size_t)cap * NN);
+    ar.add(t.sched, (size_t)cap * 3 * n);
+    ar.add(t.key, (size_t)cap * 2);
+    if (with_emap) ar.add(t.emap, (size_t)cap * (2 * n - 3));
+    else t.emap = nullptr;
+}
+
+void graph_free(GraphRound* g) {
+    if (!g) return;
+    if (g->exec) cudaGraphExecDestroy(g->exec);
+    if (g->cs) cudaStreamDestroy(g->cs);
+    if (g->mem) cudaFree(g->mem);
+    if (g->hi) cudaFreeHost(g->hi);
+    if (g->hl) cudaFreeHost(g->hl);
+    delete g;
+}
+
+// The launch sequence of one graph round on stream s (recorded under capture).
+void graph_record(Ctx& c, GraphRound& g, cudaStream_t s, int C, int maxN, int maxP, int pgrid, size_t pspc,
+                  int fgrid, size_t fspc, size_t slab_stride) {
+    const int na = g.na, prec = c.cfg.precision;
+    int* di = g.di;
+    for (GraphAln& x : g.a) {  // flags past the device counts must read as zero in the scans
+        cudaMemsetAsync(x.kept, 0, sizeof(int32_t) * ((size_t)x.cap + 1), s);
+        cudaMemsetAsync(x.good, 0, sizeof(int32_t) * ((size_t)x.cap + 1), s);
+    }
+    for (int k = 0; k < na; ++k) {
+        GraphAln& x = g.a[k];
+        AlnState& A = c.alns[x.aln];
+        const DCount Fk{x.F_cap, di + g.oF() + k};
+        launch_canon(s, x.n, Fk, x.in_edges, x.in_lens, x.fr, c.d_err);
+        launch_insert_trees(s, A.table, A.log2, Fk, x.fr, nullptr, nullptr, DRound{-1, di + g.oRD() + k}, x.fwin,
+                            c.d_err);
+        launch_enum(s, x.n, Fk, x.fr, x.nkey, x.cinfo);
+    }
+    launch_mul_counts(s, na, di + g.oF(), di + g.oM(), di + g.oNC());
+    for (int k = 0; k < na; ++k) {
+        GraphAln& x = g.a[k];
+        AlnState& A = c.alns[x.aln];
+        const DCount Fk{x.F_cap, di + g.oF() + k}, NCk{x.cap, di + g.oNC() + k}, Wk{x.cap, di + g.oW() + k};
+        const DRound rk{0, di + g.oRD() + k};
+        launch_cand_insert(s, A.table, A.log2, NCk, x.nkey, x.cinfo, x.fr, rk, x.cslot, x.flag, c.d_err, c.d_stats);
+        for (int ph = 2; ph <= 4; ++ph) launch_cand_arb(s, ph, A.table, NCk, x.cinfo, x.fr, rk, x.cslot, x.flag);
+        launch_scan(s, x.flag, x.pos, x.cap, g.scan_tmp);
+        launch_scan_total(s, x.flag, x.pos, x.cap, di + g.oW() + k);
+        launch_make_items(s, x.cap, x.flag, x.pos, x.cinfo, x.cslot, x.nkey, x.items, x.ikey);
+        launch_partials(s, prec, A.M, aln_dev(A), x.fr, 0, Fk, x.g, true, threads_for(c, x.P), x.pm);
+        if (g.mlp) {
+            const int nslot = 2 * x.n - 5;
+            launch_slot_summary(s, prec, C, aln_dev(A), x.g, Fk, nslot, x.ssum);
+            launch_item_features(s, x.n, x.items, 0, Wk, x.fr, 0, x.ssum, nslot, A.tip_sum, x.xf, x.xb);
+            mlp_forward(s, c.mlp, x.xb, Wk, x.yb);
+            launch_item_init(s, x.items, 0, Wk, x.xf, x.yb, c.cfg.tmin, c.cfg.tmax, x.init);
+        }
+    }
+    launch_prefix_counts(s, na, di + g.oW(), di + g.oGSP());
+    cudaMemsetAsync(di + g.oCP(), 0, sizeof(int), s);
+    launch_propose(s, prec, C, g.dpg, di + g.oGSP(), na, di + g.oCP(), kcfg(c), c.d_stats, g.prop_threads, pgrid,
+                   g.prop_scratch, pspc, maxP);
+    for (int k = 0; k < na; ++k) {
+        GraphAln& x = g.a[k];
+        const DCount Kk{x.cap, di + g.oK() + k};
+        launch_scan(s, x.kept, x.kpos, x.cap, g.scan_tmp);
+        launch_scan_total(s, x.kept, x.kpos, x.cap, di + g.oK() + k);
+        launch_compact_idx(s, x.cap, x.kept, x.kpos, x.kidx);
+        launch_materialize(s, x.n, Kk, x.kidx, x.items, x.fr, x.len5, x.kedges, x.klens, x.kslot);
+        launch_canon(s, x.n, Kk, x.kedges, x.klens, x.kp, c.d_err);
+    }
+    launch_prefix_counts(s, na, di + g.oK(), di + g.oGSF());
+    cudaMemsetAsync(di + g.oCF(), 0, sizeof(int), s);
+    launch_fullopt(s, prec, C, g.dfg, di + g.oGSF(), na, di + g.oCF(), maxN, maxP, kcfg(c), c.d_stats,
+                   g.full_threads, fgrid, g.full_scratch, fspc, g.slab, slab_stride);
+    for (int k = 0; k < na; ++k) {
+        GraphAln& x = g.a[k];
+        AlnState& A = c.alns[x.aln];
+        const DCount Kk{x.cap, di + g.oK() + k};
+        launch_lmax(s, Kk, x.klnl, nullptr, g.dlmax + k);
+        launch_finalize_trees(s, A.table, Kk, x.kslot, x.klnl, g.dlmax + k, x.thr, DRound{0, di + g.oRD() + k},
+                              x.good, c.d_stats);
+        launch_scan(s, x.good, x.gpos, x.cap, g.scan_tmp);
+        launch_scan_total(s, x.good, x.gpos, x.cap, di + g.oG() + k);
+        launch_compact_idx(s, x.cap, x.good, x.gpos, x.gidx);
+        launch_gather_out(s, x.n, DCount{x.cap, di + g.oG() + k}, x.gidx, x.kp, x.klnl, x.out_edges, x.out_lens,
+                          x.out_lnl, x.out_keys);
+    }
+}
+
+GraphRound* graph_create(Ctx& c, const std::vector<int>& ids, const std::vector<int>& caps,
+                         const std::vector<double>& thrs) {
+    const int na = (int)ids.size(), prec = c.cfg.precision;
+    std::unique_ptr<GraphRound, void (*)(GraphRound*)> own(new GraphRound, graph_free);
+    GraphRound& g = *own;
+    g.na = na;
+    g.a.resize(na);
+    int C = -1, maxN = 3, maxP = 1, maxCap = 1;
+    size_t slab_stride = 0;
+    for (int k = 0; k < na; ++k) {
+        AlnState& A = aln_of(c, ids[k]);
+        if (C < 0) C = A.M.C;
+        if (A.M.C != C) fail(c, PT_ERR_INVALID_ARG, "alignments of one graph must share the number of categories");
+        for (int j = 0; j < k; ++j)
+            if (ids[j] == ids[k]) fail(c, PT_ERR_INVALID_ARG, "alignment %d appears twice in a graph", ids[k]);
+        if (caps[k] < 1 || !(thrs[k] >= 0)) fail(c, PT_ERR_INVALID_ARG, "bad capacity or threshold for alignment %d", ids[k]);
+        if (!A.table) reset_table(c, A);
+        GraphAln& x = g.a[k];
+        x.aln = ids[k];
+        x.n = A.n;
+        x.m = 2 * (A.n - 3);
+        x.E = 2 * A.n - 3;
+        x.NN = 2 * A.n - 2;
+        x.P = A.P;
+        x.F_cap = caps[k];
+        if ((long long)caps[k] * x.m > (1 << 30)) fail(c, PT_ERR_INVALID_ARG, "frontier capacity too large");
+        x.cap = std::max(1, caps[k] * x.m);
+        x.thr = thrs[k];
+        maxN = std::max(maxN, A.n);
+        maxP = std::max(maxP, A.P);
+        maxCap = std::max(maxCap, x.cap);
+        slab_stride = std::max(slab_stride, fullopt_slab_bytes(prec, C, A.n, A.P));
+    }
+    g.mlp = c.mlp_on && c.mlp_ready;
+    // CTA sizes: the autotuned ones of this problem bucket when known
+    const std::string key = tune_key(prec, C, maxN, maxP);
+    g.prop_threads = g.full_threads = threads_for(c, maxP);
+    auto tt = c.tune.find(key);
+    if (tt != c.tune.end()) {
+        if (tt->second.prop_threads) g.prop_threads = tt->second.prop_threads;
+        if (tt->second.full_threads) g.full_threads = tt->second.full_threads;
+    }
+    const bool ptab = propose_smem_bytes(prec, C, maxP, true, g.prop_threads) <= c.smem_optin;
+    const bool ftab = fullopt_smem_bytes(prec, C, maxN, maxP, true, g.full_threads) <= c.smem_optin;
+    const int pgrid = std::max(1, propose_blocks_per_sm(prec, C, g.prop_threads, ptab, maxP)) * c.sm_count;
+    const int fgrid = std::max(1, fullopt_blocks_per_sm(prec, C, g.full_threads, ftab, maxN, maxP)) * c.sm_count;
+    const size_t tabb = (sumtable_bytes(prec, C, maxP) + 255) & ~size_t(255);
+    const size_t pspc = ptab ? 0 : tabb, fspc = ftab ? 0 : tabb;
+    Arena ar;
+    for (GraphAln& x : g.a) {
+        const int n = x.n, E = x.E, cap = x.cap, F = x.F_cap;
+        const size_t slots = (size_t)(2 * n - 5);
+        ar.add(x.in_edges, (size_t)F * 2 * E);
+        ar.add(x.in_lens, (size_t)F * E);
+        arena_treeset(ar, x.fr, n, F, false);
+        ar.add(x.fwin, F);
+        ar.add(x.nkey, (size_t)cap * 2);
+        ar.add(x.cinfo, (size_t)cap * 4);
+        ar.add(x.cslot, cap);
+        ar.add(x.flag, cap);
+        ar.add(x.pos, cap);
+        ar.add(x.items, (size_t)cap + 1);
+        ar.add(x.ikey, 2 * (size_t)cap + 2);
+        ar.add(x.plnl, (size_t)cap + 1);
+        ar.add(x.len5, 5 * (size_t)cap + 5);
+        ar.add(x.kept, (size_t)cap + 1);
+        ar.add(x.kpos, (size_t)cap + 1);
+        ar.add(x.kidx, (size_t)cap + 1);
+        ar.add(x.kedges, (size_t)cap * 2 * E);
+        ar.add(x.klens, (size_t)cap * E);
+        ar.add(x.kslot, (size_t)cap + 1);
+        ar.add(x.klnl, (size_t)cap + 1);
+        arena_treeset(ar, x.kp, n, cap, true);
+        ar.add(x.good, (size_t)cap + 1);
+        ar.add(x.gpos, (size_t)cap + 1);
+        ar.add(x.gidx, (size_t)cap + 1);
+        ar.add(x.out_edges, (size_t)cap * 2 * E);
+        ar.add(x.out_lens, (size_t)cap * E);
+        ar.add(x.out_lnl, (size_t)cap);
+        ar.add(x.out_keys, 2 * (size_t)cap);
+        x.g.tree_stride = slots * x.P * 4 * C;
+        x.g.scl_stride = slots * x.P;
+        ar.addv(x.g.clv, (size_t)F * x.g.tree_stride * rsize(c));
+        ar.add(x.g.scl, (size_t)F * x.g.scl_stride);
+        ar.addv(x.pm, pmat_bytes(prec, C, n, F));
+        x.ssum = x.xf = x.yb = nullptr;
+        x.xb = nullptr;
+        x.init = nullptr;
+        if (g.mlp) {
+            ar.add(x.ssum, (size_t)F * slots * 16);
+            ar.add(x.xf, ((size_t)cap + 1) * kMlpIn);
+            ar.addv(x.xb, ((size_t)cap + 64) * kMlpInPad * 2);
+            ar.add(x.yb, ((size_t)cap + 64) * kMlpOutPad);
+            ar.add(x.init, ((size_t)cap + 1) * 5);
+        }
+    }
+    ar.add(g.di, g.nints());
+    ar.add(g.dlmax, na);
+    ar.add(g.dpg, na);
+    ar.add(g.dfg, na);
+    ar.add(g.scan_tmp, (size_t)(maxCap + 1023) / 1024 + 2);
+    if (pspc) ar.addv(g.prop_scratch, pspc * pgrid);
+    if (fspc) ar.addv(g.full_scratch, fspc * fgrid);
+    ar.add(g.slab, slab_stride * fgrid);
+    ck(c, cudaMalloc(&g.mem, ar.total()), "allocating the graph round's buffers");
+    ar.carve(g.mem);
+    ck(c, cudaHostAlloc(reinterpret_cast<void**>(&g.hi), sizeof(int) * g.nints(), cudaHostAllocDefault), "pinned");
+    ck(c, cudaHostAlloc(reinterpret_cast<void**>(&g.hl), sizeof(double) * na, cudaHostAllocDefault), "pinned");
+    // static tables: m per alignment, group descriptors
+    std::fill(g.hi, g.hi + g.nints(), 0);
+    for (int k = 0; k < na; ++k) g.hi[g.oM() + k] = g.a[k].m;
+    ck(c, cudaMemcpy(g.di, g.hi, sizeof(int) * g.nints(), cudaMemcpyHostToDevice), "graph counts");
+    std::vector<PropGroup> pg(na);
+    std::vector<FullGroup> fg(na);
+    for (int k = 0; k < na; ++k) {
+        GraphAln& x = g.a[k];
+        AlnState& A = c.alns[x.aln];
+        PropGroup& p = pg[k];
+        p.M = A.M;
+        p.A = aln_dev(A);
+        p.fr = x.fr;
+        p.first = 0;
+        p.g = x.g;
+        p.Pm = x.pm;
+        p.tab = A.table;
+        p.round = DRound{0, g.di + g.oRD() + k};
+        p.lmax = g.dlmax + k;
+        p.thr = x.thr;
+        p.items = x.items;
+        p.lnl_out = x.plnl;
+        p.len5_out = x.len5;
+        p.kept = x.kept;
+        p.init = g.mlp ? x.init : nullptr;
+        FullGroup& f = fg[k];
+        f.M = A.M;
+        f.A = aln_dev(A);
+        f.ts = x.kp;
+        f.first = 0;
+        f.g = ClvGroup{nullptr, nullptr, 0, 0};
+        f.max_sweeps = c.cfg.full_max_sweeps;
+        f.lnl_out = x.klnl;
+        if (g.mlp && !A.tip_sum) {
+            ck(c, cudaMalloc(&A.tip_sum, sizeof(float) * 16 * A.n), "alloc tip summaries");
+            launch_tip_summary(c.stream, aln_dev(A), C, A.tip_sum);
+        }
+    }
+    ck(c, cudaMemcpy(g.dpg, pg.data(), sizeof(PropGroup) * na, cudaMemcpyHostToDevice), "graph groups");
+    ck(c, cudaMemcpy(g.dfg, fg.data(), sizeof(FullGroup) * na, cudaMemcpyHostToDevice), "graph groups");
+    ck(c, cudaStreamSynchronize(c.stream), "sync");
+    // capture on a stream of the graph's own (the context stream may be a legacy default stream)
+    ck(c, cudaStreamCreateWithFlags(&g.cs, cudaStreamNonBlocking), "graph stream");
+    ck(c, cudaStreamBeginCapture(g.cs, cudaStreamCaptureModeRelaxed), "begin capture");
+    const long long k0 = launch_count();
+    graph_record(c, g, g.cs, C, maxN, maxP, pgrid, pspc, fgrid, fspc, slab_stride);
+    g.kernels = launch_count() - k0;
+    cudaGraph_t graph = nullptr;
+    ck(c, cudaStreamEndCapture(g.cs, &graph), "end capture");
+    const cudaError_t e = cudaGraphInstantiate(&g.exec, graph, 0);
+    cudaGraphDestroy(graph);
+    ck(c, e, "graph instantiate");
+    return own.release();
+}
+
+void graph_run(Ctx& c, GraphRound& g, const int* nF, double* lmax, int* n_next) {
+    const int na = g.na;
+    for (int k = 0; k < na; ++k)
+        if (nF[k] < 0 || nF[k] > g.a[k].F_cap || std::isnan(lmax[k]))
+            fail(c, PT_ERR_INVALID_ARG, "frontier %d: %d trees for a capacity of %d", k, nF[k], g.a[k].F_cap);
+    int64_t hc[kStWords] = {0};
+    for (int k = 0; k < na; ++k) {
+        AlnState& A = c.alns[g.a[k].aln];
+        g.hi[g.oF() + k] = nF[k];
+        g.hi[g.oRD() + k] = ++A.round;
+        g.hl[k] = lmax[k];
+        hc[kStCand] += (int64_t)nF[k] * g.a[k].m;
+    }
+    zero_flags(c);
+    begin_stats(c);
+    ck(c, cudaMemcpyAsync(g.di + g.oF(), g.hi + g.oF(), sizeof(int) * na, cudaMemcpyHostToDevice, c.stream), "counts");
+    ck(c, cudaMemcpyAsync(g.di + g.oRD(), g.hi + g.oRD(), sizeof(int) * na, cudaMemcpyHostToDevice, c.stream), "rounds");
+    ck(c, cudaMemcpyAsync(g.dlmax, g.hl, sizeof(double) * na, cudaMemcpyHostToDevice, c.stream), "lmax");
+    Span total(c, 5);
+    ck(c, cudaGraphLaunch(g.exec, c.stream), "graph launch");
+    total.end();
+    ck(c, cudaMemcpyAsync(g.hi + g.oW(), g.di + g.oW(), sizeof(int) * 3 * na, cudaMemcpyDeviceToHost, c.stream),
+       "counts");
+    ck(c, cudaMemcpyAsync(g.hl, g.dlmax, sizeof(double) * na, cudaMemcpyDeviceToHost, c.stream), "lmax");
+    check_flags(c);  // synchronises the stream
+    for (int k = 0; k < na; ++k) {
+        hc[kStScored] += g.hi[g.oW() + k];
+        hc[kStKept] += g.hi[g.oK() + k];
+        n_next[k] = g.hi[g.oG() + k];
+        lmax[k] = g.hl[k];
+    }
+    end_stats(c, hc);
+    c.stats[kStLaunches] = g.kernels;
+    c.last_items = 0;
 }
 
 template <typename F>
@@ -1206,6 +1554,8 @@ void pt_destroy(pt_ctx* ctx) {
     Ctx& c = ctx->c;
     cudaSetDevice(c.cfg.device);
     if (c.stream) cudaStreamSynchronize(c.stream);
+    for (GraphRound* g : c.graphs) graph_free(g);
+    c.graphs.clear();
     for (auto& kv : c.bufs) if (kv.second.p) cudaFree(kv.second.p);
     for (auto& a : c.alns) {
         if (a.tips) cudaFree(a.tips);
@@ -1450,6 +1800,125 @@ static pt_status expand_batch_api(pt_ctx* ctx, int n, pt_round* rounds, bool hos
 
 pt_status pt_expand_batch(pt_ctx* ctx, int n, pt_round* rounds) { return expand_batch_api(ctx, n, rounds, true); }
 pt_status pt_expand_batch_dev(pt_ctx* ctx, int n, pt_round* rounds) { return expand_batch_api(ctx, n, rounds, false); }
+
+// ---- graph rounds (pt_graph is the opaque face of a GraphRound)
+static GraphRound* graph_of(Ctx& c, pt_graph* g) {
+    GraphRound* r = reinterpret_cast<GraphRound*>(g);
+    if (!g || std::find(c.graphs.begin(), c.graphs.end(), r) == c.graphs.end())
+        fail(c, PT_ERR_INVALID_ARG, "unknown graph");
+    return r;
+}
+
+pt_status pt_graph_create(pt_ctx* ctx, int n, const int* aln_ids, const int* frontier_caps, const double* thresholds,
+                          pt_graph** out) {
+    return guarded(ctx, [&](Ctx& c) {
+        if (n < 1 || !aln_ids || !frontier_caps || !thresholds || !out) fail(c, PT_ERR_INVALID_ARG, "bad arguments");
+        std::vector<int> ids(aln_ids, aln_ids + n), caps(frontier_caps, frontier_caps + n);
+        std::vector<double> thr(thresholds, thresholds + n);
+        GraphRound* r = graph_create(c, ids, caps, thr);
+        c.graphs.push_back(r);
+        *out = reinterpret_cast<pt_graph*>(r);
+    });
+}
+
+pt_status pt_graph_frontier_dev(pt_ctx* ctx, pt_graph* g, int k, int32_t** edges_dev, double** lengths_dev) {
+    return guarded(ctx, [&](Ctx& c) {
+        GraphRound* r = graph_of(c, g);
+        if (k < 0 || k >= r->na) fail(c, PT_ERR_INVALID_ARG, "alignment index %d out of range", k);
+        if (edges_dev) *edges_dev = r->a[k].in_edges;
+        if (lengths_dev) *lengths_dev = r->a[k].in_lens;
+    });
+}
+
+pt_status pt_graph_set_frontier(pt_ctx* ctx, pt_graph* g, int k, int n_frontier, const int32_t* edges,
+                                const double* lengths) {
+    return guarded(ctx, [&](Ctx& c) {
+        GraphRound* r = graph_of(c, g);
+        if (k < 0 || k >= r->na) fail(c, PT_ERR_INVALID_ARG, "alignment index %d out of range", k);
+        GraphAln& x = r->a[k];
+        if (n_frontier < 0 || n_frontier > x.F_cap || (n_frontier > 0 && (!edges || !lengths)))
+            fail(c, PT_ERR_INVALID_ARG, "bad frontier (%d trees, capacity %d)", n_frontier, x.F_cap);
+        validate_trees(c, x.n, n_frontier, edges, lengths);
+        if (n_frontier > 0) {
+            ck(c, cudaMemcpyAsync(x.in_edges, edges, 4 * (size_t)n_frontier * 2 * x.E, cudaMemcpyHostToDevice, c.stream),
+               "copy in");
+            ck(c, cudaMemcpyAsync(x.in_lens, lengths, 8 * (size_t)n_frontier * x.E, cudaMemcpyHostToDevice, c.stream),
+               "copy in");
+        }
+        ck(c, cudaStreamSynchronize(c.stream), "sync");
+    });
+}
+
+pt_status pt_graph_run(pt_ctx* ctx, pt_graph* g, const int* n_frontier, double* lmax_inout, int* n_next) {
+    return guarded(ctx, [&](Ctx& c) {
+        GraphRound* r = graph_of(c, g);
+        if (!n_frontier || !lmax_inout || !n_next) fail(c, PT_ERR_INVALID_ARG, "bad arguments");
+        graph_run(c, *r, n_frontier, lmax_inout, n_next);
+        collect_times(c);
+    });
+}
+
+pt_status pt_graph_next_dev(pt_ctx* ctx, pt_graph* g, int k, const int32_t** edges_dev, const double** lengths_dev,
+                            const double** lnl_dev, const uint64_t** keys_dev) {
+    return guarded(ctx, [&](Ctx& c) {
+        GraphRound* r = graph_of(c, g);
+        if (k < 0 || k >= r->na) fail(c, PT_ERR_INVALID_ARG, "alignment index %d out of range", k);
+        if (edges_dev) *edges_dev = r->a[k].out_edges;
+        if (lengths_dev) *lengths_dev = r->a[k].out_lens;
+        if (lnl_dev) *lnl_dev = r->a[k].out_lnl;
+        if (keys_dev) *keys_dev = r->a[k].out_keys;
+    });
+}
+
+pt_status pt_graph_get_next(pt_ctx* ctx, pt_graph* g, int k, int cap, int32_t* edges, double* lengths, double* lnl,
+                            pt_key* keys, int* n) {
+    return guarded(ctx, [&](Ctx& c) {
+        GraphRound* r = graph_of(c, g);
+        if (k < 0 || k >= r->na || !n) fail(c, PT_ERR_INVALID_ARG, "bad arguments");
+        GraphAln& x = r->a[k];
+        const int cnt = r->hi[r->oG() + k];
+        *n = cnt;
+        if (cnt > cap) fail(c, PT_ERR_BUFFER_TOO_SMALL, "next frontier holds %d trees, %d fit", cnt, cap);
+        if (cnt > 0) {
+            if (edges) ck(c, cudaMemcpyAsync(edges, x.out_edges, 4 * (size_t)cnt * 2 * x.E, cudaMemcpyDeviceToHost, c.stream), "copy out");
+            if (lengths) ck(c, cudaMemcpyAsync(lengths, x.out_lens, 8 * (size_t)cnt * x.E, cudaMemcpyDeviceToHost, c.stream), "copy out");
+            if (lnl) ck(c, cudaMemcpyAsync(lnl, x.out_lnl, 8 * (size_t)cnt, cudaMemcpyDeviceToHost, c.stream), "copy out");
+            if (keys) ck(c, cudaMemcpyAsync(keys, x.out_keys, 16 * (size_t)cnt, cudaMemcpyDeviceToHost, c.stream), "copy out");
+        }
+        ck(c, cudaStreamSynchronize(c.stream), "sync");
+    });
+}
+
+pt_status pt_graph_advance(pt_ctx* ctx, pt_graph* g, int* n_frontier) {
+    return guarded(ctx, [&](Ctx& c) {
+        GraphRound* r = graph_of(c, g);
+        if (!n_frontier) fail(c, PT_ERR_INVALID_ARG, "bad arguments");
+        for (int k = 0; k < r->na; ++k)
+            if (r->hi[r->oG() + k] > r->a[k].F_cap)
+                fail(c, PT_ERR_BUFFER_TOO_SMALL, "next frontier %d holds %d trees, capacity %d", k, r->hi[r->oG() + k],
+                     r->a[k].F_cap);
+        for (int k = 0; k < r->na; ++k) {
+            GraphAln& x = r->a[k];
+            const int cnt = r->hi[r->oG() + k];
+            if (cnt > 0) {
+                ck(c, cudaMemcpyAsync(x.in_edges, x.out_edges, 4 * (size_t)cnt * 2 * x.E, cudaMemcpyDeviceToDevice, c.stream), "advance");
+                ck(c, cudaMemcpyAsync(x.in_lens, x.out_lens, 8 * (size_t)cnt * x.E, cudaMemcpyDeviceToDevice, c.stream), "advance");
+            }
+            n_frontier[k] = cnt;
+        }
+        ck(c, cudaStreamSynchronize(c.stream), "sync");
+    });
+}
+
+pt_status pt_graph_destroy(pt_ctx* ctx, pt_graph* g) {
+    if (!g) return PT_OK;
+    return guarded(ctx, [&](Ctx& c) {
+        GraphRound* r = graph_of(c, g);
+        if (c.stream) cudaStreamSynchronize(c.stream);
+        c.graphs.erase(std::find(c.graphs.begin(), c.graphs.end(), r));
+        graph_free(r);
+    });
+}
 
 pt_status pt_visited(pt_ctx* ctx, int aln_id, size_t cap, pt_key* keys, uint8_t* status, double* lnl,
                      size_t* count) {

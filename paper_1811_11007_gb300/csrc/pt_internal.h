@@ -9,6 +9,27 @@
 namespace pt {
 
 constexpr int kMaxTaxa = 128;
+
+// A count known on the host (d == nullptr: the count is cap) or produced on
+// the device by an earlier kernel of the same stream (d != nullptr: the
+// count is min(*d, cap), and cap sizes the grid).  Device-side counts let a
+// whole round run without reading anything back, so it can be captured in a
+// CUDA graph and replayed.
+struct DCount {
+    int cap;
+    const int* d;
+};
+inline DCount hcount(int n) { return DCount{n, nullptr}; }
+// A round number known on the host (d == nullptr: r) or on the device (*d + r).
+struct DRound {
+    int r;
+    const int* d;
+};
+inline DRound hround(int r) { return DRound{r, nullptr}; }
+#ifdef __CUDACC__
+__device__ __forceinline__ int dcount(const DCount& c) { return c.d ? min(*c.d, c.cap) : c.cap; }
+__device__ __forceinline__ int dround(const DRound& x) { return x.d ? *x.d + x.r : x.r; }
+#endif
 constexpr int kMaxNode = 2 * kMaxTaxa - 2;
 constexpr int kMaxCat = 4;
 
@@ -105,6 +126,8 @@ size_t mlp_bwd_smem();
 void mlp_cast(cudaStream_t s, MlpDev m, const float* w);
 void mlp_forward(cudaStream_t s, MlpDev m, const void* Xb, int N, float* Y, float* Z1, void* H1, float* Z2, void* H2,
                  bool train);
+// Inference over a device row count (N.cap bounds it; rows past the count are skipped).
+void mlp_forward(cudaStream_t s, MlpDev m, const void* Xb, DCount N, float* Y);
 void mlp_loss(cudaStream_t s, const float* Y, const float* T, int N, void* dY, double* loss);
 void mlp_backward(cudaStream_t s, MlpDev m, const void* Xb, const float* Z1, const void* H1, const float* Z2,
                   const void* H2, const void* dY, int N, float* grad);
@@ -116,35 +139,44 @@ void mlp_pack(cudaStream_t s, const float* Xf, int N, void* Xb);
 // ---- launchers (pt_kernels.cu) ----
 void launch_canon(cudaStream_t s, int n, int count, const int32_t* edges, const double* lengths, TreeSet ts,
                   int32_t* err);
+void launch_canon(cudaStream_t s, int n, DCount count, const int32_t* edges, const double* lengths, TreeSet ts,
+                  int32_t* err);
 void launch_table_init(cudaStream_t s, Slot* tab, size_t nslots);
-void launch_enum(cudaStream_t s, int n, int F, TreeSet fr, uint64_t* nkey, int32_t* cinfo);
-void launch_cand_insert(cudaStream_t s, Slot* tab, int log2, int ncand, const uint64_t* nkey, const int32_t* cinfo,
-                        TreeSet fr, int round, int32_t* cslot, int32_t* flag, int32_t* err,
+void launch_enum(cudaStream_t s, int n, DCount F, TreeSet fr, uint64_t* nkey, int32_t* cinfo);
+// Candidates [0, ncand.cap): entries at or past the device count get flag 0.
+void launch_cand_insert(cudaStream_t s, Slot* tab, int log2, DCount ncand, const uint64_t* nkey, const int32_t* cinfo,
+                        TreeSet fr, DRound round, int32_t* cslot, int32_t* flag, int32_t* err,
                         unsigned long long* stats);
-void launch_cand_arb(cudaStream_t s, int phase, Slot* tab, int ncand, const int32_t* cinfo, TreeSet fr, int round,
-                     const int32_t* cslot, int32_t* flag);
+void launch_cand_arb(cudaStream_t s, int phase, Slot* tab, DCount ncand, const int32_t* cinfo, TreeSet fr,
+                     DRound round, const int32_t* cslot, int32_t* flag);
 void launch_scan(cudaStream_t s, const int32_t* in, int32_t* out, int N, int32_t* tmp);
+// *total = out[N-1] + in[N-1] (the exclusive scan's total) on the device.
+void launch_scan_total(cudaStream_t s, const int32_t* in, const int32_t* out, int N, int32_t* total);
+// Device-side counts of a graph round: ncand[k] = F[k] * m[k] and the prefix
+// sums of per-group item counts (gstart[g + 1] = gstart[g] + cnt[g]).
+void launch_mul_counts(cudaStream_t s, int na, const int* F, const int* m, int* ncand);
+void launch_prefix_counts(cudaStream_t s, int ng, const int* cnt, int* gstart);
 void launch_make_items(cudaStream_t s, int ncand, const int32_t* flag, const int32_t* pos, const int32_t* cinfo,
                        const int32_t* cslot, const uint64_t* nkey, Item* items, uint64_t* ikey);
 void launch_compact_idx(cudaStream_t s, int N, const int32_t* flag, const int32_t* pos, int32_t* idx);
-void launch_insert_trees(cudaStream_t s, Slot* tab, int log2, int count, TreeSet ts, const double* lnl,
-                         const int32_t* status, int round, int32_t* winner, int32_t* err);
-void launch_finalize_trees(cudaStream_t s, Slot* tab, int count, const int32_t* slot_of, const double* lnl,
-                           const double* lmax, double thr, int round, int32_t* good, unsigned long long* stats);
-void launch_lmax(cudaStream_t s, int count, const double* lnl, const int32_t* mask, double* lmax);
+void launch_insert_trees(cudaStream_t s, Slot* tab, int log2, DCount count, TreeSet ts, const double* lnl,
+                         const int32_t* status, DRound round, int32_t* winner, int32_t* err);
+void launch_finalize_trees(cudaStream_t s, Slot* tab, DCount count, const int32_t* slot_of, const double* lnl,
+                           const double* lmax, double thr, DRound round, int32_t* good, unsigned long long* stats);
+void launch_lmax(cudaStream_t s, DCount count, const double* lnl, const int32_t* mask, double* lmax);
 void launch_dump(cudaStream_t s, const Slot* tab, size_t nslots, int32_t* flag);
 void launch_dump_gather(cudaStream_t s, const Slot* tab, size_t nslots, const int32_t* flag, const int32_t* pos,
                         uint64_t* keys, uint8_t* status, double* lnl);
-void launch_materialize(cudaStream_t s, int n, int nk, const int32_t* kidx, const Item* items, TreeSet fr,
+void launch_materialize(cudaStream_t s, int n, DCount nk, const int32_t* kidx, const Item* items, TreeSet fr,
                         const double* len5, int32_t* edges_out, double* lengths_out, int32_t* slot_of);
-void launch_gather_out(cudaStream_t s, int n, int count, const int32_t* idx, TreeSet ts, const double* lnl,
+void launch_gather_out(cudaStream_t s, int n, DCount count, const int32_t* idx, TreeSet ts, const double* lnl,
                        int32_t* edges_out, double* lengths_out, double* lnl_out, uint64_t* keys_out);
 void launch_lengths_to_input(cudaStream_t s, int n, int count, TreeSet ts, double* lengths_out);
 
 // Partials of a group of trees (all D_v, and U_v when with_up).
 // pm: P-matrix buffer of pmat_bytes(prec, C, n, count) bytes; launch_propose reads it for the same group.
 size_t pmat_bytes(int prec, int C, int n, int count);
-void launch_partials(cudaStream_t s, int prec, const Model& M, Aln A, TreeSet ts, int first, int count, ClvGroup g,
+void launch_partials(cudaStream_t s, int prec, const Model& M, Aln A, TreeSet ts, int first, DCount count, ClvGroup g,
                      bool with_up, int threads, void* pm);
 // One group of a batched proposal launch: the work items of one alignment
 // whose frontier trees [first, first + count) have their partials in g.
@@ -156,7 +188,7 @@ struct PropGroup {
     ClvGroup g;
     const void* Pm;          // P matrices of the group's trees (launch_partials)
     Slot* tab;
-    int round;
+    DRound round;
     const double* lmax;      // lmax at the start of the round (device)
     double thr;
     const Item* items;       // the group's items; outputs are indexed like them
@@ -166,6 +198,8 @@ struct PropGroup {
     const double* init;      // learned starting lengths [count][5] or nullptr
 };
 // One group of a batched full-optimisation launch: trees [first, first + n) of ts.
+// Partials: g (tree i of the group at g.clv + i * tree_stride), or, when the
+// launch passes a slab, the launching CTA's own part of it (g unused).
 struct FullGroup {
     Model M;
     Aln A;
@@ -183,7 +217,9 @@ void launch_propose(cudaStream_t s, int prec, int C, const PropGroup* groups, co
                     size_t scratch_per_cta, int maxP);
 void launch_fullopt(cudaStream_t s, int prec, int C, const FullGroup* groups, const int* gstart, int ngroups,
                     int* counter, int maxN, int maxP, Cfg cfg, unsigned long long* stats, int threads, int grid,
-                    void* scratch, size_t scratch_per_cta);
+                    void* scratch, size_t scratch_per_cta, void* slab = nullptr, size_t slab_per_cta = 0);
+// Bytes of one CTA's partials slab for trees of n taxa and P patterns (a multiple of 256).
+size_t fullopt_slab_bytes(int prec, int C, int n, int P);
 
 // GTR+Gamma model set-up on the host (pt_api.cu); false on invalid parameters.
 bool host_build_model(const double exch[6], const double freqs[4], double alpha, int C, Model& M);
@@ -196,11 +232,12 @@ int fullopt_blocks_per_sm(int prec, int C, int threads, bool smem_tab, int maxN,
 long long launch_count();
 
 // Feature kernels of the warm start (pt_mlp.cu).
-void launch_slot_summary(cudaStream_t s, int prec, int C, Aln A, ClvGroup g, int ntrees, int nslot, float* out);
+void launch_slot_summary(cudaStream_t s, int prec, int C, Aln A, ClvGroup g, DCount ntrees, int nslot, float* out);
 void launch_tip_summary(cudaStream_t s, Aln A, int C, float* out);
-void launch_item_features(cudaStream_t s, int n, const Item* items, int i0, int i1, TreeSet fr, int first,
+// items [i0, i1): i1 may be a device count (i1.cap bounds it).
+void launch_item_features(cudaStream_t s, int n, const Item* items, int i0, DCount i1, TreeSet fr, int first,
                           const float* slot_sum, int nslot, const float* tip_sum, float* Xf, void* Xb);
-void launch_item_init(cudaStream_t s, const Item* items, int i0, int i1, const float* Xf, const float* Y, double tmin,
+void launch_item_init(cudaStream_t s, const Item* items, int i0, DCount i1, const float* Xf, const float* Y, double tmin,
                       double tmax, double* init);
 void launch_log_pairs(cudaStream_t s, const Item* items, int i0, int i1, const float* Xf, const double* len5, float* LX,
                       float* LT, unsigned long long* count, size_t cap);

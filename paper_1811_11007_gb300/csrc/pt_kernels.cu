@@ -84,12 +84,12 @@ struct CanonSmem {
     uint8_t mint[kMaxNode];
 };
 
-__global__ void k_canon(int n, int count, const int32_t* __restrict__ edges, const double* __restrict__ lengths,
+__global__ void k_canon(int n, DCount cnt, const int32_t* __restrict__ edges, const double* __restrict__ lengths,
                         TreeSet ts, int32_t* err) {
     __shared__ CanonSmem sm_all[kCanonWarps];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int tree = blockIdx.x * kCanonWarps + warp;
-    if (tree >= count) return;
+    if (tree >= dcount(cnt)) return;
     CanonSmem& s = sm_all[warp];
     const int NN = 2 * n - 2, E = 2 * n - 3;
     const int32_t* ed = edges + (size_t)tree * 2 * E;
@@ -247,9 +247,9 @@ __global__ void k_canon(int n, int count, const int32_t* __restrict__ edges, con
 // parent u, v's sibling B, v's children C < D.  Swap 0 exchanges B and C
 // (new split B u D), swap 1 exchanges B and D (new split B u C); the key
 // changes by H(new split) - H(C u D).
-__global__ void k_enum(int n, int F, TreeSet fr, uint64_t* __restrict__ nkey, int32_t* __restrict__ cinfo) {
+__global__ void k_enum(int n, DCount Fc, TreeSet fr, uint64_t* __restrict__ nkey, int32_t* __restrict__ cinfo) {
     const int m = 2 * (n - 3);
-    const long long total = (long long)F * m;
+    const long long total = (long long)dcount(Fc) * m;
     for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < total;
          c += (long long)gridDim.x * blockDim.x) {
         int f = (int)(c / m), r = (int)(c % m), j = r >> 1, sw = r & 1;
@@ -306,11 +306,13 @@ __global__ void k_table_init(Slot* tab, size_t nslots) {
     }
 }
 
-__global__ void k_cand_insert(Slot* tab, int log2, int ncand, const uint64_t* __restrict__ nkey,
-                              const int32_t* __restrict__ cinfo, TreeSet fr, int round, int32_t* cslot,
+__global__ void k_cand_insert(Slot* tab, int log2, DCount nc, const uint64_t* __restrict__ nkey,
+                              const int32_t* __restrict__ cinfo, TreeSet fr, DRound rd, int32_t* cslot,
                               int32_t* flag, int32_t* err, unsigned long long* stats) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int ncand = dcount(nc), round = dround(rd);
     int dup = 0;
+    if (i >= ncand && i < nc.cap) { cslot[i] = -1; flag[i] = 0; }  // past the device count
     if (i < ncand) {
         bool created;
         long long s = table_find_or_claim(tab, log2, nkey[2 * i], nkey[2 * i + 1], &created);
@@ -335,10 +337,11 @@ __global__ void k_cand_insert(Slot* tab, int log2, int ncand, const uint64_t* __
 // phase 2: smallest low word of the parent key among proposers with the smallest high word;
 // phase 3: smallest (edge rank, swap) among proposers with the smallest parent key;
 // phase 4: flag = this candidate is the winner of its slot.
-__global__ void k_cand_arb(int phase, Slot* tab, int ncand, const int32_t* __restrict__ cinfo, TreeSet fr, int round,
+__global__ void k_cand_arb(int phase, Slot* tab, DCount nc, const int32_t* __restrict__ cinfo, TreeSet fr, DRound rd,
                            const int32_t* __restrict__ cslot, int32_t* flag) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= ncand || !flag[i]) return;
+    if (i >= dcount(nc) || !flag[i]) return;
+    const int round = dround(rd);
     Slot* sl = &tab[cslot[i]];
     int f = cinfo[4 * i];
     unsigned long long phi = fr.key[2 * f + 1], plo = fr.key[2 * f];
@@ -373,10 +376,10 @@ __global__ void k_compact_idx(int N, const int32_t* __restrict__ flag, const int
 // Enters whole trees (starts, or a caller's frontier) as visited.  Among
 // equal keys the lowest index wins; status/lnl written by the winner.  A key
 // already present from an earlier call is left as it is (winner = -1).
-__global__ void k_insert_trees(Slot* tab, int log2, int count, TreeSet ts, const double* lnl, const int32_t* status,
-                               int round, int32_t* winner, int32_t* err) {
+__global__ void k_insert_trees(Slot* tab, int log2, DCount cnt, TreeSet ts, const double* lnl, const int32_t* status,
+                               int32_t* winner, int32_t* err) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= count) return;
+    if (i >= dcount(cnt)) return;
     bool created;
     long long s = table_find_or_claim(tab, log2, ts.key[2 * i], ts.key[2 * i + 1], &created);
     if (s < 0) { atomicExch(&err[kErrTable], 1); winner[i] = -1; return; }
@@ -388,10 +391,11 @@ __global__ void k_insert_trees(Slot* tab, int log2, int count, TreeSet ts, const
     winner[i] = (int32_t)s;
 }
 
-__global__ void k_insert_trees_fin(Slot* tab, int count, const double* lnl, const int32_t* status, int round,
+__global__ void k_insert_trees_fin(Slot* tab, DCount cnt, const double* lnl, const int32_t* status, DRound rd,
                                    int32_t* winner) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= count || winner[i] < 0) return;
+    if (i >= dcount(cnt) || winner[i] < 0) return;
+    const int round = dround(rd);
     Slot* sl = &tab[winner[i]];
     if (sl->alo != (unsigned long long)i) { winner[i] = -1; return; }
     sl->lnl = lnl ? lnl[i] : __longlong_as_double(0x7ff8000000000000ll);
@@ -406,8 +410,9 @@ __device__ __forceinline__ long long ord_of(double x) {
 __device__ __forceinline__ double of_ord(long long b) {
     return __longlong_as_double(b >= 0 ? b : (b ^ 0x7fffffffffffffffll));
 }
-__global__ void k_lmax(int count, const double* lnl, const int32_t* mask, double* lmax) {
+__global__ void k_lmax(DCount cnt, const double* lnl, const int32_t* mask, double* lmax) {
     __shared__ long long best;
+    const int count = dcount(cnt);
     if (threadIdx.x == 0) best = ord_of(*lmax);
     __syncthreads();
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < count; i += gridDim.x * blockDim.x)
@@ -427,9 +432,10 @@ __global__ void k_lmax(int count, const double* lnl, const int32_t* mask, double
 }
 
 // Visit decision of fully optimised trees: GOOD iff lnl >= lmax - thr.
-__global__ void k_finalize_trees(Slot* tab, int count, const int32_t* slot_of, const double* lnl, const double* lmax,
-                                 double thr, int round, int32_t* good, unsigned long long* stats) {
+__global__ void k_finalize_trees(Slot* tab, DCount cnt, const int32_t* slot_of, const double* lnl, const double* lmax,
+                                 double thr, DRound rd, int32_t* good, unsigned long long* stats) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int count = dcount(cnt), round = dround(rd);
     int g = 0;
     if (i < count) {
         g = lnl[i] >= *lmax - thr;
@@ -507,14 +513,28 @@ __global__ void k_scan_add(int32_t* out, int N, const int32_t* bsum) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < N) out[i] += bsum[blockIdx.x];
 }
+__global__ void k_scan_total(const int32_t* in, const int32_t* out, int N, int32_t* total) {
+    if (threadIdx.x == 0) *total = N > 0 ? out[N - 1] + in[N - 1] : 0;
+}
+__global__ void k_mul_counts(int na, const int* F, const int* m, int* ncand) {
+    const int k = threadIdx.x;
+    if (k < na) ncand[k] = F[k] * m[k];
+}
+__global__ void k_prefix_counts(int ng, const int* cnt, int* gstart) {
+    if (threadIdx.x == 0) {
+        int acc = 0;
+        gstart[0] = 0;
+        for (int g = 0; g < ng; ++g) { acc += cnt[g]; gstart[g + 1] = acc; }
+    }
+}
 
 // ---------------------------------------------------------------- tree outputs
 // Materialises NNI neighbours as edge lists in the parent's canonical
 // numbering with the five optimised lengths; the canonicaliser renumbers them.
-__global__ void k_materialize(int n, int nk, const int32_t* kidx, const Item* items, TreeSet fr, const double* len5,
+__global__ void k_materialize(int n, DCount nk, const int32_t* kidx, const Item* items, TreeSet fr, const double* len5,
                               int32_t* edges_out, double* lengths_out, int32_t* slot_of) {
     int k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= nk) return;
+    if (k >= dcount(nk)) return;
     const int NN = 2 * n - 2, E = 2 * n - 3;
     int ii = kidx[k];
     Item it = items[ii];
@@ -546,10 +566,10 @@ __global__ void k_materialize(int n, int nk, const int32_t* kidx, const Item* it
 }
 
 // Gathers trees idx[k] of a set into canonical edge lists + lengths + lnl + keys.
-__global__ void k_gather_out(int n, int count, const int32_t* idx, TreeSet ts, const double* lnl, int32_t* edges_out,
+__global__ void k_gather_out(int n, DCount cnt, const int32_t* idx, TreeSet ts, const double* lnl, int32_t* edges_out,
                              double* lengths_out, double* lnl_out, uint64_t* keys_out) {
     int k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= count) return;
+    if (k >= dcount(cnt)) return;
     const int NN = 2 * n - 2, E = 2 * n - 3;
     int t = idx ? idx[k] : k;
     const int32_t* up = ts.up + (size_t)t * NN;
@@ -864,7 +884,7 @@ template <typename R, int C>
 __device__ __forceinline__ void put_egh(const Model& M, double t, NewtonSmem<R, C>& ns, bool exact,
                                         int q = threadIdx.x) {
     if (q < 4 * C) {
-        int r = q >> 2, k = q & 3;
+        const int k = q & 3;
         if (k == 0) {
             ns.egh[0][q] = (R)(1.0 / C);
             ns.egh[1][q] = R(0);
@@ -936,16 +956,7 @@ __device__ __forceinline__ bool newton_step(double& t, double& lo, double& hi, d
     return conv;
 }
 
-// ln x for x > 0: FP32 input as 2^e * m (m in [1, 2)), ln m in FP32 and the
-// exponent part in FP64, so the rounding error is that of ln m (< 0.7) rather
-// than of ln x; FP64 input directly.
-__device__ __forceinline__ double log_split(float x) {
-    int b = __float_as_int(x);
-    int e = ((b >> 23) & 0xff) - 127;
-    if (e == -127) return (double)logf(x);
-    float m = __int_as_float((b & 0x007fffff) | 0x3f800000);
-    return (double)logf(m) + (double)e * kLn2;
-}
+// ln x of an FP64 site likelihood.
 __device__ __forceinline__ double log_split(double x) { return log(x); }
 
 // lnL of the current sum-table at length t: sum_p w_p (ln L_p + E_p ln 2), FP64 accumulation.
@@ -1103,9 +1114,9 @@ __device__ double newton_solve(const Model& M, const Cfg& cfg, const STab<R, C>&
 // ---------------------------------------------------------------- P matrices of tree sets
 // Pm[tree][v][r][16] for v = 1..NN-1 (edge (v, up v)); row per thread.
 template <typename R>
-__global__ void k_pmats(Model M, TreeSet ts, int first, int count, R* Pm) {
+__global__ void k_pmats(Model M, TreeSet ts, int first, DCount cnt, R* Pm) {
     const int n = ts.n, NN = 2 * n - 2, C = M.C;
-    long long total = (long long)count * NN * C * 4;
+    long long total = (long long)dcount(cnt) * NN * C * 4;
     for (long long x = blockIdx.x * (long long)blockDim.x + threadIdx.x; x < total;
          x += (long long)gridDim.x * blockDim.x) {
         int i = (int)(x & 3);
@@ -1122,12 +1133,13 @@ __global__ void k_pmats(Model M, TreeSet ts, int first, int count, R* Pm) {
 // ---------------------------------------------------------------- partials (K1)
 // grid (tree, site chunk).  All D_v bottom-up, then all U_v top-down.
 template <typename R, int C>
-__global__ void k_partials(Model M, Aln A, TreeSet ts, int first, ClvGroup g, const R* __restrict__ Pm_all,
+__global__ void k_partials(Model M, Aln A, TreeSet ts, int first, DCount cnt, ClvGroup g, const R* __restrict__ Pm_all,
                            int with_up) {
     extern __shared__ __align__(16) unsigned char smraw[];
     R* Pm = reinterpret_cast<R*>(smraw);
     const int n = ts.n, NN = 2 * n - 2, P = A.P;
     const int gi = blockIdx.x, tree = first + gi;
+    if (gi >= dcount(cnt)) return;  // uniform over the block
     const R* Psrc = Pm_all + (size_t)gi * NN * C * 16;
     for (int x = threadIdx.x; x < NN * C * 16; x += blockDim.x) Pm[x] = Psrc[x];
     __syncthreads();
@@ -1366,7 +1378,7 @@ __global__ void __launch_bounds__(512) k_propose(const PropGroup* __restrict__ g
             G.kept[o] = k;
             Slot* sl = &G.tab[it.slot];
             sl->lnl = f1;
-            sl->tag = ((unsigned long long)G.round << 48) | (unsigned long long)(k ? 4 : 1);
+            sl->tag = ((unsigned long long)dround(G.round) << 48) | (unsigned long long)(k ? 4 : 1);
         }
     }
     if (threadIdx.x == 0) {
@@ -1393,7 +1405,7 @@ template <typename R, int C, bool kSmemTab>
 __global__ void __launch_bounds__(512) k_fullopt(const FullGroup* __restrict__ groups, const int* __restrict__ gstart,
                                                  int ngroups, int* counter, int nn_max, Cfg cfg,
                                                  unsigned long long* stats, unsigned char* scratch,
-                                                 size_t scratch_per_cta) {
+                                                 size_t scratch_per_cta, unsigned char* slab, size_t slab_per_cta) {
     extern __shared__ __align__(16) unsigned char smraw[];
     FullSmem<R, C>& sm = *reinterpret_cast<FullSmem<R, C>*>(smraw);
     size_t off = (sizeof(FullSmem<R, C>) + 15) & ~size_t(15);
@@ -1431,8 +1443,16 @@ __global__ void __launch_bounds__(512) k_fullopt(const FullGroup* __restrict__ g
         const int32_t* ch = G.ts.ch + (size_t)tree * NN * 2;
         const int32_t* sched = G.ts.sched + (size_t)tree * 3 * n;
         double* glen = G.ts.len + (size_t)tree * NN;
-        R* clv = reinterpret_cast<R*>(G.g.clv) + (size_t)gi * G.g.tree_stride;
-        int32_t* scl = G.g.scl + (size_t)gi * G.g.scl_stride;
+        R* clv;
+        int32_t* scl;
+        if (slab) {  // this CTA's own partials, reused tree after tree
+            unsigned char* b = slab + (size_t)blockIdx.x * slab_per_cta;
+            clv = reinterpret_cast<R*>(b);
+            scl = reinterpret_cast<int32_t*>(b + (((size_t)(2 * n - 5) * P * 4 * C * sizeof(R) + 255) & ~size_t(255)));
+        } else {
+            clv = reinterpret_cast<R*>(G.g.clv) + (size_t)gi * G.g.tree_stride;
+            scl = G.g.scl + (size_t)gi * G.g.scl_stride;
+        }
         if (threadIdx.x < 16) {
             const int i = threadIdx.x >> 2, k = threadIdx.x & 3;
             sm.Mt[threadIdx.x] = (R)(M.sqpi[i] * M.R[i * 4 + k]);
@@ -1578,11 +1598,15 @@ inline int blocks_for(long long n, int t) { return (int)((n + t - 1) / t); }
 }  // namespace
 
 // ================================================================= launchers
+void launch_canon(cudaStream_t s, int n, DCount count, const int32_t* edges, const double* lengths, TreeSet ts,
+                  int32_t* err) {
+    if (count.cap <= 0) return;
+    k_canon<<<blocks_for(count.cap, kCanonWarps), 32 * kCanonWarps, 0, s>>>(n, count, edges, lengths, ts, err);
+    ++g_launches;
+}
 void launch_canon(cudaStream_t s, int n, int count, const int32_t* edges, const double* lengths, TreeSet ts,
                   int32_t* err) {
-    if (count <= 0) return;
-    k_canon<<<blocks_for(count, kCanonWarps), 32 * kCanonWarps, 0, s>>>(n, count, edges, lengths, ts, err);
-    ++g_launches;
+    launch_canon(s, n, hcount(count), edges, lengths, ts, err);
 }
 
 void launch_table_init(cudaStream_t s, Slot* tab, size_t nslots) {
@@ -1590,26 +1614,26 @@ void launch_table_init(cudaStream_t s, Slot* tab, size_t nslots) {
     ++g_launches;
 }
 
-void launch_enum(cudaStream_t s, int n, int F, TreeSet fr, uint64_t* nkey, int32_t* cinfo) {
-    long long total = (long long)F * 2 * (n - 3);
+void launch_enum(cudaStream_t s, int n, DCount F, TreeSet fr, uint64_t* nkey, int32_t* cinfo) {
+    long long total = (long long)F.cap * 2 * (n - 3);
     if (total <= 0) return;
     k_enum<<<(int)std::min<long long>(blocks_for(total, 256), 65535), 256, 0, s>>>(n, F, fr, nkey, cinfo);
     ++g_launches;
 }
 
-void launch_cand_insert(cudaStream_t s, Slot* tab, int log2, int ncand, const uint64_t* nkey, const int32_t* cinfo,
-                        TreeSet fr, int round, int32_t* cslot, int32_t* flag, int32_t* err,
+void launch_cand_insert(cudaStream_t s, Slot* tab, int log2, DCount ncand, const uint64_t* nkey, const int32_t* cinfo,
+                        TreeSet fr, DRound round, int32_t* cslot, int32_t* flag, int32_t* err,
                         unsigned long long* stats) {
-    if (ncand <= 0) return;
-    k_cand_insert<<<blocks_for(ncand, 256), 256, 0, s>>>(tab, log2, ncand, nkey, cinfo, fr, round, cslot, flag, err,
-                                                         stats);
+    if (ncand.cap <= 0) return;
+    k_cand_insert<<<blocks_for(ncand.cap, 256), 256, 0, s>>>(tab, log2, ncand, nkey, cinfo, fr, round, cslot, flag, err,
+                                                             stats);
     ++g_launches;
 }
 
-void launch_cand_arb(cudaStream_t s, int phase, Slot* tab, int ncand, const int32_t* cinfo, TreeSet fr, int round,
-                     const int32_t* cslot, int32_t* flag) {
-    if (ncand <= 0) return;
-    k_cand_arb<<<blocks_for(ncand, 256), 256, 0, s>>>(phase, tab, ncand, cinfo, fr, round, cslot, flag);
+void launch_cand_arb(cudaStream_t s, int phase, Slot* tab, DCount ncand, const int32_t* cinfo, TreeSet fr,
+                     DRound round, const int32_t* cslot, int32_t* flag) {
+    if (ncand.cap <= 0) return;
+    k_cand_arb<<<blocks_for(ncand.cap, 256), 256, 0, s>>>(phase, tab, ncand, cinfo, fr, round, cslot, flag);
     ++g_launches;
 }
 
@@ -1621,6 +1645,21 @@ void launch_scan(cudaStream_t s, const int32_t* in, int32_t* out, int N, int32_t
     k_scan_sums<<<1, 1024, 0, s>>>(tmp, nb);
     ++g_launches;
     k_scan_add<<<nb, 1024, 0, s>>>(out, N, tmp);
+    ++g_launches;
+}
+
+void launch_scan_total(cudaStream_t s, const int32_t* in, const int32_t* out, int N, int32_t* total) {
+    k_scan_total<<<1, 32, 0, s>>>(in, out, N, total);
+    ++g_launches;
+}
+
+void launch_mul_counts(cudaStream_t s, int na, const int* F, const int* m, int* ncand) {
+    k_mul_counts<<<1, 32 * ((na + 31) / 32), 0, s>>>(na, F, m, ncand);
+    ++g_launches;
+}
+
+void launch_prefix_counts(cudaStream_t s, int ng, const int* cnt, int* gstart) {
+    k_prefix_counts<<<1, 32, 0, s>>>(ng, cnt, gstart);
     ++g_launches;
 }
 
@@ -1637,25 +1676,26 @@ void launch_compact_idx(cudaStream_t s, int N, const int32_t* flag, const int32_
     ++g_launches;
 }
 
-void launch_insert_trees(cudaStream_t s, Slot* tab, int log2, int count, TreeSet ts, const double* lnl,
-                         const int32_t* status, int round, int32_t* winner, int32_t* err) {
-    if (count <= 0) return;
-    k_insert_trees<<<blocks_for(count, 256), 256, 0, s>>>(tab, log2, count, ts, lnl, status, round, winner, err);
+void launch_insert_trees(cudaStream_t s, Slot* tab, int log2, DCount count, TreeSet ts, const double* lnl,
+                         const int32_t* status, DRound round, int32_t* winner, int32_t* err) {
+    if (count.cap <= 0) return;
+    k_insert_trees<<<blocks_for(count.cap, 256), 256, 0, s>>>(tab, log2, count, ts, lnl, status, winner, err);
     ++g_launches;
-    k_insert_trees_fin<<<blocks_for(count, 256), 256, 0, s>>>(tab, count, lnl, status, round, winner);
-    ++g_launches;
-}
-
-void launch_finalize_trees(cudaStream_t s, Slot* tab, int count, const int32_t* slot_of, const double* lnl,
-                           const double* lmax, double thr, int round, int32_t* good, unsigned long long* stats) {
-    if (count <= 0) return;
-    k_finalize_trees<<<blocks_for(count, 256), 256, 0, s>>>(tab, count, slot_of, lnl, lmax, thr, round, good, stats);
+    k_insert_trees_fin<<<blocks_for(count.cap, 256), 256, 0, s>>>(tab, count, lnl, status, round, winner);
     ++g_launches;
 }
 
-void launch_lmax(cudaStream_t s, int count, const double* lnl, const int32_t* mask, double* lmax) {
-    if (count <= 0) return;
-    k_lmax<<<std::min(blocks_for(count, 256), 1024), 256, 0, s>>>(count, lnl, mask, lmax);
+void launch_finalize_trees(cudaStream_t s, Slot* tab, DCount count, const int32_t* slot_of, const double* lnl,
+                           const double* lmax, double thr, DRound round, int32_t* good, unsigned long long* stats) {
+    if (count.cap <= 0) return;
+    k_finalize_trees<<<blocks_for(count.cap, 256), 256, 0, s>>>(tab, count, slot_of, lnl, lmax, thr, round, good,
+                                                                stats);
+    ++g_launches;
+}
+
+void launch_lmax(cudaStream_t s, DCount count, const double* lnl, const int32_t* mask, double* lmax) {
+    if (count.cap <= 0) return;
+    k_lmax<<<std::min(blocks_for(count.cap, 256), 1024), 256, 0, s>>>(count, lnl, mask, lmax);
     ++g_launches;
 }
 
@@ -1670,18 +1710,19 @@ void launch_dump_gather(cudaStream_t s, const Slot* tab, size_t nslots, const in
     ++g_launches;
 }
 
-void launch_materialize(cudaStream_t s, int n, int nk, const int32_t* kidx, const Item* items, TreeSet fr,
+void launch_materialize(cudaStream_t s, int n, DCount nk, const int32_t* kidx, const Item* items, TreeSet fr,
                         const double* len5, int32_t* edges_out, double* lengths_out, int32_t* slot_of) {
-    if (nk <= 0) return;
-    k_materialize<<<blocks_for(nk, 128), 128, 0, s>>>(n, nk, kidx, items, fr, len5, edges_out, lengths_out, slot_of);
+    if (nk.cap <= 0) return;
+    k_materialize<<<blocks_for(nk.cap, 128), 128, 0, s>>>(n, nk, kidx, items, fr, len5, edges_out, lengths_out,
+                                                          slot_of);
     ++g_launches;
 }
 
-void launch_gather_out(cudaStream_t s, int n, int count, const int32_t* idx, TreeSet ts, const double* lnl,
+void launch_gather_out(cudaStream_t s, int n, DCount count, const int32_t* idx, TreeSet ts, const double* lnl,
                        int32_t* edges_out, double* lengths_out, double* lnl_out, uint64_t* keys_out) {
-    if (count <= 0) return;
-    k_gather_out<<<blocks_for(count, 128), 128, 0, s>>>(n, count, idx, ts, lnl, edges_out, lengths_out, lnl_out,
-                                                         keys_out);
+    if (count.cap <= 0) return;
+    k_gather_out<<<blocks_for(count.cap, 128), 128, 0, s>>>(n, count, idx, ts, lnl, edges_out, lengths_out, lnl_out,
+                                                             keys_out);
     ++g_launches;
 }
 
@@ -1724,16 +1765,16 @@ size_t fullopt_smem_bytes(int prec, int C, int n, int P, bool table_in_smem, int
 
 namespace {
 template <typename R, int C>
-void partials_t(cudaStream_t s, const Model& M, Aln A, TreeSet ts, int first, int count, ClvGroup g, bool with_up,
+void partials_t(cudaStream_t s, const Model& M, Aln A, TreeSet ts, int first, DCount count, ClvGroup g, bool with_up,
                 int threads, R* pm) {
     const int NN = 2 * ts.n - 2;
-    long long rows = (long long)count * NN * C * 4;
+    long long rows = (long long)count.cap * NN * C * 4;
     k_pmats<R><<<(int)std::min<long long>(blocks_for(rows, 256), 8192), 256, 0, s>>>(M, ts, first, count, pm);
     ++g_launches;
     size_t smem = (size_t)NN * C * 16 * sizeof(R);
     cudaFuncSetAttribute(k_partials<R, C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    dim3 grid(count, blocks_for(A.P, threads));
-    k_partials<R, C><<<grid, threads, smem, s>>>(M, A, ts, first, g, pm, with_up ? 1 : 0);
+    dim3 grid(count.cap, blocks_for(A.P, threads));
+    k_partials<R, C><<<grid, threads, smem, s>>>(M, A, ts, first, count, g, pm, with_up ? 1 : 0);
     ++g_launches;
 }
 }  // namespace
@@ -1742,9 +1783,9 @@ size_t pmat_bytes(int prec, int C, int n, int count) {
     return (size_t)count * (2 * n - 2) * C * 16 * (prec == 0 ? 8 : 4);
 }
 
-void launch_partials(cudaStream_t s, int prec, const Model& M, Aln A, TreeSet ts, int first, int count, ClvGroup g,
+void launch_partials(cudaStream_t s, int prec, const Model& M, Aln A, TreeSet ts, int first, DCount count, ClvGroup g,
                      bool with_up, int threads, void* pm) {
-    if (count <= 0) return;
+    if (count.cap <= 0) return;
     if (prec == 0) {
         double* q = reinterpret_cast<double*>(pm);
         if (M.C == 1) partials_t<double, 1>(s, M, A, ts, first, count, g, with_up, threads, q);
@@ -1775,18 +1816,22 @@ void propose_t(cudaStream_t s, const PropGroup* groups, const int* gstart, int n
 }
 template <typename R, int C>
 void fullopt_t(cudaStream_t s, const FullGroup* groups, const int* gstart, int ngroups, int* counter, int maxN,
-               int maxP, Cfg cfg, unsigned long long* stats, int threads, int grid, void* scratch, size_t spc) {
+               int maxP, Cfg cfg, unsigned long long* stats, int threads, int grid, void* scratch, size_t spc,
+               void* slab, size_t slab_per_cta) {
     const int prec = sizeof(R) == 8 ? 0 : 1;
     const int nn = 2 * maxN - 2;
+    unsigned char* sl = reinterpret_cast<unsigned char*>(slab);
     if (scratch) {
         const size_t smem = fullopt_smem_bytes(prec, C, maxN, maxP, false, threads);
         cudaFuncSetAttribute(k_fullopt<R, C, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         k_fullopt<R, C, false><<<grid, threads, smem, s>>>(groups, gstart, ngroups, counter, nn, cfg, stats,
-                                                           reinterpret_cast<unsigned char*>(scratch), spc);
+                                                           reinterpret_cast<unsigned char*>(scratch), spc, sl,
+                                                           slab_per_cta);
     } else {
         const size_t smem = fullopt_smem_bytes(prec, C, maxN, maxP, true, threads);
         cudaFuncSetAttribute(k_fullopt<R, C, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        k_fullopt<R, C, true><<<grid, threads, smem, s>>>(groups, gstart, ngroups, counter, nn, cfg, stats, nullptr, 0);
+        k_fullopt<R, C, true><<<grid, threads, smem, s>>>(groups, gstart, ngroups, counter, nn, cfg, stats, nullptr, 0,
+                                                          sl, slab_per_cta);
     }
     ++g_launches;
 }
@@ -1850,14 +1895,19 @@ void launch_propose(cudaStream_t s, int prec, int C, const PropGroup* groups, co
 
 void launch_fullopt(cudaStream_t s, int prec, int C, const FullGroup* groups, const int* gstart, int ngroups,
                     int* counter, int maxN, int maxP, Cfg cfg, unsigned long long* stats, int threads, int grid,
-                    void* scratch, size_t scratch_per_cta) {
+                    void* scratch, size_t scratch_per_cta, void* slab, size_t slab_per_cta) {
     if (prec == 0) {
-        if (C == 1) fullopt_t<double, 1>(s, groups, gstart, ngroups, counter, maxN, maxP, cfg, stats, threads, grid, scratch, scratch_per_cta);
-        else fullopt_t<double, 4>(s, groups, gstart, ngroups, counter, maxN, maxP, cfg, stats, threads, grid, scratch, scratch_per_cta);
+        if (C == 1) fullopt_t<double, 1>(s, groups, gstart, ngroups, counter, maxN, maxP, cfg, stats, threads, grid, scratch, scratch_per_cta, slab, slab_per_cta);
+        else fullopt_t<double, 4>(s, groups, gstart, ngroups, counter, maxN, maxP, cfg, stats, threads, grid, scratch, scratch_per_cta, slab, slab_per_cta);
     } else {
-        if (C == 1) fullopt_t<float, 1>(s, groups, gstart, ngroups, counter, maxN, maxP, cfg, stats, threads, grid, scratch, scratch_per_cta);
-        else fullopt_t<float, 4>(s, groups, gstart, ngroups, counter, maxN, maxP, cfg, stats, threads, grid, scratch, scratch_per_cta);
+        if (C == 1) fullopt_t<float, 1>(s, groups, gstart, ngroups, counter, maxN, maxP, cfg, stats, threads, grid, scratch, scratch_per_cta, slab, slab_per_cta);
+        else fullopt_t<float, 4>(s, groups, gstart, ngroups, counter, maxN, maxP, cfg, stats, threads, grid, scratch, scratch_per_cta, slab, slab_per_cta);
     }
+}
+
+size_t fullopt_slab_bytes(int prec, int C, int n, int P) {
+    const size_t slots = (size_t)(2 * n - 5), rs = prec == 0 ? 8 : 4;
+    return ((slots * P * 4 * C * rs + 255) & ~size_t(255)) + ((slots * P * 4 + 255) & ~size_t(255));
 }
 
 }  // namespace pt

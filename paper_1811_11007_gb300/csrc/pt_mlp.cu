@@ -88,10 +88,12 @@ struct FwdSmem {
 };
 
 template <bool kTrain>
-__global__ void __launch_bounds__(128) k_mlp_fwd(MlpDev m, const bf16* __restrict__ X, int N, float* __restrict__ Y,
+__global__ void __launch_bounds__(128) k_mlp_fwd(MlpDev m, const bf16* __restrict__ X, DCount Nc, float* __restrict__ Y,
                                                  float* Z1, bf16* H1, float* Z2, bf16* H2) {
     extern __shared__ __align__(16) unsigned char smraw[];
     FwdSmem& sm = *reinterpret_cast<FwdSmem*>(smraw);
+    const int N = dcount(Nc);
+    if ((int)blockIdx.x * kRows >= N) return;  // uniform over the block
     for (int i = threadIdx.x; i < kH * kInP / 2; i += blockDim.x)
         reinterpret_cast<uint32_t*>(sm.w1)[i] = reinterpret_cast<const uint32_t*>(m.w1t)[i];
     for (int i = threadIdx.x; i < kH * kH / 2; i += blockDim.x)
@@ -393,8 +395,9 @@ __global__ void k_mlp_pack(const float* Xf, int N, bf16* X) {
 // Summary of one stored vector (tree g, slot s): sum_p w_p v_p / sum_p w_p with
 // v_p the site's 4C values divided by their sum; 16 outputs ([cat][state], zero-padded).
 template <typename R, int C>
-__global__ void k_slot_summary(Aln A, ClvGroup g, int nslot, float* out) {
+__global__ void k_slot_summary(Aln A, ClvGroup g, DCount ntrees, int nslot, float* out) {
     const int tree = blockIdx.x / nslot, slot = blockIdx.x % nslot;
+    if (tree >= dcount(ntrees)) return;  // uniform over the block
     const R* base = reinterpret_cast<const R*>(g.clv) + (size_t)tree * g.tree_stride + (size_t)slot * A.P * 4 * C;
     float acc[16] = {0};
     float wsum = 0.f;
@@ -451,10 +454,10 @@ __global__ void k_tip_summary(Aln A, int C, float* out) {
 }
 
 // Feature rows of work items [i0, i1): FP32 [W][69] (for logging) and BF16 [W][80].
-__global__ void k_item_features(int n, const Item* items, int i0, int i1, TreeSet fr, int first,
+__global__ void k_item_features(int n, const Item* items, int i0, DCount i1, TreeSet fr, int first,
                                 const float* slot_sum, int nslot, const float* tip_sum, float* Xf, bf16* Xb) {
     const int k = i0 + blockIdx.x;
-    if (k >= i1) return;
+    if (k >= dcount(i1)) return;
     const Item it = items[k];
     const int NN = 2 * n - 2;
     const int32_t* up = fr.up + (size_t)it.tree * NN;
@@ -490,10 +493,10 @@ __global__ void k_item_features(int n, const Item* items, int i0, int i1, TreeSe
 
 // Warm starts [W][5] (branch order central, A, B, C, D) from predicted
 // log-ratios in member order; NaN marks "no prediction" (the inherited length is kept).
-__global__ void k_item_init(const Item* items, int i0, int i1, const float* Xf, const float* Y, double tmin,
+__global__ void k_item_init(const Item* items, int i0, DCount i1, const float* Xf, const float* Y, double tmin,
                             double tmax, double* init) {
     const int k = i0 + blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= i1) return;
+    if (k >= dcount(i1)) return;
     const Item it = items[k];
     const int brn[5] = {0, 1, it.swap == 0 ? 3 : 4, 2, it.swap == 0 ? 4 : 3};
     const float* y = Y + (size_t)(k - i0) * kOutP;
@@ -543,13 +546,21 @@ void mlp_forward(cudaStream_t s, MlpDev m, const void* Xb, int N, float* Y, floa
     const int grid = nblk(N, kRows);
     if (train) {
         cudaFuncSetAttribute(k_mlp_fwd<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(FwdSmem));
-        k_mlp_fwd<true><<<grid, 128, sizeof(FwdSmem), s>>>(m, reinterpret_cast<const bf16*>(Xb), N, Y, Z1,
+        k_mlp_fwd<true><<<grid, 128, sizeof(FwdSmem), s>>>(m, reinterpret_cast<const bf16*>(Xb), hcount(N), Y, Z1,
                                                              reinterpret_cast<bf16*>(H1), Z2, reinterpret_cast<bf16*>(H2));
     } else {
         cudaFuncSetAttribute(k_mlp_fwd<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(FwdSmem));
-        k_mlp_fwd<false><<<grid, 128, sizeof(FwdSmem), s>>>(m, reinterpret_cast<const bf16*>(Xb), N, Y, nullptr,
+        k_mlp_fwd<false><<<grid, 128, sizeof(FwdSmem), s>>>(m, reinterpret_cast<const bf16*>(Xb), hcount(N), Y, nullptr,
                                                               nullptr, nullptr, nullptr);
     }
+    ++g_launches;
+}
+
+void mlp_forward(cudaStream_t s, MlpDev m, const void* Xb, DCount N, float* Y) {
+    if (N.cap <= 0) return;
+    cudaFuncSetAttribute(k_mlp_fwd<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(FwdSmem));
+    k_mlp_fwd<false><<<nblk(N.cap, kRows), 128, sizeof(FwdSmem), s>>>(m, reinterpret_cast<const bf16*>(Xb), N, Y,
+                                                                     nullptr, nullptr, nullptr, nullptr);
     ++g_launches;
 }
 
@@ -587,15 +598,15 @@ void mlp_pack(cudaStream_t s, const float* Xf, int N, void* Xb) {
     ++g_launches;
 }
 
-void launch_slot_summary(cudaStream_t s, int prec, int C, Aln A, ClvGroup g, int ntrees, int nslot, float* out) {
-    if (ntrees <= 0 || nslot <= 0) return;
-    const int grid = ntrees * nslot;
+void launch_slot_summary(cudaStream_t s, int prec, int C, Aln A, ClvGroup g, DCount ntrees, int nslot, float* out) {
+    if (ntrees.cap <= 0 || nslot <= 0) return;
+    const int grid = ntrees.cap * nslot;
     if (prec == 0) {
-        if (C == 1) k_slot_summary<double, 1><<<grid, 256, 0, s>>>(A, g, nslot, out);
-        else k_slot_summary<double, 4><<<grid, 256, 0, s>>>(A, g, nslot, out);
+        if (C == 1) k_slot_summary<double, 1><<<grid, 256, 0, s>>>(A, g, ntrees, nslot, out);
+        else k_slot_summary<double, 4><<<grid, 256, 0, s>>>(A, g, ntrees, nslot, out);
     } else {
-        if (C == 1) k_slot_summary<float, 1><<<grid, 256, 0, s>>>(A, g, nslot, out);
-        else k_slot_summary<float, 4><<<grid, 256, 0, s>>>(A, g, nslot, out);
+        if (C == 1) k_slot_summary<float, 1><<<grid, 256, 0, s>>>(A, g, ntrees, nslot, out);
+        else k_slot_summary<float, 4><<<grid, 256, 0, s>>>(A, g, ntrees, nslot, out);
     }
     ++g_launches;
 }
@@ -605,18 +616,18 @@ void launch_tip_summary(cudaStream_t s, Aln A, int C, float* out) {
     ++g_launches;
 }
 
-void launch_item_features(cudaStream_t s, int n, const Item* items, int i0, int i1, TreeSet fr, int first,
+void launch_item_features(cudaStream_t s, int n, const Item* items, int i0, DCount i1, TreeSet fr, int first,
                           const float* slot_sum, int nslot, const float* tip_sum, float* Xf, void* Xb) {
-    if (i1 <= i0) return;
-    k_item_features<<<i1 - i0, 96, 0, s>>>(n, items, i0, i1, fr, first, slot_sum, nslot, tip_sum, Xf,
-                                            reinterpret_cast<bf16*>(Xb));
+    if (i1.cap <= i0) return;
+    k_item_features<<<i1.cap - i0, 96, 0, s>>>(n, items, i0, i1, fr, first, slot_sum, nslot, tip_sum, Xf,
+                                                reinterpret_cast<bf16*>(Xb));
     ++g_launches;
 }
 
-void launch_item_init(cudaStream_t s, const Item* items, int i0, int i1, const float* Xf, const float* Y, double tmin,
+void launch_item_init(cudaStream_t s, const Item* items, int i0, DCount i1, const float* Xf, const float* Y, double tmin,
                       double tmax, double* init) {
-    if (i1 <= i0) return;
-    k_item_init<<<nblk(i1 - i0, 128), 128, 0, s>>>(items, i0, i1, Xf, Y, tmin, tmax, init);
+    if (i1.cap <= i0) return;
+    k_item_init<<<nblk(i1.cap - i0, 128), 128, 0, s>>>(items, i0, i1, Xf, Y, tmin, tmax, init);
     ++g_launches;
 }
 

@@ -26,7 +26,9 @@ EXPORTS = ["pt_config_default", "pt_create", "pt_destroy", "pt_last_error", "pt_
            "pt_last_proposals", "pt_stage_times", "pt_version", "pt_discrete_gamma", "pt_model_eigen",
            "pt_score_topologies_noalloc", "pt_mlp_set_weights", "pt_mlp_get_weights", "pt_mlp_forward",
            "pt_mlp_loss_grad", "pt_mlp_train", "pt_mlp_enable", "pt_training_log", "pt_training_pairs",
-           "pt_expand_batch", "pt_expand_batch_dev", "pt_autotune", "pt_autotune_report"]
+           "pt_expand_batch", "pt_expand_batch_dev", "pt_autotune", "pt_autotune_report", "pt_graph_create",
+           "pt_graph_frontier_dev", "pt_graph_set_frontier", "pt_graph_run", "pt_graph_next_dev", "pt_graph_get_next",
+           "pt_graph_advance", "pt_graph_destroy"]
 MLP_PARAMS, MLP_IN, MLP_OUT = 27912, 69, 5
 _f32p = np.ctypeslib.ndpointer(np.float32, flags="C_CONTIGUOUS")
 
@@ -111,6 +113,16 @@ def lib():
             L.pt_mlp_enable.argtypes = [_vp, C.c_int]
             L.pt_training_log.argtypes = [_vp, C.c_int, C.c_size_t]
             L.pt_training_pairs.argtypes = [_vp, C.c_size_t, _vp, _vp, C.POINTER(C.c_size_t)]
+            _ip = C.POINTER(C.c_int)
+            L.pt_graph_create.argtypes = [_vp, C.c_int, _ip, _ip, C.POINTER(C.c_double), C.POINTER(_vp)]
+            L.pt_graph_frontier_dev.argtypes = [_vp, _vp, C.c_int, C.POINTER(_vp), C.POINTER(_vp)]
+            L.pt_graph_set_frontier.argtypes = [_vp, _vp, C.c_int, C.c_int, _vp, _vp]
+            L.pt_graph_run.argtypes = [_vp, _vp, _ip, C.POINTER(C.c_double), _ip]
+            L.pt_graph_next_dev.argtypes = [_vp, _vp, C.c_int, C.POINTER(_vp), C.POINTER(_vp), C.POINTER(_vp),
+                                            C.POINTER(_vp)]
+            L.pt_graph_get_next.argtypes = [_vp, _vp, C.c_int, C.c_int, _vp, _vp, _vp, _vp, _ip]
+            L.pt_graph_advance.argtypes = [_vp, _vp, _ip]
+            L.pt_graph_destroy.argtypes = [_vp, _vp]
             L.pt_score_topologies_noalloc.argtypes = [C.c_int, C.c_int, _vp, _vp, _f64p, _f64p, C.c_double, C.c_int,
                                                       C.POINTER(Config), C.c_int, _vp, _vp, _vp, _vp, C.c_int, _vp]
             _lib = L
@@ -297,6 +309,10 @@ class Context:
             out.append((arr[k].lmax, {"edges": fe[:c], "lengths": fl[:c], "lnl": fn[:c], "keys": fk[:c]}))
         return out
 
+    def graph(self, alns, frontier_caps, thresholds) -> "GraphRound":
+        """Records a graph round over alignments alns (pt_graph_create)."""
+        return GraphRound(self, alns, frontier_caps, thresholds)
+
     def expand_dev(self, aln: int, F: int, edges_ptr: int, lengths_ptr: int, threshold: float, lmax: float,
                    cap: int, out_edges_ptr: int, out_lengths_ptr: int, out_lnl_ptr: int, out_keys_ptr: int):
         """One PT round on device buffers (raw device pointers, e.g. tensor.data_ptr())."""
@@ -411,3 +427,72 @@ def run_search(ctx: Context, aln: int, starts_edges, starts_lengths, threshold: 
         lmax, front = ctx.expand(aln, front["edges"], front["lengths"], threshold, lmax)
         rounds += 1
     return lmax, rounds
+
+
+class GraphRound:
+    """A batched PT round recorded as a CUDA graph (pt_graph_*): set the
+    frontiers, run, read or advance to the next frontiers."""
+
+    def __init__(self, ctx: Context, alns, frontier_caps, thresholds):
+        self.ctx = ctx
+        self.alns = [int(a) for a in alns]
+        self.caps = [int(c) for c in frontier_caps]
+        na = len(self.alns)
+        ids = (C.c_int * na)(*self.alns)
+        caps = (C.c_int * na)(*self.caps)
+        thr = (C.c_double * na)(*[float(t) for t in thresholds])
+        h = _vp()
+        ctx._ck(lib().pt_graph_create(ctx._h, na, ids, caps, thr, C.byref(h)))
+        self._g = h
+        self.n_next = [0] * na
+
+    def close(self):
+        if getattr(self, "_g", None) and self.ctx._h:
+            lib().pt_graph_destroy(self.ctx._h, self._g)
+        self._g = None
+
+    def set_frontier(self, k: int, edges, lengths):
+        n = self.ctx._n[self.alns[k]]
+        E = 2 * n - 3
+        e = np.ascontiguousarray(edges, np.int32).reshape(-1, E, 2)
+        l = np.ascontiguousarray(lengths, np.float64).reshape(e.shape[0], E)
+        self.ctx._ck(lib().pt_graph_set_frontier(self.ctx._h, self._g, k, e.shape[0], e.ctypes.data, l.ctypes.data))
+        return e.shape[0]
+
+    def frontier_dev(self, k: int):
+        e, l = _vp(), _vp()
+        self.ctx._ck(lib().pt_graph_frontier_dev(self.ctx._h, self._g, k, C.byref(e), C.byref(l)))
+        return e.value, l.value
+
+    def run(self, n_frontier, lmax):
+        na = len(self.alns)
+        nf = (C.c_int * na)(*[int(x) for x in n_frontier])
+        lm = (C.c_double * na)(*[float(x) for x in lmax])
+        nn = (C.c_int * na)()
+        self.ctx._ck(lib().pt_graph_run(self.ctx._h, self._g, nf, lm, nn))
+        self.n_next = list(nn)
+        return list(lm), list(nn)
+
+    def next(self, k: int) -> dict:
+        n = self.ctx._n[self.alns[k]]
+        E = 2 * n - 3
+        cnt = self.n_next[k]
+        e = np.zeros((cnt, E, 2), np.int32)
+        l = np.zeros((cnt, E), np.float64)
+        f = np.zeros(cnt, np.float64)
+        y = np.zeros((cnt, 2), np.uint64)
+        got = C.c_int()
+        self.ctx._ck(lib().pt_graph_get_next(self.ctx._h, self._g, k, cnt, _ptr(e), _ptr(l), _ptr(f), _ptr(y),
+                                             C.byref(got)))
+        return {"edges": e, "lengths": l, "lnl": f, "keys": y}
+
+    def next_dev(self, k: int):
+        p = [_vp() for _ in range(4)]
+        self.ctx._ck(lib().pt_graph_next_dev(self.ctx._h, self._g, k, *[C.byref(x) for x in p]))
+        return [x.value for x in p]
+
+    def advance(self):
+        na = len(self.alns)
+        nf = (C.c_int * na)()
+        self.ctx._ck(lib().pt_graph_advance(self.ctx._h, self._g, nf))
+        return list(nf)
