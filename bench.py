@@ -11,10 +11,17 @@ lmax - 10, and the kept ones are fully optimised.  The frontier is the one a
 PT search (threshold 10, 8 random starts) reaches on the GPU during set-up.
 Unit: unique neighbours scored to convergence per second, whole job.
 
-value: device-resident inputs (pt_expand_frontier_dev), mixed precision.
-e2e:   the same step through the host-buffer entry point pt_expand_frontier
-       from pinned host memory (frontier in, next frontier out).
+value: device-resident inputs, mixed precision, the round replayed as one
+       CUDA graph (pt_graph_run; frontier resident in the graph's buffers).
+e2e:   the same graph round through the host-buffer entry points: frontier
+       copied in from pinned host memory (pt_graph_set_frontier), next
+       frontier copied out (pt_graph_get_next), inside every step.
+direct_launch: the same round issued kernel by kernel (pt_expand_frontier_dev);
+       its per-stage CUDA events give the kernel times of the rooflines.
 fp64:  the plain FP64 GPU path on the same frontier.
+--workload batch16: 16 alignments (taxa ~ U[20,100], sites ~ U[300,5000]),
+       256 frontier trees each (random topologies with optimised lengths),
+       one graph round over all of them per step.
 --impl reference: the FP64 CPU oracle, timed on this host's cores on a
 bounded sample of the same step.
 """
@@ -51,6 +58,7 @@ def parse():
     p.add_argument("--no-autotune", action="store_true", help="default CTA sizes (for profiling runs)")
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--cpu-sample", type=int, default=1, help="frontier trees in the CPU baseline sample")
+    p.add_argument("--workload", default="round27", choices=["round27", "batch16"])
     return p.parse_args()
 
 
@@ -260,8 +268,31 @@ def run_ours(args, rank, world, dev):
         return {"ms": ms, "units": units, "launches": launches, "prop_ms": prop_ms, "part_ms": part_ms,
                 "stats": stats, "flops": flops, "times": times, "full_ms": full_ms, "full_flops": full_flops}
 
+    # kernel by kernel: its per-stage CUDA events give the kernel times of the rooflines
+    res = timed(ctx, aid, step_dev, args.steps, args.warmup)
+
+    # the round as one CUDA graph, recorded once and replayed every step (the headline)
+    g = ctx.graph([aid], [F], [THRESH])
+    g.set_frontier(0, front["edges"], front["lengths"])
+
+    def step_graph(c, i):
+        c.reset_visited(i)
+        _, nn = g.run([F], [lmax0])
+        st = c.stats()
+        return st["scored"], st["launches"] + 1, c.stage_times(), st, nn[0]
+
+    # the graph round must reproduce the kernel-by-kernel round exactly
+    _, _, _, _, cnt_d = step_dev(ctx, aid)
+    keys_d = o_k[:cnt_d].cpu().numpy().astype(np.uint64)
+    lnl_d = o_n[:cnt_d].cpu().numpy()
+    step_graph(ctx, aid)
+    nxt = g.next(0)
+    graph_check = {"next_frontier": int(cnt_d),
+                   "identical": bool(len(nxt["keys"]) == cnt_d and np.array_equal(nxt["keys"], keys_d)
+                                     and np.array_equal(nxt["lnl"], lnl_d))}
+
     with ClockSampler(dev) as clk:
-        res = timed(ctx, aid, step_dev, args.steps, args.warmup)
+        resg = timed(ctx, aid, step_graph, args.steps, args.warmup)
     clocks = clk.summary()
 
     # end to end: host buffers (pinned), copies inside every step
@@ -275,18 +306,20 @@ def run_ours(args, rank, world, dev):
 
     def step_host(c, i):
         c.reset_visited(i)
-        lm = C.c_double(lmax0)
+        L = pt.lib()
+        c._ck(L.pt_graph_set_frontier(c._h, g._g, 0, F, C.c_void_p(h_e.data_ptr()), C.c_void_p(h_l.data_ptr())))
+        nf, lm, nn = (C.c_int * 1)(F), (C.c_double * 1)(lmax0), (C.c_int * 1)()
+        c._ck(L.pt_graph_run(c._h, g._g, nf, lm, nn))
+        st = c.stats()
         cnt = C.c_int()
-        c._ck(pt.lib().pt_expand_frontier(c._h, i, F, C.c_void_p(h_e.data_ptr()), C.c_void_p(h_l.data_ptr()),
-                                          THRESH, C.byref(lm), cap, C.c_void_p(ho_e.data_ptr()),
-                                          C.c_void_p(ho_l.data_ptr()), C.c_void_p(ho_n.data_ptr()),
-                                          C.c_void_p(ho_k.data_ptr()), C.byref(cnt)))
+        c._ck(L.pt_graph_get_next(c._h, g._g, 0, cap, C.c_void_p(ho_e.data_ptr()), C.c_void_p(ho_l.data_ptr()),
+                                  C.c_void_p(ho_n.data_ptr()), C.c_void_p(ho_k.data_ptr()), C.byref(cnt)))
         bytes_io["h2d"] = F * E * 2 * 4 + F * E * 8
         bytes_io["d2h"] = cnt.value * (E * 2 * 4 + E * 8 + 8 + 16)
-        st = c.stats()
         return st["scored"], st["launches"] + 1, c.stage_times(), st, cnt.value
 
     e2e = timed(ctx, aid, step_host, args.steps, 1)
+    g.close()
 
     plain = None
     if learned is not None:
@@ -302,7 +335,7 @@ def run_ours(args, rank, world, dev):
     out = None
     if rank == 0:
         pk = peaks()
-        value = res["units"] / (res["ms"] / 1e3)
+        value = resg["units"] / (resg["ms"] / 1e3)
         sm_max = pk.get("sm_max_mhz", 2070.0)
         nsm = torch.cuda.get_device_properties(dev).multi_processor_count
         alu_peak = nsm * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
@@ -325,13 +358,13 @@ def run_ours(args, rank, world, dev):
         out = {
             "metric": "branch-optimised topologies/sec (unique NNI neighbours scored per PT round)",
             "value": value,
-            "path": "learned warm start + batched persistent launch + FP32 partials / FP64 reductions"
-                    if learned is not None else "batched persistent launch + FP32 partials / FP64 reductions",
+            "path": ("learned warm start + " if learned is not None else "") +
+                    "batched persistent launches replayed as one CUDA graph + FP32 partials / FP64 reductions",
             "unit": "topologies/s",
             "n_gpus": world,
             "steps": args.steps,
             "warmup": args.warmup,
-            "ms_per_step": res["ms"] / args.steps,
+            "ms_per_step": resg["ms"] / args.steps,
             "higher_is_better": True,
             "scaling": "weak",
             "vs_baseline": None,
@@ -346,6 +379,10 @@ def run_ours(args, rank, world, dev):
                            F * (2 * N_TAXA - 5) * P * 68 / 1e9)},
             "e2e": {"value": e2e["units"] / (e2e["ms"] / 1e3), "unit": "topologies/s",
                     "h2d_bytes_per_step": bytes_io["h2d"], "d2h_bytes_per_step": bytes_io["d2h"]},
+            "direct_launch": {"value": res["units"] / (res["ms"] / 1e3), "unit": "topologies/s",
+                              "ms_per_step": res["ms"] / args.steps, "gpu_launches": res["launches"],
+                              "note": "the same round issued kernel by kernel with host reads of the counts"},
+            "graph_check": graph_check,
             "fp64_gpu": ({"value": fp64["units"] / (fp64["ms"] / 1e3), "unit": "topologies/s",
                           "ms_per_step": fp64["ms"] / max(1, min(args.steps, 2)),
                           "note": "plain FP64 GPU path, plain Newton start, same frontier"} if fp64 else None),
@@ -366,10 +403,112 @@ def run_ours(args, rank, world, dev):
                        "full_sweeps_per_kept_tree": st["full_sweeps"] / max(st["kept"], 1),
                        "nonconverged": st["nonconverged"]},
             "autotune": ctx.autotune_report(),
-            "gpu_launches": res["launches"],
+            "gpu_launches": resg["launches"],
             "clocks": clocks,
         }
     return out, (a, front, lmax0)
+
+
+def batch16_alignments(rank: int):
+    """16 GTR+G4 alignments of uneven shape: taxa ~ U[20, 100], sites ~ U[300, 5000]."""
+    from paper_1811_11007_gb300 import synth
+    rng = np.random.default_rng(synth.SEED_BASE + 3 + 1000 * rank)
+    out = []
+    for i in range(16):
+        n = int(rng.integers(20, 101))
+        sites = int(rng.integers(300, 5001))
+        out.append(synth.simulate(n, sites, synth.SEED_BASE + 300 + 1000 * rank + i, model="gtr", alpha=0.5,
+                                  mean_branch=0.05))
+    return out
+
+
+def run_batch16(args, rank, world, dev):
+    """One graph round over 16 uneven alignments per step, 256 frontier trees
+    each (random topologies with fully optimised lengths; lmax = the best)."""
+    import torch
+    from paper_1811_11007_gb300 import pt, synth
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.current_stream()
+    alns = batch16_alignments(rank)
+    F = args.frontier
+    ctx = pt.Context(precision="mixed", table_log2=22, stream=stream)
+    ctx.autotune(not args.no_autotune)
+    ids, fronts, lmax0 = [], [], []
+    for i, a in enumerate(alns):
+        aid = ctx.load_alignment(a.codes)
+        ctx.set_model(aid, a.exch, a.freqs, 0.5, 4)
+        e, l = synth.random_trees(a.codes.shape[0], F, synth.SEED_BASE + 400 + 1000 * rank + i)
+        lnl, lens, _ = ctx.score(aid, e, l, mode="full")
+        ids.append(aid)
+        fronts.append((e, lens))
+        lmax0.append(float(np.max(lnl)))
+    parts = [{"aln": aid, "edges": e, "lengths": l, "threshold": THRESH, "lmax": lm}
+             for aid, (e, l), lm in zip(ids, fronts, lmax0)]
+
+    def run_steps(step, steps, warmup):
+        for _ in range(warmup):
+            step()
+        torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        units, launches, times = 0, 0, {}
+        e0.record(stream)
+        for _ in range(steps):
+            for aid in ids:
+                ctx.reset_visited(aid)
+            step()
+            st = ctx.stats()
+            units += st["scored"]
+            launches += st["launches"] + len(ids)
+            times = ctx.stage_times()
+        e1.record(stream)
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+        ms, units = reduce_over_ranks(e0.elapsed_time(e1), units, world, device=f"cuda:{dev}")
+        return {"ms": ms, "units": units, "launches": launches, "times": times, "stats": ctx.stats()}
+
+    def direct():
+        for aid in ids:
+            ctx.reset_visited(aid)
+        return ctx.expand_batch(parts)
+
+    res_d = run_steps(direct, max(1, min(args.steps, 2)), 1)  # kernel by kernel (also tunes CTA sizes)
+    g = ctx.graph(ids, [F] * len(ids), [THRESH] * len(ids))
+    for k, (e, l) in enumerate(fronts):
+        g.set_frontier(k, e, l)
+    ref = direct()
+    for aid in ids:
+        ctx.reset_visited(aid)
+    g.run([F] * len(ids), lmax0)
+    same = all(np.array_equal(g.next(k)["keys"], ref[k][1]["keys"]) for k in range(len(ids)))
+    with ClockSampler(dev) as clk:
+        res = run_steps(lambda: g.run([F] * len(ids), lmax0), args.steps, args.warmup)
+    g.close()
+    if rank != 0:
+        return None
+    st = res["stats"]
+    shapes = [(a.codes.shape[0], ctx.alignment_info(aid)[1]) for a, aid in zip(alns, ids)]
+    return {
+        "metric": "branch-optimised topologies/sec (unique NNI neighbours scored per PT round)",
+        "value": res["units"] / (res["ms"] / 1e3), "unit": "topologies/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": res["ms"] / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32 partials + f64 reductions",
+        "data": "synthetic (seeded simulation; the paper's datasets are not available)",
+        "config": {"workload": f"batched graph round: 16 alignments (taxa 20-100, sites 300-5000), {F} frontier "
+                               f"trees each (random topologies, optimised lengths), GTR+G4, threshold {THRESH}",
+                   "alignments": [{"taxa": n, "patterns": P} for n, P in shapes],
+                   "neighbours_per_step": st["scored"], "kept_per_step": st["kept"],
+                   "parallelism": f"replicas x{world}", "l2": "inputs larger than L2"},
+        "direct_launch": {"value": res_d["units"] / (res_d["ms"] / 1e3), "unit": "topologies/s",
+                          "ms_per_step": res_d["ms"] / max(1, min(args.steps, 2))},
+        "graph_check": {"identical_next_frontiers": bool(same)},
+        "stage_ms_per_step": res_d["times"],
+        "autotune": ctx.autotune_report(),
+        "gpu_launches": res["launches"],
+        "clocks": clk.summary(),
+    }
 
 
 def cpu_baseline(a, front, lmax0, sample):
@@ -444,6 +583,13 @@ def main():
         build.build()
     if world > 1:
         torch.distributed.barrier()
+    if args.workload == "batch16":
+        out = run_batch16(args, rank, world, local)
+        if rank == 0:
+            print(json.dumps(out))
+        if world > 1:
+            torch.distributed.destroy_process_group()
+        return
     out, (a, front, lmax0) = run_ours(args, rank, world, local)
     if rank == 0:
         if world == 1 and not args.no_cpu:

@@ -1125,7 +1125,8 @@ struct GraphRound {
     bool mlp = false;
     int prop_threads = 0, full_threads = 0;
     // di layout: F [na], m [na], ncand [na], W [na], K [na], G [na], round [na],
-    // gstart (proposal) [na + 1], gstart (full optimisation) [na + 1], two counters
+    // gstart (proposal) [na + 1], gstart (full optimisation) [na + 1], two counters,
+    // perm [na] (group order of the persistent launches: larger problems first)
     int oF() const { return 0; }
     int oM() const { return na; }
     int oNC() const { return 2 * na; }
@@ -1137,7 +1138,8 @@ struct GraphRound {
     int oGSF() const { return 8 * na + 1; }
     int oCP() const { return 9 * na + 2; }
     int oCF() const { return 9 * na + 3; }
-    int nints() const { return 9 * na + 4; }
+    int oPerm() const { return 9 * na + 4; }
+    int nints() const { return 10 * na + 4; }
 };
 
 // Lays buffers out in one allocation: add() records a request, carve() assigns.
@@ -1227,7 +1229,7 @@ void graph_record(Ctx& c, GraphRound& g, cudaStream_t s, int C, int maxN, int ma
             launch_item_init(s, x.items, 0, Wk, x.xf, x.yb, c.cfg.tmin, c.cfg.tmax, x.init);
         }
     }
-    launch_prefix_counts(s, na, di + g.oW(), di + g.oGSP());
+    launch_prefix_counts(s, na, di + g.oW(), di + g.oPerm(), di + g.oGSP());
     cudaMemsetAsync(di + g.oCP(), 0, sizeof(int), s);
     launch_propose(s, prec, C, g.dpg, di + g.oGSP(), na, di + g.oCP(), kcfg(c), c.d_stats, g.prop_threads, pgrid,
                    g.prop_scratch, pspc, maxP);
@@ -1240,7 +1242,7 @@ void graph_record(Ctx& c, GraphRound& g, cudaStream_t s, int C, int maxN, int ma
         launch_materialize(s, x.n, Kk, x.kidx, x.items, x.fr, x.len5, x.kedges, x.klens, x.kslot);
         launch_canon(s, x.n, Kk, x.kedges, x.klens, x.kp, c.d_err);
     }
-    launch_prefix_counts(s, na, di + g.oK(), di + g.oGSF());
+    launch_prefix_counts(s, na, di + g.oK(), di + g.oPerm(), di + g.oGSF());
     cudaMemsetAsync(di + g.oCF(), 0, sizeof(int), s);
     launch_fullopt(s, prec, C, g.dfg, di + g.oGSF(), na, di + g.oCF(), maxN, maxP, kcfg(c), c.d_stats,
                    g.full_threads, fgrid, g.full_scratch, fspc, g.slab, slab_stride);
@@ -1368,8 +1370,17 @@ GraphRound* graph_create(Ctx& c, const std::vector<int>& ids, const std::vector<
     ck(c, cudaHostAlloc(reinterpret_cast<void**>(&g.hi), sizeof(int) * g.nints(), cudaHostAllocDefault), "pinned");
     ck(c, cudaHostAlloc(reinterpret_cast<void**>(&g.hl), sizeof(double) * na, cudaHostAllocDefault), "pinned");
     // static tables: m per alignment, group descriptors
+    // persistent launches take larger problems first (dynamic scheduling then balances the tail)
+    std::vector<int> order(na);
+    for (int k = 0; k < na; ++k) order[k] = k;
+    std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
+        return (size_t)g.a[x].P * g.a[x].n > (size_t)g.a[y].P * g.a[y].n;
+    });
     std::fill(g.hi, g.hi + g.nints(), 0);
-    for (int k = 0; k < na; ++k) g.hi[g.oM() + k] = g.a[k].m;
+    for (int k = 0; k < na; ++k) {
+        g.hi[g.oM() + k] = g.a[k].m;
+        g.hi[g.oPerm() + k] = order[k];
+    }
     ck(c, cudaMemcpy(g.di, g.hi, sizeof(int) * g.nints(), cudaMemcpyHostToDevice), "graph counts");
     std::vector<PropGroup> pg(na);
     std::vector<FullGroup> fg(na);
@@ -1405,8 +1416,14 @@ GraphRound* graph_create(Ctx& c, const std::vector<int>& ids, const std::vector<
             launch_tip_summary(c.stream, aln_dev(A), C, A.tip_sum);
         }
     }
-    ck(c, cudaMemcpy(g.dpg, pg.data(), sizeof(PropGroup) * na, cudaMemcpyHostToDevice), "graph groups");
-    ck(c, cudaMemcpy(g.dfg, fg.data(), sizeof(FullGroup) * na, cudaMemcpyHostToDevice), "graph groups");
+    std::vector<PropGroup> pgo(na);
+    std::vector<FullGroup> fgo(na);
+    for (int j = 0; j < na; ++j) {
+        pgo[j] = pg[order[j]];
+        fgo[j] = fg[order[j]];
+    }
+    ck(c, cudaMemcpy(g.dpg, pgo.data(), sizeof(PropGroup) * na, cudaMemcpyHostToDevice), "graph groups");
+    ck(c, cudaMemcpy(g.dfg, fgo.data(), sizeof(FullGroup) * na, cudaMemcpyHostToDevice), "graph groups");
     ck(c, cudaStreamSynchronize(c.stream), "sync");
     // capture on a stream of the graph's own (the context stream may be a legacy default stream)
     ck(c, cudaStreamCreateWithFlags(&g.cs, cudaStreamNonBlocking), "graph stream");

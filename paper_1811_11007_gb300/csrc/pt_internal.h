@@ -153,9 +153,10 @@ void launch_scan(cudaStream_t s, const int32_t* in, int32_t* out, int N, int32_t
 // *total = out[N-1] + in[N-1] (the exclusive scan's total) on the device.
 void launch_scan_total(cudaStream_t s, const int32_t* in, const int32_t* out, int N, int32_t* total);
 // Device-side counts of a graph round: ncand[k] = F[k] * m[k] and the prefix
-// sums of per-group item counts (gstart[g + 1] = gstart[g] + cnt[g]).
+// sums of per-group item counts, groups in the order perm (gstart[g + 1] =
+// gstart[g] + cnt[perm[g]]; perm may be null for the identity).
 void launch_mul_counts(cudaStream_t s, int na, const int* F, const int* m, int* ncand);
-void launch_prefix_counts(cudaStream_t s, int ng, const int* cnt, int* gstart);
+void launch_prefix_counts(cudaStream_t s, int ng, const int* cnt, const int* perm, int* gstart);
 void launch_make_items(cudaStream_t s, int ncand, const int32_t* flag, const int32_t* pos, const int32_t* cinfo,
                        const int32_t* cslot, const uint64_t* nkey, Item* items, uint64_t* ikey);
 void launch_compact_idx(cudaStream_t s, int N, const int32_t* flag, const int32_t* pos, int32_t* idx);

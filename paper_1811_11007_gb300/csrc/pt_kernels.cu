@@ -520,11 +520,11 @@ __global__ void k_mul_counts(int na, const int* F, const int* m, int* ncand) {
     const int k = threadIdx.x;
     if (k < na) ncand[k] = F[k] * m[k];
 }
-__global__ void k_prefix_counts(int ng, const int* cnt, int* gstart) {
+__global__ void k_prefix_counts(int ng, const int* cnt, const int* perm, int* gstart) {
     if (threadIdx.x == 0) {
         int acc = 0;
         gstart[0] = 0;
-        for (int g = 0; g < ng; ++g) { acc += cnt[g]; gstart[g + 1] = acc; }
+        for (int g = 0; g < ng; ++g) { acc += cnt[perm ? perm[g] : g]; gstart[g + 1] = acc; }
     }
 }
 
@@ -1658,8 +1658,8 @@ void launch_mul_counts(cudaStream_t s, int na, const int* F, const int* m, int* 
     ++g_launches;
 }
 
-void launch_prefix_counts(cudaStream_t s, int ng, const int* cnt, int* gstart) {
-    k_prefix_counts<<<1, 32, 0, s>>>(ng, cnt, gstart);
+void launch_prefix_counts(cudaStream_t s, int ng, const int* cnt, const int* perm, int* gstart) {
+    k_prefix_counts<<<1, 32, 0, s>>>(ng, cnt, perm, gstart);
     ++g_launches;
 }
 
