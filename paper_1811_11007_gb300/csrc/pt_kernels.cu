@@ -1041,12 +1041,15 @@ __device__ double newton_solve(const Model& M, const Cfg& cfg, const STab<R, C>&
         for (int p = threadIdx.x; p < P; p += blockDim.x) {
             R s[4 * C];
             st.get(p, s);
-            R L = e[0] * s[0], L1 = g[0] * s[0], L2 = h[0] * s[0];
+            // the stationary slots (k = 0) have zero derivative coefficients
+            R L = e[0] * s[0], L1 = g[1] * s[1], L2 = h[1] * s[1];
 #pragma unroll
             for (int q = 1; q < 4 * C; ++q) {
                 L = fma(e[q], s[q], L);
-                L1 = fma(g[q], s[q], L1);
-                L2 = fma(h[q], s[q], L2);
+                if ((q & 3) != 0 && q != 1) {
+                    L1 = fma(g[q], s[q], L1);
+                    L2 = fma(h[q], s[q], L2);
+                }
             }
             R inv = Prec<R>::rcp(L);
             R a = L1 * inv, b = L2 * inv;
@@ -1498,6 +1501,9 @@ __global__ void __launch_bounds__(512) k_fullopt(const FullGroup* __restrict__ g
             for (int p = threadIdx.x; p < P; p += blockDim.x) {
                 R X[4 * C], Y[4 * C];
                 int cx, cy;
+                // D_v first: its load then overlaps the two below instead of waiting
+                // behind the store of U_v (the same array, so it could not be hoisted)
+                load_raw<R, C>(srcD(v), p, Y, cy);
                 if (v == n) {
                     load_raw<R, C>(tip0, p, X, cx);
                 } else {
@@ -1517,7 +1523,6 @@ __global__ void __launch_bounds__(512) k_fullopt(const FullGroup* __restrict__ g
                         scl[(size_t)slot * P + p] = cx;
                     }
                 }
-                load_raw<R, C>(srcD(v), p, Y, cy);
                 const int ex = normalise<R, C>(X), ey = normalise<R, C>(Y);
                 R s4[4 * C];
                 sumtable<R, C>(sm.Mt, sm.pi, X, Y, s4);
