@@ -64,14 +64,20 @@ typedef enum {
 
 enum { PT_PREC_FP64 = 0, PT_PREC_MIXED = 1 };   /* FP64 everywhere / FP32 partials + FP64 reductions */
 enum { PT_SCORE_FIXED = 0, PT_SCORE_FULL = 1 }; /* lnL at the given lengths / after full optimisation */
-enum { PT_PROPOSE_FIVE = 0, PT_PROPOSE_CENTRAL = 1 };
+/* Proposal optimisation of a neighbour before the keep decision ("Phylogenetic
+ * Topographer", loop step 6a and the radius option after it): the five
+ * branches an NNI touches; the new (central) branch only, the paper's default
+ * radius 0; or every branch, the paper's radius -1 (full optimisation of the
+ * neighbour from its inherited lengths; the visit then re-optimises the kept
+ * ones from there, as in the other modes). */
+enum { PT_PROPOSE_FIVE = 0, PT_PROPOSE_CENTRAL = 1, PT_PROPOSE_FULL = 2 };
 enum { PT_ST_REJECTED = 1, PT_ST_GOOD = 2, PT_ST_BAD = 3 };
 
 typedef struct {
     int device;           /* CUDA device ordinal */
     int precision;        /* PT_PREC_* */
     int table_log2;       /* visited table of 2^table_log2 slots per alignment (10..30) */
-    int propose_mode;     /* PT_PROPOSE_FIVE (default) or PT_PROPOSE_CENTRAL (the paper's radius 0) */
+    int propose_mode;     /* PT_PROPOSE_FIVE (default), PT_PROPOSE_CENTRAL (radius 0) or PT_PROPOSE_FULL (radius -1) */
     double tmin, tmax;    /* branch-length bounds */
     double newton_tol;    /* stop when a Newton step moves the length by <= newton_tol */
     int newton_maxit;     /* evaluations per branch per visit of that branch */

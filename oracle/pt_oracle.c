@@ -56,7 +56,7 @@ typedef struct {
     double rates[OR_MAXCAT];
     double tmin, tmax, newton_tol, sweep_tol;
     int newton_maxit, full_max_sweeps, prop_max_sweeps;
-    int prop_mode;   /* 0 = five branches around the NNI edge, 1 = central only */
+    int prop_mode;   /* 0 = five branches around the NNI edge, 1 = central only, 2 = every branch */
     /* counters (diagnostics for tests) */
     long n_newton_evals, n_newton_nonconv;
 } or_problem;
@@ -711,9 +711,12 @@ static void apply_nni(const or_tree *t, const or_quartet *q, int swap, or_tree *
  * NNI touches in the order central, A, B, C, D (prop_mode 0), or the central
  * branch only (prop_mode 1, the paper's radius-0 default).  Stop rule as for
  * the full optimisation (no length moved by more than sweep_tol), capped at
- * prop_max_sweeps; the result is the exact lnL at the final lengths. */
+ * prop_max_sweeps; the result is the exact lnL at the final lengths.
+ * prop_mode 2 is the paper's radius -1: the full optimisation of the
+ * neighbour from its inherited lengths. */
 static double propose_optimise(or_problem *pb, or_tree *nt, const or_quartet *q, int swap)
 {
+    if (pb->prop_mode == 2) return full_optimise(pb, nt, NULL);
     int s = swap == 0 ? q->c : q->d, o = swap == 0 ? q->d : q->c;
     /* after the swap: u holds a and s, v holds b and o */
     int br[5][2];

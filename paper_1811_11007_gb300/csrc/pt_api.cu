@@ -832,8 +832,40 @@ void expand_batch(Ctx& c, const std::vector<RoundIn>& ins, std::vector<RoundOut>
     std::stable_sort(chunks.begin(), chunks.end(), [&](const Chunk& x, const Chunk& y) {
         return (size_t)ar[x.k].a->P * ar[x.k].n > (size_t)ar[y.k].a->P * ar[y.k].n;
     });
+    // full radius: every proposal is the full optimisation of the neighbour from
+    // its inherited lengths (one batched full-optimisation launch)
+    const bool full_radius = c.cfg.propose_mode == PT_PROPOSE_FULL;
+    std::vector<TreeSet> pps(na);
+    std::vector<int32_t*> pslot(na, nullptr);
+    if (full_radius) {
+        Span sp3(c, 3);
+        std::vector<FullJob> pj;
+        for (int k = 0; k < na; ++k) {
+            AR& r = ar[k];
+            if (r.W == 0) continue;
+            const std::string pre = "b" + std::to_string(k) + ".";
+            const int E = 2 * r.n - 3;
+            launch_len5_inherit(c.stream, r.n, hcount(r.W), items + r.ibase, r.fr, len5 + (size_t)5 * r.ibase);
+            int32_t* pe = buf<int32_t>(c, pre + "pp.edges", (size_t)r.W * 2 * E);
+            double* pl = buf<double>(c, pre + "pp.lens", (size_t)r.W * E);
+            pslot[k] = buf<int32_t>(c, pre + "pp.slot", r.W);
+            launch_materialize(c.stream, r.n, hcount(r.W), nullptr, items + r.ibase, r.fr, len5 + (size_t)5 * r.ibase,
+                               pe, pl, pslot[k]);
+            pps[k] = treeset(c, pre + "pp", r.n, r.W, true);
+            launch_canon(c.stream, r.n, r.W, pe, pl, pps[k], c.d_err);
+            pj.push_back(FullJob{r.a, pps[k], 0, r.W, plnl + r.ibase, c.cfg.full_max_sweeps});
+        }
+        check_flags(c);
+        run_full_jobs(c, pj);
+        for (int k = 0; k < na; ++k) {
+            AR& r = ar[k];
+            launch_prop_full_finish(c.stream, hcount(r.W), items + r.ibase, plnl + r.ibase, r.lmax, ins[k].thr,
+                                    hround(r.round), r.a->table, kept + r.ibase);
+        }
+        sp3.end();
+    }
     size_t ci = 0;
-    while (ci < chunks.size()) {
+    while (!full_radius && ci < chunks.size()) {
         size_t used = 0, ce = ci;
         while (ce < chunks.size()) {
             const AlnState& a = *ar[chunks[ce].k].a;
@@ -993,8 +1025,14 @@ void expand_batch(Ctx& c, const std::vector<RoundIn>& ins, std::vector<RoundOut>
         int32_t* kedges = buf<int32_t>(c, pre + "kept.edges", (size_t)r.K * 2 * (2 * r.n - 3) + 2);
         double* klens = buf<double>(c, pre + "kept.lens", (size_t)r.K * (2 * r.n - 3) + 1);
         r.kslot = buf<int32_t>(c, pre + "kept.slot", r.K + 1);
-        launch_materialize(c.stream, r.n, hcount(r.K), r.kidx, items + r.ibase, r.fr, len5 + (size_t)5 * r.ibase, kedges, klens,
-                           r.kslot);
+        if (full_radius) {  // the visit starts from the proposal's fully optimised tree
+            launch_gather_out(c.stream, r.n, hcount(r.K), r.kidx, pps[k], plnl + r.ibase, kedges, klens, nullptr,
+                              nullptr);
+            launch_gather_i32(c.stream, hcount(r.K), r.kidx, pslot[k], r.kslot);
+        } else {
+            launch_materialize(c.stream, r.n, hcount(r.K), r.kidx, items + r.ibase, r.fr, len5 + (size_t)5 * r.ibase,
+                               kedges, klens, r.kslot);
+        }
         r.klnl = buf<double>(c, pre + "kp.lnl", r.K + 1);
         r.kp = treeset(c, pre + "kp", r.n, std::max(r.K, 1), true);
         if (r.K > 0) {
@@ -1294,6 +1332,8 @@ GraphRound* graph_create(Ctx& c, const std::vector<int>& ids, const std::vector<
         maxCap = std::max(maxCap, x.cap);
         slab_stride = std::max(slab_stride, fullopt_slab_bytes(prec, C, A.n, A.P));
     }
+    if (c.cfg.propose_mode == PT_PROPOSE_FULL)
+        fail(c, PT_ERR_INVALID_ARG, "graph rounds take five-branch or central proposals (not full radius)");
     g.mlp = c.mlp_on && c.mlp_ready;
     // CTA sizes: the autotuned ones of this problem bucket when known
     const std::string key = tune_key(prec, C, maxN, maxP);
@@ -1540,8 +1580,8 @@ pt_status pt_create(pt_ctx** out, const pt_config* cfg) {
     if (cfg) c.cfg = *cfg; else pt_config_default(&c.cfg);
     if (c.cfg.table_log2 < 10 || c.cfg.table_log2 > 30 || c.cfg.precision < 0 || c.cfg.precision > 1 ||
         !(c.cfg.tmin > 0) || !(c.cfg.tmax > c.cfg.tmin) || c.cfg.newton_maxit < 1 || c.cfg.full_max_sweeps < 0 ||
-        c.cfg.prop_max_sweeps < 1 || (c.cfg.threads != 0 && (c.cfg.threads < 32 || c.cfg.threads > 512 ||
-                                                             c.cfg.threads % 32))) {
+        c.cfg.prop_max_sweeps < 1 || c.cfg.propose_mode < PT_PROPOSE_FIVE || c.cfg.propose_mode > PT_PROPOSE_FULL ||
+        (c.cfg.threads != 0 && (c.cfg.threads < 32 || c.cfg.threads > 512 || c.cfg.threads % 32))) {
         delete ctx;
         return PT_ERR_INVALID_ARG;
     }

@@ -168,8 +168,18 @@ void launch_lmax(cudaStream_t s, DCount count, const double* lnl, const int32_t*
 void launch_dump(cudaStream_t s, const Slot* tab, size_t nslots, int32_t* flag);
 void launch_dump_gather(cudaStream_t s, const Slot* tab, size_t nslots, const int32_t* flag, const int32_t* pos,
                         uint64_t* keys, uint8_t* status, double* lnl);
+// Neighbour trees of items kidx[k] (kidx null: items 0..nk-1) as edge lists
+// with the parent's lengths and the five proposal lengths len5 [item][5].
 void launch_materialize(cudaStream_t s, int n, DCount nk, const int32_t* kidx, const Item* items, TreeSet fr,
                         const double* len5, int32_t* edges_out, double* lengths_out, int32_t* slot_of);
+// len5 [item][5] = the parent's lengths of the five NNI branches (central, A, B, C, D).
+void launch_len5_inherit(cudaStream_t s, int n, DCount count, const Item* items, TreeSet fr, double* len5);
+// Keep decision and visited-table record of fully optimised proposals (full-radius mode):
+// kept[o] = lnl[o] >= *lmax - thr; the item's slot gets lnl and the proposal status.
+void launch_prop_full_finish(cudaStream_t s, DCount count, const Item* items, const double* lnl, const double* lmax,
+                             double thr, DRound round, Slot* tab, int32_t* kept);
+// dst[k] = src[idx[k]]
+void launch_gather_i32(cudaStream_t s, DCount count, const int32_t* idx, const int32_t* src, int32_t* dst);
 void launch_gather_out(cudaStream_t s, int n, DCount count, const int32_t* idx, TreeSet ts, const double* lnl,
                        int32_t* edges_out, double* lengths_out, double* lnl_out, uint64_t* keys_out);
 void launch_lengths_to_input(cudaStream_t s, int n, int count, TreeSet ts, double* lengths_out);

@@ -536,7 +536,7 @@ __global__ void k_materialize(int n, DCount nk, const int32_t* kidx, const Item*
     int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= dcount(nk)) return;
     const int NN = 2 * n - 2, E = 2 * n - 3;
-    int ii = kidx[k];
+    int ii = kidx ? kidx[k] : k;
     Item it = items[ii];
     const int32_t* up = fr.up + (size_t)it.tree * NN;
     const int32_t* ch = fr.ch + (size_t)it.tree * NN * 2;
@@ -563,6 +563,37 @@ __global__ void k_materialize(int n, DCount nk, const int32_t* kidx, const Item*
         eo[2 * (w - 1) + 1] = p;
         lo[w - 1] = l;
     }
+}
+
+__global__ void k_len5_inherit(int n, DCount cnt, const Item* items, TreeSet fr, double* len5) {
+    const int o = blockIdx.x * blockDim.x + threadIdx.x;
+    if (o >= dcount(cnt)) return;
+    const int NN = 2 * n - 2;
+    const Item it = items[o];
+    const int32_t* up = fr.up + (size_t)it.tree * NN;
+    const int32_t* ch = fr.ch + (size_t)it.tree * NN * 2;
+    const double* len = fr.len + (size_t)it.tree * NN;
+    const int v = it.v, u = up[v];
+    const int sib = ch[2 * u] == v ? ch[2 * u + 1] : ch[2 * u];
+    const int node[5] = {v, u, sib, ch[2 * v], ch[2 * v + 1]};
+    for (int b = 0; b < 5; ++b) len5[(size_t)o * 5 + b] = len[node[b]];
+}
+
+__global__ void k_prop_full_finish(DCount cnt, const Item* items, const double* lnl, const double* lmax, double thr,
+                                   DRound rd, Slot* tab, int32_t* kept) {
+    const int o = blockIdx.x * blockDim.x + threadIdx.x;
+    if (o >= dcount(cnt)) return;
+    const double f = lnl[o];
+    const int k = f >= *lmax - thr;
+    kept[o] = k;
+    Slot* sl = &tab[items[o].slot];
+    sl->lnl = f;
+    sl->tag = ((unsigned long long)dround(rd) << 48) | (unsigned long long)(k ? 4 : 1);
+}
+
+__global__ void k_gather_i32(DCount cnt, const int32_t* idx, const int32_t* src, int32_t* dst) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < dcount(cnt)) dst[k] = src[idx[k]];
 }
 
 // Gathers trees idx[k] of a set into canonical edge lists + lengths + lnl + keys.
@@ -1728,6 +1759,25 @@ void launch_gather_out(cudaStream_t s, int n, DCount count, const int32_t* idx, 
     if (count.cap <= 0) return;
     k_gather_out<<<blocks_for(count.cap, 128), 128, 0, s>>>(n, count, idx, ts, lnl, edges_out, lengths_out, lnl_out,
                                                              keys_out);
+    ++g_launches;
+}
+
+void launch_len5_inherit(cudaStream_t s, int n, DCount count, const Item* items, TreeSet fr, double* len5) {
+    if (count.cap <= 0) return;
+    k_len5_inherit<<<blocks_for(count.cap, 128), 128, 0, s>>>(n, count, items, fr, len5);
+    ++g_launches;
+}
+
+void launch_prop_full_finish(cudaStream_t s, DCount count, const Item* items, const double* lnl, const double* lmax,
+                             double thr, DRound round, Slot* tab, int32_t* kept) {
+    if (count.cap <= 0) return;
+    k_prop_full_finish<<<blocks_for(count.cap, 256), 256, 0, s>>>(count, items, lnl, lmax, thr, round, tab, kept);
+    ++g_launches;
+}
+
+void launch_gather_i32(cudaStream_t s, DCount count, const int32_t* idx, const int32_t* src, int32_t* dst) {
+    if (count.cap <= 0) return;
+    k_gather_i32<<<blocks_for(count.cap, 256), 256, 0, s>>>(count, idx, src, dst);
     ++g_launches;
 }
 

@@ -16,7 +16,7 @@ from . import build as _build
 
 PREC_FP64, PREC_MIXED = 0, 1
 SCORE_FIXED, SCORE_FULL = 0, 1
-PROPOSE_FIVE, PROPOSE_CENTRAL = 0, 1
+PROPOSE_FIVE, PROPOSE_CENTRAL, PROPOSE_FULL = 0, 1, 2
 ST_REJECTED, ST_GOOD, ST_BAD = 1, 2, 3
 STATUS = {0: "OK", 1: "INVALID_ARG", 2: "OOM", 3: "TABLE_FULL", 4: "BUFFER_TOO_SMALL", 5: "CUDA", 6: "TIMEOUT",
           7: "STATE"}
@@ -181,7 +181,7 @@ class Context:
         cfg.device = device
         cfg.precision = {"fp64": PREC_FP64, "mixed": PREC_MIXED}[precision]
         cfg.table_log2 = table_log2
-        cfg.propose_mode = {"five": PROPOSE_FIVE, "central": PROPOSE_CENTRAL}[propose]
+        cfg.propose_mode = {"five": PROPOSE_FIVE, "central": PROPOSE_CENTRAL, "full": PROPOSE_FULL}[propose]
         for k, v in overrides.items():
             setattr(cfg, k, v)
         self.cfg = cfg

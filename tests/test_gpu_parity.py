@@ -168,11 +168,11 @@ def test_finite_threshold_search_matches_oracle(prec, n, sites, T, seed):
 
 
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])
-@pytest.mark.parametrize("mode", ["five", "central"])
+@pytest.mark.parametrize("mode", ["five", "central", "full"])
 def test_proposals_match_oracle(prec, mode):
     n = 11
     a, pb = _setup(n, 700, 41, ncat=4)
-    pb.settings(prop_mode=0 if mode == "five" else 1)
+    pb.settings(prop_mode={"five": 0, "central": 1, "full": 2}[mode])
     e, l = synth.random_trees(n, 2, 42)
     ctx, aid = _ctx(prec, a, 4, table_log2=14, propose=mode)
     lmax, front = ctx.begin(aid, e, l, np.inf)
@@ -189,7 +189,7 @@ def test_proposals_match_oracle(prec, mode):
         assert len(k) == 1
         lp, nbe, nbl = pb.propose(pe, plen, k[0])
         assert abs(props["lnl"][i] - lp) <= _tol(prec, lp), (i, props["lnl"][i], lp)
-        if prec != "fp64":
+        if prec != "fp64" or mode == "full":  # full radius: len5 holds the inherited lengths
             continue
         # the five lengths by split: central, A, B, C, D
         up = {int(x): int(y) for x, y in pe}
@@ -210,6 +210,32 @@ def test_proposals_match_oracle(prec, mode):
         sl = _split_lengths(n, nbe, nbl)
         want = [sl[central], sl[A_split], sl[B], sl[Cc], sl[D]]
         np.testing.assert_allclose(props["len5"][i], want, rtol=1e-4, atol=1e-6)
+    ctx.close()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_full_radius_search_matches_oracle(prec):
+    """Radius -1 proposals (every branch optimised before the keep decision)."""
+    n, sites, T, seed = 8, 400, 3.0, 35
+    a, pb = _setup(n, sites, seed, ncat=4)
+    pb.settings(prop_mode=2)
+    e, l = synth.random_trees(n, 3, seed + 1)
+    s = oracle.Search(pb, e, l, T)
+    s.run()
+    ov = s.visited()
+    margin = _margins(ov, T).min()
+    if margin < 10 * TOL[prec]:
+        pytest.skip(f"decision within {margin:.2e} of the threshold: ambiguous at {prec} tolerance")
+    ctx, aid = _ctx(prec, a, 4, table_log2=16, propose="full")
+    lmax, rounds = pt.run_search(ctx, aid, e, l, T)
+    vis = ctx.visited(aid)
+    gd = dict(zip(pt.keys_to_int(vis["keys"]), zip(vis["status"], vis["lnl"])))
+    od = dict(zip(pt.keys_to_int(ov["keys"]), zip(ov["status"], ov["lnl"])))
+    assert set(gd) == set(od)
+    for k, (st, x) in od.items():
+        assert gd[k][0] == st, (k, gd[k], st)
+        assert abs(gd[k][1] - x) <= _tol(prec, x)
+    assert abs(lmax - s.lmax) <= _tol(prec, lmax)
     ctx.close()
 
 

@@ -210,3 +210,38 @@ def test_hill_climb_improves():
     assert lhc == pytest.approx(pb.loglik(he, hl), abs=1e-8)
     if moves:
         assert lhc > l0
+
+
+def test_full_radius_proposal_is_full_optimisation():
+    """prop_mode 2 (the paper's radius -1): the proposal of a neighbour is the
+    full optimisation of that neighbour from its inherited lengths."""
+    n = 8
+    a = synth.simulate(n, 400, 919, model="gtr", alpha=0.5)
+    tips, w = synth.compress_patterns(a.codes)
+    pb = oracle.Problem(tips, w, a.exch, a.freqs, 0.5, 4)
+    lnl, lens, _ = pb.full_optimise(a.tree_edges, np.full(2 * n - 3, 0.1))
+    nbe, nbl, _ = oracle.nni_neighbours(n, a.tree_edges, lens)
+    pb.settings(prop_mode=2)
+    for k in range(len(nbe)):
+        lp, pe, plen = pb.propose(a.tree_edges, lens, k)
+        lf, lensf, _ = pb.full_optimise(nbe[k], nbl[k])
+        np.testing.assert_array_equal(pe, nbe[k])
+        assert lp == pytest.approx(lf, abs=1e-9)
+        np.testing.assert_allclose(plen, lensf, rtol=1e-7, atol=1e-9)
+        # no branch of a fully optimised neighbour can improve alone: the Newton
+        # step -d1/d2 it would take is within the sweep tolerance's reach
+        for e in range(2 * n - 3):
+            _, d1, d2 = pb.edge_derivs(pe, plen, e)
+            assert abs(d1 / d2) < 1e-5 or (plen[e] <= 1e-6 + 2e-8 and d1 < 0)  # at the bound (Newton tol 1e-8)
+
+
+def test_full_radius_infinite_threshold_visits_every_topology():
+    n = 6
+    a = synth.simulate(n, 300, 921, model="jc")
+    tips, w = synth.compress_patterns(a.codes)
+    pb = oracle.Problem(tips, w, a.exch, a.freqs, 1.0, 1)
+    pb.settings(prop_mode=2)
+    e, l = synth.random_trees(n, 1, 922)
+    s = oracle.Search(pb, e, l, float("inf"))
+    s.run()
+    assert len(s.visited()["keys"]) == COUNTS[n]
