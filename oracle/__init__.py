@@ -49,6 +49,7 @@ def lib():
             L.or_problem_new.restype = C.c_void_p
             L.or_problem_new.argtypes = [C.c_int, C.c_int, C.c_int, _u8p, _f64p, _f64p, _f64p, C.c_double]
             L.or_problem_free.argtypes = [C.c_void_p]
+            L.or_problem_prior.argtypes = [C.c_void_p, C.c_double]
             L.or_problem_settings.argtypes = [C.c_void_p, C.c_double, C.c_double, C.c_double, C.c_int,
                                               C.c_double, C.c_int, C.c_int, C.c_int]
             L.or_problem_model.argtypes = [C.c_void_p, _f64p, _f64p]
@@ -186,6 +187,10 @@ class Problem:
                  full_max_sweeps=64, prop_max_sweeps=8, prop_mode=0):
         lib().or_problem_settings(self._p, tmin, tmax, newton_tol, newton_maxit, sweep_tol,
                                   full_max_sweeps, prop_max_sweeps, prop_mode)
+
+    def set_prior(self, rate: float):
+        """MAP objective with an Exponential(rate) prior on every branch length (0 = ML)."""
+        lib().or_problem_prior(self._p, float(rate))
 
     def model(self):
         Q = np.zeros(16, np.float64)

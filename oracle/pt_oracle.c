@@ -57,6 +57,7 @@ typedef struct {
     double tmin, tmax, newton_tol, sweep_tol;
     int newton_maxit, full_max_sweeps, prop_max_sweeps;
     int prop_mode;   /* 0 = five branches around the NNI edge, 1 = central only, 2 = every branch */
+    double prior_rate; /* 0: maximum likelihood; > 0: MAP under an Exponential(prior_rate) prior per branch */
     /* counters (diagnostics for tests) */
     long n_newton_evals, n_newton_nonconv;
 } or_problem;
@@ -228,6 +229,7 @@ or_problem *or_problem_new(int n, int P, int C, const uint8_t *tips, const doubl
     pb->newton_tol = 1e-8; pb->newton_maxit = 50;
     pb->sweep_tol = 1e-6; pb->full_max_sweeps = 64; pb->prop_max_sweeps = 8;
     pb->prop_mode = 0;
+    pb->prior_rate = 0.0;
     return pb;
 }
 
@@ -236,6 +238,12 @@ void or_problem_free(or_problem *pb)
     if (!pb) return;
     free(pb->tips); free(pb->w); free(pb);
 }
+
+/* MAP objective ("Phylogenetic Topographer", its optional exponential branch
+ * length prior): every branch length gets an Exponential(rate) prior, so a
+ * topology's score is lnL + sum over its 2n-3 branches of (ln rate - rate t);
+ * rate 0 restores maximum likelihood (score = lnL). */
+void or_problem_prior(or_problem *pb, double rate) { pb->prior_rate = rate; }
 
 void or_problem_settings(or_problem *pb, double tmin, double tmax, double newton_tol, int newton_maxit,
                          double sweep_tol, int full_max_sweeps, int prop_max_sweeps, int prop_mode)
@@ -474,6 +482,7 @@ static double newton_branch(or_problem *pb, const double *X, const int *sx, cons
     for (int it = 0; it < pb->newton_maxit; ++it) {
         double f, d1, d2;
         branch_eval(pb, X, sx, Y, sy, t, &f, &d1, &d2);
+        d1 -= pb->prior_rate;    /* the prior's ln rate - rate t has slope -rate */
         if (d1 == 0.0) return t; /* flat (e.g. a branch to an all-gap leaf) */
         if (d1 > 0.0) lo = t; else hi = t;
         double tn;
@@ -509,6 +518,21 @@ static double optimise_edge(or_problem *pb, or_tree *t, int u, int v)
 static double tree_lnl(const or_problem *pb, const or_tree *t)
 {
     return lnl_rooted(pb, t, t->n, NULL); /* node n is always an inner node */
+}
+
+/* The objective of a topology at its lengths: lnL, plus the log prior
+ * density of the lengths under the MAP objective. */
+static double tree_score(const or_problem *pb, const or_tree *t)
+{
+    double f = tree_lnl(pb, t);
+    if (pb->prior_rate > 0.0) {
+        double sum = 0.0;
+        for (int u = 0; u < t->nnode; ++u)
+            for (int j = 0; j < t->deg[u]; ++j)
+                if (t->adj[u][j] > u) sum += t->len[u][j]; /* each edge once */
+        f += (2 * t->n - 3) * log(pb->prior_rate) - pb->prior_rate * sum;
+    }
+    return f;
 }
 
 /* ------------------------------------------------------------------------- */
@@ -551,7 +575,7 @@ static double full_optimise(or_problem *pb, or_tree *t, int *sweeps_out)
         if (moved <= pb->sweep_tol) { ++s; break; }
     }
     if (sweeps_out) *sweeps_out = s;
-    return tree_lnl(pb, t);
+    return tree_score(pb, t);
 }
 
 /* ------------------------------------------------------------------------- */
@@ -736,7 +760,7 @@ static double propose_optimise(or_problem *pb, or_tree *nt, const or_quartet *q,
         }
         if (moved <= pb->sweep_tol) break;
     }
-    return tree_lnl(pb, nt);
+    return tree_score(pb, nt);
 }
 
 /* ------------------------------------------------------------------------- */
