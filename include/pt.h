@@ -86,6 +86,10 @@ typedef struct {
     int prop_max_sweeps;  /* cap on sweeps of the proposal optimisation */
     int threads;          /* threads per CTA for the site loops (0 = automatic) */
     size_t mem_budget;    /* device bytes for partial-likelihood buffers per launch group (0 = automatic) */
+    double branch_prior_rate; /* 0: maximum likelihood (default).  > 0: MAP objective ("Phylogenetic
+                               * Topographer", its optional exponential branch-length prior): every length
+                               * has an Exponential(rate) prior, each Newton step maximises lnL - rate t,
+                               * and every reported lnL is the score lnL + (2n-3) ln rate - rate sum(t) */
 } pt_config;
 
 /* Fills cfg with the defaults: device 0, mixed precision, 2^22 slots, five
@@ -256,6 +260,18 @@ pt_status pt_graph_destroy(pt_ctx *ctx, pt_graph *g);
  * the count. */
 pt_status pt_visited(pt_ctx *ctx, int aln_id, size_t cap, pt_key *keys, uint8_t *status, double *lnl,
                      size_t *count);
+
+/* HLS split frequencies ("Split Frequency Comparison"): for n_trees trees of
+ * alignment aln_id's taxa (edge lists as pt_expand_frontier's, lengths not
+ * needed) with scores lnl (typically the GOOD trees of a search), the
+ * frequency of a split is the sum over the trees containing it of
+ * exp(lnl - max lnl), divided by the sum over all trees.  Outputs the
+ * non-trivial splits (the side without taxon 0 as a 128-bit leaf mask, low
+ * word first) with their frequencies and tree counts, by decreasing
+ * frequency; the majority-rule consensus is the splits above 0.5.  Two-call
+ * pattern as pt_visited (all-NULL outputs: count only). */
+pt_status pt_split_frequencies(pt_ctx *ctx, int aln_id, int n_trees, const int32_t *edges, const double *lnl,
+                               size_t cap, uint64_t *splits, double *freq, int64_t *trees, size_t *count);
 
 /* Clears (allocating on first use) the visited table and round counter of
  * an alignment. */

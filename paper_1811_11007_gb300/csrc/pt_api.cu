@@ -161,6 +161,8 @@ Cfg kcfg(const Ctx& c) {
     k.full_max_sweeps = c.cfg.full_max_sweeps;
     k.prop_max_sweeps = c.cfg.prop_max_sweeps;
     k.propose_mode = c.cfg.propose_mode;
+    k.prior_rate = c.cfg.branch_prior_rate;
+    k.prior_log = c.cfg.branch_prior_rate > 0 ? std::log(c.cfg.branch_prior_rate) : 0.0;
     return k;
 }
 
@@ -1570,6 +1572,7 @@ void pt_config_default(pt_config* cfg) {
     cfg->prop_max_sweeps = 8;
     cfg->threads = 0;
     cfg->mem_budget = 0;
+    cfg->branch_prior_rate = 0.0;
 }
 
 pt_status pt_create(pt_ctx** out, const pt_config* cfg) {
@@ -1581,6 +1584,7 @@ pt_status pt_create(pt_ctx** out, const pt_config* cfg) {
     if (c.cfg.table_log2 < 10 || c.cfg.table_log2 > 30 || c.cfg.precision < 0 || c.cfg.precision > 1 ||
         !(c.cfg.tmin > 0) || !(c.cfg.tmax > c.cfg.tmin) || c.cfg.newton_maxit < 1 || c.cfg.full_max_sweeps < 0 ||
         c.cfg.prop_max_sweeps < 1 || c.cfg.propose_mode < PT_PROPOSE_FIVE || c.cfg.propose_mode > PT_PROPOSE_FULL ||
+        !(c.cfg.branch_prior_rate >= 0) || !std::isfinite(c.cfg.branch_prior_rate) ||
         (c.cfg.threads != 0 && (c.cfg.threads < 32 || c.cfg.threads > 512 || c.cfg.threads % 32))) {
         delete ctx;
         return PT_ERR_INVALID_ARG;
@@ -2004,6 +2008,76 @@ pt_status pt_visited(pt_ctx* ctx, int aln_id, size_t cap, pt_key* keys, uint8_t*
         ck(c, cudaStreamSynchronize(c.stream), "sync");
         const bool query = !keys && !status && !lnl;
         if (!query && cap < (size_t)tot) fail(c, PT_ERR_BUFFER_TOO_SMALL, "visited set has %d entries", tot);
+    });
+}
+
+pt_status pt_split_frequencies(pt_ctx* ctx, int aln_id, int n_trees, const int32_t* edges, const double* lnl,
+                               size_t cap, uint64_t* splits, double* freq, int64_t* trees, size_t* count) {
+    return guarded(ctx, [&](Ctx& c) {
+        AlnState& a = aln_of(c, aln_id, false);
+        if (n_trees < 1 || !edges || !lnl || !count) fail(c, PT_ERR_INVALID_ARG, "bad arguments");
+        const int n = a.n, E = 2 * n - 3;
+        double lmax = -INFINITY;
+        for (int t = 0; t < n_trees; ++t) {
+            if (!std::isfinite(lnl[t])) fail(c, PT_ERR_INVALID_ARG, "lnl[%d] is not finite", t);
+            lmax = std::max(lmax, lnl[t]);
+        }
+        std::vector<double> unit_len((size_t)n_trees * E, 0.1);  // lengths are not used
+        validate_trees(c, n, n_trees, edges, unit_len.data());
+        zero_flags(c);
+        int32_t* de = buf<int32_t>(c, "sf.e", (size_t)n_trees * 2 * E);
+        double* dl = buf<double>(c, "sf.l", (size_t)n_trees * E);
+        double* dn = buf<double>(c, "sf.lnl", n_trees);
+        double* dm = buf<double>(c, "sf.lmax", 1);
+        ck(c, cudaMemcpyAsync(de, edges, 4 * (size_t)n_trees * 2 * E, cudaMemcpyHostToDevice, c.stream), "copy in");
+        ck(c, cudaMemcpyAsync(dl, unit_len.data(), 8 * (size_t)n_trees * E, cudaMemcpyHostToDevice, c.stream), "copy in");
+        ck(c, cudaMemcpyAsync(dn, lnl, 8 * (size_t)n_trees, cudaMemcpyHostToDevice, c.stream), "copy in");
+        ck(c, cudaMemcpyAsync(dm, &lmax, 8, cudaMemcpyHostToDevice, c.stream), "copy in");
+        TreeSet ts = treeset(c, "sf", n, n_trees, true);
+        launch_canon(c.stream, n, n_trees, de, dl, ts, c.d_err);
+        // a table at most half full: 2 x (trees x non-trivial splits) slots, rounded up to a power of two
+        int log2 = 10;
+        while (((size_t)1 << log2) < 2 * (size_t)n_trees * std::max(n - 3, 1) && log2 < 30) ++log2;
+        const size_t ns = (size_t)1 << log2;
+        SplitSlot* tab = buf<SplitSlot>(c, "sf.tab", ns);
+        launch_split_frequencies(c.stream, ts, n_trees, dn, dm, tab, log2, c.d_err);
+        check_flags(c);
+        int32_t* flag = buf<int32_t>(c, "sf.flag", ns);
+        int32_t* pos = buf<int32_t>(c, "sf.pos", ns);
+        launch_split_dump(c.stream, tab, ns, flag, nullptr, nullptr, nullptr, nullptr, false);
+        const int tot = scan_count(c, flag, pos, (int)ns);
+        uint64_t* dk = buf<uint64_t>(c, "sf.k", 2 * (size_t)tot + 2);
+        double* dw = buf<double>(c, "sf.w", (size_t)tot + 1);
+        unsigned long long* dt = buf<unsigned long long>(c, "sf.t", (size_t)tot + 1);
+        launch_split_dump(c.stream, tab, ns, flag, pos, dk, dw, dt, true);
+        std::vector<uint64_t> hk(2 * (size_t)tot);
+        std::vector<double> hw(tot);
+        std::vector<unsigned long long> ht(tot);
+        if (tot) {
+            ck(c, cudaMemcpyAsync(hk.data(), dk, 16 * (size_t)tot, cudaMemcpyDeviceToHost, c.stream), "copy out");
+            ck(c, cudaMemcpyAsync(hw.data(), dw, 8 * (size_t)tot, cudaMemcpyDeviceToHost, c.stream), "copy out");
+            ck(c, cudaMemcpyAsync(ht.data(), dt, 8 * (size_t)tot, cudaMemcpyDeviceToHost, c.stream), "copy out");
+        }
+        ck(c, cudaStreamSynchronize(c.stream), "sync");
+        // normalisation: the trees' summed weight (FP64, in input order)
+        double W = 0.0;
+        for (int t = 0; t < n_trees; ++t) W += std::exp(lnl[t] - lmax);
+        std::vector<int> order(tot);
+        for (int i = 0; i < tot; ++i) order[i] = i;
+        std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
+            if (hw[x] != hw[y]) return hw[x] > hw[y];
+            return hk[2 * x + 1] != hk[2 * y + 1] ? hk[2 * x + 1] < hk[2 * y + 1] : hk[2 * x] < hk[2 * y];
+        });
+        *count = (size_t)tot;
+        const size_t k = std::min(cap, (size_t)tot);
+        for (size_t i = 0; i < k; ++i) {
+            const int j = order[i];
+            if (splits) { splits[2 * i] = hk[2 * j]; splits[2 * i + 1] = hk[2 * j + 1]; }
+            if (freq) freq[i] = hw[j] / W;
+            if (trees) trees[i] = (int64_t)ht[j];
+        }
+        const bool query = !splits && !freq && !trees;
+        if (!query && cap < (size_t)tot) fail(c, PT_ERR_BUFFER_TOO_SMALL, "%d distinct splits", tot);
     });
 }
 

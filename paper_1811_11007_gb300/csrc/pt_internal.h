@@ -53,6 +53,8 @@ struct Aln {
 struct Cfg {
     double tmin, tmax, newton_tol, sweep_tol;
     int newton_maxit, full_max_sweeps, prop_max_sweeps, propose_mode;
+    double prior_rate;  // 0: maximum likelihood; > 0: MAP, Exponential(prior_rate) on every branch
+    double prior_log;   // ln(prior_rate) (0 without a prior)
 };
 
 // Canonical rooted trees (rooted at leaf 0, inner nodes renumbered n.. in
@@ -180,6 +182,21 @@ void launch_prop_full_finish(cudaStream_t s, DCount count, const Item* items, co
                              double thr, DRound round, Slot* tab, int32_t* kept);
 // dst[k] = src[idx[k]]
 void launch_gather_i32(cudaStream_t s, DCount count, const int32_t* idx, const int32_t* src, int32_t* dst);
+
+// Split-frequency table (HLS post-processing): split bitset -> summed weight,
+// number of trees.  32 bytes, 16-byte aligned for the 128-bit CAS.
+struct SplitSlot {
+    unsigned long long klo, khi;
+    double w;
+    unsigned long long trees;
+};
+// Clears the table (2^log2 slots) and adds exp(lnl[t] - *lmax) of each of
+// count canonical trees to each of its non-trivial splits.
+void launch_split_frequencies(cudaStream_t s, TreeSet ts, int count, const double* lnl, const double* lmax,
+                              SplitSlot* tab, int log2, int32_t* err);
+// Dump of the occupied slots: flag pass (gather false), then gather at pos.
+void launch_split_dump(cudaStream_t s, const SplitSlot* tab, size_t nslots, int32_t* flag, const int32_t* pos,
+                       uint64_t* splits, double* w, unsigned long long* trees, bool gather);
 void launch_gather_out(cudaStream_t s, int n, DCount count, const int32_t* idx, TreeSet ts, const double* lnl,
                        int32_t* edges_out, double* lengths_out, double* lnl_out, uint64_t* keys_out);
 void launch_lengths_to_input(cudaStream_t s, int n, int count, TreeSet ts, double* lengths_out);

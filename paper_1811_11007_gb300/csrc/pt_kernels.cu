@@ -466,6 +466,59 @@ __global__ void k_dump_gather(const Slot* tab, size_t nslots, const int32_t* fla
     }
 }
 
+// ---------------------------------------------------------------- split frequencies
+// Split table: 128-bit split bitset (side without taxon 0) -> summed weight.
+// Tree i adds w_i = exp(lnl_i - max lnl) to each of its n-3 non-trivial splits
+// (the leaf sets below its inner nodes other than the first; trees are rooted
+// at leaf 0, so those sets never hold taxon 0).
+__global__ void k_split_init(SplitSlot* tab, size_t nslots) {
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < nslots; i += (size_t)gridDim.x * blockDim.x) {
+        tab[i].klo = 0; tab[i].khi = 0; tab[i].w = 0.0; tab[i].trees = 0;
+    }
+}
+
+__global__ void k_split_add(TreeSet ts, int count, const double* lnl, const double* lmax, SplitSlot* tab, int log2,
+                            int32_t* err) {
+    const int n = ts.n, NN = 2 * n - 2, per = n - 3;
+    const long long x = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (x >= (long long)count * per) return;
+    const int t = (int)(x / per), v = n + 1 + (int)(x % per);
+    const uint64_t* bits = ts.bits + ((size_t)t * NN + v) * 2;
+    const unsigned long long lo = bits[0], hi = bits[1];
+    const double w = exp(lnl[t] - *lmax);
+    const unsigned long long mask = (1ull << log2) - 1;
+    const unsigned __int128 key = ((unsigned __int128)hi << 64) | lo;
+    size_t h = slot_hash(lo, hi, mask);
+    for (int p = 0; p < kMaxProbe; ++p) {
+        const size_t i = (h + p) & mask;
+        unsigned __int128* kp = reinterpret_cast<unsigned __int128*>(&tab[i].klo);
+        const unsigned __int128 old = atomicCAS(kp, (unsigned __int128)0, key);
+        if (old == 0 || old == key) {
+            atomicAdd(&tab[i].w, w);
+            atomicAdd(&tab[i].trees, 1ull);
+            return;
+        }
+    }
+    atomicExch(&err[kErrTable], 1);
+}
+
+__global__ void k_split_flag(const SplitSlot* tab, size_t nslots, int32_t* flag) {
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < nslots; i += (size_t)gridDim.x * blockDim.x)
+        flag[i] = (tab[i].klo | tab[i].khi) ? 1 : 0;
+}
+
+__global__ void k_split_gather(const SplitSlot* tab, size_t nslots, const int32_t* flag, const int32_t* pos,
+                               uint64_t* splits, double* w, unsigned long long* trees) {
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < nslots; i += (size_t)gridDim.x * blockDim.x) {
+        if (!flag[i]) continue;
+        const int p = pos[i];
+        splits[2 * p] = tab[i].klo;
+        splits[2 * p + 1] = tab[i].khi;
+        w[p] = tab[i].w;
+        trees[p] = tab[i].trees;
+    }
+}
+
 // ---------------------------------------------------------------- scan
 __global__ void k_scan_block(const int32_t* in, int32_t* out, int N, int32_t* bsum) {
     __shared__ int32_t ws[32];
@@ -1058,6 +1111,7 @@ __device__ double newton_solve(const Model& M, const Cfg& cfg, const STab<R, C>&
     double t = fmin(fmax(t0, lo), hi);
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = (blockDim.x + 31) >> 5;
     const int top = nw > 8 ? 8 : nw > 4 ? 4 : nw > 2 ? 2 : 1;  // first butterfly offset
+    const bool prior = __double_as_longlong(cfg.prior_rate) != 0;
     put_egh<R, C>(M, t, ns, false);
     if (threadIdx.x == 0) ns.tb = t;
     __syncthreads();
@@ -1118,7 +1172,9 @@ __device__ double newton_solve(const Model& M, const Cfg& cfg, const STab<R, C>&
                 D += __shfl_xor_sync(0xffffffffu, D, o);
                 Df += __shfl_xor_sync(0xffffffffu, Df, o);
             }
-            const double D1 = __shfl_sync(0xffffffffu, D, 0), D2 = __shfl_sync(0xffffffffu, D, 16);
+            double D1 = __shfl_sync(0xffffffffu, D, 0);
+            const double D2 = __shfl_sync(0xffffffffu, D, 16);
+            if (prior) D1 -= cfg.prior_rate;  // MAP: the prior's slope
             const float D2f = __shfl_sync(0xffffffffu, Df, 16);
             const bool done = newton_step(t, lo, hi, D1, D2, D2f, cfg.newton_tol);
             const bool last = done || it + 1 == cfg.newton_maxit;
@@ -1322,7 +1378,7 @@ __global__ void __launch_bounds__(512) k_propose(const PropGroup* __restrict__ g
         }
         if (threadIdx.x < 5) {
             double t0 = len[bnode[threadIdx.x]];
-            if (G.init) {  // learned warm start; NaN = keep the inherited length
+            if (G.init && (nb == 5 || threadIdx.x == 0)) {  // warm start of the optimised branches; NaN = keep
                 const double y = G.init[(size_t)o * 5 + threadIdx.x];
                 if (y == y) t0 = y;
             }
@@ -1403,9 +1459,15 @@ __global__ void __launch_bounds__(512) k_propose(const PropGroup* __restrict__ g
             if (moved <= cfg.sweep_tol) break;
         }
         // exact lnL at the final lengths: the last sum-table at its new length
-        const double f1 = eval_lnl<R, C>(M, st, P, tlast, sm.ns);
+        double f1 = eval_lnl<R, C>(M, st, P, tlast, sm.ns);
         sweeps_total += sweeps;
         if (threadIdx.x == 0) {
+            if (__double_as_longlong(cfg.prior_rate) != 0) {  // MAP: log prior of the neighbour's lengths
+                double sum = 0.0;
+                for (int w = 1; w < NN; ++w) sum += len[w];
+                for (int b = 0; b < 5; ++b) sum += sm.T[b] - len[bnode[b]];
+                f1 += (double)(NN - 1) * cfg.prior_log - cfg.prior_rate * sum;
+            }
             G.lnl_out[o] = f1;
             for (int b = 0; b < 5; ++b) G.len5_out[(size_t)o * 5 + b] = sm.T[b];
             const int k = f1 >= *G.lmax - G.thr;
@@ -1616,11 +1678,18 @@ __global__ void __launch_bounds__(512) k_fullopt(const FullGroup* __restrict__ g
             if (moved <= cfg.sweep_tol) break;
         }
         // exact lnL at the final lengths (the last visited edge's sum-table)
-        const double f1 = eval_lnl<R, C>(M, st, P, G.max_sweeps == 0 ? len[n] : tlast, sm.ns);
+        double f1 = eval_lnl<R, C>(M, st, P, G.max_sweeps == 0 ? len[n] : tlast, sm.ns);
         sweeps_total += sweeps;
         __syncthreads();
         for (int v = threadIdx.x; v < NN; v += blockDim.x) glen[v] = len[v];
-        if (threadIdx.x == 0) G.lnl_out[gi] = f1;
+        if (threadIdx.x == 0) {
+            if (__double_as_longlong(cfg.prior_rate) != 0) {  // MAP: log prior of the lengths
+                double sum = 0.0;
+                for (int w = 1; w < NN; ++w) sum += len[w];
+                f1 += (double)(NN - 1) * cfg.prior_log - cfg.prior_rate * sum;
+            }
+            G.lnl_out[gi] = f1;
+        }
     }
     if (threadIdx.x == 0) {
         atomicAdd(&stats[kStFullEvals], evals_total);
@@ -1759,6 +1828,26 @@ void launch_gather_out(cudaStream_t s, int n, DCount count, const int32_t* idx, 
     if (count.cap <= 0) return;
     k_gather_out<<<blocks_for(count.cap, 128), 128, 0, s>>>(n, count, idx, ts, lnl, edges_out, lengths_out, lnl_out,
                                                              keys_out);
+    ++g_launches;
+}
+
+void launch_split_frequencies(cudaStream_t s, TreeSet ts, int count, const double* lnl, const double* lmax,
+                              SplitSlot* tab, int log2, int32_t* err) {
+    const size_t nslots = (size_t)1 << log2;
+    k_split_init<<<(int)std::min<size_t>((nslots + 255) / 256, 4096), 256, 0, s>>>(tab, nslots);
+    ++g_launches;
+    const long long work = (long long)count * (ts.n - 3);
+    if (work > 0) {
+        k_split_add<<<blocks_for(work, 256), 256, 0, s>>>(ts, count, lnl, lmax, tab, log2, err);
+        ++g_launches;
+    }
+}
+
+void launch_split_dump(cudaStream_t s, const SplitSlot* tab, size_t nslots, int32_t* flag, const int32_t* pos,
+                       uint64_t* splits, double* w, unsigned long long* trees, bool gather) {
+    const int grid = (int)std::min<size_t>((nslots + 255) / 256, 4096);
+    if (!gather) k_split_flag<<<grid, 256, 0, s>>>(tab, nslots, flag);
+    else k_split_gather<<<grid, 256, 0, s>>>(tab, nslots, flag, pos, splits, w, trees);
     ++g_launches;
 }
 

@@ -13,6 +13,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cmath>
 #include <cstdint>
 #include <mutex>
 
@@ -62,7 +63,8 @@ extern "C" pt_status pt_score_topologies_noalloc(int n_taxa, int n_patterns, con
     pt_config cfg;
     if (cfg_in) cfg = *cfg_in; else pt_config_default(&cfg);
     if (cfg.precision < 0 || cfg.precision > 1 || !(cfg.tmin > 0) || !(cfg.tmax > cfg.tmin) || cfg.newton_maxit < 1 ||
-        cfg.full_max_sweeps < 0 || (cfg.threads != 0 && (cfg.threads < 32 || cfg.threads > 512 || cfg.threads % 32)))
+        cfg.full_max_sweeps < 0 || !(cfg.branch_prior_rate >= 0) || !std::isfinite(cfg.branch_prior_rate) ||
+        (cfg.threads != 0 && (cfg.threads < 32 || cfg.threads > 512 || cfg.threads % 32)))
         return PT_ERR_INVALID_ARG;
     Model M;
     if (!host_build_model(exch, freqs, alpha, n_cats, M)) return PT_ERR_INVALID_ARG;
@@ -151,6 +153,8 @@ extern "C" pt_status pt_score_topologies_noalloc(int n_taxa, int n_patterns, con
     k.full_max_sweeps = cfg.full_max_sweeps;
     k.prop_max_sweeps = cfg.prop_max_sweeps;
     k.propose_mode = cfg.propose_mode;
+    k.prior_rate = cfg.branch_prior_rate;
+    k.prior_log = cfg.branch_prior_rate > 0 ? std::log(cfg.branch_prior_rate) : 0.0;
     Aln A{n, P, tips_dev, weights_dev};
     FullGroup* d_group = reinterpret_cast<FullGroup*>(base + o_grp);
     int* d_gstart = reinterpret_cast<int*>(base + o_grp + sizeof(FullGroup));

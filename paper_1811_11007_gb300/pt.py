@@ -28,7 +28,7 @@ EXPORTS = ["pt_config_default", "pt_create", "pt_destroy", "pt_last_error", "pt_
            "pt_mlp_loss_grad", "pt_mlp_train", "pt_mlp_enable", "pt_training_log", "pt_training_pairs",
            "pt_expand_batch", "pt_expand_batch_dev", "pt_autotune", "pt_autotune_report", "pt_graph_create",
            "pt_graph_frontier_dev", "pt_graph_set_frontier", "pt_graph_run", "pt_graph_next_dev", "pt_graph_get_next",
-           "pt_graph_advance", "pt_graph_destroy"]
+           "pt_graph_advance", "pt_graph_destroy", "pt_split_frequencies"]
 MLP_PARAMS, MLP_IN, MLP_OUT = 27912, 69, 5
 _f32p = np.ctypeslib.ndpointer(np.float32, flags="C_CONTIGUOUS")
 
@@ -50,7 +50,7 @@ class Config(C.Structure):
     _fields_ = [("device", C.c_int), ("precision", C.c_int), ("table_log2", C.c_int), ("propose_mode", C.c_int),
                 ("tmin", C.c_double), ("tmax", C.c_double), ("newton_tol", C.c_double), ("newton_maxit", C.c_int),
                 ("sweep_tol", C.c_double), ("full_max_sweeps", C.c_int), ("prop_max_sweeps", C.c_int),
-                ("threads", C.c_int), ("mem_budget", C.c_size_t)]
+                ("threads", C.c_int), ("mem_budget", C.c_size_t), ("branch_prior_rate", C.c_double)]
 
 
 _lib = None
@@ -123,6 +123,8 @@ def lib():
             L.pt_graph_get_next.argtypes = [_vp, _vp, C.c_int, C.c_int, _vp, _vp, _vp, _vp, _ip]
             L.pt_graph_advance.argtypes = [_vp, _vp, _ip]
             L.pt_graph_destroy.argtypes = [_vp, _vp]
+            L.pt_split_frequencies.argtypes = [_vp, C.c_int, C.c_int, _vp, _vp, C.c_size_t, _vp, _vp, _vp,
+                                               C.POINTER(C.c_size_t)]
             L.pt_score_topologies_noalloc.argtypes = [C.c_int, C.c_int, _vp, _vp, _f64p, _f64p, C.c_double, C.c_int,
                                                       C.POINTER(Config), C.c_int, _vp, _vp, _vp, _vp, C.c_int, _vp]
             _lib = L
@@ -308,6 +310,22 @@ class Context:
             c = arr[k].n_kept
             out.append((arr[k].lmax, {"edges": fe[:c], "lengths": fl[:c], "lnl": fn[:c], "keys": fk[:c]}))
         return out
+
+    def split_frequencies(self, aln: int, edges, lnl) -> dict:
+        """Score-weighted split frequencies of a set of trees (pt_split_frequencies)."""
+        n = self._n[aln]
+        e = np.ascontiguousarray(edges, np.int32).reshape(-1, 2 * n - 3, 2)
+        f = np.ascontiguousarray(lnl, np.float64).reshape(-1)
+        cnt = C.c_size_t()
+        self._ck(lib().pt_split_frequencies(self._h, aln, e.shape[0], e.ctypes.data, f.ctypes.data, 0, None, None,
+                                            None, C.byref(cnt)))
+        k = cnt.value
+        sp = np.zeros((k, 2), np.uint64)
+        fr = np.zeros(k, np.float64)
+        tr = np.zeros(k, np.int64)
+        self._ck(lib().pt_split_frequencies(self._h, aln, e.shape[0], e.ctypes.data, f.ctypes.data, k, _ptr(sp),
+                                            _ptr(fr), _ptr(tr), C.byref(cnt)))
+        return {"splits": sp, "freq": fr, "trees": tr}
 
     def graph(self, alns, frontier_caps, thresholds) -> "GraphRound":
         """Records a graph round over alignments alns (pt_graph_create)."""

@@ -239,6 +239,53 @@ def test_full_radius_search_matches_oracle(prec):
     ctx.close()
 
 
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_map_scoring_matches_oracle(prec):
+    """MAP objective (Exponential(10) prior on every length): fixed and fully
+    optimised scores and the MAP lengths against the oracle."""
+    import math
+    n, rate = 10, 10.0
+    a, pb = _setup(n, 600, 301, ncat=4)
+    pb.set_prior(rate)
+    e, l = synth.random_trees(n, 4, 302)
+    ctx, aid = _ctx(prec, a, 4, branch_prior_rate=rate)
+    fixed, _, _ = ctx.score(aid, e, l, mode="fixed")
+    lnl, lens, _ = ctx.score(aid, e, l, mode="full")
+    for i in range(len(e)):
+        want_fixed = pb.loglik(e[i], l[i]) + (2 * n - 3) * math.log(rate) - rate * float(np.sum(l[i]))
+        assert abs(fixed[i] - want_fixed) <= _tol(prec, want_fixed)
+        want, wl, _ = pb.full_optimise(e[i], l[i])
+        assert abs(lnl[i] - want) <= _tol(prec, want), (i, lnl[i], want)
+        if prec == "fp64":
+            np.testing.assert_allclose(lens[i], wl, rtol=1e-4, atol=1e-6)
+    ctx.close()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_map_search_matches_oracle(prec):
+    n, sites, T, seed, rate = 9, 500, 3.0, 303, 10.0
+    a, pb = _setup(n, sites, seed, ncat=4)
+    pb.set_prior(rate)
+    e, l = synth.random_trees(n, 3, seed + 1)
+    s = oracle.Search(pb, e, l, T)
+    s.run()
+    ov = s.visited()
+    margin = _margins(ov, T).min()
+    if margin < 10 * TOL[prec]:
+        pytest.skip(f"decision within {margin:.2e} of the threshold: ambiguous at {prec} tolerance")
+    ctx, aid = _ctx(prec, a, 4, table_log2=16, branch_prior_rate=rate)
+    lmax, rounds = pt.run_search(ctx, aid, e, l, T)
+    vis = ctx.visited(aid)
+    gd = dict(zip(pt.keys_to_int(vis["keys"]), zip(vis["status"], vis["lnl"])))
+    od = dict(zip(pt.keys_to_int(ov["keys"]), zip(ov["status"], ov["lnl"])))
+    assert set(gd) == set(od)
+    for k, (st, x) in od.items():
+        assert gd[k][0] == st, (k, gd[k], st)
+        assert abs(gd[k][1] - x) <= _tol(prec, x)
+    assert abs(lmax - s.lmax) <= _tol(prec, lmax)
+    ctx.close()
+
+
 def test_edge_cases():
     # 3 taxa: no internal edge, no neighbour; 4 taxa with gaps; a start given twice
     for n in (3, 4):
