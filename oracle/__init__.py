@@ -50,6 +50,9 @@ def lib():
             L.or_problem_new.argtypes = [C.c_int, C.c_int, C.c_int, _u8p, _f64p, _f64p, _f64p, C.c_double]
             L.or_problem_free.argtypes = [C.c_void_p]
             L.or_problem_prior.argtypes = [C.c_void_p, C.c_double]
+            L.or_problem_reopt.argtypes = [C.c_void_p, C.c_int]
+            L.or_visit_optimise.argtypes = [C.c_void_p, C.c_int, _i32p, _f64p, C.POINTER(C.c_double),
+                                            C.POINTER(C.c_double)]
             L.or_problem_settings.argtypes = [C.c_void_p, C.c_double, C.c_double, C.c_double, C.c_int,
                                               C.c_double, C.c_int, C.c_int, C.c_int]
             L.or_problem_model.argtypes = [C.c_void_p, _f64p, _f64p]
@@ -187,6 +190,20 @@ class Problem:
                  full_max_sweeps=64, prop_max_sweeps=8, prop_mode=0):
         lib().or_problem_settings(self._p, tmin, tmax, newton_tol, newton_maxit, sweep_tol,
                                   full_max_sweeps, prop_max_sweeps, prop_mode)
+
+    def set_reopt_alpha(self, on: bool):
+        """Visits re-optimise the Gamma shape jointly with the branch lengths."""
+        lib().or_problem_reopt(self._p, 1 if on else 0)
+
+    def visit_optimise(self, edges, lengths):
+        """A visit's optimisation: (score, lengths, Gamma shape)."""
+        lens = np.array(lengths, np.float64, copy=True)
+        out, al = C.c_double(), C.c_double()
+        rc = lib().or_visit_optimise(self._p, self.n, np.ascontiguousarray(edges, np.int32).reshape(-1), lens,
+                                     C.byref(out), C.byref(al))
+        if rc:
+            raise ValueError("not a binary tree")
+        return out.value, lens, al.value
 
     def set_prior(self, rate: float):
         """MAP objective with an Exponential(rate) prior on every branch length (0 = ML)."""

@@ -58,6 +58,8 @@ typedef struct {
     int newton_maxit, full_max_sweeps, prop_max_sweeps;
     int prop_mode;   /* 0 = five branches around the NNI edge, 1 = central only, 2 = every branch */
     double prior_rate; /* 0: maximum likelihood; > 0: MAP under an Exponential(prior_rate) prior per branch */
+    double alpha;      /* Gamma shape of the model (the rates above are its category means) */
+    int reopt_alpha;   /* 1: every visit re-optimises the Gamma shape with the branch lengths */
     /* counters (diagnostics for tests) */
     long n_newton_evals, n_newton_nonconv;
 } or_problem;
@@ -221,6 +223,7 @@ or_problem *or_problem_new(int n, int P, int C, const uint8_t *tips, const doubl
     memcpy(pb->tips, tips, (size_t)n * P);
     memcpy(pb->w, w, sizeof(double) * P);
     for (int i = 0; i < 4; ++i) pb->pi[i] = freqs[i];
+    pb->alpha = alpha;
     if (or_gtr_q(exch, freqs, pb->Q) || or_gamma_rates(alpha, C, pb->rates)) {
         free(pb->tips); free(pb->w); free(pb);
         return NULL;
@@ -244,6 +247,12 @@ void or_problem_free(or_problem *pb)
  * topology's score is lnL + sum over its 2n-3 branches of (ln rate - rate t);
  * rate 0 restores maximum likelihood (score = lnL). */
 void or_problem_prior(or_problem *pb, double rate) { pb->prior_rate = rate; }
+
+/* Model re-optimisation ("Phylogenetic Topographer": optimising the shape of
+ * the Gamma rate heterogeneity for each visited topology): on = 1 makes every
+ * visit (full optimisation of a start or a kept neighbour) optimise the shape
+ * jointly with the branch lengths; proposals keep the model's shape. */
+void or_problem_reopt(or_problem *pb, int on) { pb->reopt_alpha = on; }
 
 void or_problem_settings(or_problem *pb, double tmin, double tmax, double newton_tol, int newton_maxit,
                          double sweep_tol, int full_max_sweeps, int prop_max_sweeps, int prop_mode)
@@ -578,6 +587,71 @@ static double full_optimise(or_problem *pb, or_tree *t, int *sweeps_out)
     return tree_score(pb, t);
 }
 
+/* READING (the paper gives no procedure): the shape is searched on u = ln alpha
+ * in [ln 0.02, ln 100] by golden-section search with a fixed 40 steps (final
+ * bracket ~4e-8 wide; its midpoint is the new shape), at fixed branch
+ * lengths, maximising lnL; then the lengths are fully re-optimised at the new
+ * shape.  Shape search and length optimisation alternate until the shape
+ * moves by at most 1e-6 in ln alpha (at most 16 alternations).  The visit's
+ * score is the objective at the final shape and lengths. */
+#define OR_ALPHA_LO 0.02
+#define OR_ALPHA_HI 100.0
+#define OR_GOLDEN_STEPS 40
+
+static void set_alpha(or_problem *pb, double alpha)
+{
+    or_gamma_rates(alpha, pb->C, pb->rates);
+}
+
+static double golden_alpha(or_problem *pb, const or_tree *t)
+{
+    const double g = 0.5 * (sqrt(5.0) - 1.0);
+    double a = log(OR_ALPHA_LO), b = log(OR_ALPHA_HI);
+    double x1 = b - g * (b - a), x2 = a + g * (b - a);
+    set_alpha(pb, exp(x1));
+    double f1 = tree_lnl(pb, t);
+    set_alpha(pb, exp(x2));
+    double f2 = tree_lnl(pb, t);
+    for (int it = 0; it < OR_GOLDEN_STEPS; ++it) {
+        if (f1 >= f2) {
+            b = x2; x2 = x1; f2 = f1;
+            x1 = b - g * (b - a);
+            set_alpha(pb, exp(x1));
+            f1 = tree_lnl(pb, t);
+        } else {
+            a = x1; x1 = x2; f1 = f2;
+            x2 = a + g * (b - a);
+            set_alpha(pb, exp(x2));
+            f2 = tree_lnl(pb, t);
+        }
+    }
+    return exp(0.5 * (a + b));
+}
+
+/* Full optimisation of lengths and (C > 1 and reopt_alpha) the Gamma shape.
+ * alpha_out (may be NULL) receives the final shape; the problem's rates are
+ * the model's again on return. */
+static double visit_optimise(or_problem *pb, or_tree *t, double *alpha_out)
+{
+    double alpha = pb->alpha;
+    if (!pb->reopt_alpha || pb->C == 1) {
+        if (alpha_out) *alpha_out = alpha;
+        return full_optimise(pb, t, NULL);
+    }
+    double f = full_optimise(pb, t, NULL);
+    for (int alt = 0; alt < 16; ++alt) {
+        double a2 = golden_alpha(pb, t);
+        set_alpha(pb, a2);
+        f = full_optimise(pb, t, NULL);
+        int done = fabs(log(a2) - log(alpha)) <= 1e-6;
+        alpha = a2;
+        if (done) break;
+    }
+    set_alpha(pb, pb->alpha);
+    if (alpha_out) *alpha_out = alpha;
+    return f;
+}
+
 /* ------------------------------------------------------------------------- */
 /* Split-set key (replaces the paper's sorted-Newick key).                      */
 /* ------------------------------------------------------------------------- */
@@ -805,6 +879,16 @@ int or_full_optimise(or_problem *pb, int n, const int32_t *edges, double *length
     return 0;
 }
 
+/* A visit: full optimisation, with the Gamma shape too when reopt_alpha is on. */
+int or_visit_optimise(or_problem *pb, int n, const int32_t *edges, double *lengths, double *lnl, double *alpha)
+{
+    or_tree t;
+    if (n != pb->n || tree_from_edges(n, edges, lengths, &t)) return -1;
+    *lnl = visit_optimise(pb, &t, alpha);
+    for (int e = 0; e < 2 * n - 3; ++e) lengths[e] = tree_len(&t, edges[2 * e], edges[2 * e + 1]);
+    return 0;
+}
+
 int or_tree_key(int n, const int32_t *edges, uint64_t key[2])
 {
     or_tree t;
@@ -995,7 +1079,7 @@ or_search *or_search_new(or_problem *pb, int n_start, const int32_t *edges, cons
         uint64_t k[2];
         tree_key(&ts[i], k);
         if (set_find(&s->vis, k)) continue;
-        l[i] = full_optimise(pb, &ts[i], NULL);
+        l[i] = visit_optimise(pb, &ts[i], NULL);
         or_entry *e = set_insert(&s->vis, k);
         entry_fill(e, &ts[i], OR_BAD, l[i], NAN, 0);
         keep[i] = 1;
@@ -1089,7 +1173,7 @@ int or_search_round(or_problem *pb, or_search *s)
     double lmax = lmax0;
     double *fl = (double *)malloc(sizeof(double) * (size_t)(nk > 0 ? nk : 1));
     for (int i = 0; i < nk; ++i) {
-        fl[i] = full_optimise(pb, &kept[i], NULL);
+        fl[i] = visit_optimise(pb, &kept[i], NULL);
         if (fl[i] > lmax) lmax = fl[i];
     }
     s->lmax = lmax;
