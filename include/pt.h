@@ -90,6 +90,15 @@ typedef struct {
                                * Topographer", its optional exponential branch-length prior): every length
                                * has an Exponential(rate) prior, each Newton step maximises lnL - rate t,
                                * and every reported lnL is the score lnL + (2n-3) ln rate - rate sum(t) */
+    int reopt_alpha;      /* 1: every visit (full optimisation of a start, a kept neighbour or a FULL
+                           * pt_score_topologies tree) also re-optimises the Gamma shape of its tree
+                           * ("Phylogenetic Topographer": optimising the model for each visited
+                           * topology): golden-section search on ln alpha in [ln 0.02, ln 100], 40 steps,
+                           * at fixed lengths, alternating with full length optimisation until the shape
+                           * moves by <= 1e-6 in ln alpha (16 alternations at most).  A proposal uses its
+                           * parent's shape (recorded in the visited table by the parent's visit).  Graph
+                           * rounds and the allocation-free entry point reject it.  0 (default): the
+                           * model's shape. */
 } pt_config;
 
 /* Fills cfg with the defaults: device 0, mixed precision, 2^22 slots, five
@@ -272,6 +281,12 @@ pt_status pt_visited(pt_ctx *ctx, int aln_id, size_t cap, pt_key *keys, uint8_t 
  * pattern as pt_visited (all-NULL outputs: count only). */
 pt_status pt_split_frequencies(pt_ctx *ctx, int aln_id, int n_trees, const int32_t *edges, const double *lnl,
                                size_t cap, uint64_t *splits, double *freq, int64_t *trees, size_t *count);
+
+/* Gamma shapes of the trees output by the last pt_score_topologies (FULL:
+ * input order), pt_begin, pt_expand_frontier(_dev) or batched round on an
+ * alignment (next-frontier order); the model's shape unless reopt_alpha is on.
+ * *count = number of trees; PT_ERR_BUFFER_TOO_SMALL when cap is smaller. */
+pt_status pt_last_alphas(pt_ctx *ctx, int aln_id, int cap, double *alphas, int *count);
 
 /* Clears (allocating on first use) the visited table and round counter of
  * an alignment. */

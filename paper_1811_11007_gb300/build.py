@@ -26,7 +26,8 @@ def _stale(obj: str, deps: list[str]) -> bool:
 
 def build(force: bool = False, verbose: bool = False) -> str:
     os.makedirs(OUT_DIR, exist_ok=True)
-    headers = [os.path.join(CSRC, "pt_internal.h"), os.path.join(ROOT, "include", "pt.h")]
+    headers = [os.path.join(CSRC, "pt_internal.h"), os.path.join(CSRC, "pt_gamma.h"),
+               os.path.join(ROOT, "include", "pt.h")]
     procs, objs = [], []
     for src in SOURCES:
         path = os.path.join(CSRC, src)

@@ -3,6 +3,7 @@
 // kernels of pt_kernels.cu; this file validates, sizes, launches and copies.
 #include "pt.h"
 #include "pt_internal.h"
+#include "pt_gamma.h"
 
 #include <cuda_runtime.h>
 
@@ -36,6 +37,8 @@ struct AlnState {
     int log2 = 0;
     int round = 0;
     float* tip_sum = nullptr;  // [n][16] leaf summaries for the warm-start features
+    double alpha = 1.0;        // Gamma shape of the model
+    std::vector<double> last_alphas;  // shapes of the last call's output trees (shape re-optimisation)
 };
 
 struct GraphRound;
@@ -251,74 +254,6 @@ struct Span {
 };
 
 // ---------------------------------------------------------------- model set-up (host)
-// Regularised lower incomplete gamma P(a, x): series for x < a + 1, else
-// 1 - Q(a, x) with Q as a continued fraction (modified Lentz).
-double inc_gamma_p(double a, double x) {
-    if (x <= 0) return 0.0;
-    const double lead = std::exp(a * std::log(x) - x - std::lgamma(a));
-    if (x < a + 1.0) {
-        double sum = 1.0 / a, term = sum;
-        for (int k = 1; k < 10000; ++k) {
-            term *= x / (a + k);
-            sum += term;
-            if (term < sum * 1e-17) break;
-        }
-        return sum * lead;
-    }
-    double f = x + 1.0 - a;
-    if (std::fabs(f) < 1e-300) f = 1e-300;
-    double Cc = f, D = 0.0;
-    for (int k = 1; k < 10000; ++k) {
-        double an = k * (a - k), bn = x + 2.0 * k + 1.0 - a;
-        D = bn + an * D;
-        if (std::fabs(D) < 1e-300) D = 1e-300;
-        Cc = bn + an / Cc;
-        if (std::fabs(Cc) < 1e-300) Cc = 1e-300;
-        D = 1.0 / D;
-        double delta = Cc * D;
-        f *= delta;
-        if (std::fabs(delta - 1.0) < 1e-16) break;
-    }
-    return 1.0 - lead / f;
-}
-
-// y with P(a, y) = q: Newton on P (derivative = Gamma(a) density), kept in a
-// shrinking bracket, bisection when a step leaves it.
-double inc_gamma_inv(double a, double q) {
-    double lo = 0.0, hi = std::max(1.0, a);
-    while (inc_gamma_p(a, hi) < q) hi *= 2.0;
-    double y = 0.5 * (lo + hi);
-    for (int it = 0; it < 200; ++it) {
-        double f = inc_gamma_p(a, y) - q;
-        if (f < 0) lo = y; else hi = y;
-        double dens = std::exp((a - 1.0) * std::log(y) - y - std::lgamma(a));
-        double yn = y - f / dens;
-        if (!(yn > lo && yn < hi)) yn = 0.5 * (lo + hi);
-        if (std::fabs(yn - y) <= 1e-15 * y || hi - lo <= 1e-300) { y = yn; break; }
-        y = yn;
-    }
-    return y;
-}
-
-// Mean rate of each of C equal-probability categories of Gamma(alpha, rate alpha).
-bool discrete_gamma(double alpha, int C, double* rates) {
-    if (C == 1) { rates[0] = 1.0; return true; }
-    if (!(alpha > 0.0) || C < 1 || C > kMaxCat) return false;
-    double prev = 0.0, tot = 0.0;
-    for (int k = 0; k < C; ++k) {
-        double cum = 1.0;
-        if (k + 1 < C) {
-            double b = inc_gamma_inv(alpha, (double)(k + 1) / C) / alpha;  // category bound on the rate scale
-            cum = inc_gamma_p(alpha + 1.0, alpha * b);
-        }
-        rates[k] = (cum - prev) * C;
-        prev = cum;
-        tot += rates[k];
-    }
-    for (int k = 0; k < C; ++k) rates[k] *= C / tot;
-    return true;
-}
-
 // Symmetric 4x4 eigen-decomposition by cyclic Jacobi rotations.
 void jacobi4(double A[16], double V[16], double lam[4]) {
     for (int i = 0; i < 16; ++i) V[i] = (i % 5 == 0) ? 1.0 : 0.0;
@@ -528,12 +463,13 @@ struct FullJob {
     int first, count;
     double* lnl_d;
     int max_sweeps;
+    const double* rates = nullptr;  // per-tree category rates [count][kMaxCat], or null: the model's
 };
 
 // Runs full-optimisation jobs in one persistent launch over all of them.  The
 // partials live in per-CTA slabs (a CTA reuses its slab tree after tree), so
 // memory grows with the grid, not with the number of trees.
-void run_full_jobs(Ctx& c, std::vector<FullJob> jobs) {
+void run_full_jobs(Ctx& c, std::vector<FullJob> jobs, bool allow_tune = true) {
     const int prec = c.cfg.precision;
     jobs.erase(std::remove_if(jobs.begin(), jobs.end(), [](const FullJob& j) { return j.count <= 0; }), jobs.end());
     if (jobs.empty()) return;
@@ -557,6 +493,7 @@ void run_full_jobs(Ctx& c, std::vector<FullJob> jobs) {
             gp.g = ClvGroup{nullptr, nullptr, 0, 0};
             gp.max_sweeps = j.max_sweeps;
             gp.lnl_out = j.lnl_d;
+            gp.rates = j.rates;
             groups.push_back(gp);
             counts.push_back(j.count);
             maxN = std::max(maxN, a.n);
@@ -601,7 +538,7 @@ void run_full_jobs(Ctx& c, std::vector<FullJob> jobs) {
         // tune on launches with enough trees to fill the GPU, and again when a
         // launch is much larger than the one the bucket was tuned on
         const bool big = total >= 2 * c.sm_count && (!have || total >= 4 * it->second.full_items);
-        if (c.autotune && big) {
+        if (allow_tune && c.autotune && big) {
             // the kernel writes the optimised lengths back: trials start from a saved copy
             std::vector<std::pair<double*, size_t>> ranges;
             size_t nlen = 0;
@@ -649,6 +586,102 @@ void run_full_jobs(Ctx& c, std::vector<FullJob> jobs) {
     }
 }
 
+// Visits (the full optimisation of kept trees, starts and FULL scoring).  With
+// reopt_alpha and C > 1 every tree's Gamma shape is re-optimised with its
+// lengths: a golden-section search on ln alpha over [ln 0.02, ln 100] (40
+// steps, every tree in lockstep, each step one fixed-length lnL launch over
+// all trees with per-tree category rates) alternates with full length
+// optimisation at the new shapes, until no shape moves by more than 1e-6 in
+// ln alpha (16 alternations at most; a tree that has converged keeps its
+// shape).  alphas (host, may be null) receives the final shapes per job.
+void visit_jobs(Ctx& c, std::vector<FullJob> jobs, std::vector<std::vector<double>>* alphas = nullptr) {
+    const bool reopt = c.cfg.reopt_alpha && !jobs.empty() && jobs[0].a->M.C > 1;
+    if (alphas) {
+        alphas->assign(jobs.size(), {});
+        for (size_t j = 0; j < jobs.size(); ++j) (*alphas)[j].assign(std::max(jobs[j].count, 0), jobs[j].a->alpha);
+    }
+    if (!reopt) {
+        run_full_jobs(c, jobs);
+        return;
+    }
+    const int C = jobs[0].a->M.C;
+    std::vector<size_t> off(jobs.size() + 1, 0);
+    for (size_t j = 0; j < jobs.size(); ++j) off[j + 1] = off[j] + std::max(jobs[j].count, 0);
+    const size_t T = off.back();
+    if (T == 0) return;
+    double* d_alpha = buf<double>(c, "shape.alpha", T);
+    double* d_rates = buf<double>(c, "shape.rates", T * kMaxCat);
+    double* d_f = buf<double>(c, "shape.f", T);
+    std::vector<double> h_alpha(T), cur(T), f1(T), f2(T), ga(T), gb(T), x1(T), x2(T), hf(T);
+    for (size_t j = 0; j < jobs.size(); ++j)
+        for (size_t t = off[j]; t < off[j + 1]; ++t) cur[t] = jobs[j].a->alpha;
+    std::vector<FullJob> full = jobs, fixed = jobs;
+    for (size_t j = 0; j < jobs.size(); ++j) {
+        full[j].rates = fixed[j].rates = d_rates + off[j] * kMaxCat;
+        fixed[j].max_sweeps = 0;
+        fixed[j].lnl_d = d_f + off[j];
+    }
+    auto set_rates = [&](const std::vector<double>& al) {
+        ck(c, cudaMemcpyAsync(d_alpha, al.data(), 8 * T, cudaMemcpyHostToDevice, c.stream), "shapes");
+        launch_gamma_rates(c.stream, (int)T, C, d_alpha, d_rates);
+    };
+    auto eval = [&](const std::vector<double>& u, std::vector<double>& f) {  // lnL at shapes exp(u), fixed lengths
+        for (size_t t = 0; t < T; ++t) h_alpha[t] = std::exp(u[t]);
+        set_rates(h_alpha);
+        run_full_jobs(c, fixed, false);
+        ck(c, cudaMemcpyAsync(hf.data(), d_f, 8 * T, cudaMemcpyDeviceToHost, c.stream), "lnL");
+        ck(c, cudaStreamSynchronize(c.stream), "sync");
+        f = hf;
+    };
+    set_rates(cur);
+    run_full_jobs(c, full);
+    std::vector<char> done(T, 0);
+    const double g = 0.5 * (std::sqrt(5.0) - 1.0), lo = std::log(0.02), hi = std::log(100.0);
+    for (int alt = 0; alt < 16; ++alt) {
+        for (size_t t = 0; t < T; ++t) {
+            ga[t] = lo;
+            gb[t] = hi;
+            x1[t] = hi - g * (hi - lo);
+            x2[t] = lo + g * (hi - lo);
+        }
+        eval(x1, f1);
+        eval(x2, f2);
+        std::vector<double> probe(T);
+        std::vector<char> left(T);
+        for (int it = 0; it < 40; ++it) {
+            for (size_t t = 0; t < T; ++t) {
+                left[t] = f1[t] >= f2[t];
+                if (left[t]) {
+                    gb[t] = x2[t]; x2[t] = x1[t]; f2[t] = f1[t];
+                    x1[t] = gb[t] - g * (gb[t] - ga[t]);
+                    probe[t] = x1[t];
+                } else {
+                    ga[t] = x1[t]; x1[t] = x2[t]; f1[t] = f2[t];
+                    x2[t] = ga[t] + g * (gb[t] - ga[t]);
+                    probe[t] = x2[t];
+                }
+            }
+            std::vector<double> fp;
+            eval(probe, fp);
+            for (size_t t = 0; t < T; ++t) (left[t] ? f1[t] : f2[t]) = fp[t];
+        }
+        bool all = true;
+        std::vector<double> next(T);
+        for (size_t t = 0; t < T; ++t) {
+            next[t] = done[t] ? cur[t] : std::exp(0.5 * (ga[t] + gb[t]));
+            if (!done[t] && std::fabs(std::log(next[t]) - std::log(cur[t])) <= 1e-6) done[t] = 1;
+            all = all && done[t];
+        }
+        cur = next;
+        set_rates(cur);
+        run_full_jobs(c, full);
+        if (all) break;
+    }
+    if (alphas)
+        for (size_t j = 0; j < jobs.size(); ++j)
+            for (size_t t = off[j]; t < off[j + 1]; ++t) (*alphas)[j][t - off[j]] = cur[t];
+}
+
 // Canonicalise + score `count` trees already on the device.  FULL mode runs
 // the full optimisation; lnl_d [count] receives lnL; ts holds the result.
 void score_core(Ctx& c, AlnState& a, int count, const int32_t* edges_d, const double* lens_d, int mode,
@@ -656,7 +689,14 @@ void score_core(Ctx& c, AlnState& a, int count, const int32_t* edges_d, const do
     ts = treeset(c, tsname, a.n, count, true);
     launch_canon(c.stream, a.n, count, edges_d, lens_d, ts, c.d_err);
     check_flags(c);
-    run_full_jobs(c, {FullJob{&a, ts, 0, count, lnl_d, mode == PT_SCORE_FULL ? c.cfg.full_max_sweeps : 0}});
+    if (mode == PT_SCORE_FULL) {  // a visit (with the Gamma shape too when enabled)
+        std::vector<std::vector<double>> al;
+        visit_jobs(c, {FullJob{&a, ts, 0, count, lnl_d, c.cfg.full_max_sweeps}}, &al);
+        a.last_alphas = al.empty() ? std::vector<double>() : al[0];
+    } else {
+        run_full_jobs(c, {FullJob{&a, ts, 0, count, lnl_d, 0}});
+        a.last_alphas.assign(std::max(count, 0), a.alpha);
+    }
 }
 
 // The GOOD set of a begin/expand: indices into a tree set.
@@ -692,7 +732,12 @@ void begin_core(Ctx& c, AlnState& a, int ns, const int32_t* edges_d, const doubl
     ck(c, cudaMemcpyAsync(c.d_lmax, &ninf, 8, cudaMemcpyHostToDevice, c.stream), "lmax init");
     launch_lmax(c.stream, hcount(ns), lnl, winner, c.d_lmax);
     int32_t* good = buf<int32_t>(c, "kp.good", ns);
-    launch_finalize_trees(c.stream, a.table, hcount(ns), winner, lnl, c.d_lmax, thr, hround(0), good, c.d_stats);
+    double* sal = nullptr;
+    if (c.cfg.reopt_alpha && (int)a.last_alphas.size() == ns) {  // record the visits' shapes in the table
+        sal = buf<double>(c, "kp.alpha", ns);
+        ck(c, cudaMemcpyAsync(sal, a.last_alphas.data(), 8 * (size_t)ns, cudaMemcpyHostToDevice, c.stream), "shapes");
+    }
+    launch_finalize_trees(c.stream, a.table, hcount(ns), winner, lnl, c.d_lmax, thr, hround(0), good, c.d_stats, sal);
     // dedup starts: a start that lost its key is not GOOD
     std::vector<int32_t> w(ns), gd(ns);
     ck(c, cudaMemcpyAsync(w.data(), winner, 4 * (size_t)ns, cudaMemcpyDeviceToHost, c.stream), "read winners");
@@ -701,6 +746,11 @@ void begin_core(Ctx& c, AlnState& a, int ns, const int32_t* edges_d, const doubl
     check_flags(c);
     std::vector<int32_t> idx;
     for (int i = 0; i < ns; ++i) if (w[i] >= 0 && gd[i]) idx.push_back(i);
+    {  // shapes of the GOOD starts, in output order
+        std::vector<double> all = a.last_alphas;
+        a.last_alphas.clear();
+        for (int i : idx) a.last_alphas.push_back(i < (int)all.size() ? all[i] : a.alpha);
+    }
     out.ts = ts;
     out.idx = buf<int32_t>(c, "kp.idx", idx.size() + 1);
     if (!idx.empty())
@@ -733,6 +783,7 @@ void expand_batch(Ctx& c, const std::vector<RoundIn>& ins, std::vector<RoundOut>
         uint64_t* nkey;
         int32_t *cinfo, *cslot, *flag, *pos, *kpos, *kidx, *kslot, *good, *gpos, *gidx;
         double *klnl, *lmax;
+        double* frates = nullptr;  // frontier trees' category rates (shape re-optimisation)
         std::vector<int32_t> tpos;
     };
     std::vector<AR> ar(na);
@@ -761,6 +812,13 @@ void expand_batch(Ctx& c, const std::vector<RoundIn>& ins, std::vector<RoundOut>
         r.lmax = d_lmax + k;
         r.fr = treeset(c, pre + "fr", a.n, std::max(r.F, 1), false);
         launch_canon(c.stream, a.n, r.F, ins[k].edges_d, ins[k].lens_d, r.fr, c.d_err);
+        if (c.cfg.reopt_alpha && a.M.C > 1 && r.F > 0) {
+            // proposals use their parent's shape: the one its visit recorded in the table
+            double* fal = buf<double>(c, pre + "fr.alpha", r.F);
+            r.frates = buf<double>(c, pre + "fr.rates", (size_t)r.F * kMaxCat);
+            launch_frontier_alpha(c.stream, r.fr, r.F, a.table, a.log2, a.alpha, fal);
+            launch_gamma_rates(c.stream, r.F, a.M.C, fal, r.frates);
+        }
         int32_t* fwin = buf<int32_t>(c, pre + "fr.win", r.F);
         launch_insert_trees(c.stream, a.table, a.log2, hcount(r.F), r.fr, nullptr, nullptr, hround(r.round - 1), fwin,
                             c.d_err);
@@ -897,7 +955,7 @@ void expand_batch(Ctx& c, const std::vector<RoundIn>& ins, std::vector<RoundOut>
             void* pm = wave + off;
             off += (pmat_bytes(prec, C, a.n, ch.cnt) + 255) & ~size_t(255);
             launch_partials(c.stream, prec, a.M, aln_dev(a), r.fr, ch.f0, hcount(ch.cnt), g, true, threads_for(c, a.P),
-                            pm);
+                            pm, r.frates);
             ck(c, cudaGetLastError(), "partials launch");
             const int gi0 = r.ibase + ch.i0, cnt_items = ch.i1 - ch.i0;
             const double* init = nullptr;
@@ -937,6 +995,7 @@ void expand_batch(Ctx& c, const std::vector<RoundIn>& ins, std::vector<RoundOut>
             gp.len5_out = len5 + (size_t)5 * gi0;
             gp.kept = kept + gi0;
             gp.init = init;
+            gp.rates = r.frates;
             groups.push_back(gp);
             counts.push_back(cnt_items);
             maxP = std::max(maxP, a.P);
@@ -1015,6 +1074,7 @@ void expand_batch(Ctx& c, const std::vector<RoundIn>& ins, std::vector<RoundOut>
     // ---- C. visit the kept neighbours
     Span sp4(c, 4);
     std::vector<FullJob> jobs;
+    std::vector<int> job_of(na, -1);
     int Ktot = 0;
     for (int k = 0; k < na; ++k) {
         AR& r = ar[k];
@@ -1039,12 +1099,14 @@ void expand_batch(Ctx& c, const std::vector<RoundIn>& ins, std::vector<RoundOut>
         r.kp = treeset(c, pre + "kp", r.n, std::max(r.K, 1), true);
         if (r.K > 0) {
             launch_canon(c.stream, r.n, r.K, kedges, klens, r.kp, c.d_err);
+            job_of[k] = (int)jobs.size();
             jobs.push_back(FullJob{r.a, r.kp, 0, r.K, r.klnl, c.cfg.full_max_sweeps});
         }
     }
     hc[kStKept] = Ktot;
     check_flags(c);
-    if (!jobs.empty()) run_full_jobs(c, jobs);
+    std::vector<std::vector<double>> shapes;
+    if (!jobs.empty()) visit_jobs(c, jobs, &shapes);
     // ---- lmax, GOOD / BAD, next frontiers
     outs.assign(na, RoundOut());
     for (int k = 0; k < na; ++k) {
@@ -1052,8 +1114,14 @@ void expand_batch(Ctx& c, const std::vector<RoundIn>& ins, std::vector<RoundOut>
         const std::string pre = "b" + std::to_string(k) + ".";
         launch_lmax(c.stream, hcount(r.K), r.klnl, nullptr, r.lmax);
         r.good = buf<int32_t>(c, pre + "kp.good", r.K + 1);
+        double* kal = nullptr;
+        if (c.cfg.reopt_alpha && job_of[k] >= 0) {  // record the visits' shapes in the table
+            kal = buf<double>(c, pre + "kp.alpha", r.K);
+            ck(c, cudaMemcpyAsync(kal, shapes[job_of[k]].data(), 8 * (size_t)r.K, cudaMemcpyHostToDevice, c.stream),
+               "shapes");
+        }
         launch_finalize_trees(c.stream, r.a->table, hcount(r.K), r.kslot, r.klnl, r.lmax, ins[k].thr, hround(r.round), r.good,
-                              c.d_stats);
+                              c.d_stats, kal);
         r.gpos = buf<int32_t>(c, pre + "kp.gpos", r.K + 1);
         r.G = scan_count(c, r.good, r.gpos, r.K);
         r.gidx = buf<int32_t>(c, pre + "kp.idx", r.G + 1);
@@ -1062,6 +1130,14 @@ void expand_batch(Ctx& c, const std::vector<RoundIn>& ins, std::vector<RoundOut>
         outs[k].idx = r.gidx;
         outs[k].lnl = r.klnl;
         outs[k].count = r.G;
+        // shapes of the next frontier's trees, in output order
+        r.a->last_alphas.assign(r.G, r.a->alpha);
+        if (c.cfg.reopt_alpha && job_of[k] >= 0 && r.G > 0) {
+            std::vector<int32_t> gi(r.G);
+            ck(c, cudaMemcpyAsync(gi.data(), r.gidx, 4 * (size_t)r.G, cudaMemcpyDeviceToHost, c.stream), "idx");
+            ck(c, cudaStreamSynchronize(c.stream), "sync");
+            for (int g = 0; g < r.G; ++g) r.a->last_alphas[g] = shapes[job_of[k]][gi[g]];
+        }
     }
     sp4.end();
     total.end();
@@ -1336,6 +1412,8 @@ GraphRound* graph_create(Ctx& c, const std::vector<int>& ids, const std::vector<
     }
     if (c.cfg.propose_mode == PT_PROPOSE_FULL)
         fail(c, PT_ERR_INVALID_ARG, "graph rounds take five-branch or central proposals (not full radius)");
+    if (c.cfg.reopt_alpha)
+        fail(c, PT_ERR_INVALID_ARG, "graph rounds keep the model's Gamma shape (reopt_alpha off)");
     g.mlp = c.mlp_on && c.mlp_ready;
     // CTA sizes: the autotuned ones of this problem bucket when known
     const std::string key = tune_key(prec, C, maxN, maxP);
@@ -1445,6 +1523,7 @@ GraphRound* graph_create(Ctx& c, const std::vector<int>& ids, const std::vector<
         p.len5_out = x.len5;
         p.kept = x.kept;
         p.init = g.mlp ? x.init : nullptr;
+        p.rates = nullptr;
         FullGroup& f = fg[k];
         f.M = A.M;
         f.A = aln_dev(A);
@@ -1453,6 +1532,7 @@ GraphRound* graph_create(Ctx& c, const std::vector<int>& ids, const std::vector<
         f.g = ClvGroup{nullptr, nullptr, 0, 0};
         f.max_sweeps = c.cfg.full_max_sweeps;
         f.lnl_out = x.klnl;
+        f.rates = nullptr;
         if (g.mlp && !A.tip_sum) {
             ck(c, cudaMalloc(&A.tip_sum, sizeof(float) * 16 * A.n), "alloc tip summaries");
             launch_tip_summary(c.stream, aln_dev(A), C, A.tip_sum);
@@ -1573,6 +1653,7 @@ void pt_config_default(pt_config* cfg) {
     cfg->threads = 0;
     cfg->mem_budget = 0;
     cfg->branch_prior_rate = 0.0;
+    cfg->reopt_alpha = 0;
 }
 
 pt_status pt_create(pt_ctx** out, const pt_config* cfg) {
@@ -1585,6 +1666,7 @@ pt_status pt_create(pt_ctx** out, const pt_config* cfg) {
         !(c.cfg.tmin > 0) || !(c.cfg.tmax > c.cfg.tmin) || c.cfg.newton_maxit < 1 || c.cfg.full_max_sweeps < 0 ||
         c.cfg.prop_max_sweeps < 1 || c.cfg.propose_mode < PT_PROPOSE_FIVE || c.cfg.propose_mode > PT_PROPOSE_FULL ||
         !(c.cfg.branch_prior_rate >= 0) || !std::isfinite(c.cfg.branch_prior_rate) ||
+        c.cfg.reopt_alpha < 0 || c.cfg.reopt_alpha > 1 ||
         (c.cfg.threads != 0 && (c.cfg.threads < 32 || c.cfg.threads > 512 || c.cfg.threads % 32))) {
         delete ctx;
         return PT_ERR_INVALID_ARG;
@@ -1698,6 +1780,7 @@ pt_status pt_set_model(pt_ctx* ctx, int aln_id, const double exch[6], const doub
         Model M;
         if (!build_model(exch, freqs, alpha, n_cats, M, why)) fail(c, PT_ERR_INVALID_ARG, "%s", why.c_str());
         a.M = M;
+        a.alpha = alpha;
         a.has_model = true;
         if (a.tip_sum) { cudaFree(a.tip_sum); a.tip_sum = nullptr; }
     });
@@ -2078,6 +2161,16 @@ pt_status pt_split_frequencies(pt_ctx* ctx, int aln_id, int n_trees, const int32
         }
         const bool query = !splits && !freq && !trees;
         if (!query && cap < (size_t)tot) fail(c, PT_ERR_BUFFER_TOO_SMALL, "%d distinct splits", tot);
+    });
+}
+
+pt_status pt_last_alphas(pt_ctx* ctx, int aln_id, int cap, double* alphas, int* count) {
+    return guarded(ctx, [&](Ctx& c) {
+        AlnState& a = aln_of(c, aln_id, false);
+        if (!count || (cap > 0 && !alphas)) fail(c, PT_ERR_INVALID_ARG, "bad arguments");
+        *count = (int)a.last_alphas.size();
+        for (int i = 0; i < std::min(cap, *count); ++i) alphas[i] = a.last_alphas[i];
+        if (alphas && cap < *count) fail(c, PT_ERR_BUFFER_TOO_SMALL, "%d shapes", *count);
     });
 }
 

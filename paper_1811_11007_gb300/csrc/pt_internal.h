@@ -73,12 +73,14 @@ struct TreeSet {
 };
 constexpr int kUpd = 1 << 16;
 
-// Visited-table slot (48 bytes, 16-byte aligned for the 128-bit CAS).
+// Visited-table slot (64 bytes, 16-byte aligned for the 128-bit CAS).
 struct Slot {
     unsigned long long klo, khi;
     unsigned long long tag;   // round << 48 | (proposer rank during a round, status after)
     unsigned long long ahi, alo; // arbitration: smallest parent key of this round's proposers
     double lnl;
+    double alpha;             // Gamma shape found by the visit (shape re-optimisation), else NaN
+    double pad;
 };
 constexpr unsigned long long kTagEmpty = ~0ull;
 
@@ -164,8 +166,12 @@ void launch_make_items(cudaStream_t s, int ncand, const int32_t* flag, const int
 void launch_compact_idx(cudaStream_t s, int N, const int32_t* flag, const int32_t* pos, int32_t* idx);
 void launch_insert_trees(cudaStream_t s, Slot* tab, int log2, DCount count, TreeSet ts, const double* lnl,
                          const int32_t* status, DRound round, int32_t* winner, int32_t* err);
+// alpha (may be null) is recorded in the visited trees' slots.
 void launch_finalize_trees(cudaStream_t s, Slot* tab, DCount count, const int32_t* slot_of, const double* lnl,
-                           const double* lmax, double thr, DRound round, int32_t* good, unsigned long long* stats);
+                           const double* lmax, double thr, DRound round, int32_t* good, unsigned long long* stats,
+                           const double* alpha = nullptr);
+// alpha[f] = the shape recorded in the visited table for frontier tree f's key, else base.
+void launch_frontier_alpha(cudaStream_t s, TreeSet fr, int count, const Slot* tab, int log2, double base, double* alpha);
 void launch_lmax(cudaStream_t s, DCount count, const double* lnl, const int32_t* mask, double* lmax);
 void launch_dump(cudaStream_t s, const Slot* tab, size_t nslots, int32_t* flag);
 void launch_dump_gather(cudaStream_t s, const Slot* tab, size_t nslots, const int32_t* flag, const int32_t* pos,
@@ -194,6 +200,8 @@ struct SplitSlot {
 // count canonical trees to each of its non-trivial splits.
 void launch_split_frequencies(cudaStream_t s, TreeSet ts, int count, const double* lnl, const double* lmax,
                               SplitSlot* tab, int log2, int32_t* err);
+// rates [t][kMaxCat] = discrete Gamma category means of shape alpha[t] (C categories).
+void launch_gamma_rates(cudaStream_t s, int count, int C, const double* alpha, double* rates);
 // Dump of the occupied slots: flag pass (gather false), then gather at pos.
 void launch_split_dump(cudaStream_t s, const SplitSlot* tab, size_t nslots, int32_t* flag, const int32_t* pos,
                        uint64_t* splits, double* w, unsigned long long* trees, bool gather);
@@ -204,8 +212,9 @@ void launch_lengths_to_input(cudaStream_t s, int n, int count, TreeSet ts, doubl
 // Partials of a group of trees (all D_v, and U_v when with_up).
 // pm: P-matrix buffer of pmat_bytes(prec, C, n, count) bytes; launch_propose reads it for the same group.
 size_t pmat_bytes(int prec, int C, int n, int count);
+// rates (may be null: the model's): per-tree category rates [tree][kMaxCat], indexed like ts.
 void launch_partials(cudaStream_t s, int prec, const Model& M, Aln A, TreeSet ts, int first, DCount count, ClvGroup g,
-                     bool with_up, int threads, void* pm);
+                     bool with_up, int threads, void* pm, const double* rates = nullptr);
 // One group of a batched proposal launch: the work items of one alignment
 // whose frontier trees [first, first + count) have their partials in g.
 struct PropGroup {
@@ -224,6 +233,7 @@ struct PropGroup {
     double* len5_out;
     int32_t* kept;
     const double* init;      // learned starting lengths [count][5] or nullptr
+    const double* rates;     // per-frontier-tree category rates [tree][kMaxCat] (shape re-optimisation), or null
 };
 // One group of a batched full-optimisation launch: trees [first, first + n) of ts.
 // Partials: g (tree i of the group at g.clv + i * tree_stride), or, when the
@@ -236,6 +246,7 @@ struct FullGroup {
     ClvGroup g;
     int max_sweeps;
     double* lnl_out;
+    const double* rates;  // per-tree category rates [count][kMaxCat] (shape re-optimisation), or null: M.rates
 };
 // Batched launches over groups: gstart [ngroups + 1] is the prefix sum of the
 // groups' item (tree) counts (device); counter (device, zeroed) hands out the

@@ -13,6 +13,7 @@
 // d2 lnL/dt2 (FP64) and the per-sweep lnL, so every pass over sites runs
 // without barriers.
 #include "pt_internal.h"
+#include "pt_gamma.h"
 
 #include <cuda_runtime.h>
 
@@ -303,6 +304,7 @@ __global__ void k_table_init(Slot* tab, size_t nslots) {
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < nslots; i += (size_t)gridDim.x * blockDim.x) {
         tab[i].klo = 0; tab[i].khi = 0; tab[i].tag = kTagEmpty; tab[i].ahi = kTagEmpty; tab[i].alo = kTagEmpty;
         tab[i].lnl = __longlong_as_double(0x7ff8000000000000ll);
+        tab[i].alpha = __longlong_as_double(0x7ff8000000000000ll);
     }
 }
 
@@ -433,7 +435,8 @@ __global__ void k_lmax(DCount cnt, const double* lnl, const int32_t* mask, doubl
 
 // Visit decision of fully optimised trees: GOOD iff lnl >= lmax - thr.
 __global__ void k_finalize_trees(Slot* tab, DCount cnt, const int32_t* slot_of, const double* lnl, const double* lmax,
-                                 double thr, DRound rd, int32_t* good, unsigned long long* stats) {
+                                 double thr, DRound rd, int32_t* good, unsigned long long* stats,
+                                 const double* alpha) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     const int count = dcount(cnt), round = dround(rd);
     int g = 0;
@@ -443,6 +446,7 @@ __global__ void k_finalize_trees(Slot* tab, DCount cnt, const int32_t* slot_of, 
         if (slot_of && slot_of[i] >= 0) {
             Slot* sl = &tab[slot_of[i]];
             sl->lnl = lnl[i];
+            if (alpha) sl->alpha = alpha[i];
             sl->tag = ((unsigned long long)round << 48) | (unsigned long long)(g ? 2 : 3);
         }
     }
@@ -464,6 +468,32 @@ __global__ void k_dump_gather(const Slot* tab, size_t nslots, const int32_t* fla
         status[p] = (uint8_t)(t == kTagEmpty ? 0 : (t & 0xff));
         lnl[p] = tab[i].lnl;
     }
+}
+
+// ---------------------------------------------------------------- Gamma shape
+// Shape of each frontier tree: the one its visit recorded in the visited table
+// (read-only probe of the key), else the model's.
+__global__ void k_frontier_alpha(TreeSet fr, int count, const Slot* tab, int log2, double base, double* alpha) {
+    const int f = blockIdx.x * blockDim.x + threadIdx.x;
+    if (f >= count) return;
+    const unsigned long long lo = fr.key[2 * f], hi = fr.key[2 * f + 1], mask = (1ull << log2) - 1;
+    double a = base;
+    size_t h = slot_hash(lo, hi, mask);
+    for (int p = 0; p < kMaxProbe; ++p) {
+        const Slot& sl = tab[(h + p) & mask];
+        if (sl.klo == lo && sl.khi == hi) {
+            if (sl.alpha == sl.alpha) a = sl.alpha;
+            break;
+        }
+        if (!(sl.klo | sl.khi)) break;
+    }
+    alpha[f] = a;
+}
+
+// Category rates [t][kMaxCat] of tree t's shape alpha[t] (one thread per tree).
+__global__ void k_gamma_rates(int count, int C, const double* alpha, double* rates) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < count) discrete_gamma(alpha[t], C, rates + (size_t)t * kMaxCat);
 }
 
 // ---------------------------------------------------------------- split frequencies
@@ -934,7 +964,7 @@ __device__ __forceinline__ float2 warp_sum_comp(float x) {
 }
 
 template <typename R, int C>
-__device__ __forceinline__ void init_newton_smem(const Model& M, NewtonSmem<R, C>& ns) {
+__device__ __forceinline__ void init_newton_smem(const Model& M, NewtonSmem<R, C>& ns, const double* rates) {
     for (int x = threadIdx.x; x < 64; x += blockDim.x) {
         int k = x & 3, ij = x >> 2, i = ij >> 2, j = ij & 3;
         ns.W[x] = M.isqpi[i] * M.sqpi[j] * M.R[i * 4 + k] * M.R[j * 4 + k];
@@ -954,7 +984,7 @@ __device__ __forceinline__ void init_newton_smem(const Model& M, NewtonSmem<R, C
         ns.leader = lead;
     }
     for (int q = threadIdx.x; q < 4 * C; q += blockDim.x) {
-        ns.lr[q] = M.lam[q & 3] * M.rates[q >> 2];
+        ns.lr[q] = M.lam[q & 3] * rates[q >> 2];
         ns.lrf[q] = (float)ns.lr[q];
     }
 }
@@ -1204,7 +1234,7 @@ __device__ double newton_solve(const Model& M, const Cfg& cfg, const STab<R, C>&
 // ---------------------------------------------------------------- P matrices of tree sets
 // Pm[tree][v][r][16] for v = 1..NN-1 (edge (v, up v)); row per thread.
 template <typename R>
-__global__ void k_pmats(Model M, TreeSet ts, int first, DCount cnt, R* Pm) {
+__global__ void k_pmats(Model M, TreeSet ts, int first, DCount cnt, R* Pm, const double* rates) {
     const int n = ts.n, NN = 2 * n - 2, C = M.C;
     long long total = (long long)dcount(cnt) * NN * C * 4;
     for (long long x = blockIdx.x * (long long)blockDim.x + threadIdx.x; x < total;
@@ -1216,7 +1246,8 @@ __global__ void k_pmats(Model M, TreeSet ts, int first, DCount cnt, R* Pm) {
         int v = (int)(y % NN);
         int t = (int)(y / NN);
         double l = ts.len[(size_t)(first + t) * NN + v];
-        pmat_row<R>(M, l * M.rates[r], i, Pm + ((((size_t)t * NN + v) * C + r) * 16 + i * 4));
+        const double rr = rates ? rates[(size_t)(first + t) * kMaxCat + r] : M.rates[r];
+        pmat_row<R>(M, l * rr, i, Pm + ((((size_t)t * NN + v) * C + r) * 16 + i * 4));
     }
 }
 
@@ -1349,7 +1380,8 @@ __global__ void __launch_bounds__(512) k_propose(const PropGroup* __restrict__ g
             sm.Mt[threadIdx.x] = (R)(M.sqpi[i] * M.R[i * 4 + k]);
             if (threadIdx.x < 4) sm.pi[threadIdx.x] = (R)M.pi[threadIdx.x];
         }
-        init_newton_smem<R, C>(M, sm.ns);
+        const double* rr = G.rates ? G.rates + (size_t)it.tree * kMaxCat : M.rates;  // the parent's shape
+        init_newton_smem<R, C>(M, sm.ns, rr);
         if (threadIdx.x == 0) {
             const int node[4] = {u, it.swap == 0 ? c0 : c1, sib, it.swap == 0 ? c1 : c0};
             const int brn[4] = {1, it.swap == 0 ? 3 : 4, 2, it.swap == 0 ? 4 : 3};
@@ -1388,7 +1420,7 @@ __global__ void __launch_bounds__(512) k_propose(const PropGroup* __restrict__ g
         if (G.init) {  // P matrices at the starting lengths
             for (int z = threadIdx.x; z < 5 * 4 * C; z += blockDim.x) {
                 const int b = z / (4 * C), q = z % (4 * C);
-                sm.ex5[b][q] = exp(M.lam[q & 3] * M.rates[q >> 2] * sm.T[b]);
+                sm.ex5[b][q] = exp(M.lam[q & 3] * rr[q >> 2] * sm.T[b]);
             }
             __syncthreads();
             for (int z = threadIdx.x; z < 5 * 16 * C; z += blockDim.x) {
@@ -1554,12 +1586,14 @@ __global__ void __launch_bounds__(512) k_fullopt(const FullGroup* __restrict__ g
             sm.Mt[threadIdx.x] = (R)(M.sqpi[i] * M.R[i * 4 + k]);
             if (threadIdx.x < 4) sm.pi[threadIdx.x] = (R)M.pi[threadIdx.x];
         }
-        init_newton_smem<R, C>(M, sm.ns);
+        // per-tree category rates (a visit that re-optimises the Gamma shape), else the model's
+        const double* rr = G.rates ? G.rates + (size_t)gi * kMaxCat : M.rates;
+        init_newton_smem<R, C>(M, sm.ns, rr);
         for (int v = threadIdx.x; v < NN; v += blockDim.x) len[v] = glen[v];
         __syncthreads();
         for (int z = threadIdx.x; z < NN * C * 4; z += blockDim.x) {
             const int v = z / (C * 4), r = (z / 4) % C, i = z & 3;
-            if (v > 0) pmat_row<R>(M, len[v] * M.rates[r], i, Pm + ((size_t)v * C + r) * 16 + i * 4);
+            if (v > 0) pmat_row<R>(M, len[v] * rr[r], i, Pm + ((size_t)v * C + r) * 16 + i * 4);
         }
         __syncthreads();
         auto srcD = [&](int v) {
@@ -1791,10 +1825,11 @@ void launch_insert_trees(cudaStream_t s, Slot* tab, int log2, DCount count, Tree
 }
 
 void launch_finalize_trees(cudaStream_t s, Slot* tab, DCount count, const int32_t* slot_of, const double* lnl,
-                           const double* lmax, double thr, DRound round, int32_t* good, unsigned long long* stats) {
+                           const double* lmax, double thr, DRound round, int32_t* good, unsigned long long* stats,
+                           const double* alpha) {
     if (count.cap <= 0) return;
     k_finalize_trees<<<blocks_for(count.cap, 256), 256, 0, s>>>(tab, count, slot_of, lnl, lmax, thr, round, good,
-                                                                stats);
+                                                                stats, alpha);
     ++g_launches;
 }
 
@@ -1828,6 +1863,19 @@ void launch_gather_out(cudaStream_t s, int n, DCount count, const int32_t* idx, 
     if (count.cap <= 0) return;
     k_gather_out<<<blocks_for(count.cap, 128), 128, 0, s>>>(n, count, idx, ts, lnl, edges_out, lengths_out, lnl_out,
                                                              keys_out);
+    ++g_launches;
+}
+
+void launch_frontier_alpha(cudaStream_t s, TreeSet fr, int count, const Slot* tab, int log2, double base,
+                           double* alpha) {
+    if (count <= 0) return;
+    k_frontier_alpha<<<blocks_for(count, 128), 128, 0, s>>>(fr, count, tab, log2, base, alpha);
+    ++g_launches;
+}
+
+void launch_gamma_rates(cudaStream_t s, int count, int C, const double* alpha, double* rates) {
+    if (count <= 0) return;
+    k_gamma_rates<<<blocks_for(count, 64), 64, 0, s>>>(count, C, alpha, rates);
     ++g_launches;
 }
 
@@ -1910,10 +1958,10 @@ size_t fullopt_smem_bytes(int prec, int C, int n, int P, bool table_in_smem, int
 namespace {
 template <typename R, int C>
 void partials_t(cudaStream_t s, const Model& M, Aln A, TreeSet ts, int first, DCount count, ClvGroup g, bool with_up,
-                int threads, R* pm) {
+                int threads, R* pm, const double* rates) {
     const int NN = 2 * ts.n - 2;
     long long rows = (long long)count.cap * NN * C * 4;
-    k_pmats<R><<<(int)std::min<long long>(blocks_for(rows, 256), 8192), 256, 0, s>>>(M, ts, first, count, pm);
+    k_pmats<R><<<(int)std::min<long long>(blocks_for(rows, 256), 8192), 256, 0, s>>>(M, ts, first, count, pm, rates);
     ++g_launches;
     size_t smem = (size_t)NN * C * 16 * sizeof(R);
     cudaFuncSetAttribute(k_partials<R, C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -1928,16 +1976,16 @@ size_t pmat_bytes(int prec, int C, int n, int count) {
 }
 
 void launch_partials(cudaStream_t s, int prec, const Model& M, Aln A, TreeSet ts, int first, DCount count, ClvGroup g,
-                     bool with_up, int threads, void* pm) {
+                     bool with_up, int threads, void* pm, const double* rates) {
     if (count.cap <= 0) return;
     if (prec == 0) {
         double* q = reinterpret_cast<double*>(pm);
-        if (M.C == 1) partials_t<double, 1>(s, M, A, ts, first, count, g, with_up, threads, q);
-        else partials_t<double, 4>(s, M, A, ts, first, count, g, with_up, threads, q);
+        if (M.C == 1) partials_t<double, 1>(s, M, A, ts, first, count, g, with_up, threads, q, rates);
+        else partials_t<double, 4>(s, M, A, ts, first, count, g, with_up, threads, q, rates);
     } else {
         float* q = reinterpret_cast<float*>(pm);
-        if (M.C == 1) partials_t<float, 1>(s, M, A, ts, first, count, g, with_up, threads, q);
-        else partials_t<float, 4>(s, M, A, ts, first, count, g, with_up, threads, q);
+        if (M.C == 1) partials_t<float, 1>(s, M, A, ts, first, count, g, with_up, threads, q, rates);
+        else partials_t<float, 4>(s, M, A, ts, first, count, g, with_up, threads, q, rates);
     }
 }
 

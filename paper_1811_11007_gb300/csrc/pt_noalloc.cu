@@ -64,6 +64,7 @@ extern "C" pt_status pt_score_topologies_noalloc(int n_taxa, int n_patterns, con
     if (cfg_in) cfg = *cfg_in; else pt_config_default(&cfg);
     if (cfg.precision < 0 || cfg.precision > 1 || !(cfg.tmin > 0) || !(cfg.tmax > cfg.tmin) || cfg.newton_maxit < 1 ||
         cfg.full_max_sweeps < 0 || !(cfg.branch_prior_rate >= 0) || !std::isfinite(cfg.branch_prior_rate) ||
+        cfg.reopt_alpha != 0 ||  // this entry point keeps the model's Gamma shape
         (cfg.threads != 0 && (cfg.threads < 32 || cfg.threads > 512 || cfg.threads % 32)))
         return PT_ERR_INVALID_ARG;
     Model M;
@@ -170,6 +171,7 @@ extern "C" pt_status pt_score_topologies_noalloc(int n_taxa, int n_patterns, con
         gp.g = g;
         gp.max_sweeps = mode == PT_SCORE_FULL ? cfg.full_max_sweeps : 0;
         gp.lnl_out = lnl_out_dev + f0;
+        gp.rates = nullptr;
         const int gs[2] = {0, cnt};
         if (cudaMemcpyAsync(d_group, &gp, sizeof gp, cudaMemcpyHostToDevice, stream) != cudaSuccess ||
             cudaMemcpyAsync(d_gstart, gs, sizeof gs, cudaMemcpyHostToDevice, stream) != cudaSuccess ||

@@ -28,7 +28,7 @@ EXPORTS = ["pt_config_default", "pt_create", "pt_destroy", "pt_last_error", "pt_
            "pt_mlp_loss_grad", "pt_mlp_train", "pt_mlp_enable", "pt_training_log", "pt_training_pairs",
            "pt_expand_batch", "pt_expand_batch_dev", "pt_autotune", "pt_autotune_report", "pt_graph_create",
            "pt_graph_frontier_dev", "pt_graph_set_frontier", "pt_graph_run", "pt_graph_next_dev", "pt_graph_get_next",
-           "pt_graph_advance", "pt_graph_destroy", "pt_split_frequencies"]
+           "pt_graph_advance", "pt_graph_destroy", "pt_split_frequencies", "pt_last_alphas"]
 MLP_PARAMS, MLP_IN, MLP_OUT = 27912, 69, 5
 _f32p = np.ctypeslib.ndpointer(np.float32, flags="C_CONTIGUOUS")
 
@@ -50,7 +50,8 @@ class Config(C.Structure):
     _fields_ = [("device", C.c_int), ("precision", C.c_int), ("table_log2", C.c_int), ("propose_mode", C.c_int),
                 ("tmin", C.c_double), ("tmax", C.c_double), ("newton_tol", C.c_double), ("newton_maxit", C.c_int),
                 ("sweep_tol", C.c_double), ("full_max_sweeps", C.c_int), ("prop_max_sweeps", C.c_int),
-                ("threads", C.c_int), ("mem_budget", C.c_size_t), ("branch_prior_rate", C.c_double)]
+                ("threads", C.c_int), ("mem_budget", C.c_size_t), ("branch_prior_rate", C.c_double),
+                ("reopt_alpha", C.c_int)]
 
 
 _lib = None
@@ -123,6 +124,7 @@ def lib():
             L.pt_graph_get_next.argtypes = [_vp, _vp, C.c_int, C.c_int, _vp, _vp, _vp, _vp, _ip]
             L.pt_graph_advance.argtypes = [_vp, _vp, _ip]
             L.pt_graph_destroy.argtypes = [_vp, _vp]
+            L.pt_last_alphas.argtypes = [_vp, C.c_int, C.c_int, _vp, C.POINTER(C.c_int)]
             L.pt_split_frequencies.argtypes = [_vp, C.c_int, C.c_int, _vp, _vp, C.c_size_t, _vp, _vp, _vp,
                                                C.POINTER(C.c_size_t)]
             L.pt_score_topologies_noalloc.argtypes = [C.c_int, C.c_int, _vp, _vp, _f64p, _f64p, C.c_double, C.c_int,
@@ -309,6 +311,14 @@ class Context:
             fe, fl, fn, fk = keep[6 * k + 2: 6 * k + 6]
             c = arr[k].n_kept
             out.append((arr[k].lmax, {"edges": fe[:c], "lengths": fl[:c], "lnl": fn[:c], "keys": fk[:c]}))
+        return out
+
+    def last_alphas(self, aln: int) -> np.ndarray:
+        """Gamma shapes of the last call's output trees (pt_last_alphas)."""
+        cnt = C.c_int()
+        self._ck(lib().pt_last_alphas(self._h, aln, 0, None, C.byref(cnt)))
+        out = np.zeros(cnt.value, np.float64)
+        self._ck(lib().pt_last_alphas(self._h, aln, cnt.value, _ptr(out), C.byref(cnt)))
         return out
 
     def split_frequencies(self, aln: int, edges, lnl) -> dict:

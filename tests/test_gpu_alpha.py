@@ -1,0 +1,104 @@
+"""Gamma-shape re-optimisation per visit (reopt_alpha) against the oracle."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1811_11007_gb300 import pt, synth
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"fp64": 1e-8, "mixed": 1e-3}
+# proposal scores at the parent's searched shape (see the search test)
+PROP_TOL = {"fp64": 1e-5, "mixed": 1e-2}
+ATOL = {"fp64": 1e-5, "mixed": 2e-2}  # relative tolerance on the shape
+
+
+def _tol(prec, x):
+    return TOL[prec] + (1e-12 * abs(x) if prec == "fp64" else 0.0)
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1811_11007_gb300 import build
+    build.build()
+
+
+def _problem(n, sites, seed, base):
+    a = synth.simulate(n, sites, seed, model="gtr", alpha=0.5)
+    tips, w = synth.compress_patterns(a.codes)
+    pb = oracle.Problem(tips, w, a.exch, a.freqs, base, 4)
+    pb.set_reopt_alpha(True)
+    return a, pb
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_scoring_with_shape_reoptimisation(prec):
+    n, base = 9, 1.0
+    a, pb = _problem(n, 700, 631, base)
+    e, l = synth.random_trees(n, 3, 632)
+    e = np.concatenate([e, a.tree_edges[None]])
+    l = np.concatenate([l, np.full((1, 2 * n - 3), 0.1)])
+    with pt.Context(precision=prec, reopt_alpha=1) as ctx:
+        aid = ctx.load_alignment(a.codes)
+        ctx.set_model(aid, a.exch, a.freqs, base, 4)
+        lnl, lens, _ = ctx.score(aid, e, l, mode="full")
+        alphas = ctx.last_alphas(aid)
+        assert len(alphas) == len(e)
+        for i in range(len(e)):
+            f, wl, al = pb.visit_optimise(e[i], l[i])
+            assert abs(lnl[i] - f) <= _tol(prec, f), (i, lnl[i], f)
+            assert alphas[i] == pytest.approx(al, rel=ATOL[prec])
+            if prec == "fp64":
+                np.testing.assert_allclose(lens[i], wl, rtol=1e-4, atol=1e-6)
+        # with the option off the model's shape is kept and reported
+        ctx2 = pt.Context(precision=prec)
+        aid2 = ctx2.load_alignment(a.codes)
+        ctx2.set_model(aid2, a.exch, a.freqs, base, 4)
+        lnl0, _, _ = ctx2.score(aid2, e, l, mode="full")
+        np.testing.assert_array_equal(ctx2.last_alphas(aid2), np.full(len(e), base))
+        assert np.all(lnl >= lnl0 - 2 * TOL[prec])
+        ctx2.close()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_search_with_shape_reoptimisation(prec):
+    n, T, base = 7, 3.0, 1.0
+    a, pb = _problem(n, 400, 633, base)
+    e, l = synth.random_trees(n, 2, 634)
+    s = oracle.Search(pb, e, l, T)
+    s.run()
+    ov = s.visited()
+    od = dict(zip(pt.keys_to_int(ov["keys"]), zip(ov["status"], ov["lnl"])))
+    # skip decisions closer to the threshold than the precision can resolve
+    from test_gpu_parity import _margins
+    lmax = s.lmax
+    if _margins(ov, T).min() < 10 * PROP_TOL[prec]:
+        pytest.skip("a decision lies within tolerance of the threshold")
+    with pt.Context(precision=prec, table_log2=14, reopt_alpha=1) as ctx:
+        aid = ctx.load_alignment(a.codes)
+        ctx.set_model(aid, a.exch, a.freqs, base, 4)
+        lm, rounds = pt.run_search(ctx, aid, e, l, T)
+        vis = ctx.visited(aid)
+        gd = dict(zip(pt.keys_to_int(vis["keys"]), zip(vis["status"], vis["lnl"])))
+        assert set(gd) == set(od)
+        # Proposals are scored at their parent's shape, which a value-based search pins
+        # only as far as lnL noise allows (~1e-7 in ln alpha in FP64, ~1e-4 with FP32
+        # partials), and a neighbour's score is first-order sensitive to the shape: their
+        # scores agree to PROP_TOL; visits (flat in the shape at their own optimum) to TOL.
+        prop_tol = PROP_TOL[prec]
+        bad = [(k, st, x, gd[k]) for k, (st, x) in od.items()
+               if gd[k][0] != st or not abs(gd[k][1] - x) <= (prop_tol if st == oracle.REJECTED else _tol(prec, x))]
+        assert not bad, bad
+        assert abs(lm - lmax) <= _tol(prec, lmax)
+
+
+def test_graph_rounds_reject_shape_reoptimisation():
+    a, _ = _problem(8, 200, 635, 1.0)
+    with pt.Context(precision="mixed", table_log2=12, reopt_alpha=1) as ctx:
+        aid = ctx.load_alignment(a.codes)
+        ctx.set_model(aid, a.exch, a.freqs, 1.0, 4)
+        with pytest.raises(pt.PTError):
+            ctx.graph([aid], [4], [3.0])
