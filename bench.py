@@ -43,6 +43,11 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 N_TAXA, N_SITES, THRESH, N_STARTS = 27, 2000, 10.0, 8
+# DRAM bytes per unit of the two persistent kernels on this workload, from one ncu capture of each
+# (dram__bytes_read.sum + dram__bytes_write.sum of a 2055-neighbour / 375-tree launch, divided by
+# its units; profiles/k_propose_27taxa_925patterns.md, profiles/k_fullopt_27taxa_925patterns.md)
+DRAM_PER_NEIGHBOUR = 125.9e6 / 2055
+DRAM_PER_KEPT_TREE = 12.37e9 / 375
 FP32_LANES_PER_SM = 128
 
 
@@ -350,11 +355,15 @@ def run_ours(args, rank, world, dev):
         peak_note = f"FP32 FMA: {nsm} SMs x 128 lanes x 2 flop x {sm_max:.0f} MHz (recipe unit counts)"
         prop_roof = {"bound": "alu", "kernel": "k_propose (proposal Newton, five branches)", "achieved": achieved_tf,
                      "peak": alu_peak, "unit": "TFLOP/s", "frac": (achieved_tf / alu_peak) if achieved_tf else None,
-                     "traffic": None, "ms_per_step": res["prop_ms"] / args.steps, "peak_note": peak_note}
+                     "traffic": DRAM_PER_NEIGHBOUR * res["stats"]["scored"],
+                     "traffic_note": "bytes per launch: ncu DRAM bytes per neighbour x neighbours of this launch",
+                     "ms_per_step": res["prop_ms"] / args.steps, "peak_note": peak_note}
         full_tf = res["full_flops"] / (res["full_ms"] / 1e3) / 1e12 if res["full_ms"] > 0 else None
         full_roof = {"bound": "alu", "kernel": "k_fullopt (visit: full optimisation)", "achieved": full_tf,
                      "peak": alu_peak, "unit": "TFLOP/s", "frac": (full_tf / alu_peak) if full_tf else None,
-                     "traffic": None, "ms_per_step": res["full_ms"] / args.steps, "peak_note": peak_note}
+                     "traffic": DRAM_PER_KEPT_TREE * res["stats"]["kept"],
+                     "traffic_note": "bytes per launch: ncu DRAM bytes per kept tree x kept trees of this launch",
+                     "ms_per_step": res["full_ms"] / args.steps, "peak_note": peak_note}
         dominant = full_roof if res["full_ms"] > res["prop_ms"] else prop_roof
         out = {
             "metric": "branch-optimised topologies/sec (unique NNI neighbours scored per PT round)",
