@@ -951,6 +951,7 @@ typedef struct {
     int status;
     double lnl;       /* proposal lnL for rejected ones, full lnL otherwise */
     double plnl;      /* proposal lnL (NaN for starts) */
+    double alpha;     /* Gamma shape: the visit's (visited trees), the parent's (proposals) */
     int round;
     uint64_t *splits; /* exact split set, for the injectivity check */
     int32_t *edges; double *lengths;
@@ -1079,9 +1080,11 @@ or_search *or_search_new(or_problem *pb, int n_start, const int32_t *edges, cons
         uint64_t k[2];
         tree_key(&ts[i], k);
         if (set_find(&s->vis, k)) continue;
-        l[i] = visit_optimise(pb, &ts[i], NULL);
+        double al;
+        l[i] = visit_optimise(pb, &ts[i], &al);
         or_entry *e = set_insert(&s->vis, k);
         entry_fill(e, &ts[i], OR_BAD, l[i], NAN, 0);
+        e->alpha = al;
         keep[i] = 1;
         if (l[i] > s->lmax) s->lmax = l[i];
     }
@@ -1121,6 +1124,7 @@ or_search *or_search_from_frontier(or_problem *pb, int nf, const int32_t *edges,
         if (set_find(&s->vis, k)) continue;
         or_entry *e = set_insert(&s->vis, k);
         entry_fill(e, &t, OR_GOOD, NAN, NAN, 0);
+        e->alpha = pb->alpha;  /* given without a shape: the model's */
         s->front[s->nfront++] = t;
     }
     qsort(s->front, s->nfront, sizeof(or_tree), tree_cmp_key);
@@ -1163,17 +1167,25 @@ int or_search_round(or_problem *pb, or_search *s)
         or_tree nt;
         const or_quartet *q = &qall[(size_t)cs[i].parent * (n - 3) + cs[i].qi];
         apply_nni(&s->front[cs[i].parent], q, cs[i].swap, &nt);
+        /* READING: with shape re-optimisation a proposal is scored with its parent's shape
+         * (the one its visit found), the shape its inherited lengths were optimised at */
+        const or_entry *pe = set_find(&s->vis, cs[i].pkey);
+        const double ap = pb->reopt_alpha && pe ? pe->alpha : pb->alpha;
+        if (ap != pb->alpha) set_alpha(pb, ap);
         double lp = propose_optimise(pb, &nt, q, cs[i].swap);
+        if (ap != pb->alpha) set_alpha(pb, pb->alpha);
         s->n_scored++;
         or_entry *e = set_insert(&s->vis, cs[i].nkey);
         int keepit = lp >= lmax0 - T;
         entry_fill(e, &nt, OR_REJECTED, lp, lp, s->round);
+        e->alpha = ap;
         if (keepit) { kept[nk] = nt; kl[nk] = lp; ++nk; }
     }
     double lmax = lmax0;
     double *fl = (double *)malloc(sizeof(double) * (size_t)(nk > 0 ? nk : 1));
+    double *fa = (double *)malloc(sizeof(double) * (size_t)(nk > 0 ? nk : 1));
     for (int i = 0; i < nk; ++i) {
-        fl[i] = visit_optimise(pb, &kept[i], NULL);
+        fl[i] = visit_optimise(pb, &kept[i], &fa[i]);
         if (fl[i] > lmax) lmax = fl[i];
     }
     s->lmax = lmax;
@@ -1190,13 +1202,14 @@ int or_search_round(or_problem *pb, or_search *s)
         e->lengths = (double *)malloc(sizeof(double) * (2 * n - 3));
         tree_to_edges(&kept[i], e->edges, e->lengths);
         e->lnl = fl[i];
+        e->alpha = fa[i];
         if (fl[i] >= lmax - T) { e->status = OR_GOOD; nfront[nf++] = kept[i]; s->n_good++; }
         else e->status = OR_BAD;
     }
     qsort(nfront, nf, sizeof(or_tree), tree_cmp_key);
     free(s->front);
     s->front = nfront; s->nfront = nf;
-    free(cs); free(qall); free(kept); free(kl); free(fl);
+    free(cs); free(qall); free(kept); free(kl); free(fl); free(fa);
     return nf;
 }
 
