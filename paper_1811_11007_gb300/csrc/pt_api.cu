@@ -464,6 +464,7 @@ struct FullJob {
     double* lnl_d;
     int max_sweeps;
     const double* rates = nullptr;  // per-tree category rates [count][kMaxCat], or null: the model's
+    const int32_t* order = nullptr; // processing order of the trees (longest first), or null
 };
 
 // Runs full-optimisation jobs in one persistent launch over all of them.  The
@@ -494,6 +495,7 @@ void run_full_jobs(Ctx& c, std::vector<FullJob> jobs, bool allow_tune = true) {
             gp.max_sweeps = j.max_sweeps;
             gp.lnl_out = j.lnl_d;
             gp.rates = j.rates;
+            gp.order = j.order;
             groups.push_back(gp);
             counts.push_back(j.count);
             maxN = std::max(maxN, a.n);
@@ -872,6 +874,7 @@ void expand_batch(Ctx& c, const std::vector<RoundIn>& ins, std::vector<RoundOut>
     double* plnl = buf<double>(c, "items.lnl", Wtot + 1);
     double* len5 = buf<double>(c, "items.len5", 5 * (size_t)Wtot + 5);
     int32_t* kept = buf<int32_t>(c, "items.kept", Wtot + 1);
+    float* icost = buf<float>(c, "items.cost", Wtot + 1);
     const bool use_mlp = c.mlp_on && c.mlp_ready;
     const bool feats = use_mlp || c.log_on;
     float* xf_all = feats ? buf<float>(c, "mlp.xf", (size_t)(Wtot + 1) * kMlpIn) : nullptr;
@@ -996,6 +999,7 @@ void expand_batch(Ctx& c, const std::vector<RoundIn>& ins, std::vector<RoundOut>
             gp.kept = kept + gi0;
             gp.init = init;
             gp.rates = r.frates;
+            gp.cost_out = icost + gi0;
             groups.push_back(gp);
             counts.push_back(cnt_items);
             maxP = std::max(maxP, a.P);
@@ -1101,6 +1105,11 @@ void expand_batch(Ctx& c, const std::vector<RoundIn>& ins, std::vector<RoundOut>
             launch_canon(c.stream, r.n, r.K, kedges, klens, r.kp, c.d_err);
             job_of[k] = (int)jobs.size();
             jobs.push_back(FullJob{r.a, r.kp, 0, r.K, r.klnl, c.cfg.full_max_sweeps});
+            if (!full_radius) {  // longest predicted full optimisations first
+                int32_t* ord = buf<int32_t>(c, pre + "kept.order", r.K);
+                launch_cost_order(c.stream, hcount(r.K), r.kidx, icost + r.ibase, ord);
+                jobs.back().order = ord;
+            }
         }
     }
     hc[kStKept] = Ktot;
@@ -1207,7 +1216,8 @@ struct GraphAln {
     int32_t* in_edges;
     double* in_lens;
     TreeSet fr, kp;
-    int32_t *fwin, *cinfo, *cslot, *flag, *pos, *kept, *kpos, *kidx, *kslot, *good, *gpos, *gidx, *kedges;
+    int32_t *fwin, *cinfo, *cslot, *flag, *pos, *kept, *kpos, *kidx, *kslot, *good, *gpos, *gidx, *kedges, *ord;
+    float* icost;
     uint64_t *nkey, *ikey;
     Item* items;
     double *plnl, *len5, *klens, *klnl;
@@ -1356,6 +1366,7 @@ void graph_record(Ctx& c, GraphRound& g, cudaStream_t s, int C, int maxN, int ma
         launch_scan_total(s, x.kept, x.kpos, x.cap, di + g.oK() + k);
         launch_compact_idx(s, x.cap, x.kept, x.kpos, x.kidx);
         launch_materialize(s, x.n, Kk, x.kidx, x.items, x.fr, x.len5, x.kedges, x.klens, x.kslot);
+        launch_cost_order(s, Kk, x.kidx, x.icost, x.ord);
         launch_canon(s, x.n, Kk, x.kedges, x.klens, x.kp, c.d_err);
     }
     launch_prefix_counts(s, na, di + g.oK(), di + g.oPerm(), di + g.oGSF());
@@ -1447,6 +1458,8 @@ GraphRound* graph_create(Ctx& c, const std::vector<int>& ids, const std::vector<
         ar.add(x.plnl, (size_t)cap + 1);
         ar.add(x.len5, 5 * (size_t)cap + 5);
         ar.add(x.kept, (size_t)cap + 1);
+        ar.add(x.icost, (size_t)cap + 1);
+        ar.add(x.ord, (size_t)cap + 1);
         ar.add(x.kpos, (size_t)cap + 1);
         ar.add(x.kidx, (size_t)cap + 1);
         ar.add(x.kedges, (size_t)cap * 2 * E);
@@ -1524,6 +1537,7 @@ GraphRound* graph_create(Ctx& c, const std::vector<int>& ids, const std::vector<
         p.kept = x.kept;
         p.init = g.mlp ? x.init : nullptr;
         p.rates = nullptr;
+        p.cost_out = x.icost;
         FullGroup& f = fg[k];
         f.M = A.M;
         f.A = aln_dev(A);
@@ -1533,6 +1547,7 @@ GraphRound* graph_create(Ctx& c, const std::vector<int>& ids, const std::vector<
         f.max_sweeps = c.cfg.full_max_sweeps;
         f.lnl_out = x.klnl;
         f.rates = nullptr;
+        f.order = x.ord;
         if (g.mlp && !A.tip_sum) {
             ck(c, cudaMalloc(&A.tip_sum, sizeof(float) * 16 * A.n), "alloc tip summaries");
             launch_tip_summary(c.stream, aln_dev(A), C, A.tip_sum);

@@ -200,6 +200,11 @@ struct SplitSlot {
 // count canonical trees to each of its non-trivial splits.
 void launch_split_frequencies(cudaStream_t s, TreeSet ts, int count, const double* lnl, const double* lmax,
                               SplitSlot* tab, int log2, int32_t* err);
+// order = the kept trees k < count by decreasing predicted cost cost[kidx[k]]
+// (binned in steps of 1/32, the last bin open; ties in any order): the longest
+// full optimisations start first, so the launch's tail is short.  Trees whose
+// proposal moved its five lengths far from the inherited ones take more sweeps.
+void launch_cost_order(cudaStream_t s, DCount count, const int32_t* kidx, const float* cost, int32_t* order);
 // rates [t][kMaxCat] = discrete Gamma category means of shape alpha[t] (C categories).
 void launch_gamma_rates(cudaStream_t s, int count, int C, const double* alpha, double* rates);
 // Dump of the occupied slots: flag pass (gather false), then gather at pos.
@@ -232,6 +237,8 @@ struct PropGroup {
     double* lnl_out;
     double* len5_out;
     int32_t* kept;
+    float* cost_out;         // per item: sum over the five branches of |ln(optimised / inherited length)|,
+                             // the predictor of its full optimisation's cost; or null
     const double* init;      // learned starting lengths [count][5] or nullptr
     const double* rates;     // per-frontier-tree category rates [tree][kMaxCat] (shape re-optimisation), or null
 };
@@ -247,6 +254,7 @@ struct FullGroup {
     int max_sweeps;
     double* lnl_out;
     const double* rates;  // per-tree category rates [count][kMaxCat] (shape re-optimisation), or null: M.rates
+    const int32_t* order; // processing order of the group's trees (a permutation), or null: 0, 1, ...
 };
 // Batched launches over groups: gstart [ngroups + 1] is the prefix sum of the
 // groups' item (tree) counts (device); counter (device, zeroed) hands out the

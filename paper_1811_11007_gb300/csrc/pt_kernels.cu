@@ -470,6 +470,28 @@ __global__ void k_dump_gather(const Slot* tab, size_t nslots, const int32_t* fla
     }
 }
 
+// ---------------------------------------------------------------- scheduling order
+// Counting sort of the kept trees by predicted cost (one block): a histogram of
+// the binned costs, bins in decreasing order, scatter with per-bin cursors.
+__global__ void k_cost_order(DCount cnt, const int32_t* kidx, const float* cost, int32_t* order) {
+    __shared__ int hist[65], start[65];
+    const int K = dcount(cnt);
+    for (int b = threadIdx.x; b < 65; b += blockDim.x) hist[b] = 0;
+    __syncthreads();
+    auto bin = [&](int k) {
+        const float x = cost[kidx[k]] * 32.f;
+        return x == x ? 1 + (int)fminf(63.f, fmaxf(0.f, x)) : 64;  // NaN: first
+    };
+    for (int k = threadIdx.x; k < K; k += blockDim.x) atomicAdd(&hist[bin(k)], 1);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int acc = 0;
+        for (int b = 64; b >= 1; --b) { start[b] = acc; acc += hist[b]; }
+    }
+    __syncthreads();
+    for (int k = threadIdx.x; k < K; k += blockDim.x) order[atomicAdd(&start[bin(k)], 1)] = k;
+}
+
 // ---------------------------------------------------------------- Gamma shape
 // Shape of each frontier tree: the one its visit recorded in the visited table
 // (read-only probe of the key), else the model's.
@@ -1502,6 +1524,11 @@ __global__ void __launch_bounds__(512) k_propose(const PropGroup* __restrict__ g
             }
             G.lnl_out[o] = f1;
             for (int b = 0; b < 5; ++b) G.len5_out[(size_t)o * 5 + b] = sm.T[b];
+            if (G.cost_out) {  // how far the proposal moved the five lengths: predicts the visit's cost
+                float cst = 0.f;
+                for (int b = 0; b < 5; ++b) cst += fabsf(logf((float)(sm.T[b] / len[bnode[b]])));
+                G.cost_out[o] = cst;
+            }
             const int k = f1 >= *G.lmax - G.thr;
             G.kept[o] = k;
             Slot* sl = &G.tab[it.slot];
@@ -1557,7 +1584,7 @@ __global__ void __launch_bounds__(512) k_fullopt(const FullGroup* __restrict__ g
         const int x = sm.next;
         if (x >= total) break;
         const FullGroup& G = groups[sm.grp];
-        const int gi = x - gstart[sm.grp];
+        const int gi = G.order ? G.order[x - gstart[sm.grp]] : x - gstart[sm.grp];
         const Model& M = G.M;
         const Aln& A = G.A;
         const int n = G.ts.n, NN = 2 * n - 2, P = A.P;
@@ -1870,6 +1897,12 @@ void launch_frontier_alpha(cudaStream_t s, TreeSet fr, int count, const Slot* ta
                            double* alpha) {
     if (count <= 0) return;
     k_frontier_alpha<<<blocks_for(count, 128), 128, 0, s>>>(fr, count, tab, log2, base, alpha);
+    ++g_launches;
+}
+
+void launch_cost_order(cudaStream_t s, DCount count, const int32_t* kidx, const float* cost, int32_t* order) {
+    if (count.cap <= 0) return;
+    k_cost_order<<<1, 1024, 0, s>>>(count, kidx, cost, order);
     ++g_launches;
 }
 

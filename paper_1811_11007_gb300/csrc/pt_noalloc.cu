@@ -172,6 +172,7 @@ extern "C" pt_status pt_score_topologies_noalloc(int n_taxa, int n_patterns, con
         gp.max_sweeps = mode == PT_SCORE_FULL ? cfg.full_max_sweeps : 0;
         gp.lnl_out = lnl_out_dev + f0;
         gp.rates = nullptr;
+        gp.order = nullptr;
         const int gs[2] = {0, cnt};
         if (cudaMemcpyAsync(d_group, &gp, sizeof gp, cudaMemcpyHostToDevice, stream) != cudaSuccess ||
             cudaMemcpyAsync(d_gstart, gs, sizeof gs, cudaMemcpyHostToDevice, stream) != cudaSuccess ||
