@@ -1,0 +1,123 @@
+"""The benchmarked PT round at its full size and in its launch configuration:
+27 taxa x 2000 sites GTR+G4 (alpha 0.5), the frontier (up to 256 trees) a
+threshold-10 search reaches from 8 random starts, learned warm start,
+autotuned CTA sizes, replayed as a CUDA graph.  Checked against the FP64
+oracle on sampled outputs (proposals one by one, visits of kept trees) and by
+properties that hold at any size (the scored key set equals the oracle's NNI
+enumeration minus the frontier, the threshold rules, the raised lmax), and the
+graph round against the same round issued kernel by kernel, bit for bit.
+Proposals are compared with the oracle on the same round run from the plain
+start (inherited lengths, as the oracle starts): a proposal still moving
+after the 8-sweep cap ends where its start led it, so under the learned start
+its score may differ from the oracle's by more than the tolerance (and a
+neighbour whose central branch collapses can reach another local optimum of
+its outer branches); the two rounds must still decide identically.
+Mixed precision: |dlnL| <= 1e-3 nats, branch lengths within 1e-4 relative."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1811_11007_gb300 import pt, synth
+
+pytestmark = pytest.mark.gpu
+TOL = 1e-3
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1811_11007_gb300 import build
+    build.build()
+
+
+def test_benchmark_round_full_size():
+    import bench
+    n, T = bench.N_TAXA, bench.THRESH
+    a, starts = bench.workload(0)
+    tips, w = synth.compress_patterns(a.codes)
+    pb = oracle.Problem(tips, w, a.exch, a.freqs, 0.5, 4)
+    with pt.Context(precision="mixed", table_log2=22) as ctx:
+        bench.train_warm_start(ctx, 0)
+        aid = ctx.load_alignment(a.codes)
+        ctx.set_model(aid, a.exch, a.freqs, 0.5, 4)
+        lmax0, front, _ = bench.build_frontier(ctx, aid, starts, 256)
+        F = len(front["edges"])
+        assert F >= 64
+        ctx.autotune(True)
+        ctx.reset_visited(aid)
+        lm_d, nxt_d = ctx.expand(aid, front["edges"], front["lengths"], T, lmax0)
+        props = ctx.last_proposals()
+        st = ctx.stats()
+        assert ctx.autotune_report()  # the round was large enough to tune its CTA sizes
+        # the headline launch: the same round recorded as a CUDA graph, at the tuned sizes
+        g = ctx.graph([aid], [F], [T])
+        try:
+            g.set_frontier(0, front["edges"], front["lengths"])
+            ctx.reset_visited(aid)
+            lm_g, nn = g.run([F], [lmax0])
+            nxt_g = g.next(0)
+        finally:
+            g.close()
+        # the same round from the plain start (the oracle's starting point)
+        ctx.mlp_enable(False)
+        ctx.reset_visited(aid)
+        lm_p, nxt_p = ctx.expand(aid, front["edges"], front["lengths"], T, lmax0)
+        props_p = ctx.last_proposals()
+    assert lm_g[0] == lm_d and nn[0] == len(nxt_d["keys"])
+    for k in ("keys", "lnl", "lengths", "edges"):
+        np.testing.assert_array_equal(nxt_g[k], nxt_d[k])
+
+    # scored set: every NNI neighbour of every frontier tree, the frontier itself excluded
+    fkeys = {oracle.tree_key(n, e) for e in front["edges"]}
+    nb_keys, origin = set(), {}
+    for f in range(F):
+        _, _, nk = oracle.nni_neighbours(n, front["edges"][f], front["lengths"][f])
+        for j, (lo, hi) in enumerate(nk):
+            kk = (int(lo), int(hi))
+            nb_keys.add(kk)
+            origin.setdefault((f, kk), j)
+    want = nb_keys - fkeys
+    got = [(int(lo), int(hi)) for lo, hi in props["keys"]]
+    assert len(got) == len(set(got)) == st["scored"]
+    assert set(got) == want
+
+    # threshold rules and lmax
+    prop_lnl = dict(zip(got, props["lnl"]))
+    nxt_keys = [(int(lo), int(hi)) for lo, hi in nxt_d["keys"]]
+    assert len(nxt_keys) > 0
+    for kk, x in zip(nxt_keys, nxt_d["lnl"]):
+        assert prop_lnl[kk] >= lmax0 - T      # kept at proposal time
+        assert x >= lm_d - T                  # kept after its visit
+    assert lm_d == max(lmax0, float(np.max(nxt_d["lnl"])))
+
+    # plain start: the same scored set; proposals sampled against the oracle, one by one
+    got_p = [(int(lo), int(hi)) for lo, hi in props_p["keys"]]
+    assert set(got_p) == want
+    diff = np.abs(np.array([prop_lnl[k] for k in got_p]) - props_p["lnl"])
+    print(f"learned vs plain start: proposals differing by > {TOL}: {np.sum(diff > TOL)} of {len(diff)}, "
+          f"max {diff.max():.4f} nats; next frontier {len(nxt_keys)} vs {len(nxt_p['keys'])} trees")
+    # the learned start decides nothing differently: the same neighbours pass the proposal
+    # threshold, the same next frontier, lmax within the tolerance
+    cut = lmax0 - T
+    assert {k for k in got if prop_lnl[k] >= cut} == {k for k, x in zip(got_p, props_p["lnl"]) if x >= cut}
+    assert nxt_keys == [(int(lo), int(hi)) for lo, hi in nxt_p["keys"]]
+    np.testing.assert_allclose(nxt_d["lnl"], nxt_p["lnl"], rtol=0, atol=TOL)
+    assert abs(lm_d - lm_p) <= TOL
+    pb.settings()
+    for i in np.linspace(0, len(got_p) - 1, 12).astype(int):
+        f = int(props_p["parent"][i])
+        j = origin[(f, got_p[i])]
+        lp, _, _ = pb.propose(front["edges"][f], front["lengths"][f], j)
+        assert abs(props_p["lnl"][i] - lp) <= TOL, (i, props_p["lnl"][i], lp)
+
+    # sampled visits: the oracle's lnL at the GPU's lengths, and its own full
+    # optimisation from them (the GPU's lengths are already at the optimum)
+    for i in np.linspace(0, len(nxt_keys) - 1, 6).astype(int):
+        e, l, x = nxt_d["edges"][i], nxt_d["lengths"][i], nxt_d["lnl"][i]
+        assert oracle.tree_key(n, e) == nxt_keys[i]
+        assert abs(pb.loglik(e, l) - x) <= TOL, (i, pb.loglik(e, l), x)
+        want_lnl, wl, _ = pb.full_optimise(e, l)
+        assert abs(want_lnl - x) <= TOL, (i, want_lnl, x)
+        np.testing.assert_allclose(l, wl, rtol=1e-4, atol=1e-6)
