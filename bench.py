@@ -330,6 +330,7 @@ def run_ours(args, rank, world, dev):
 
     plain = None
     if learned is not None:
+        judge = ctx.mlp_judge(aid)  # the plain start's judgement of the network on this alignment
         ctx.mlp_enable(False)
         plain = timed(ctx, aid, step_dev, max(1, min(args.steps, 3)), 1)
         ctx.mlp_enable(True)
@@ -400,7 +401,7 @@ def run_ours(args, rank, world, dev):
             "mixed_plain_start": ({"value": plain["units"] / (plain["ms"] / 1e3), "unit": "topologies/s",
                                    "prop_evals_per_neighbour": plain["stats"]["prop_evals"] /
                                    max(plain["stats"]["scored"], 1)} if plain else None),
-            "learned_warm_start": learned,
+            "learned_warm_start": (dict(learned, judge=judge) if learned else None),
             "roofline": dominant,
             "rooflines": {"k_propose": prop_roof, "k_fullopt": full_roof},
             "roofline_hbm": {"bound": "hbm", "achieved": achieved_gb, "peak": hbm_peak, "unit": "GB/s",

@@ -363,8 +363,27 @@ pt_status pt_mlp_loss_grad(pt_ctx *ctx, int n_rows, const float *x, const float 
  * of `batch` rows (a multiple of 64) drawn with replacement by a
  * counter-based generator from `seed`; *final_loss = last batch's loss. */
 pt_status pt_mlp_train(pt_ctx *ctx, int steps, int batch, double lr, uint64_t seed, double *final_loss);
-/* Uses (1) or stops using (0) the network as the proposal warm start. */
+/* Uses (1) or stops using (0) the network as the proposal warm start.
+ * The plain start stays the judge of the network on each alignment: the
+ * proposals of an alignment take the chosen start (first the network),
+ * except every 16th one (by its index in the round), which takes the other
+ * start, and the Newton evaluations of the two groups are counted on the
+ * device after every proposal launch (batched and graph rounds alike).
+ * Whenever both groups hold 256 proposals, the network is chosen for the
+ * following rounds if it needs at least 2 % fewer evaluations per proposal
+ * than the inherited lengths, the inherited lengths otherwise, and the counts
+ * are halved, so the choice follows the search as its trees change.  Either
+ * start gives the same optimum to the Newton tolerance.  Turning the network
+ * on, new weights and training reset every judge; a new model (pt_set_model)
+ * resets its alignment's. */
 pt_status pt_mlp_enable(pt_ctx *ctx, int on);
+/* Judge of the learned start on an alignment: out[0] proposals started from
+ * the network and out[1] their Newton evaluations, out[2] proposals started
+ * from the inherited lengths and out[3] theirs (counts since the last
+ * decision, halved at each decision), out[4] the state (0 no decision yet,
+ * network chosen; 1 network chosen; 2 inherited lengths chosen).  All zero
+ * before the alignment's first proposal launch with the network on. */
+pt_status pt_mlp_judge(pt_ctx *ctx, int aln_id, int64_t out[5]);
 /* Logs (features, log(optimised / inherited) lengths) of every proposal of later rounds
  * into a device buffer of `capacity` pairs (pairs beyond it are dropped);
  * changing the capacity clears the log. */

@@ -37,6 +37,7 @@ struct AlnState {
     int log2 = 0;
     int round = 0;
     float* tip_sum = nullptr;  // [n][16] leaf summaries for the warm-start features
+    Judge* judge = nullptr;    // device: judge of the learned start on this alignment
     double alpha = 1.0;        // Gamma shape of the model
     std::vector<double> last_alphas;  // shapes of the last call's output trees (shape re-optimisation)
 };
@@ -175,6 +176,21 @@ int threads_for(const Ctx& c, int P) {
 }
 
 Aln aln_dev(const AlnState& a) { return Aln{a.n, a.P, a.tips, a.w}; }
+
+// The judge of the learned start on an alignment (allocated open on first use).
+Judge* judge_of(Ctx& c, AlnState& a) {
+    if (!a.judge) {
+        ck(c, cudaMalloc(&a.judge, sizeof(Judge)), "alloc judge");
+        ck(c, cudaMemsetAsync(a.judge, 0, sizeof(Judge), c.stream), "reset judge");
+    }
+    return a.judge;
+}
+
+// New weights, training or re-enabling: every judge starts over (open).
+void reset_judges(Ctx& c) {
+    for (auto& a : c.alns)
+        if (a.judge) ck(c, cudaMemsetAsync(a.judge, 0, sizeof(Judge), c.stream), "reset judge");
+}
 
 size_t rsize(const Ctx& c) { return c.cfg.precision == PT_PREC_FP64 ? 8 : 4; }
 
@@ -879,6 +895,7 @@ void expand_batch(Ctx& c, const std::vector<RoundIn>& ins, std::vector<RoundOut>
     const bool feats = use_mlp || c.log_on;
     float* xf_all = feats ? buf<float>(c, "mlp.xf", (size_t)(Wtot + 1) * kMlpIn) : nullptr;
     double* init_all = use_mlp ? buf<double>(c, "mlp.init", (size_t)(Wtot + 1) * 5) : nullptr;
+    int32_t* ievals = use_mlp ? buf<int32_t>(c, "items.evals", Wtot + 1) : nullptr;
     struct Chunk {
         int k, f0, cnt, i0, i1;
     };
@@ -978,7 +995,7 @@ void expand_batch(Ctx& c, const std::vector<RoundIn>& ins, std::vector<RoundOut>
                     float* yb = buf<float>(c, "mlp.y", (size_t)(cnt_items + 64) * kMlpOutPad);
                     mlp_forward(c.stream, c.mlp, xb, cnt_items, yb, nullptr, nullptr, nullptr, nullptr, false);
                     launch_item_init(c.stream, items + r.ibase, ch.i0, hcount(ch.i1), xf, yb, c.cfg.tmin, c.cfg.tmax,
-                                     init_all + (size_t)gi0 * 5);
+                                     init_all + (size_t)gi0 * 5, judge_of(c, a));
                     init = init_all + (size_t)gi0 * 5;
                 }
             }
@@ -998,6 +1015,7 @@ void expand_batch(Ctx& c, const std::vector<RoundIn>& ins, std::vector<RoundOut>
             gp.len5_out = len5 + (size_t)5 * gi0;
             gp.kept = kept + gi0;
             gp.init = init;
+            gp.evals_out = ievals ? ievals + gi0 : nullptr;
             gp.rates = r.frates;
             gp.cost_out = icost + gi0;
             groups.push_back(gp);
@@ -1074,6 +1092,8 @@ void expand_batch(Ctx& c, const std::vector<RoundIn>& ins, std::vector<RoundOut>
             }
         ci = ce;
     }
+    if (use_mlp && !full_radius)  // the judges take this round's proposals
+        for (int k = 0; k < na; ++k) launch_judge(c.stream, hcount(ar[k].W), ievals + ar[k].ibase, judge_of(c, *ar[k].a));
     c.last_items = Wtot;
     // ---- C. visit the kept neighbours
     Span sp4(c, 4);
@@ -1218,6 +1238,7 @@ struct GraphAln {
     TreeSet fr, kp;
     int32_t *fwin, *cinfo, *cslot, *flag, *pos, *kept, *kpos, *kidx, *kslot, *good, *gpos, *gidx, *kedges, *ord;
     float* icost;
+    int32_t* ievals;  // per item Newton evaluations (judge of the learned start), with the learned start only
     uint64_t *nkey, *ikey;
     Item* items;
     double *plnl, *len5, *klens, *klnl;
@@ -1352,13 +1373,18 @@ void graph_record(Ctx& c, GraphRound& g, cudaStream_t s, int C, int maxN, int ma
             launch_slot_summary(s, prec, C, aln_dev(A), x.g, Fk, nslot, x.ssum);
             launch_item_features(s, x.n, x.items, 0, Wk, x.fr, 0, x.ssum, nslot, A.tip_sum, x.xf, x.xb);
             mlp_forward(s, c.mlp, x.xb, Wk, x.yb);
-            launch_item_init(s, x.items, 0, Wk, x.xf, x.yb, c.cfg.tmin, c.cfg.tmax, x.init);
+            launch_item_init(s, x.items, 0, Wk, x.xf, x.yb, c.cfg.tmin, c.cfg.tmax, x.init, A.judge);
         }
     }
     launch_prefix_counts(s, na, di + g.oW(), di + g.oPerm(), di + g.oGSP());
     cudaMemsetAsync(di + g.oCP(), 0, sizeof(int), s);
     launch_propose(s, prec, C, g.dpg, di + g.oGSP(), na, di + g.oCP(), kcfg(c), c.d_stats, g.prop_threads, pgrid,
                    g.prop_scratch, pspc, maxP);
+    if (g.mlp)  // the judges take this round's proposals
+        for (int k = 0; k < na; ++k) {
+            GraphAln& x = g.a[k];
+            launch_judge(s, DCount{x.cap, di + g.oW() + k}, x.ievals, c.alns[x.aln].judge);
+        }
     for (int k = 0; k < na; ++k) {
         GraphAln& x = g.a[k];
         const DCount Kk{x.cap, di + g.oK() + k};
@@ -1482,7 +1508,9 @@ GraphRound* graph_create(Ctx& c, const std::vector<int>& ids, const std::vector<
         x.ssum = x.xf = x.yb = nullptr;
         x.xb = nullptr;
         x.init = nullptr;
+        x.ievals = nullptr;
         if (g.mlp) {
+            ar.add(x.ievals, (size_t)cap + 1);
             ar.add(x.ssum, (size_t)F * slots * 16);
             ar.add(x.xf, ((size_t)cap + 1) * kMlpIn);
             ar.addv(x.xb, ((size_t)cap + 64) * kMlpInPad * 2);
@@ -1536,6 +1564,7 @@ GraphRound* graph_create(Ctx& c, const std::vector<int>& ids, const std::vector<
         p.len5_out = x.len5;
         p.kept = x.kept;
         p.init = g.mlp ? x.init : nullptr;
+        p.evals_out = g.mlp ? x.ievals : nullptr;
         p.rates = nullptr;
         p.cost_out = x.icost;
         FullGroup& f = fg[k];
@@ -1552,6 +1581,7 @@ GraphRound* graph_create(Ctx& c, const std::vector<int>& ids, const std::vector<
             ck(c, cudaMalloc(&A.tip_sum, sizeof(float) * 16 * A.n), "alloc tip summaries");
             launch_tip_summary(c.stream, aln_dev(A), C, A.tip_sum);
         }
+        if (g.mlp) judge_of(c, A);
     }
     std::vector<PropGroup> pgo(na);
     std::vector<FullGroup> fgo(na);
@@ -1720,6 +1750,7 @@ void pt_destroy(pt_ctx* ctx) {
         if (a.w) cudaFree(a.w);
         if (a.table) cudaFree(a.table);
         if (a.tip_sum) cudaFree(a.tip_sum);
+        if (a.judge) cudaFree(a.judge);
     }
     for (void* p : {(void*)c.mlp_w, (void*)c.mlp_g, (void*)c.mlp_m1, (void*)c.mlp_m2, c.mlp.w1t, c.mlp.w2t, c.mlp.w3t,
                     c.mlp.w2r, c.mlp.w3r, (void*)c.log_x, (void*)c.log_t, (void*)c.log_count})
@@ -1798,6 +1829,7 @@ pt_status pt_set_model(pt_ctx* ctx, int aln_id, const double exch[6], const doub
         a.alpha = alpha;
         a.has_model = true;
         if (a.tip_sum) { cudaFree(a.tip_sum); a.tip_sum = nullptr; }
+        if (a.judge) ck(c, cudaMemsetAsync(a.judge, 0, sizeof(Judge), c.stream), "reset judge");  // a new model
     });
 }
 
@@ -2339,6 +2371,7 @@ pt_status pt_mlp_set_weights(pt_ctx* ctx, const float* w, size_t n) {
         ck(c, cudaStreamSynchronize(c.stream), "sync");
         c.adam_t = 0;
         c.mlp_ready = true;
+        reset_judges(c);
     });
 }
 
@@ -2410,6 +2443,7 @@ pt_status pt_mlp_train(pt_ctx* ctx, int steps, int batch, double lr, uint64_t se
             mlp_cast(c.stream, c.mlp, c.mlp_w);
         }
         if (final_loss) ck(c, cudaMemcpyAsync(final_loss, dl, 8, cudaMemcpyDeviceToHost, c.stream), "copy");
+        reset_judges(c);
         ck(c, cudaStreamSynchronize(c.stream), "sync");
     });
 }
@@ -2417,7 +2451,25 @@ pt_status pt_mlp_train(pt_ctx* ctx, int steps, int batch, double lr, uint64_t se
 pt_status pt_mlp_enable(pt_ctx* ctx, int on) {
     return guarded(ctx, [&](Ctx& c) {
         if (on && !c.mlp_ready) fail(c, PT_ERR_STATE, "no MLP weights (pt_mlp_set_weights)");
+        if (on && !c.mlp_on) reset_judges(c);
         c.mlp_on = on != 0;
+    });
+}
+
+pt_status pt_mlp_judge(pt_ctx* ctx, int aln_id, int64_t out[5]) {
+    return guarded(ctx, [&](Ctx& c) {
+        if (!out) fail(c, PT_ERR_INVALID_ARG, "null output");
+        AlnState& a = aln_of(c, aln_id, false);
+        Judge j{};
+        if (a.judge) {
+            ck(c, cudaMemcpyAsync(&j, a.judge, sizeof(Judge), cudaMemcpyDeviceToHost, c.stream), "copy judge");
+            ck(c, cudaStreamSynchronize(c.stream), "sync");
+        }
+        out[0] = (int64_t)j.items[0];
+        out[1] = (int64_t)j.evals[0];
+        out[2] = (int64_t)j.items[1];
+        out[3] = (int64_t)j.evals[1];
+        out[4] = j.state;
     });
 }
 

@@ -240,6 +240,7 @@ struct PropGroup {
     float* cost_out;         // per item: sum over the five branches of |ln(optimised / inherited length)|,
                              // the predictor of its full optimisation's cost; or null
     const double* init;      // learned starting lengths [count][5] or nullptr
+    int32_t* evals_out;      // per item: Newton evaluations of its proposal (judge of the learned start), or null
     const double* rates;     // per-frontier-tree category rates [tree][kMaxCat] (shape re-optimisation), or null
 };
 // One group of a batched full-optimisation launch: trees [first, first + n) of ts.
@@ -284,8 +285,32 @@ void launch_tip_summary(cudaStream_t s, Aln A, int C, float* out);
 // items [i0, i1): i1 may be a device count (i1.cap bounds it).
 void launch_item_features(cudaStream_t s, int n, const Item* items, int i0, DCount i1, TreeSet fr, int first,
                           const float* slot_sum, int nslot, const float* tip_sum, float* Xf, void* Xb);
+// Judge of the learned start, one per alignment (device): the Newton
+// evaluations and item counts of proposals started from the network [0] and
+// from the inherited lengths [1].  Items take the chosen start (the network
+// while state is kJudgeOpen or kJudgeLearned, the inherited lengths under
+// kJudgePlain) except every kJudgeEvery-th item of the alignment, the sample,
+// which takes the other one.  Whenever both groups hold kJudgeMin items the
+// network is chosen if it saves at least kJudgeMargin of the evaluations per
+// item, the inherited lengths otherwise, and the counts are halved (the choice
+// follows the recent rounds: a search's early rounds can favour one start and
+// its later rounds the other).
+struct Judge {
+    unsigned long long evals[2], items[2];
+    int state;
+    int pad;
+};
+enum { kJudgeOpen = 0, kJudgeLearned = 1, kJudgePlain = 2 };
+constexpr int kJudgeEvery = 16;
+constexpr unsigned long long kJudgeMin = 256;
+constexpr double kJudgeMargin = 0.02;
+
+// learned starting lengths of items [i0, i1) (NaN: keep the inherited length),
+// following the judge's state and sample
 void launch_item_init(cudaStream_t s, const Item* items, int i0, DCount i1, const float* Xf, const float* Y, double tmin,
-                      double tmax, double* init);
+                      double tmax, double* init, const Judge* judge);
+// folds one round's proposals of an alignment (items [0, count), evals per item) into its judge
+void launch_judge(cudaStream_t s, DCount count, const int32_t* evals, Judge* judge);
 void launch_log_pairs(cudaStream_t s, const Item* items, int i0, int i1, const float* Xf, const double* len5, float* LX,
                       float* LT, unsigned long long* count, size_t cap);
 

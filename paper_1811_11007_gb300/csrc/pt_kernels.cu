@@ -1348,6 +1348,7 @@ struct ProposeSmem {
     int mbr[4];          // branch of each member
     int bmem[5];         // member of each branch (-1: central)
     double ex5[5][4 * C];
+    int warm[5];         // branch b starts from a learned length (its P matrices are recomputed)
     int next, grp;       // work item taken from the counter, its group
     NewtonSmem<R, C> ns;
 };
@@ -1432,21 +1433,24 @@ __global__ void __launch_bounds__(512) k_propose(const PropGroup* __restrict__ g
         }
         if (threadIdx.x < 5) {
             double t0 = len[bnode[threadIdx.x]];
+            int warm = 0;
             if (G.init && (nb == 5 || threadIdx.x == 0)) {  // warm start of the optimised branches; NaN = keep
                 const double y = G.init[(size_t)o * 5 + threadIdx.x];
-                if (y == y) t0 = y;
+                if (y == y) { t0 = y; warm = 1; }
             }
             sm.T[threadIdx.x] = t0;
+            sm.warm[threadIdx.x] = warm;
         }
         __syncthreads();
-        if (G.init) {  // P matrices at the starting lengths
+        if (G.init) {  // P matrices at the learned starting lengths (the others are the parent's)
             for (int z = threadIdx.x; z < 5 * 4 * C; z += blockDim.x) {
                 const int b = z / (4 * C), q = z % (4 * C);
-                sm.ex5[b][q] = exp(M.lam[q & 3] * rr[q >> 2] * sm.T[b]);
+                if (sm.warm[b]) sm.ex5[b][q] = exp(M.lam[q & 3] * rr[q >> 2] * sm.T[b]);
             }
             __syncthreads();
             for (int z = threadIdx.x; z < 5 * 16 * C; z += blockDim.x) {
                 const int b = z / (16 * C), q = z % (16 * C), r = q >> 4, ij = q & 15;
+                if (!sm.warm[b]) continue;
                 double acc = 0.0;
 #pragma unroll
                 for (int k = 0; k < 4; ++k) acc += sm.ns.W[ij * 4 + k] * sm.ex5[b][r * 4 + k];
@@ -1455,7 +1459,7 @@ __global__ void __launch_bounds__(512) k_propose(const PropGroup* __restrict__ g
             __syncthreads();
         }
         double tlast = 0.0;  // length of the last branch solved (every thread)
-        int sweeps = 0;
+        int sweeps = 0, item_evals = 0;
         for (int sw = 0; sw < cfg.prop_max_sweeps; ++sw) {
             ++sweeps;
             double moved = 0.0;
@@ -1506,6 +1510,7 @@ __global__ void __launch_bounds__(512) k_propose(const PropGroup* __restrict__ g
                 const double t = newton_solve<R, C>(M, cfg, st, P, told, sm.ns, ev, conv, sm.Pm[b]);
                 moved = fmax(moved, fabs(t - told));
                 evals_total += ev;
+                item_evals += ev;
                 if (!conv) ++nonconv;
                 if (threadIdx.x == 0) sm.T[b] = t;  // read again only after later barriers
                 tlast = t;
@@ -1523,6 +1528,7 @@ __global__ void __launch_bounds__(512) k_propose(const PropGroup* __restrict__ g
                 f1 += (double)(NN - 1) * cfg.prior_log - cfg.prior_rate * sum;
             }
             G.lnl_out[o] = f1;
+            if (G.evals_out) G.evals_out[o] = item_evals;
             for (int b = 0; b < 5; ++b) G.len5_out[(size_t)o * 5 + b] = sm.T[b];
             if (G.cost_out) {  // how far the proposal moved the five lengths: predicts the visit's cost
                 float cst = 0.f;

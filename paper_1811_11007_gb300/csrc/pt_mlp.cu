@@ -491,10 +491,18 @@ __global__ void k_item_features(int n, const Item* items, int i0, DCount i1, Tre
     }
 }
 
+// Whether item k of an alignment starts from the network under judge state st:
+// the chosen start, except for the judge's sample (every kJudgeEvery-th item),
+// which takes the other one.
+__device__ __forceinline__ bool judge_learned(int st, int k) {
+    return (st != kJudgePlain) != (k % kJudgeEvery == 0);
+}
+
 // Warm starts [W][5] (branch order central, A, B, C, D) from predicted
-// log-ratios in member order; NaN marks "no prediction" (the inherited length is kept).
+// log-ratios in member order; NaN marks "no prediction" (the inherited length is
+// kept), as for every item the judge assigns the inherited start.
 __global__ void k_item_init(const Item* items, int i0, DCount i1, const float* Xf, const float* Y, double tmin,
-                            double tmax, double* init) {
+                            double tmax, double* init, const Judge* judge) {
     const int k = i0 + blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= dcount(i1)) return;
     const Item it = items[k];
@@ -502,9 +510,53 @@ __global__ void k_item_init(const Item* items, int i0, DCount i1, const float* X
     const float* y = Y + (size_t)(k - i0) * kOutP;
     const float* x = Xf + (size_t)(k - i0) * kIn;
     double* o = init + (size_t)(k - i0) * 5;
+    const bool plain = judge && !judge_learned(judge->state, k);
     for (int j = 0; j < 5; ++j) {
         const double t = exp((double)x[j] + (double)y[j]);
-        o[brn[j]] = (isfinite(t) && t >= tmin && t <= tmax) ? t : __longlong_as_double(0x7ff8000000000000ll);
+        o[brn[j]] = (!plain && isfinite(t) && t >= tmin && t <= tmax) ? t : __longlong_as_double(0x7ff8000000000000ll);
+    }
+}
+
+// One block: adds a round's proposals of one alignment to its judge (group 0
+// started from the network, group 1 from the inherited lengths); once both
+// groups hold kJudgeMin items it chooses the start for the next rounds and
+// halves its counts, so that the choice follows the recent rounds.
+__global__ void k_judge(DCount count, const int32_t* evals, Judge* judge) {
+    __shared__ unsigned long long red[4][32];
+    const int st = judge->state;  // the state this round's starts were assigned under
+    unsigned long long ev[2] = {0, 0}, it[2] = {0, 0};
+    const int cnt = dcount(count);
+    for (int k = threadIdx.x; k < cnt; k += blockDim.x) {
+        const int g = judge_learned(st, k) ? 0 : 1;
+        ev[g] += (unsigned long long)evals[k];
+        it[g] += 1;
+    }
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    unsigned long long v[4] = {ev[0], ev[1], it[0], it[1]};
+    for (int q = 0; q < 4; ++q) {
+        for (int o = 16; o; o >>= 1) v[q] += __shfl_xor_sync(0xffffffffu, v[q], o);
+        if (lane == 0) red[q][w] = v[q];
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int q = 0; q < 4; ++q) {
+            unsigned long long t = 0;
+            for (int i = 0; i < nw; ++i) t += red[q][i];
+            v[q] = t;
+        }
+        judge->evals[0] += v[0];
+        judge->evals[1] += v[1];
+        judge->items[0] += v[2];
+        judge->items[1] += v[3];
+        if (judge->items[0] >= kJudgeMin && judge->items[1] >= kJudgeMin) {
+            const double learned = (double)judge->evals[0] / (double)judge->items[0];
+            const double plain = (double)judge->evals[1] / (double)judge->items[1];
+            judge->state = learned <= (1.0 - kJudgeMargin) * plain ? kJudgeLearned : kJudgePlain;
+            for (int g = 0; g < 2; ++g) {
+                judge->evals[g] >>= 1;
+                judge->items[g] >>= 1;
+            }
+        }
     }
 }
 
@@ -625,9 +677,15 @@ void launch_item_features(cudaStream_t s, int n, const Item* items, int i0, DCou
 }
 
 void launch_item_init(cudaStream_t s, const Item* items, int i0, DCount i1, const float* Xf, const float* Y, double tmin,
-                      double tmax, double* init) {
+                      double tmax, double* init, const Judge* judge) {
     if (i1.cap <= i0) return;
-    k_item_init<<<nblk(i1.cap - i0, 128), 128, 0, s>>>(items, i0, i1, Xf, Y, tmin, tmax, init);
+    k_item_init<<<nblk(i1.cap - i0, 128), 128, 0, s>>>(items, i0, i1, Xf, Y, tmin, tmax, init, judge);
+    ++g_launches;
+}
+
+void launch_judge(cudaStream_t s, DCount count, const int32_t* evals, Judge* judge) {
+    if (count.cap <= 0 || !judge) return;
+    k_judge<<<1, 256, 0, s>>>(count, evals, judge);
     ++g_launches;
 }
 

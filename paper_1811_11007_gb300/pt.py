@@ -25,7 +25,7 @@ EXPORTS = ["pt_config_default", "pt_create", "pt_destroy", "pt_last_error", "pt_
            "pt_expand_frontier", "pt_expand_frontier_dev", "pt_visited", "pt_reset_visited", "pt_stats",
            "pt_last_proposals", "pt_stage_times", "pt_version", "pt_discrete_gamma", "pt_model_eigen",
            "pt_score_topologies_noalloc", "pt_mlp_set_weights", "pt_mlp_get_weights", "pt_mlp_forward",
-           "pt_mlp_loss_grad", "pt_mlp_train", "pt_mlp_enable", "pt_training_log", "pt_training_pairs",
+           "pt_mlp_loss_grad", "pt_mlp_train", "pt_mlp_enable", "pt_mlp_judge", "pt_training_log", "pt_training_pairs",
            "pt_expand_batch", "pt_expand_batch_dev", "pt_autotune", "pt_autotune_report", "pt_graph_create",
            "pt_graph_frontier_dev", "pt_graph_set_frontier", "pt_graph_run", "pt_graph_next_dev", "pt_graph_get_next",
            "pt_graph_advance", "pt_graph_destroy", "pt_split_frequencies", "pt_last_alphas"]
@@ -112,6 +112,7 @@ def lib():
             L.pt_mlp_loss_grad.argtypes = [_vp, C.c_int, _f32p, _f32p, C.POINTER(C.c_double), _f32p]
             L.pt_mlp_train.argtypes = [_vp, C.c_int, C.c_int, C.c_double, C.c_uint64, C.POINTER(C.c_double)]
             L.pt_mlp_enable.argtypes = [_vp, C.c_int]
+            L.pt_mlp_judge.argtypes = [_vp, C.c_int, C.POINTER(C.c_int64)]
             L.pt_training_log.argtypes = [_vp, C.c_int, C.c_size_t]
             L.pt_training_pairs.argtypes = [_vp, C.c_size_t, _vp, _vp, C.POINTER(C.c_size_t)]
             _ip = C.POINTER(C.c_int)
@@ -418,6 +419,13 @@ class Context:
 
     def mlp_enable(self, on: bool = True):
         self._ck(lib().pt_mlp_enable(self._h, 1 if on else 0))
+
+    def mlp_judge(self, aln: int) -> dict:
+        """The plain start's judgement of the network on an alignment (pt_mlp_judge)."""
+        out = (C.c_int64 * 5)()
+        self._ck(lib().pt_mlp_judge(self._h, aln, out))
+        return {"learned_items": out[0], "learned_evals": out[1], "plain_items": out[2], "plain_evals": out[3],
+                "state": ("open", "learned", "plain")[out[4]]}
 
     def training_log(self, on: bool = True, capacity: int = 1 << 20):
         self._ck(lib().pt_training_log(self._h, 1 if on else 0, capacity))
