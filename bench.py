@@ -46,7 +46,7 @@ N_TAXA, N_SITES, THRESH, N_STARTS = 27, 2000, 10.0, 8
 # DRAM bytes per unit of the two persistent kernels on this workload, from one ncu capture of each
 # (dram__bytes_read.sum + dram__bytes_write.sum of a 2055-neighbour / 375-tree launch, divided by
 # its units; profiles/k_propose_27taxa_925patterns.md, profiles/k_fullopt_27taxa_925patterns.md)
-DRAM_PER_NEIGHBOUR = 125.95e6 / 2055
+DRAM_PER_NEIGHBOUR = 126.28e6 / 2055
 DRAM_PER_KEPT_TREE = 12.488e9 / 375
 FP32_LANES_PER_SM = 128
 
