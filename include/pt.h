@@ -116,6 +116,20 @@ const char *pt_last_error(const pt_ctx *ctx);
  * the caller, e.g. PyTorch's current stream; NULL = the legacy stream). */
 pt_status pt_set_stream(pt_ctx *ctx, void *cuda_stream);
 
+/* Device memory from the caller (e.g. PyTorch's caching allocator): every
+ * later device allocation of the context -- visited tables, alignments,
+ * working buffers, graph rounds, network weights -- is alloc(bytes, user),
+ * which must return memory on the context's device aligned to 256 bytes, or
+ * NULL (the call then fails with PT_ERR_OOM).  A block is returned with the
+ * free function it was allocated under, free(ptr, user), after the
+ * context's stream has been synchronised (queued kernels may still read
+ * it); pt_destroy returns every block.  alloc = free = NULL goes back to
+ * cudaMalloc / cudaFree for later allocations.  Blocks allocated before the
+ * call keep their allocator.  (No counterpart in the paper: the framework's
+ * memory stays with the caller.) */
+pt_status pt_set_allocator(pt_ctx *ctx, void *(*alloc)(size_t bytes, void *user),
+                           void (*free_fn)(void *ptr, void *user), void *user);
+
 /* Copies an alignment, compresses identical columns into site patterns with
  * integer weights, and uploads it.  codes: [n_taxa][n_sites] bytes, 0..3 =
  * A C G T, 4 = gap / unknown (contributes an all-ones tip vector, i.e. the

@@ -14,6 +14,7 @@
 #include <cstring>
 #include <functional>
 #include <map>
+#include <unordered_map>
 #include <memory>
 #include <string>
 #include <vector>
@@ -45,6 +46,11 @@ struct AlnState {
 struct GraphRound;
 
 struct Ctx {
+    // caller's device allocator (pt_set_allocator); blocks it made, with their free function
+    void* (*ualloc)(size_t, void*) = nullptr;
+    void (*ufree)(void*, void*) = nullptr;
+    void* uarg = nullptr;
+    std::unordered_map<void*, std::pair<void (*)(void*, void*), void*>> ublocks;
     pt_config cfg{};
     std::vector<GraphRound*> graphs;  // graph rounds recorded on this context
     cudaStream_t stream = nullptr;
@@ -115,6 +121,36 @@ void ck(Ctx& c, cudaError_t e, const char* what) {
     }
 }
 
+// Device memory of the context: the caller's allocator when set, else cudaMalloc.
+void* dev_alloc(Ctx& c, size_t bytes, const char* what) {
+    void* p = nullptr;
+    if (c.ualloc) {
+        p = c.ualloc(bytes, c.uarg);
+        if (!p) fail(c, PT_ERR_OOM, "%s: the caller's allocator returned no memory (%zu bytes)", what, bytes);
+        c.ublocks[p] = {c.ufree, c.uarg};
+        return p;
+    }
+    ck(c, cudaMalloc(&p, bytes), what);
+    return p;
+}
+template <typename T>
+void dev_alloc(Ctx& c, T** out, size_t bytes, const char* what) {
+    *out = reinterpret_cast<T*>(dev_alloc(c, bytes, what));
+}
+// Returns a block to the allocator it came from (a caller's block only once the
+// context's stream has drained: queued kernels may still read it).
+void dev_free(Ctx& c, void* p) {
+    if (!p) return;
+    auto it = c.ublocks.find(p);
+    if (it == c.ublocks.end()) {
+        cudaFree(p);
+        return;
+    }
+    cudaStreamSynchronize(c.stream);
+    it->second.first(p, it->second.second);
+    c.ublocks.erase(it);
+}
+
 // Grow-only named device buffer.  cudaFree synchronises the device, so a
 // buffer still referenced by queued kernels is never released early.
 template <typename T>
@@ -122,11 +158,11 @@ T* buf(Ctx& c, const std::string& name, size_t count) {
     DevBuf& b = c.bufs[name];
     size_t bytes = std::max<size_t>(count * sizeof(T), 16);
     if (b.n < bytes) {
-        if (b.p) cudaFree(b.p);
+        if (b.p) dev_free(c, b.p);
         b.p = nullptr;
         b.n = 0;
         size_t nb = bytes + bytes / 4;
-        ck(c, cudaMalloc(&b.p, nb), ("allocating " + name).c_str());
+        b.p = dev_alloc(c, nb, ("allocating " + name).c_str());
         b.n = nb;
     }
     return reinterpret_cast<T*>(b.p);
@@ -180,7 +216,7 @@ Aln aln_dev(const AlnState& a) { return Aln{a.n, a.P, a.tips, a.w}; }
 // The judge of the learned start on an alignment (allocated open on first use).
 Judge* judge_of(Ctx& c, AlnState& a) {
     if (!a.judge) {
-        ck(c, cudaMalloc(&a.judge, sizeof(Judge)), "alloc judge");
+        dev_alloc(c, &a.judge, sizeof(Judge), "alloc judge");
         ck(c, cudaMemsetAsync(a.judge, 0, sizeof(Judge), c.stream), "reset judge");
     }
     return a.judge;
@@ -729,9 +765,9 @@ struct RoundOut {
 // Allocates (first use) and clears the visited table of an alignment.
 void reset_table(Ctx& c, AlnState& a) {
     if (!a.table || a.log2 != c.cfg.table_log2) {
-        if (a.table) cudaFree(a.table);
+        if (a.table) dev_free(c, a.table);
         a.table = nullptr;
-        ck(c, cudaMalloc(&a.table, sizeof(Slot) << c.cfg.table_log2), "allocating visited table");
+        dev_alloc(c, &a.table, sizeof(Slot) << c.cfg.table_log2, "allocating visited table");
         a.log2 = c.cfg.table_log2;
     }
     launch_table_init(c.stream, a.table, (size_t)1 << a.log2);
@@ -982,7 +1018,7 @@ void expand_batch(Ctx& c, const std::vector<RoundIn>& ins, std::vector<RoundOut>
             if (feats) {
                 const int nslot = 2 * a.n - 5;
                 if (!a.tip_sum) {
-                    ck(c, cudaMalloc(&a.tip_sum, sizeof(float) * 16 * a.n), "alloc tip summaries");
+                    dev_alloc(c, &a.tip_sum, sizeof(float) * 16 * a.n, "alloc tip summaries");
                     launch_tip_summary(c.stream, aln_dev(a), C, a.tip_sum);
                 }
                 float* ssum = buf<float>(c, "mlp.ssum", (size_t)ch.cnt * nslot * 16);
@@ -1328,11 +1364,11 @@ void arena_treeset(Arena& ar, TreeSet& t, int n, int cap, bool with_emap) {
     else t.emap = nullptr;
 }
 
-void graph_free(GraphRound* g) {
+void graph_free(Ctx& c, GraphRound* g) {
     if (!g) return;
     if (g->exec) cudaGraphExecDestroy(g->exec);
     if (g->cs) cudaStreamDestroy(g->cs);
-    if (g->mem) cudaFree(g->mem);
+    if (g->mem) dev_free(c, g->mem);
     if (g->hi) cudaFreeHost(g->hi);
     if (g->hl) cudaFreeHost(g->hl);
     delete g;
@@ -1417,7 +1453,8 @@ void graph_record(Ctx& c, GraphRound& g, cudaStream_t s, int C, int maxN, int ma
 GraphRound* graph_create(Ctx& c, const std::vector<int>& ids, const std::vector<int>& caps,
                          const std::vector<double>& thrs) {
     const int na = (int)ids.size(), prec = c.cfg.precision;
-    std::unique_ptr<GraphRound, void (*)(GraphRound*)> own(new GraphRound, graph_free);
+    auto del = [&c](GraphRound* r) { graph_free(c, r); };
+    std::unique_ptr<GraphRound, decltype(del)> own(new GraphRound, del);
     GraphRound& g = *own;
     g.na = na;
     g.a.resize(na);
@@ -1526,7 +1563,7 @@ GraphRound* graph_create(Ctx& c, const std::vector<int>& ids, const std::vector<
     if (pspc) ar.addv(g.prop_scratch, pspc * pgrid);
     if (fspc) ar.addv(g.full_scratch, fspc * fgrid);
     ar.add(g.slab, slab_stride * fgrid);
-    ck(c, cudaMalloc(&g.mem, ar.total()), "allocating the graph round's buffers");
+    dev_alloc(c, &g.mem, ar.total(), "allocating the graph round's buffers");
     ar.carve(g.mem);
     ck(c, cudaHostAlloc(reinterpret_cast<void**>(&g.hi), sizeof(int) * g.nints(), cudaHostAllocDefault), "pinned");
     ck(c, cudaHostAlloc(reinterpret_cast<void**>(&g.hl), sizeof(double) * na, cudaHostAllocDefault), "pinned");
@@ -1578,7 +1615,7 @@ GraphRound* graph_create(Ctx& c, const std::vector<int>& ids, const std::vector<
         f.rates = nullptr;
         f.order = x.ord;
         if (g.mlp && !A.tip_sum) {
-            ck(c, cudaMalloc(&A.tip_sum, sizeof(float) * 16 * A.n), "alloc tip summaries");
+            dev_alloc(c, &A.tip_sum, sizeof(float) * 16 * A.n, "alloc tip summaries");
             launch_tip_summary(c.stream, aln_dev(A), C, A.tip_sum);
         }
         if (g.mlp) judge_of(c, A);
@@ -1722,9 +1759,9 @@ pt_status pt_create(pt_ctx** out, const pt_config* cfg) {
         ck(c, cudaGetDeviceProperties(&prop, c.cfg.device), "cudaGetDeviceProperties");
         c.sm_count = prop.multiProcessorCount;
         c.smem_optin = prop.sharedMemPerBlockOptin;
-        ck(c, cudaMalloc(&c.d_err, sizeof(int32_t) * kErrWords), "alloc");
-        ck(c, cudaMalloc(&c.d_stats, sizeof(unsigned long long) * kStWords), "alloc");
-        ck(c, cudaMalloc(&c.d_lmax, 8), "alloc");
+        dev_alloc(c, &c.d_err, sizeof(int32_t) * kErrWords, "alloc");
+        dev_alloc(c, &c.d_stats, sizeof(unsigned long long) * kStWords, "alloc");
+        dev_alloc(c, &c.d_lmax, 8, "alloc");
         ck(c, cudaMemset(c.d_err, 0, sizeof(int32_t) * kErrWords), "memset");
         size_t fr, tot;
         ck(c, cudaMemGetInfo(&fr, &tot), "cudaMemGetInfo");
@@ -1742,22 +1779,22 @@ void pt_destroy(pt_ctx* ctx) {
     Ctx& c = ctx->c;
     cudaSetDevice(c.cfg.device);
     if (c.stream) cudaStreamSynchronize(c.stream);
-    for (GraphRound* g : c.graphs) graph_free(g);
+    for (GraphRound* g : c.graphs) graph_free(c, g);
     c.graphs.clear();
-    for (auto& kv : c.bufs) if (kv.second.p) cudaFree(kv.second.p);
+    for (auto& kv : c.bufs) if (kv.second.p) dev_free(c, kv.second.p);
     for (auto& a : c.alns) {
-        if (a.tips) cudaFree(a.tips);
-        if (a.w) cudaFree(a.w);
-        if (a.table) cudaFree(a.table);
-        if (a.tip_sum) cudaFree(a.tip_sum);
-        if (a.judge) cudaFree(a.judge);
+        if (a.tips) dev_free(c, a.tips);
+        if (a.w) dev_free(c, a.w);
+        if (a.table) dev_free(c, a.table);
+        if (a.tip_sum) dev_free(c, a.tip_sum);
+        if (a.judge) dev_free(c, a.judge);
     }
     for (void* p : {(void*)c.mlp_w, (void*)c.mlp_g, (void*)c.mlp_m1, (void*)c.mlp_m2, c.mlp.w1t, c.mlp.w2t, c.mlp.w3t,
                     c.mlp.w2r, c.mlp.w3r, (void*)c.log_x, (void*)c.log_t, (void*)c.log_count})
-        if (p) cudaFree(p);
-    if (c.d_err) cudaFree(c.d_err);
-    if (c.d_stats) cudaFree(c.d_stats);
-    if (c.d_lmax) cudaFree(c.d_lmax);
+        if (p) dev_free(c, p);
+    if (c.d_err) dev_free(c, c.d_err);
+    if (c.d_stats) dev_free(c, c.d_stats);
+    if (c.d_lmax) dev_free(c, c.d_lmax);
     for (auto& e : c.evpool) cudaEventDestroy(e);
     delete ctx;
 }
@@ -1766,6 +1803,15 @@ const char* pt_last_error(const pt_ctx* ctx) { return ctx ? ctx->c.err.c_str() :
 
 pt_status pt_set_stream(pt_ctx* ctx, void* stream) {
     return guarded(ctx, [&](Ctx& c) { c.stream = reinterpret_cast<cudaStream_t>(stream); });
+}
+
+pt_status pt_set_allocator(pt_ctx* ctx, void* (*alloc)(size_t, void*), void (*free_fn)(void*, void*), void* user) {
+    return guarded(ctx, [&](Ctx& c) {
+        if ((alloc == nullptr) != (free_fn == nullptr)) fail(c, PT_ERR_INVALID_ARG, "alloc and free_fn go together");
+        c.ualloc = alloc;
+        c.ufree = free_fn;
+        c.uarg = alloc ? user : nullptr;
+    });
 }
 
 pt_status pt_load_alignment(pt_ctx* ctx, int n_taxa, int n_sites, const uint8_t* codes, int* aln_id) {
@@ -1800,8 +1846,8 @@ pt_status pt_load_alignment(pt_ctx* ctx, int n_taxa, int n_sites, const uint8_t*
         a.n = n_taxa;
         a.sites = n_sites;
         a.P = P;
-        ck(c, cudaMalloc(&a.tips, tips.size()), "alloc tips");
-        ck(c, cudaMalloc(&a.w, 4 * (size_t)P), "alloc weights");
+        dev_alloc(c, &a.tips, tips.size(), "alloc tips");
+        dev_alloc(c, &a.w, 4 * (size_t)P, "alloc weights");
         ck(c, cudaMemcpy(a.tips, tips.data(), tips.size(), cudaMemcpyHostToDevice), "copy tips");
         ck(c, cudaMemcpy(a.w, w.data(), 4 * (size_t)P, cudaMemcpyHostToDevice), "copy weights");
         c.alns.push_back(a);
@@ -1828,7 +1874,7 @@ pt_status pt_set_model(pt_ctx* ctx, int aln_id, const double exch[6], const doub
         a.M = M;
         a.alpha = alpha;
         a.has_model = true;
-        if (a.tip_sum) { cudaFree(a.tip_sum); a.tip_sum = nullptr; }
+        if (a.tip_sum) { dev_free(c, a.tip_sum); a.tip_sum = nullptr; }
         if (a.judge) ck(c, cudaMemsetAsync(a.judge, 0, sizeof(Judge), c.stream), "reset judge");  // a new model
     });
 }
@@ -2107,7 +2153,7 @@ pt_status pt_graph_destroy(pt_ctx* ctx, pt_graph* g) {
         GraphRound* r = graph_of(c, g);
         if (c.stream) cudaStreamSynchronize(c.stream);
         c.graphs.erase(std::find(c.graphs.begin(), c.graphs.end(), r));
-        graph_free(r);
+        graph_free(c, r);
     });
 }
 
@@ -2316,15 +2362,15 @@ pt_status pt_stage_times(pt_ctx* ctx, double* ms, int cap) {
 namespace {
 void mlp_alloc(Ctx& c) {
     if (c.mlp_w) return;
-    ck(c, cudaMalloc(&c.mlp_w, sizeof(float) * kMlpParams), "alloc mlp");
-    ck(c, cudaMalloc(&c.mlp_g, sizeof(float) * kMlpParams), "alloc mlp");
-    ck(c, cudaMalloc(&c.mlp_m1, sizeof(float) * kMlpParams), "alloc mlp");
-    ck(c, cudaMalloc(&c.mlp_m2, sizeof(float) * kMlpParams), "alloc mlp");
-    ck(c, cudaMalloc(&c.mlp.w1t, 2 * kMlpHidden * kMlpInPad), "alloc mlp");
-    ck(c, cudaMalloc(&c.mlp.w2t, 2 * kMlpHidden * kMlpHidden), "alloc mlp");
-    ck(c, cudaMalloc(&c.mlp.w3t, 2 * kMlpOutPad * kMlpHidden), "alloc mlp");
-    ck(c, cudaMalloc(&c.mlp.w2r, 2 * kMlpHidden * kMlpHidden), "alloc mlp");
-    ck(c, cudaMalloc(&c.mlp.w3r, 2 * kMlpHidden * kMlpOutPad), "alloc mlp");
+    dev_alloc(c, &c.mlp_w, sizeof(float) * kMlpParams, "alloc mlp");
+    dev_alloc(c, &c.mlp_g, sizeof(float) * kMlpParams, "alloc mlp");
+    dev_alloc(c, &c.mlp_m1, sizeof(float) * kMlpParams, "alloc mlp");
+    dev_alloc(c, &c.mlp_m2, sizeof(float) * kMlpParams, "alloc mlp");
+    dev_alloc(c, &c.mlp.w1t, 2 * kMlpHidden * kMlpInPad, "alloc mlp");
+    dev_alloc(c, &c.mlp.w2t, 2 * kMlpHidden * kMlpHidden, "alloc mlp");
+    dev_alloc(c, &c.mlp.w3t, 2 * kMlpOutPad * kMlpHidden, "alloc mlp");
+    dev_alloc(c, &c.mlp.w2r, 2 * kMlpHidden * kMlpHidden, "alloc mlp");
+    dev_alloc(c, &c.mlp.w3r, 2 * kMlpHidden * kMlpOutPad, "alloc mlp");
     c.mlp.b1 = c.mlp_w + kOffB1;
     c.mlp.b2 = c.mlp_w + kOffB2;
     c.mlp.b3 = c.mlp_w + kOffB3;
@@ -2477,13 +2523,13 @@ pt_status pt_training_log(pt_ctx* ctx, int on, size_t capacity) {
     return guarded(ctx, [&](Ctx& c) {
         if (on && capacity == 0) fail(c, PT_ERR_INVALID_ARG, "zero capacity");
         if (on && capacity != c.log_cap) {
-            for (void* p : {(void*)c.log_x, (void*)c.log_t}) if (p) cudaFree(p);
+            for (void* p : {(void*)c.log_x, (void*)c.log_t}) if (p) dev_free(c, p);
             c.log_x = nullptr;
             c.log_t = nullptr;
             c.log_cap = 0;
-            ck(c, cudaMalloc(&c.log_x, sizeof(float) * kMlpIn * capacity), "alloc log");
-            ck(c, cudaMalloc(&c.log_t, sizeof(float) * kMlpOut * capacity), "alloc log");
-            if (!c.log_count) ck(c, cudaMalloc(&c.log_count, 8), "alloc log");
+            dev_alloc(c, &c.log_x, sizeof(float) * kMlpIn * capacity, "alloc log");
+            dev_alloc(c, &c.log_t, sizeof(float) * kMlpOut * capacity, "alloc log");
+            if (!c.log_count) dev_alloc(c, &c.log_count, 8, "alloc log");
             ck(c, cudaMemsetAsync(c.log_count, 0, 8, c.stream), "memset");
             c.log_cap = capacity;
         }

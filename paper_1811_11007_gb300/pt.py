@@ -20,7 +20,8 @@ PROPOSE_FIVE, PROPOSE_CENTRAL, PROPOSE_FULL = 0, 1, 2
 ST_REJECTED, ST_GOOD, ST_BAD = 1, 2, 3
 STATUS = {0: "OK", 1: "INVALID_ARG", 2: "OOM", 3: "TABLE_FULL", 4: "BUFFER_TOO_SMALL", 5: "CUDA", 6: "TIMEOUT",
           7: "STATE"}
-EXPORTS = ["pt_config_default", "pt_create", "pt_destroy", "pt_last_error", "pt_set_stream", "pt_load_alignment",
+EXPORTS = ["pt_config_default", "pt_create", "pt_destroy", "pt_last_error", "pt_set_stream", "pt_set_allocator",
+           "pt_load_alignment",
            "pt_alignment_info", "pt_set_model", "pt_model_rates", "pt_score_topologies", "pt_begin",
            "pt_expand_frontier", "pt_expand_frontier_dev", "pt_visited", "pt_reset_visited", "pt_stats",
            "pt_last_proposals", "pt_stage_times", "pt_version", "pt_discrete_gamma", "pt_model_eigen",
@@ -63,6 +64,26 @@ _u8p = np.ctypeslib.ndpointer(np.uint8, flags="C_CONTIGUOUS")
 _vp = C.c_void_p
 
 
+_ALLOC_T = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p)
+_FREE_T = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p)
+
+
+def torch_allocator(device: int = 0, stream=None):
+    """(alloc, free) over PyTorch's caching allocator, for Context.set_allocator."""
+    import torch
+
+    def alloc(nbytes):
+        try:
+            return torch.cuda.caching_allocator_alloc(nbytes, device, stream)
+        except RuntimeError:  # out of memory: the library reports PT_ERR_OOM
+            return 0
+
+    def free(ptr):
+        torch.cuda.caching_allocator_delete(ptr)
+
+    return alloc, free
+
+
 def library_path() -> str:
     return _build.LIB
 
@@ -82,6 +103,7 @@ def lib():
             L.pt_last_error.restype = C.c_char_p
             L.pt_last_error.argtypes = [_vp]
             L.pt_set_stream.argtypes = [_vp, _vp]
+            L.pt_set_allocator.argtypes = [_vp, _ALLOC_T, _FREE_T, _vp]
             L.pt_load_alignment.argtypes = [_vp, C.c_int, C.c_int, _u8p, C.POINTER(C.c_int)]
             L.pt_alignment_info.argtypes = [_vp, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int)]
             L.pt_set_model.argtypes = [_vp, C.c_int, _f64p, _f64p, C.c_double, C.c_int]
@@ -196,6 +218,7 @@ class Context:
             raise PTError(st, "pt_create failed")
         self._h = h
         self._n = {}
+        self._alloc_cb = None
         if stream is not None:
             self.set_stream(stream)
 
@@ -216,6 +239,18 @@ class Context:
     def _ck(self, st):
         if st:
             raise PTError(st, lib().pt_last_error(self._h).decode())
+
+    def set_allocator(self, alloc=None, free=None):
+        """Device memory from the caller (pt_set_allocator): alloc(nbytes) -> device
+        pointer (0 = out of memory), free(ptr); None, None = back to cudaMalloc."""
+        if alloc is None:
+            self._ck(lib().pt_set_allocator(self._h, _ALLOC_T(), _FREE_T(), None))
+            return
+        ca = _ALLOC_T(lambda n, user: alloc(n) or None)
+        cf = _FREE_T(lambda p, user: free(p))
+        self._ck(lib().pt_set_allocator(self._h, ca, cf, None))
+        # callbacks stay referenced for as long as blocks made under them can be returned
+        self._alloc_cb = (self._alloc_cb or ()) + (ca, cf)
 
     def set_stream(self, stream):
         """stream: a torch.cuda.Stream, an int handle, or None."""
