@@ -54,7 +54,8 @@ FP32_LANES_PER_SM = 128
 def parse():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
-    p.add_argument("--steps", type=int, default=5)
+    p.add_argument("--steps", type=int, default=None,
+                   help="timed steps (default: 50 for round27, ~1 s of timed work; 5 for batch16; 3 for the oracle)")
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--frontier", type=int, default=256)
@@ -65,7 +66,10 @@ def parse():
     p.add_argument("--cpu-sample", type=int, default=0, help="frontier trees in the CPU baseline sample (0: one per thread)")
     p.add_argument("--cpu-threads", type=int, default=0, help="threads of the CPU baseline (0: all cores)")
     p.add_argument("--workload", default="round27", choices=["round27", "batch16"])
-    return p.parse_args()
+    args = p.parse_args()
+    if args.steps is None:  # about a second of timed GPU work; the oracle's steps take ~10 s each
+        args.steps = 3 if args.impl == "reference" else (5 if args.workload == "batch16" else 50)
+    return args
 
 
 def peaks():
@@ -91,6 +95,12 @@ class ClockSampler:
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
+            # the sampler is live before the timed work starts: wait for its first
+            # line (at most 5 s) and keep only the samples taken after it
+            t0 = time.time()
+            while not self.rows and time.time() - t0 < 5.0 and self.proc.poll() is None:
+                time.sleep(0.01)
+            self.rows.clear()
         except Exception:
             self.proc = None
         return self
