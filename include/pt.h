@@ -380,16 +380,18 @@ pt_status pt_mlp_train(pt_ctx *ctx, int steps, int batch, double lr, uint64_t se
 /* Uses (1) or stops using (0) the network as the proposal warm start.
  * The plain start stays the judge of the network on each alignment: the
  * proposals of an alignment take the chosen start (first the network),
- * except every 16th one (by its index in the round), which takes the other
- * start, and the Newton evaluations of the two groups are counted on the
- * device after every proposal launch (batched and graph rounds alike).
- * Whenever both groups hold 256 proposals, the network is chosen for the
- * following rounds if it needs at least 2 % fewer evaluations per proposal
- * than the inherited lengths, the inherited lengths otherwise, and the counts
- * are halved, so the choice follows the search as its trees change.  Either
- * start gives the same optimum to the Newton tolerance.  Turning the network
- * on, new weights and training reset every judge; a new model (pt_set_model)
- * resets its alignment's. */
+ * except a sample -- every 4th proposal (by its index in the round) until the
+ * first decision, every 16th after it -- which takes the other start, and the
+ * Newton evaluations of the two groups are counted on the device after every
+ * proposal launch (batched and graph rounds alike).  The network is chosen
+ * for the following rounds if it needs more than 2 % fewer evaluations per
+ * proposal than the inherited lengths, the inherited lengths otherwise:
+ * decided as soon as a Welch t statistic of that difference reaches 3 (at
+ * least 32 proposals per group), else on the means once both groups hold
+ * 256; each decision halves the counts, so the choice follows the search as
+ * its trees change.  Either start gives the same optimum to the Newton
+ * tolerance.  Turning the network on, new weights and training reset every
+ * judge; a new model (pt_set_model) resets its alignment's. */
 pt_status pt_mlp_enable(pt_ctx *ctx, int on);
 /* Judge of the learned start on an alignment: out[0] proposals started from
  * the network and out[1] their Newton evaluations, out[2] proposals started

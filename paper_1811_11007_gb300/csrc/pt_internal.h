@@ -286,24 +286,30 @@ void launch_tip_summary(cudaStream_t s, Aln A, int C, float* out);
 void launch_item_features(cudaStream_t s, int n, const Item* items, int i0, DCount i1, TreeSet fr, int first,
                           const float* slot_sum, int nslot, const float* tip_sum, float* Xf, void* Xb);
 // Judge of the learned start, one per alignment (device): the Newton
-// evaluations and item counts of proposals started from the network [0] and
-// from the inherited lengths [1].  Items take the chosen start (the network
-// while state is kJudgeOpen or kJudgeLearned, the inherited lengths under
-// kJudgePlain) except every kJudgeEvery-th item of the alignment, the sample,
-// which takes the other one.  Whenever both groups hold kJudgeMin items the
-// network is chosen if it saves at least kJudgeMargin of the evaluations per
-// item, the inherited lengths otherwise, and the counts are halved (the choice
-// follows the recent rounds: a search's early rounds can favour one start and
-// its later rounds the other).
+// evaluations (sum, sum of squares) and item counts of proposals started from
+// the network [0] and from the inherited lengths [1].  Items take the chosen
+// start (the network while state is kJudgeOpen or kJudgeLearned, the inherited
+// lengths under kJudgePlain) except the sample, which takes the other one:
+// every kJudgeEveryOpen-th item of the alignment before the first decision,
+// every kJudgeEvery-th after it.  The network is chosen when it saves more
+// than kJudgeMargin of the evaluations per item, the inherited lengths when it
+// does not: decided as soon as a Welch t statistic of that difference reaches
+// kJudgeT (both groups >= kJudgeMinT items), or on the means once both hold
+// kJudgeMin.  Each decision halves the counts (the choice follows the recent
+// rounds: a search's early rounds can favour one start and its later rounds
+// the other).
 struct Judge {
-    unsigned long long evals[2], items[2];
+    unsigned long long evals[2], items[2], sq[2];
     int state;
     int pad;
 };
 enum { kJudgeOpen = 0, kJudgeLearned = 1, kJudgePlain = 2 };
+constexpr int kJudgeEveryOpen = 4;
 constexpr int kJudgeEvery = 16;
+constexpr unsigned long long kJudgeMinT = 32;
 constexpr unsigned long long kJudgeMin = 256;
 constexpr double kJudgeMargin = 0.02;
+constexpr double kJudgeT = 3.0;
 
 // learned starting lengths of items [i0, i1) (NaN: keep the inherited length),
 // following the judge's state and sample

@@ -492,10 +492,10 @@ __global__ void k_item_features(int n, const Item* items, int i0, DCount i1, Tre
 }
 
 // Whether item k of an alignment starts from the network under judge state st:
-// the chosen start, except for the judge's sample (every kJudgeEvery-th item),
-// which takes the other one.
+// the chosen start, except for the judge's sample, which takes the other one.
 __device__ __forceinline__ bool judge_learned(int st, int k) {
-    return (st != kJudgePlain) != (k % kJudgeEvery == 0);
+    const bool sample = k % (st == kJudgeOpen ? kJudgeEveryOpen : kJudgeEvery) == 0;
+    return (st != kJudgePlain) != sample;
 }
 
 // Warm starts [W][5] (branch order central, A, B, C, D) from predicted
@@ -518,45 +518,56 @@ __global__ void k_item_init(const Item* items, int i0, DCount i1, const float* X
 }
 
 // One block: adds a round's proposals of one alignment to its judge (group 0
-// started from the network, group 1 from the inherited lengths); once both
-// groups hold kJudgeMin items it chooses the start for the next rounds and
-// halves its counts, so that the choice follows the recent rounds.
+// started from the network, group 1 from the inherited lengths) and, when the
+// evidence suffices, chooses the start for the next rounds and halves its
+// counts, so that the choice follows the recent rounds.
 __global__ void k_judge(DCount count, const int32_t* evals, Judge* judge) {
-    __shared__ unsigned long long red[4][32];
+    __shared__ unsigned long long red[6][32];
     const int st = judge->state;  // the state this round's starts were assigned under
-    unsigned long long ev[2] = {0, 0}, it[2] = {0, 0};
+    unsigned long long v[6] = {0, 0, 0, 0, 0, 0};  // evals, items, squares per group
     const int cnt = dcount(count);
     for (int k = threadIdx.x; k < cnt; k += blockDim.x) {
         const int g = judge_learned(st, k) ? 0 : 1;
-        ev[g] += (unsigned long long)evals[k];
-        it[g] += 1;
+        const unsigned long long e = (unsigned long long)evals[k];
+        v[g] += e;
+        v[2 + g] += 1;
+        v[4 + g] += e * e;
     }
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    unsigned long long v[4] = {ev[0], ev[1], it[0], it[1]};
-    for (int q = 0; q < 4; ++q) {
+    for (int q = 0; q < 6; ++q) {
         for (int o = 16; o; o >>= 1) v[q] += __shfl_xor_sync(0xffffffffu, v[q], o);
         if (lane == 0) red[q][w] = v[q];
     }
     __syncthreads();
-    if (threadIdx.x == 0) {
-        for (int q = 0; q < 4; ++q) {
-            unsigned long long t = 0;
-            for (int i = 0; i < nw; ++i) t += red[q][i];
-            v[q] = t;
-        }
-        judge->evals[0] += v[0];
-        judge->evals[1] += v[1];
-        judge->items[0] += v[2];
-        judge->items[1] += v[3];
-        if (judge->items[0] >= kJudgeMin && judge->items[1] >= kJudgeMin) {
-            const double learned = (double)judge->evals[0] / (double)judge->items[0];
-            const double plain = (double)judge->evals[1] / (double)judge->items[1];
-            judge->state = learned <= (1.0 - kJudgeMargin) * plain ? kJudgeLearned : kJudgePlain;
-            for (int g = 0; g < 2; ++g) {
-                judge->evals[g] >>= 1;
-                judge->items[g] >>= 1;
-            }
-        }
+    if (threadIdx.x != 0) return;
+    for (int q = 0; q < 6; ++q) {
+        unsigned long long t = 0;
+        for (int i = 0; i < nw; ++i) t += red[q][i];
+        v[q] = t;
+    }
+    Judge& J = *judge;
+    for (int g = 0; g < 2; ++g) {
+        J.evals[g] += v[g];
+        J.items[g] += v[2 + g];
+        J.sq[g] += v[4 + g];
+    }
+    const double n0 = (double)J.items[0], n1 = (double)J.items[1];
+    if (J.items[0] < kJudgeMinT || J.items[1] < kJudgeMinT) return;
+    const double m0 = J.evals[0] / n0, m1 = J.evals[1] / n1;
+    const double s0 = fmax((J.sq[0] - n0 * m0 * m0) / (n0 - 1.0), 0.0), s1 = fmax((J.sq[1] - n1 * m1 * m1) / (n1 - 1.0), 0.0);
+    const double k = 1.0 - kJudgeMargin;
+    // d > 0: the network saves more than the margin
+    const double d = k * m1 - m0, se = sqrt(s0 / n0 + k * k * s1 / n1);
+    int next = -1;
+    if (se > 0.0 && d >= kJudgeT * se) next = kJudgeLearned;
+    else if (se > 0.0 && -d >= kJudgeT * se) next = kJudgePlain;
+    else if (J.items[0] >= kJudgeMin && J.items[1] >= kJudgeMin) next = d >= 0.0 ? kJudgeLearned : kJudgePlain;
+    if (next < 0) return;
+    J.state = next;
+    for (int g = 0; g < 2; ++g) {
+        J.evals[g] >>= 1;
+        J.items[g] >>= 1;
+        J.sq[g] >>= 1;
     }
 }
 

@@ -2,8 +2,8 @@
 benchmarked round (27 taxa x 2000 sites, ~5400 proposals per round, so the
 judge decides after every round): the trained network is chosen; a network
 made harmful (its output layer scaled up 10x: far-off starting lengths) is
-dropped after one round.  Every 16th proposal takes the start not chosen (the
-judge's sample), so once the harmful network is dropped each proposal outside
+dropped after one round.  Every 4th proposal before the judge's first decision,
+every 16th after it, takes the start not chosen (the judge's sample), so once the harmful network is dropped each proposal outside
 the sample equals the round without the network bit for bit; decisions are
 identical throughout, in batched rounds and in graph replays."""
 import numpy as np
@@ -58,7 +58,7 @@ def test_judge_keeps_a_helpful_network_and_drops_a_harmful_one():
         j = ctx.mlp_judge(aid)
         print("trained network (counts halved at the decision):", j)
         assert j["state"] == "learned"
-        assert j["plain_items"] == ((W + 15) // 16) >> 1 and j["learned_items"] == (W - (W + 15) // 16) >> 1
+        assert j["plain_items"] == ((W + 3) // 4) >> 1 and j["learned_items"] == (W - (W + 3) // 4) >> 1
         assert abs(2 * (j["plain_evals"] + j["learned_evals"]) - st_t["prop_evals"]) <= 2
         assert j["learned_evals"] / j["learned_items"] < 0.98 * j["plain_evals"] / j["plain_items"]
         _decides_like(lm_t, nx_t, lm_p, nx_p)
