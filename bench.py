@@ -556,9 +556,16 @@ def cpu_baseline(a, front, lmax0, sample, threads):
         res = list(ex.map(one, range(k)))
     dt = time.perf_counter() - t0
     scored, kept = sum(r[0] for r in res), sum(r[1] for r in res)
+    # the same oracle on one core: the round of the first sample tree alone
+    t1 = time.perf_counter()
+    s1, k1 = one(0)
+    d1 = time.perf_counter() - t1
     return {"value": scored / dt, "unit": "topologies/s", "cores": min(threads, k), "kind": "oracle",
             "sample": f"one PT round on each of {k} frontier trees ({scored} neighbours scored, {kept} fully "
-                      f"optimised) in {dt:.1f} s on {min(threads, k)} threads"}
+                      f"optimised) in {dt:.1f} s on {min(threads, k)} threads",
+            "single_thread": {"value": s1 / d1, "unit": "topologies/s", "cores": 1,
+                              "sample": f"one PT round on frontier tree 0 ({s1} neighbours scored, {k1} fully "
+                                        f"optimised) in {d1:.1f} s on 1 thread"}}
 
 
 def run_reference(args, rank, world):
