@@ -26,9 +26,11 @@
  *
  * Parity status: every function here is pinned by a CPU test (closed forms,
  * brute force, library routines, invariants, the (2n-5)!! topology count),
- * except the finite-threshold visited sets and the proposal lengths, which the
- * paper gives no values for ("parity unpinned"; they are pinned only through
- * invariants and the oracle-vs-GPU comparison).
+ * except the finite-threshold visited sets and, beyond four taxa, the proposal
+ * lengths, which the paper gives no values for ("parity unpinned"; they are
+ * pinned only through invariants and the oracle-vs-GPU comparison).  On four
+ * taxa the five branches of a proposal are the whole tree, and the proposal
+ * is pinned to the likelihood maximum found by a library optimiser.
  */
 #include <math.h>
 #include <stdint.h>
