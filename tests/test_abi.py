@@ -1,6 +1,7 @@
 """Host-side checks of libpt that need no GPU: the library loads, exports
-every entry point pt.h declares, and its model set-up agrees with the oracle
-and with scipy."""
+every entry point pt.h declares, the binding declares each with the header's
+number of parameters, and its model set-up agrees with the oracle and with
+scipy."""
 import re
 import os
 
@@ -63,3 +64,43 @@ def test_invalid_gamma_rejected():
         pt.discrete_gamma(-1.0, 4)
     with pytest.raises(pt.PTError):
         pt.discrete_gamma(0.5, 9)
+
+
+def _prototypes():
+    """name -> number of parameters of every function prototype in pt.h."""
+    src = open(os.path.join(ROOT, "include", "pt.h")).read()
+    src = re.sub(r"/\*.*?\*/", " ", src, flags=re.S)
+    src = re.sub(r"//[^\n]*", " ", src)
+    out = {}
+    for m in re.finditer(r"\b(pt_[a-z_]+)\s*\(", src):
+        # a prototype: the name follows a return type, and the parameter list ends with ");"
+        head = src[:m.start()].rstrip()
+        if not re.search(r"(pt_status|void|int|char|size_t)\s*\*?$", head):
+            continue
+        depth, i = 1, m.end()
+        while depth:
+            depth += {"(": 1, ")": -1}.get(src[i], 0)
+            i += 1
+        if not src[i:].lstrip().startswith(";"):
+            continue
+        params = src[m.end():i - 1].strip()
+        if params in ("", "void"):
+            out[m.group(1)] = 0
+            continue
+        depth, n = 0, 1
+        for ch in params:
+            depth += {"(": 1, ")": -1}.get(ch, 0)
+            n += ch == "," and depth == 0
+        out[m.group(1)] = n
+    return out
+
+
+def test_binding_arity_matches_header():
+    protos = _prototypes()
+    assert set(protos) == set(pt.EXPORTS)
+    L = pt.lib()
+    for name, n in sorted(protos.items()):
+        argtypes = getattr(L, name).argtypes
+        if argtypes is None:  # called without declared argument types
+            continue
+        assert len(argtypes) == n, f"{name}: pt.h has {n} parameters, the binding declares {len(argtypes)}"
