@@ -198,18 +198,26 @@ def test_proposal_touches_only_five_branches():
         assert np.count_nonzero(np.abs(plen - nbl[k]) > 0) <= 1
 
 
-def test_hill_climb_improves():
-    n = 10
-    a = synth.simulate(n, 600, 1010, model="gtr", alpha=0.5)
+@pytest.mark.parametrize("n,seed", [(10, 4), (8, 5)])
+def test_hill_climb_stop_rule(n, seed):
+    """The hill-climb's result re-checked against its rules: it starts from the
+    full optimisation, each move gains, the final lengths are a full optimum,
+    and at the final tree the neighbour with the best proposal score (ties: the
+    smallest key), fully optimised from its proposal lengths, gains <= 1e-6."""
+    a = synth.simulate(n, 600, 1000 + seed, model="gtr", alpha=0.5)
     tips, w = synth.compress_patterns(a.codes)
     pb = oracle.Problem(tips, w, a.exch, a.freqs, 0.5, 4)
-    e, l = synth.random_trees(n, 1, 4)
+    e, l = synth.random_trees(n, 1, seed)
     l0, _, _ = pb.full_optimise(e[0], l[0])
     lhc, he, hl, moves = pb.hill_climb(e[0], l[0])
-    assert lhc >= l0 - 1e-9
+    assert moves >= 1  # a random start is improved at least once
+    assert lhc > l0 + 1e-6 * moves
     assert lhc == pytest.approx(pb.loglik(he, hl), abs=1e-8)
-    if moves:
-        assert lhc > l0
+    assert pb.full_optimise(he, hl)[0] == pytest.approx(lhc, abs=1e-7)
+    _, _, nk = oracle.nni_neighbours(n, he, hl)
+    best = max(range(len(nk)), key=lambda k: (pb.propose(he, hl, k)[0], -_k(nk[k])))
+    _, be, bl = pb.propose(he, hl, best)
+    assert pb.full_optimise(be, bl)[0] <= lhc + 1e-6
 
 
 def test_full_radius_proposal_is_full_optimisation():
