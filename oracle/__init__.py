@@ -94,6 +94,8 @@ def lib():
             L.or_search_frontier_trees.argtypes = [C.c_void_p, _i32p, _f64p]
             L.or_search_dump.restype = C.c_size_t
             L.or_search_dump.argtypes = [C.c_void_p, _u64p, _i32p, _f64p, _f64p, _i32p, C.c_void_p, C.c_void_p]
+            L.or_search_proposers.restype = C.c_size_t
+            L.or_search_proposers.argtypes = [C.c_void_p, _u64p, _u64p, _i32p]
             L.or_search_free.argtypes = [C.c_void_p]
             L.or_hill_climb.argtypes = [C.c_void_p, C.c_int, _i32p, _f64p, C.c_int, C.POINTER(C.c_double)]
             _lib = L
@@ -341,3 +343,15 @@ class Search:
             out["edges"] = edges[:k]
             out["lengths"] = lens[:k]
         return out
+
+    def proposers(self):
+        """The proposer that won each visited key's round, in visited()'s
+        order: parent key and rearranged edge's split as [count][2] uint64
+        (low word first), and the swap (-1 for starts and given frontiers)."""
+        L = lib()
+        cnt = L.or_search_count(self._s)
+        pk = np.zeros((max(cnt, 1), 2), np.uint64)
+        sp = np.zeros((max(cnt, 1), 2), np.uint64)
+        sw = np.zeros(max(cnt, 1), np.int32)
+        k = L.or_search_proposers(self._s, pk.reshape(-1), sp.reshape(-1), sw)
+        return {"parent_key": pk[:k], "split": sp[:k], "swap": sw[:k]}

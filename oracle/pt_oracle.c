@@ -955,6 +955,8 @@ typedef struct {
     double plnl;      /* proposal lnL (NaN for starts) */
     double alpha;     /* Gamma shape: the visit's (visited trees), the parent's (proposals) */
     int round;
+    uint64_t ppkey[2], psplit[2]; /* the proposer that won this key's round: parent key, */
+    int pswap;                    /* split of the edge it rearranged, swap (-1: not proposed) */
     uint64_t *splits; /* exact split set, for the injectivity check */
     int32_t *edges; double *lengths;
 } or_entry;
@@ -1004,6 +1006,7 @@ static void entry_fill(or_entry *e, const or_tree *t, int status, double lnl, do
 {
     int n = t->n;
     e->status = status; e->lnl = lnl; e->plnl = plnl; e->round = round;
+    e->pswap = -1; e->ppkey[0] = e->ppkey[1] = e->psplit[0] = e->psplit[1] = 0;
     e->splits = (uint64_t *)malloc(sizeof(uint64_t) * 2 * (n > 3 ? n - 3 : 1));
     tree_splits(t, (uint64_t(*)[2])e->splits);
     e->edges = (int32_t *)malloc(sizeof(int32_t) * 2 * (2 * n - 3));
@@ -1181,6 +1184,9 @@ int or_search_round(or_problem *pb, or_search *s)
         int keepit = lp >= lmax0 - T;
         entry_fill(e, &nt, OR_REJECTED, lp, lp, s->round);
         e->alpha = ap;
+        memcpy(e->ppkey, cs[i].pkey, sizeof e->ppkey);
+        memcpy(e->psplit, cs[i].split, sizeof e->psplit);
+        e->pswap = cs[i].swap;
         if (keepit) { kept[nk] = nt; kl[nk] = lp; ++nk; }
     }
     double lmax = lmax0;
@@ -1254,6 +1260,23 @@ size_t or_search_dump(const or_search *s, uint64_t *keys, int32_t *status, doubl
         status[k] = e->status; lnl[k] = e->lnl; plnl[k] = e->plnl; round[k] = e->round;
         if (edges) memcpy(edges + (size_t)k * 2 * ne, e->edges, sizeof(int32_t) * 2 * ne);
         if (lengths) memcpy(lengths + (size_t)k * ne, e->lengths, sizeof(double) * ne);
+        ++k;
+    }
+    return k;
+}
+
+/* The winning proposer of every entry, in or_search_dump's order: parent key
+ * [cnt][2], split of the rearranged edge [cnt][2] (both low word first) and
+ * swap (-1 for trees that were not proposed: starts, given frontiers). */
+size_t or_search_proposers(const or_search *s, uint64_t *pkey, uint64_t *split, int32_t *swap)
+{
+    size_t k = 0;
+    for (size_t i = 0; i < s->vis.cap; ++i) {
+        const or_entry *e = &s->vis.e[i];
+        if (!e->status) continue;
+        pkey[2 * k] = e->ppkey[0]; pkey[2 * k + 1] = e->ppkey[1];
+        split[2 * k] = e->psplit[0]; split[2 * k + 1] = e->psplit[1];
+        swap[k] = e->pswap;
         ++k;
     }
     return k;

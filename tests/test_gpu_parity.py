@@ -334,3 +334,55 @@ def test_table_full_is_reported():
         pt.run_search(ctx, aid, e, l, np.inf)
     assert ex.value.status == 3
     ctx.close()
+
+
+def _canonical_split(n, edges, v):
+    """Leaf set below node v of a canonical edge list (edge k = (k+1, parent of k+1), rooted at leaf 0)."""
+    up = {int(x): int(y) for x, y in np.asarray(edges).reshape(-1, 2)}
+    s = 0
+    for leaf in range(1, n):
+        x = leaf
+        while x != 0:
+            if x == v:
+                s |= 1 << leaf
+                break
+            x = up[x]
+    return s
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_proposers_match_oracle(prec):
+    """The proposer that wins each contested key (smallest parent key, edge split, swap) is the
+    oracle's, bit for bit, round by round (the round-synchronous reading of the paper's
+    "if unvisited" check)."""
+    n, T = 8, 15.0
+    a, pb = _setup(n, 400, 808, ncat=4)
+    e, l = synth.random_trees(n, 12, 809)
+    s = oracle.Search(pb, e, l, T)
+    for _ in range(3):
+        if s.frontier_size:
+            s.round()
+    ov = s.visited()
+    if _margins(ov, T).min() < 10 * TOL[prec]:
+        pytest.skip("a decision within tolerance of the threshold")
+    opr = s.proposers()
+    want = {}
+    for k, r, pk, sp, sw in zip(pt.keys_to_int(ov["keys"]), ov["round"], opr["parent_key"], opr["split"], opr["swap"]):
+        if r >= 1:
+            want[k] = (int(r), pt.keys_to_int(pk[None])[0], int(sp[0]) | (int(sp[1]) << 64), int(sw))
+    ctx, aid = _ctx(prec, a, 4, table_log2=16)
+    lmax, front = ctx.begin(aid, e, l, T)
+    got, contested = {}, 0
+    for r in range(1, 4):
+        if not len(front["edges"]):
+            break
+        pkeys = pt.keys_to_int(front["keys"])
+        lmax, nxt = ctx.expand(aid, front["edges"], front["lengths"], T, lmax)
+        pr = ctx.last_proposals()
+        for kk, f, v, sw in zip(pt.keys_to_int(pr["keys"]), pr["parent"], pr["edge_node"], pr["swap"]):
+            got[kk] = (r, pkeys[f], _canonical_split(n, front["edges"][f], int(v)), int(sw))
+        contested += ctx.stats()["candidates"] - ctx.stats()["scored"] - ctx.stats()["duplicates"]
+        front = nxt
+    ctx.close()
+    assert got == want
+    assert contested > 0  # some keys had several proposers in a round

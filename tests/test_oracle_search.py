@@ -253,3 +253,53 @@ def test_full_radius_infinite_threshold_visits_every_topology():
     s = oracle.Search(pb, e, l, float("inf"))
     s.run()
     assert len(s.visited()["keys"]) == COUNTS[n]
+
+
+def test_min_proposer_arbitration():
+    """Within a round, a neighbour proposed by several frontier trees is scored
+    once, from the proposer with the smallest (parent key, split of the
+    rearranged edge, swap): the round-synchronous reading of the paper's "if
+    unvisited" check ("Phylogenetic Topographer", loop step 6).  Re-derived
+    from the output: every proposer of each scored key is re-enumerated from
+    the previous round's GOOD trees, the recorded winner must be the
+    lexicographic minimum, and the stored proposal score and (for rejected
+    neighbours) lengths must be the proposal optimisation from that winner's
+    inherited lengths -- which differ between proposers, so scoring from any
+    other proposer fails the check."""
+    n, T = 8, 15.0
+    a = synth.simulate(n, 400, 808, model="gtr", alpha=0.5, mean_branch=0.1)
+    tips, w = synth.compress_patterns(a.codes)
+    pb = oracle.Problem(tips, w, a.exch, a.freqs, 0.5, 4)
+    e, l = synth.random_trees(n, 12, 809)
+    s = oracle.Search(pb, e, l, T)
+    for _ in range(3):
+        if s.frontier_size:
+            s.round()
+    v = s.visited(with_trees=True)
+    pr = s.proposers()
+    assert np.all(pr["swap"][v["round"] == 0] == -1)
+    contested = distinct_scores = 0
+    for r in range(1, int(v["round"].max()) + 1):
+        parents = np.nonzero((v["round"] == r - 1) & (v["status"] == oracle.GOOD))[0]
+        cands = {}
+        for p in parents:
+            pe, pl = v["edges"][p], v["lengths"][p]
+            splits = sorted(_k(x) for x in oracle.tree_splits(n, pe))  # canonical edge order: ascending split
+            _, _, nk = oracle.nni_neighbours(n, pe, pl)
+            for k in range(len(nk)):
+                cands.setdefault(_k(nk[k]), []).append((_k(v["keys"][p]), splits[k // 2], k % 2, p, k))
+        for i in np.nonzero(v["round"] == r)[0]:
+            cs = cands[_k(v["keys"][i])]
+            win = min(cs)
+            assert (_k(pr["parent_key"][i]), _k(pr["split"][i]), int(pr["swap"][i])) == win[:3]
+            lp, _, plen = pb.propose(v["edges"][win[3]], v["lengths"][win[3]], win[4])
+            assert v["plnl"][i] == pytest.approx(lp, abs=1e-9)
+            if v["status"][i] == oracle.REJECTED:
+                np.testing.assert_allclose(v["lengths"][i], plen, rtol=1e-12, atol=0)
+            others = [c for c in cs if c[:3] != win[:3]]
+            if others:
+                contested += 1
+                lo = pb.propose(v["edges"][others[0][3]], v["lengths"][others[0][3]], others[0][4])[0]
+                distinct_scores += abs(lo - lp) > 1e-6
+    # the case must exercise the rule: keys with several proposers whose scores differ
+    assert contested >= 5 and distinct_scores >= 3, (contested, distinct_scores)
