@@ -173,6 +173,24 @@ pt_status pt_begin(pt_ctx *ctx, int aln_id, int n_start, const int32_t *edges, c
                    double threshold, double *lmax_out, int cap, int32_t *front_edges, double *front_lengths,
                    double *front_lnl, pt_key *front_keys, int *n_front);
 
+/* Hill-climbs from n_trees start trees, all in lockstep (they stand in for the
+ * paper's RAxML starts: PT is seeded with local maxima of the likelihood,
+ * section "Maximum Likelihood Estimation of Local Maxima").  Each tree is
+ * fully optimised from its given lengths; then, as long as it improves, all
+ * 2(n-3) NNI neighbours of the current tree are proposal-optimised (the
+ * context's five-branch or central mode; the visited table is neither read
+ * nor written), the neighbour with the best proposal lnL (ties: the smallest
+ * key) is fully optimised from its proposal lengths, and the climb moves to
+ * it iff its lnL exceeds the current one by more than 1e-6.  At most
+ * max_moves moves per tree.  Outputs, per input tree in input order (any may
+ * be NULL): the final tree as a canonical edge list [n_trees][2n-3][2] with
+ * its lengths [n_trees][2n-3], lnL, key, and the number of moves.  The Gamma
+ * shape stays the model's.  Errors: PT_ERR_INVALID_ARG (bad trees or
+ * arguments, or propose_mode PT_PROPOSE_FULL). */
+pt_status pt_hill_climb(pt_ctx *ctx, int aln_id, int n_trees, const int32_t *edges, const double *lengths,
+                        int max_moves, int32_t *edges_out, double *lengths_out, double *lnl_out, pt_key *keys_out,
+                        int32_t *moves_out);
+
 /* One round of PT on a frontier (loop step 6 for every frontier tree, then
  * steps 1-5 for every neighbour it keeps).  Every NNI neighbour (2(n-3) per
  * tree) whose key is not yet visited is proposal-optimised once -- among
@@ -434,15 +452,18 @@ pt_status pt_training_pairs(pt_ctx *ctx, size_t cap, float *x, float *t, size_t 
  * the partial likelihoods of at least one tree, (2 n_taxa - 5) * n_patterns
  * * (16 * n_cats + 4) bytes in mixed precision (twice the 16 in FP64), plus
  * a sum-table when it does not fit in shared memory; e.g. 27 taxa x 2000
- * patterns x 4 categories is 6.7 MB per tree.  Larger requests return
- * PT_ERR_INVALID_ARG without touching the device.  All calls share the one
+ * patterns x 4 categories is 6.7 MB per tree.  All trees are scored in one
+ * persistent launch whose CTAs each reuse one such partials buffer tree
+ * after tree, so the number of trees only costs their canonical forms.
+ * Larger requests return PT_ERR_INVALID_ARG without touching the device.  All calls share the one
  * array and it keeps the last call's contents: calls that overlap on the GPU
  * (different streams or host threads at once) race and must be serialised
  * by the caller.  The first call on a device looks up the array's device
  * address (cudaGetSymbolAddress, once per device, with that device current);
  * make that first call before any stream capture.  Returns PT_OK,
  * PT_ERR_INVALID_ARG (bad argument, a tree that is not binary on
- * 0..n_taxa-1, or beyond the size limit) or PT_ERR_CUDA. */
+ * 0..n_taxa-1, a branch length that is not finite and >= 0, or beyond the
+ * size limit) or PT_ERR_CUDA. */
 pt_status pt_score_topologies_noalloc(int n_taxa, int n_patterns, const uint8_t *tips_dev,
                                       const int32_t *weights_dev, const double exch[6], const double freqs[4],
                                       double alpha, int n_cats, const pt_config *cfg, int n_trees,

@@ -5,6 +5,13 @@ x * Phi(x); loss = mean over rows and the 5 outputs of the squared error.
 Flat parameter layout: W1 [80][128], b1 [128], W2 [128][128], b2 [128],
 W3 [128][8], b3 [8]; each layer computes y = x W + b.  Written from those
 definitions with numpy; it shares nothing with the CUDA kernels.
+
+bf16=True applies the network's stated precision (BF16 weights, inputs and
+activations, FP32 accumulation): the hidden activations gelu(z), the output
+gradient and the back-propagated pre-activation gradients are rounded to
+BF16 where the network stores them in that format; everything else stays
+FP64, so the result differs from a BF16/FP32 implementation only by the
+rounding of its FP32 sums.
 """
 from __future__ import annotations
 
@@ -42,31 +49,33 @@ def _pad(x):
     return np.concatenate([x, np.zeros((x.shape[0], INP - IN))], axis=1)
 
 
-def forward(w, x):
+def forward(w, x, bf16=False):
+    q = to_bf16 if bf16 else (lambda a: a)
     p = unpack(w)
     X = _pad(x)
     z1 = X @ p["W1"] + p["b1"]
-    h1 = gelu(z1)
+    h1 = q(gelu(z1))
     z2 = h1 @ p["W2"] + p["b2"]
-    h2 = gelu(z2)
+    h2 = q(gelu(z2))
     y = h2 @ p["W3"] + p["b3"]
     return y[:, :OUT], (X, z1, h1, z2, h2)
 
 
-def loss_grad(w, x, t):
+def loss_grad(w, x, t, bf16=False):
+    q = to_bf16 if bf16 else (lambda a: a)
     p = unpack(w)
-    y, (X, z1, h1, z2, h2) = forward(w, x)
+    y, (X, z1, h1, z2, h2) = forward(w, x, bf16)
     t = np.asarray(t, np.float64).reshape(-1, OUT)
     n = y.shape[0]
     e = y - t
     loss = float(np.sum(e * e) / (n * OUT))
     dy = np.zeros((n, OUTP))
-    dy[:, :OUT] = 2.0 * e / (n * OUT)
+    dy[:, :OUT] = q(2.0 * e / (n * OUT))
     g = {"W3": h2.T @ dy, "b3": dy.sum(0)}
-    dz2 = (dy @ p["W3"].T) * gelu_d(z2)
+    dz2 = q((dy @ p["W3"].T) * gelu_d(z2))
     g["W2"] = h1.T @ dz2
     g["b2"] = dz2.sum(0)
-    dz1 = (dz2 @ p["W2"].T) * gelu_d(z1)
+    dz1 = q((dz2 @ p["W2"].T) * gelu_d(z1))
     g["W1"] = X.T @ dz1
     g["b1"] = dz1.sum(0)
     return loss, pack(g)

@@ -230,10 +230,13 @@ void reset_judges(Ctx& c) {
 
 size_t rsize(const Ctx& c) { return c.cfg.precision == PT_PREC_FP64 ? 8 : 4; }
 
-// bytes of the partial-likelihood buffers of one tree
+// bytes of the partial-likelihood buffers of one tree: 8 bytes per value in
+// both precisions (FP64; or FP32 partials plus their FP32 residuals), and the
+// scalers
 size_t tree_clv_bytes(const Ctx& c, const AlnState& a) {
+    (void)c;
     size_t slots = (size_t)(2 * a.n - 5);
-    return slots * a.P * (4 * (size_t)a.M.C * rsize(c) + 4);
+    return slots * a.P * (4 * (size_t)a.M.C * 8 + 4);
 }
 
 int chunk_trees(const Ctx& c, const AlnState& a) {
@@ -251,6 +254,7 @@ void check_flags(Ctx& c) {
     ck(c, cudaMemcpyAsync(h, c.d_err, sizeof h, cudaMemcpyDeviceToHost, c.stream), "read flags");
     ck(c, cudaStreamSynchronize(c.stream), "stream sync");
     if (h[kErrTree]) fail(c, PT_ERR_INVALID_ARG, "tree %d is not an unrooted binary tree on leaves 0..n-1", h[kErrTree] - 1);
+    if (h[kErrLen]) fail(c, PT_ERR_INVALID_ARG, "tree %d has a branch length that is not finite and >= 0", h[kErrLen] - 1);
     if (h[kErrTable]) fail(c, PT_ERR_TABLE_FULL, "visited table probe limit reached (raise table_log2)");
     if (h[kErrKey]) fail(c, PT_ERR_STATE, "neighbour key mismatch (internal error)");
 }
@@ -828,7 +832,12 @@ struct RoundIn {
 // then every NNI neighbour of every frontier in one persistent proposal
 // launch per memory wave, then every kept neighbour in one full-optimisation
 // launch per wave.  The single-alignment round is a batch of one.
-void expand_batch(Ctx& c, const std::vector<RoundIn>& ins, std::vector<RoundOut>& outs) {
+// climb: a hill-climb's neighbourhood scoring instead -- every NNI neighbour of
+// every frontier tree is proposal-optimised (no visited table, no dedup, no
+// learned start), items f*m .. f*m+m-1 belong to frontier tree f, and the call
+// returns after the proposal launch (buffers "items", "items.key",
+// "items.lnl", "items.len5" and tree set "b0.fr" hold the results).
+void expand_batch(Ctx& c, const std::vector<RoundIn>& ins, std::vector<RoundOut>& outs, bool climb = false) {
     const int na = (int)ins.size(), prec = c.cfg.precision;
     struct AR {
         AlnState* a;
@@ -857,16 +866,16 @@ void expand_batch(Ctx& c, const std::vector<RoundIn>& ins, std::vector<RoundOut>
         AR& r = ar[k];
         r.a = &aln_of(c, ins[k].aln);
         AlnState& a = *r.a;
-        if (!a.table) reset_table(c, a);
+        if (!a.table && !climb) reset_table(c, a);
         const std::string pre = "b" + std::to_string(k) + ".";
         r.n = a.n;
         r.m = 2 * (a.n - 3);
         r.F = ins[k].F;
-        r.round = ++a.round;
+        r.round = climb ? a.round : ++a.round;
         r.lmax = d_lmax + k;
         r.fr = treeset(c, pre + "fr", a.n, std::max(r.F, 1), false);
         launch_canon(c.stream, a.n, r.F, ins[k].edges_d, ins[k].lens_d, r.fr, c.d_err);
-        if (c.cfg.reopt_alpha && a.M.C > 1 && r.F > 0) {
+        if (c.cfg.reopt_alpha && a.M.C > 1 && r.F > 0 && !climb) {
             // proposals use their parent's shape: the one its visit recorded in the table
             double* fal = buf<double>(c, pre + "fr.alpha", r.F);
             r.frates = buf<double>(c, pre + "fr.rates", (size_t)r.F * kMaxCat);
@@ -874,8 +883,9 @@ void expand_batch(Ctx& c, const std::vector<RoundIn>& ins, std::vector<RoundOut>
             launch_gamma_rates(c.stream, r.F, a.M.C, fal, r.frates);
         }
         int32_t* fwin = buf<int32_t>(c, pre + "fr.win", r.F);
-        launch_insert_trees(c.stream, a.table, a.log2, hcount(r.F), r.fr, nullptr, nullptr, hround(r.round - 1), fwin,
-                            c.d_err);
+        if (!climb)
+            launch_insert_trees(c.stream, a.table, a.log2, hcount(r.F), r.fr, nullptr, nullptr, hround(r.round - 1),
+                                fwin, c.d_err);
         ck(c, cudaMemcpyAsync(r.lmax, &ins[k].lmax, 8, cudaMemcpyHostToDevice, c.stream), "lmax");
         r.ncand = r.F * r.m;
         hc[kStCand] += r.ncand;
@@ -892,6 +902,10 @@ void expand_batch(Ctx& c, const std::vector<RoundIn>& ins, std::vector<RoundOut>
     for (int k = 0; k < na; ++k) {
         AR& r = ar[k];
         AlnState& a = *r.a;
+        if (climb) {  // every neighbour is scored, none has a table slot
+            launch_fill_i32(c.stream, r.ncand, r.flag, 1, r.cslot, -1);
+            continue;
+        }
         launch_cand_insert(c.stream, a.table, a.log2, hcount(r.ncand), r.nkey, r.cinfo, r.fr, hround(r.round), r.cslot,
                            r.flag, c.d_err, c.d_stats);
         for (int ph = 2; ph <= 4; ++ph)
@@ -927,8 +941,8 @@ void expand_batch(Ctx& c, const std::vector<RoundIn>& ins, std::vector<RoundOut>
     double* len5 = buf<double>(c, "items.len5", 5 * (size_t)Wtot + 5);
     int32_t* kept = buf<int32_t>(c, "items.kept", Wtot + 1);
     float* icost = buf<float>(c, "items.cost", Wtot + 1);
-    const bool use_mlp = c.mlp_on && c.mlp_ready;
-    const bool feats = use_mlp || c.log_on;
+    const bool use_mlp = c.mlp_on && c.mlp_ready && !climb;
+    const bool feats = use_mlp || (c.log_on && !climb);
     float* xf_all = feats ? buf<float>(c, "mlp.xf", (size_t)(Wtot + 1) * kMlpIn) : nullptr;
     double* init_all = use_mlp ? buf<double>(c, "mlp.init", (size_t)(Wtot + 1) * 5) : nullptr;
     int32_t* ievals = use_mlp ? buf<int32_t>(c, "items.evals", Wtot + 1) : nullptr;
@@ -1006,6 +1020,11 @@ void expand_batch(Ctx& c, const std::vector<RoundIn>& ins, std::vector<RoundOut>
             g.scl_stride = slots * a.P;
             g.clv = wave + off;
             off += ((g.tree_stride * rsize(c) * ch.cnt) + 255) & ~size_t(255);
+            g.clv_lo = nullptr;
+            if (prec == PT_PREC_MIXED) {  // residuals of the FP32 partials (pairs for the scores)
+                g.clv_lo = wave + off;
+                off += ((g.tree_stride * 4 * ch.cnt) + 255) & ~size_t(255);
+            }
             g.scl = reinterpret_cast<int32_t*>(wave + off);
             off += ((g.scl_stride * 4 * ch.cnt) + 255) & ~size_t(255);
             void* pm = wave + off;
@@ -1042,7 +1061,7 @@ void expand_batch(Ctx& c, const std::vector<RoundIn>& ins, std::vector<RoundOut>
             gp.first = ch.f0;
             gp.g = g;
             gp.Pm = pm;
-            gp.tab = a.table;
+            gp.tab = climb ? nullptr : a.table;
             gp.round = hround(r.round);
             gp.lmax = r.lmax;
             gp.thr = ins[ch.k].thr;
@@ -1131,6 +1150,13 @@ void expand_batch(Ctx& c, const std::vector<RoundIn>& ins, std::vector<RoundOut>
     if (use_mlp && !full_radius)  // the judges take this round's proposals
         for (int k = 0; k < na; ++k) launch_judge(c.stream, hcount(ar[k].W), ievals + ar[k].ibase, judge_of(c, *ar[k].a));
     c.last_items = Wtot;
+    if (climb) {
+        total.end();
+        outs.clear();
+        check_flags(c);
+        end_stats(c, hc);
+        return;
+    }
     // ---- C. visit the kept neighbours
     Span sp4(c, 4);
     std::vector<FullJob> jobs;
@@ -1221,6 +1247,115 @@ void expand_core(Ctx& c, AlnState& a, int F, const int32_t* edges_d, const doubl
     expand_batch(c, ins, outs);
     out = outs[0];
     *lmax_inout = out.lmax;
+}
+
+// Hill-climbs of T trees in lockstep (the stand-in for the paper's RAxML
+// starts, section "Maximum Likelihood Estimation of Local Maxima"): each tree
+// is fully optimised; then, while it improves, every NNI neighbour of it is
+// proposal-optimised, the neighbour with the best proposal score (ties: the
+// smallest key) is fully optimised from its proposal lengths, and the climb
+// moves there iff that gains more than 1e-6 over the current score.  At most
+// max_moves moves per tree.  The host holds each tree's canonical edge list,
+// lengths, score and key between steps; every likelihood is computed by the
+// kernels (the proposal launch of the batched round, full optimisation).
+void climb_core(Ctx& c, AlnState& a, int T, const int32_t* edges_d, const double* lens_d, int max_moves,
+                std::vector<int32_t>& he, std::vector<double>& hl, std::vector<double>& hlnl,
+                std::vector<uint64_t>& hkey, std::vector<int32_t>& hmoves) {
+    const int n = a.n, E = 2 * n - 3, m = 2 * (n - 3), id = (int)(&a - c.alns.data());
+    int64_t tot[kStWords] = {0};
+    auto add_stats = [&]() { for (int i = 0; i < kStWords; ++i) tot[i] += c.stats[i]; };
+    TreeSet cur = treeset(c, "hc.cur", n, T, true);
+    double* clnl = buf<double>(c, "hc.lnl", T);
+    launch_canon(c.stream, n, T, edges_d, lens_d, cur, c.d_err);
+    check_flags(c);
+    run_full_jobs(c, {FullJob{&a, cur, 0, T, clnl, c.cfg.full_max_sweeps}});
+    he.assign((size_t)T * 2 * E, 0);
+    hl.assign((size_t)T * E, 0.0);
+    hlnl.assign(T, 0.0);
+    hkey.assign((size_t)T * 2, 0);
+    hmoves.assign(T, 0);
+    auto fetch = [&](int cnt, const TreeSet& ts, const double* lnl, std::vector<int32_t>& e, std::vector<double>& l,
+                     std::vector<double>& x, std::vector<uint64_t>& k) {
+        int32_t* ge = buf<int32_t>(c, "hc.ge", (size_t)cnt * 2 * E);
+        double* gl = buf<double>(c, "hc.gl", (size_t)cnt * E);
+        double* gx = buf<double>(c, "hc.gx", cnt);
+        uint64_t* gk = buf<uint64_t>(c, "hc.gk", (size_t)cnt * 2);
+        launch_gather_out(c.stream, n, hcount(cnt), nullptr, ts, lnl, ge, gl, gx, gk);
+        e.resize((size_t)cnt * 2 * E);
+        l.resize((size_t)cnt * E);
+        x.resize(cnt);
+        k.resize((size_t)cnt * 2);
+        ck(c, cudaMemcpyAsync(e.data(), ge, 4 * e.size(), cudaMemcpyDeviceToHost, c.stream), "climb copy");
+        ck(c, cudaMemcpyAsync(l.data(), gl, 8 * l.size(), cudaMemcpyDeviceToHost, c.stream), "climb copy");
+        ck(c, cudaMemcpyAsync(x.data(), gx, 8 * x.size(), cudaMemcpyDeviceToHost, c.stream), "climb copy");
+        ck(c, cudaMemcpyAsync(k.data(), gk, 8 * k.size(), cudaMemcpyDeviceToHost, c.stream), "climb copy");
+        ck(c, cudaStreamSynchronize(c.stream), "sync");
+    };
+    fetch(T, cur, clnl, he, hl, hlnl, hkey);
+    end_stats(c, nullptr);
+    add_stats();
+    std::vector<char> active(T, m > 0 ? 1 : 0);
+    std::vector<int32_t> pe, ne;
+    std::vector<double> pl, nl, nx;
+    std::vector<uint64_t> nk;
+    for (int step = 0; step < max_moves; ++step) {
+        std::vector<int> act;
+        for (int t = 0; t < T; ++t)
+            if (active[t]) act.push_back(t);
+        if (act.empty()) break;
+        const int F = (int)act.size();
+        pe.resize((size_t)F * 2 * E);
+        pl.resize((size_t)F * E);
+        for (int f = 0; f < F; ++f) {
+            std::copy_n(he.begin() + (size_t)act[f] * 2 * E, 2 * E, pe.begin() + (size_t)f * 2 * E);
+            std::copy_n(hl.begin() + (size_t)act[f] * E, E, pl.begin() + (size_t)f * E);
+        }
+        int32_t* fe = buf<int32_t>(c, "hc.fe", pe.size());
+        double* fl = buf<double>(c, "hc.fl", pl.size());
+        ck(c, cudaMemcpyAsync(fe, pe.data(), 4 * pe.size(), cudaMemcpyHostToDevice, c.stream), "climb copy");
+        ck(c, cudaMemcpyAsync(fl, pl.data(), 8 * pl.size(), cudaMemcpyHostToDevice, c.stream), "climb copy");
+        std::vector<RoundIn> ins{RoundIn{id, F, fe, fl, INFINITY, 0.0}};
+        std::vector<RoundOut> outs;
+        begin_stats(c);
+        expand_batch(c, ins, outs, true);
+        add_stats();
+        // the buffers of the proposal launch (same names and sizes as expand_batch's)
+        const int W = F * m;
+        const Item* items = buf<Item>(c, "items", W + 1);
+        const uint64_t* ikey = buf<uint64_t>(c, "items.key", 2 * (size_t)W + 2);
+        const double* plnl = buf<double>(c, "items.lnl", W + 1);
+        const double* len5 = buf<double>(c, "items.len5", 5 * (size_t)W + 5);
+        TreeSet fr = treeset(c, "b0.fr", n, std::max(F, 1), false);
+        int32_t* best = buf<int32_t>(c, "hc.best", F);
+        launch_climb_best(c.stream, F, m, plnl, ikey, best);
+        int32_t* ke = buf<int32_t>(c, "hc.ke", (size_t)F * 2 * E);
+        double* kl = buf<double>(c, "hc.kl", (size_t)F * E);
+        int32_t* ks = buf<int32_t>(c, "hc.ks", F);
+        launch_materialize(c.stream, n, hcount(F), best, items, fr, len5, ke, kl, ks);
+        TreeSet kp = treeset(c, "hc.kp", n, F, true);
+        launch_canon(c.stream, n, F, ke, kl, kp, c.d_err);
+        check_flags(c);
+        double* klnl = buf<double>(c, "hc.klnl", F);
+        begin_stats(c);
+        run_full_jobs(c, {FullJob{&a, kp, 0, F, klnl, c.cfg.full_max_sweeps}});
+        end_stats(c, nullptr);
+        add_stats();
+        fetch(F, kp, klnl, ne, nl, nx, nk);
+        for (int f = 0; f < F; ++f) {
+            const int t = act[f];
+            if (nx[f] > hlnl[t] + 1e-6) {  // NaN never moves
+                std::copy_n(ne.begin() + (size_t)f * 2 * E, 2 * E, he.begin() + (size_t)t * 2 * E);
+                std::copy_n(nl.begin() + (size_t)f * E, E, hl.begin() + (size_t)t * E);
+                hkey[2 * t] = nk[2 * f];
+                hkey[2 * t + 1] = nk[2 * f + 1];
+                hlnl[t] = nx[f];
+                ++hmoves[t];
+            } else {
+                active[t] = 0;
+            }
+        }
+    }
+    for (int i = 0; i < kStWords; ++i) c.stats[i] = tot[i];
 }
 
 void collect_times(Ctx& c) {
@@ -1540,6 +1675,8 @@ GraphRound* graph_create(Ctx& c, const std::vector<int>& ids, const std::vector<
         x.g.tree_stride = slots * x.P * 4 * C;
         x.g.scl_stride = slots * x.P;
         ar.addv(x.g.clv, (size_t)F * x.g.tree_stride * rsize(c));
+        x.g.clv_lo = nullptr;
+        if (prec == PT_PREC_MIXED) ar.addv(x.g.clv_lo, (size_t)F * x.g.tree_stride * 4);
         ar.add(x.g.scl, (size_t)F * x.g.scl_stride);
         ar.addv(x.pm, pmat_bytes(prec, C, n, F));
         x.ssum = x.xf = x.yb = nullptr;
@@ -1941,6 +2078,38 @@ pt_status pt_begin(pt_ctx* ctx, int aln_id, int n_start, const int32_t* edges, c
         end_stats(c, nullptr);
         write_out(c, a, o, cap, front_edges, front_lengths, front_lnl, reinterpret_cast<uint64_t*>(front_keys), true,
                   n_front);
+        collect_times(c);
+    });
+}
+
+pt_status pt_hill_climb(pt_ctx* ctx, int aln_id, int n_trees, const int32_t* edges, const double* lengths,
+                        int max_moves, int32_t* edges_out, double* lengths_out, double* lnl_out, pt_key* keys_out,
+                        int32_t* moves_out) {
+    return guarded(ctx, [&](Ctx& c) {
+        AlnState& a = aln_of(c, aln_id);
+        if (n_trees < 1 || !edges || !lengths || max_moves < 0)
+            fail(c, PT_ERR_INVALID_ARG, "bad arguments");
+        if (c.cfg.propose_mode == PT_PROPOSE_FULL)
+            fail(c, PT_ERR_INVALID_ARG, "the hill-climb scores neighbours by the five-branch or central proposal");
+        validate_trees(c, a.n, n_trees, edges, lengths);
+        const int E = 2 * a.n - 3;
+        zero_flags(c);
+        begin_stats(c);
+        const long long l0 = launch_count();
+        int32_t* de = buf<int32_t>(c, "hcin.e", (size_t)n_trees * 2 * E);
+        double* dl = buf<double>(c, "hcin.l", (size_t)n_trees * E);
+        ck(c, cudaMemcpyAsync(de, edges, 4 * (size_t)n_trees * 2 * E, cudaMemcpyHostToDevice, c.stream), "copy in");
+        ck(c, cudaMemcpyAsync(dl, lengths, 8 * (size_t)n_trees * E, cudaMemcpyHostToDevice, c.stream), "copy in");
+        std::vector<int32_t> he, hm;
+        std::vector<double> hl, hx;
+        std::vector<uint64_t> hk;
+        climb_core(c, a, n_trees, de, dl, max_moves, he, hl, hx, hk, hm);
+        c.stats[kStLaunches] = launch_count() - l0;
+        if (edges_out) std::memcpy(edges_out, he.data(), 4 * he.size());
+        if (lengths_out) std::memcpy(lengths_out, hl.data(), 8 * hl.size());
+        if (lnl_out) std::memcpy(lnl_out, hx.data(), 8 * hx.size());
+        if (keys_out) std::memcpy(keys_out, hk.data(), 8 * hk.size());
+        if (moves_out) std::memcpy(moves_out, hm.data(), 4 * hm.size());
         collect_times(c);
     });
 }

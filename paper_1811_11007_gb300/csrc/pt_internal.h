@@ -85,7 +85,8 @@ struct Slot {
 constexpr unsigned long long kTagEmpty = ~0ull;
 
 // Device error flags (int32 words).
-enum { kErrTree = 0, kErrTable = 1, kErrKey = 2, kErrNumeric = 3, kErrWords = 8 };
+// kErrLen: a branch length that is not finite and >= 0 (tree index + 1).
+enum { kErrTree = 0, kErrTable = 1, kErrKey = 2, kErrNumeric = 3, kErrLen = 4, kErrWords = 8 };
 // Device counters (int64 words), match pt_stats.
 enum {
     kStCand = 0, kStDup = 1, kStScored = 2, kStKept = 3, kStGood = 4, kStPropEvals = 5, kStFullEvals = 6,
@@ -95,10 +96,14 @@ enum {
 // A group of trees sharing one partial-likelihood buffer: tree g's vectors
 // start at clv + g * tree_stride (R elements), scalers at scl + g * scl_stride.
 // Slots: D_v (v inner, n-2 of them) then U_v (v inner except the first, n-3).
+// Mixed precision: clv_lo (same layout as clv) holds the FP32 residuals of
+// the partials, clv + clv_lo being the pair form the scores use; null when
+// absent (FP64 path, or partials made by the full optimisation itself).
 struct ClvGroup {
     void* clv;
     int32_t* scl;
     size_t tree_stride, scl_stride;
+    void* clv_lo;
 };
 
 // Work item of the proposal kernel: frontier tree, internal edge node, swap,
@@ -164,6 +169,11 @@ void launch_prefix_counts(cudaStream_t s, int ng, const int* cnt, const int* per
 void launch_make_items(cudaStream_t s, int ncand, const int32_t* flag, const int32_t* pos, const int32_t* cinfo,
                        const int32_t* cslot, const uint64_t* nkey, Item* items, uint64_t* ikey);
 void launch_compact_idx(cudaStream_t s, int N, const int32_t* flag, const int32_t* pos, int32_t* idx);
+// a[i] = va (and b[i] = vb when b is not null) for i < N
+void launch_fill_i32(cudaStream_t s, int N, int32_t* a, int32_t va, int32_t* b = nullptr, int32_t vb = 0);
+// Hill-climb move choice: best[f] = the item of tree f (items f*m .. f*m+m-1) with
+// the largest score lnl, ties by the smallest key ikey (high word first).
+void launch_climb_best(cudaStream_t s, int F, int m, const double* lnl, const uint64_t* ikey, int32_t* best);
 void launch_insert_trees(cudaStream_t s, Slot* tab, int log2, DCount count, TreeSet ts, const double* lnl,
                          const int32_t* status, DRound round, int32_t* winner, int32_t* err);
 // alpha (may be null) is recorded in the visited trees' slots.
@@ -216,6 +226,7 @@ void launch_lengths_to_input(cudaStream_t s, int n, int count, TreeSet ts, doubl
 
 // Partials of a group of trees (all D_v, and U_v when with_up).
 // pm: P-matrix buffer of pmat_bytes(prec, C, n, count) bytes; launch_propose reads it for the same group.
+// Mixed precision with g.clv_lo set: the partials are made as pairs (h in clv, l in clv_lo).
 size_t pmat_bytes(int prec, int C, int n, int count);
 // rates (may be null: the model's): per-tree category rates [tree][kMaxCat], indexed like ts.
 void launch_partials(cudaStream_t s, int prec, const Model& M, Aln A, TreeSet ts, int first, DCount count, ClvGroup g,

@@ -210,6 +210,11 @@ __global__ void k_canon(int n, DCount cnt, const int32_t* __restrict__ edges, co
         }
         if (!ok) atomicCAS(&err[kErrTree], 0, tree + 1);
     }
+    if (lengths)  // device-resident inputs are checked here: finite, non-negative lengths
+        for (int e = lane; e < E; e += 32) {
+            const double x = lengths[(size_t)tree * E + e];
+            if (!(x >= 0.0 && x <= 1.7976931348623157e308)) atomicCAS(&err[kErrLen], 0, tree + 1);
+        }
     ok = __shfl_sync(0xffffffffu, ok, 0);
     __syncwarp();
     if (!ok) {
@@ -373,6 +378,44 @@ __global__ void k_make_items(int ncand, const int32_t* __restrict__ flag, const 
 __global__ void k_compact_idx(int N, const int32_t* __restrict__ flag, const int32_t* __restrict__ pos, int32_t* idx) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < N && flag[i]) idx[pos[i]] = i;
+}
+
+__global__ void k_fill_i32(int N, int32_t* a, int32_t va, int32_t* b, int32_t vb) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < N) {
+        a[i] = va;
+        if (b) b[i] = vb;
+    }
+}
+
+// Hill-climb move choice: per tree f (items f*m .. f*m+m-1, every neighbour of
+// the tree), the neighbour with the best proposal score, ties by the smallest
+// key (high word first); a NaN score never wins.  One warp per tree.
+__global__ void k_climb_best(int F, int m, const double* __restrict__ lnl, const uint64_t* __restrict__ ikey,
+                             int32_t* best) {
+    const int f = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+    if (f >= F) return;
+    double bl = -INFINITY;
+    unsigned long long bhi = ~0ull, blo = ~0ull;
+    int bi = -1;
+    for (int r = lane; r < m; r += 32) {
+        const int i = f * m + r;
+        const double x = lnl[i];
+        const unsigned long long hi = ikey[2 * i + 1], lo = ikey[2 * i];
+        if (!(x == x)) continue;
+        if (bi < 0 || x > bl || (x == bl && (hi < bhi || (hi == bhi && lo < blo)))) {
+            bl = x; bhi = hi; blo = lo; bi = i;
+        }
+    }
+    for (int o = 16; o; o >>= 1) {
+        const double x = __shfl_xor_sync(0xffffffffu, bl, o);
+        const unsigned long long hi = __shfl_xor_sync(0xffffffffu, bhi, o), lo = __shfl_xor_sync(0xffffffffu, blo, o);
+        const int i = __shfl_xor_sync(0xffffffffu, bi, o);
+        if (i >= 0 && (bi < 0 || x > bl || (x == bl && (hi < bhi || (hi == bhi && lo < blo))))) {
+            bl = x; bhi = hi; blo = lo; bi = i;
+        }
+    }
+    if (lane == 0) best[f] = bi < 0 ? f * m : bi;
 }
 
 // Enters whole trees (starts, or a caller's frontier) as visited.  Among
@@ -835,6 +878,286 @@ __device__ __forceinline__ void store_vec(R* dst, int p, const R* y) {
     }
 }
 
+// ---------------------------------------------------------------- compensated FP32 (scores of the mixed path)
+// The mixed path runs its Newton iterations on FP32 partials, but every score
+// it reports comes from partials carried as unevaluated sums h + l of two FP32
+// numbers (|l| <= ulp(h)/2, about 48 significant bits): FP32 rounding errors of
+// a partial repeat at every site that shares its sub-pattern (a constant
+// column below a node, say, at thousands of sites), so at 10^4 sites they add
+// up to ~1e-3 nats; the pairs bring that below 1e-6.  Error-free steps:
+// Dekker's product by FMA (a*b = p + fma(a, b, -p)) and Knuth's two-sum.
+// Explicit _rn intrinsics keep the compiler from contracting them.
+struct F2 {
+    float h, l;
+};
+__device__ __forceinline__ F2 f2_two_sum(float a, float b) {
+    const float s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    return F2{s, __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb))};
+}
+// h + l renormalised, for |h| >= |l| (Dekker's fast two-sum)
+__device__ __forceinline__ F2 f2_norm(float h, float l) {
+    const float s = __fadd_rn(h, l);
+    return F2{s, __fsub_rn(l, __fsub_rn(s, h))};
+}
+__device__ __forceinline__ F2 f2_mul(F2 a, F2 b) {
+    const float p = __fmul_rn(a.h, b.h);
+    float e = __fmaf_rn(a.h, b.h, -p);
+    e = __fmaf_rn(a.h, b.l, e);
+    e = __fmaf_rn(a.l, b.h, e);
+    return f2_norm(p, e);
+}
+__device__ __forceinline__ F2 f2_add(F2 a, F2 b) {
+    const F2 s = f2_two_sum(a.h, b.h);
+    return f2_norm(s.h, __fadd_rn(s.l, __fadd_rn(a.l, b.l)));
+}
+__device__ __forceinline__ F2 f2_of(double x) {
+    const float h = (float)x;
+    return F2{h, (float)(x - (double)h)};
+}
+
+// y_r = P_r x_r for pairs: P as (Ph, Pl) [C][16] row-major, x and y as (h, l)
+// [4C].  Every term is non-negative (probabilities times likelihoods); the
+// exact products Ph x_h are summed by two-sums, the small terms (product
+// errors, Ph x_l, Pl x_h, the sums' errors) in a plain FP32 correction.
+template <int C>
+__device__ __forceinline__ void f2_apply(const float* Ph, const float* Pl, const float* xh, const float* xl, float* yh,
+                                         float* yl) {
+#pragma unroll
+    for (int r = 0; r < C; ++r)
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const float* ph = Ph + r * 16 + i * 4;
+            const float* pl = Pl + r * 16 + i * 4;
+            float s = __fmul_rn(ph[0], xh[r * 4]);
+            float c = __fmaf_rn(ph[0], xh[r * 4], -s);
+            c = __fmaf_rn(ph[0], xl[r * 4], c);
+            c = __fmaf_rn(pl[0], xh[r * 4], c);
+#pragma unroll
+            for (int j = 1; j < 4; ++j) {
+                const float p = __fmul_rn(ph[j], xh[r * 4 + j]);
+                c = __fadd_rn(c, __fmaf_rn(ph[j], xh[r * 4 + j], -p));
+                c = __fmaf_rn(ph[j], xl[r * 4 + j], c);
+                c = __fmaf_rn(pl[j], xh[r * 4 + j], c);
+                const F2 t = f2_two_sum(s, p);
+                s = t.h;
+                c = __fadd_rn(c, t.l);
+            }
+            const F2 y = f2_norm(s, c);
+            yh[r * 4 + i] = y.h;
+            yl[r * 4 + i] = y.l;
+        }
+}
+
+// One category of f2_apply: y = P x with P as (Ph, Pl) [16] row-major.
+__device__ __forceinline__ void f2_apply4(const float* ph, const float* pl, const float* xh, const float* xl, float* yh,
+                                          float* yl) {
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        float s = __fmul_rn(ph[i * 4], xh[0]);
+        float c = __fmaf_rn(ph[i * 4], xh[0], -s);
+        c = __fmaf_rn(ph[i * 4], xl[0], c);
+        c = __fmaf_rn(pl[i * 4], xh[0], c);
+#pragma unroll
+        for (int j = 1; j < 4; ++j) {
+            const float p = __fmul_rn(ph[i * 4 + j], xh[j]);
+            c = __fadd_rn(c, __fmaf_rn(ph[i * 4 + j], xh[j], -p));
+            c = __fmaf_rn(ph[i * 4 + j], xl[j], c);
+            c = __fmaf_rn(pl[i * 4 + j], xh[j], c);
+            const F2 t = f2_two_sum(s, p);
+            s = t.h;
+            c = __fadd_rn(c, t.l);
+        }
+        const F2 y = f2_norm(s, c);
+        yh[i] = y.h;
+        yl[i] = y.l;
+    }
+}
+
+// x *= y for 4 pairs
+__device__ __forceinline__ void f2_mul4(float* xh, float* xl, const float* yh, const float* yl) {
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const F2 t = f2_mul(F2{xh[i], xl[i]}, F2{yh[i], yl[i]});
+        xh[i] = t.h;
+        xl[i] = t.l;
+    }
+}
+
+// exact power-of-two scaling of 4 pairs to max h in [1, 2); the exponent removed
+__device__ __forceinline__ int f2_normalise4(float* h, float* l) {
+    const float mx = fmaxf(fmaxf(h[0], h[1]), fmaxf(h[2], h[3]));
+    if (!(mx > 0.f)) return 0;
+    int e = ((__float_as_int(mx) >> 23) & 0xff) - 127;
+    if (e < -125) e = -125;
+    const float m = __int_as_float((127 - e) << 23);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        h[i] *= m;
+        l[i] *= m;
+    }
+    return e;
+}
+
+// x * 2^-d for d >= 0 (0 when far below the FP32 range: negligible next to the other term)
+__device__ __forceinline__ F2 f2_down(F2 x, int d) {
+    if (d > 120) return F2{0.f, 0.f};
+    const float m = __int_as_float((127 - d) << 23);
+    return F2{x.h * m, x.l * m};
+}
+
+// acc * 2^E += x * 2^e (pairs with exponents; acc.h == 0 means empty)
+__device__ __forceinline__ void f2_merge(F2& acc, int& E, F2 x, int e) {
+    if (!(acc.h > 0.f)) { acc = x; E = e; return; }
+    if (e > E) { acc = f2_down(acc, e - E); E = e; }
+    else x = f2_down(x, E - e);
+    acc = f2_add(acc, x);
+}
+
+// Source of a pair vector at a site: a tip (code lookup, exact) or a stored
+// slot (h and l arrays of the same layout, one scaler count).
+template <int C>
+struct Src2 {
+    const float* h;
+    const float* l;
+    const int32_t* scl;
+    const uint8_t* tip;
+};
+
+// y = P x for a pair source at site p; cnt = its scaler count.
+template <int C>
+__device__ __forceinline__ void f2_apply_src(const float* Ph, const float* Pl, const Src2<C>& s, int p, float* yh,
+                                             float* yl, int& cnt) {
+    if (s.tip) {
+        const int code = s.tip[p];
+        cnt = 0;
+#pragma unroll
+        for (int r = 0; r < C; ++r)
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                yh[r * 4 + i] = code >= 4 ? 1.f : Ph[r * 16 + i * 4 + (code & 3)];
+                yl[r * 4 + i] = code >= 4 ? 0.f : Pl[r * 16 + i * 4 + (code & 3)];
+            }
+        return;
+    }
+    float xh[4 * C], xl[4 * C];
+    const float4* a = reinterpret_cast<const float4*>(s.h + (size_t)p * 4 * C);
+    const float4* b = reinterpret_cast<const float4*>(s.l + (size_t)p * 4 * C);
+#pragma unroll
+    for (int q = 0; q < C; ++q) {
+        const float4 u = a[q], v = b[q];
+        xh[4 * q] = u.x; xh[4 * q + 1] = u.y; xh[4 * q + 2] = u.z; xh[4 * q + 3] = u.w;
+        xl[4 * q] = v.x; xl[4 * q + 1] = v.y; xl[4 * q + 2] = v.z; xl[4 * q + 3] = v.w;
+    }
+    cnt = s.scl[p];
+    f2_apply<C>(Ph, Pl, xh, xl, yh, yl);
+}
+
+// Category r of y = P_r x for a pair source at site p (P: [C][16] pairs).
+template <int C>
+__device__ __forceinline__ void f2_apply_src4(const float* Ph, const float* Pl, const Src2<C>& s, int p, int r, float* yh,
+                                              float* yl) {
+    if (s.tip) {
+        const int code = s.tip[p];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            yh[i] = code >= 4 ? 1.f : Ph[r * 16 + i * 4 + (code & 3)];
+            yl[i] = code >= 4 ? 0.f : Pl[r * 16 + i * 4 + (code & 3)];
+        }
+        return;
+    }
+    const float4 u = reinterpret_cast<const float4*>(s.h + (size_t)p * 4 * C)[r];
+    const float4 v = reinterpret_cast<const float4*>(s.l + (size_t)p * 4 * C)[r];
+    const float xh[4] = {u.x, u.y, u.z, u.w}, xl[4] = {v.x, v.y, v.z, v.w};
+    f2_apply4(Ph + r * 16, Pl + r * 16, xh, xl, yh, yl);
+}
+
+// y0 *= y1 elementwise (pairs)
+template <int C>
+__device__ __forceinline__ void f2_mul_vec(float* ah, float* al, const float* bh, const float* bl) {
+#pragma unroll
+    for (int q = 0; q < 4 * C; ++q) {
+        const F2 t = f2_mul(F2{ah[q], al[q]}, F2{bh[q], bl[q]});
+        ah[q] = t.h;
+        al[q] = t.l;
+    }
+}
+
+// exact power-of-two scaling of a pair vector to max h in [1, 2); returns the exponent removed
+template <int C>
+__device__ __forceinline__ int f2_normalise(float* h, float* l) {
+    float mx = h[0];
+#pragma unroll
+    for (int q = 1; q < 4 * C; ++q) mx = fmaxf(mx, h[q]);
+    if (!(mx > 0.f)) return 0;
+    int e = ((__float_as_int(mx) >> 23) & 0xff) - 127;
+    if (e < -125) e = -125;
+    const float m = __int_as_float((127 - e) << 23);
+#pragma unroll
+    for (int q = 0; q < 4 * C; ++q) {
+        h[q] *= m;
+        l[q] *= m;
+    }
+    return e;
+}
+
+// threshold rescale of a stored pair vector (as rescale(): by 2^32 when every h < 2^-32)
+template <int C>
+__device__ __forceinline__ int f2_rescale(float* h, float* l) {
+    float mx = h[0];
+#pragma unroll
+    for (int q = 1; q < 4 * C; ++q) mx = fmaxf(mx, h[q]);
+    if (mx < Prec<float>::thresh()) {
+#pragma unroll
+        for (int q = 0; q < 4 * C; ++q) {
+            h[q] *= Prec<float>::mult();
+            l[q] *= Prec<float>::mult();
+        }
+        return 1;
+    }
+    return 0;
+}
+
+template <int C>
+__device__ __forceinline__ void f2_store(float* dh, float* dl, int p, const float* h, const float* l) {
+#pragma unroll
+    for (int q = 0; q < C; ++q) {
+        reinterpret_cast<float4*>(dh + (size_t)p * 4 * C)[q] = make_float4(h[4 * q], h[4 * q + 1], h[4 * q + 2], h[4 * q + 3]);
+        reinterpret_cast<float4*>(dl + (size_t)p * 4 * C)[q] = make_float4(l[4 * q], l[4 * q + 1], l[4 * q + 2], l[4 * q + 3]);
+    }
+}
+
+// Site likelihood across a branch as a pair: L = (1/C) sum_r sum_i pi_i X_ri Z_ri
+// with Z = P Y (P of the branch), X and Y normalised.  pi as pairs (pih, pil).
+template <int C>
+__device__ __forceinline__ F2 f2_site_lik(const float* pih, const float* pil, const float* Xh, const float* Xl,
+                                          const float* Zh, const float* Zl) {
+    F2 acc{0.f, 0.f};
+#pragma unroll
+    for (int q = 0; q < 4 * C; ++q) {
+        const F2 t = f2_mul(f2_mul(F2{Xh[q], Xl[q]}, F2{Zh[q], Zl[q]}), F2{pih[q & 3], pil[q & 3]});
+        acc = f2_add(acc, t);
+    }
+    return F2{acc.h * (1.0f / C), acc.l * (1.0f / C)};  // 1/C is a power of two for C = 1, 2, 4
+}
+
+// ln of a pair site likelihood times 2^E, in FP64
+__device__ __forceinline__ double f2_log(F2 L, int E) {
+    return log((double)L.h + (double)L.l) + (double)E * kLn2;
+}
+
+// Entry q (< 16C) of P_r(t) of a branch as a pair (FP64 sum, split once):
+// W[(i*4+j)*4+k] = isqpi_i sqpi_j R_ik R_jk, ex[r*4+k] = exp(lam_k rate_r t).
+__device__ __forceinline__ void f2_pmat_entry(const double* W, const double* ex, int q, float* Ph, float* Pl) {
+    const int r = q >> 4, ij = q & 15;
+    double acc = 0.0;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) acc += W[ij * 4 + k] * ex[r * 4 + k];
+    const F2 v = f2_of(acc);
+    Ph[q] = v.h;
+    Pl[q] = v.l;
+}
+
 // L2 prefetch hint for [p, p + bytes): the block's threads request its
 // 128-byte lines in turn (every address lies inside the range).
 __device__ __forceinline__ void prefetch_l2(const void* p, size_t bytes) {
@@ -1253,10 +1576,148 @@ __device__ double newton_solve(const Model& M, const Cfg& cfg, const STab<R, C>&
     return ns.tb;
 }
 
+// ---------------------------------------------------------------- pair scores (mixed precision)
+// Scores of the mixed path, computed from pair partials (F2) category by
+// category (each category normalised on its own, merged with its exponent):
+// sum over the calling block's sites of w_p ln L_p, reduced over the block
+// into red[32] (FP64) and returned in every thread.  Kept out of line so the
+// FP32 Newton loops around them keep their registers.
+__device__ __forceinline__ double block_sum(double acc, double (*red)[2]) {
+    acc = warp_sum(acc);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5][0] = acc;
+    __syncthreads();
+    double tot = 0.0;
+    for (int i = 0; i < (int)((blockDim.x + 31) >> 5); ++i) tot += red[i][0];
+    __syncthreads();
+    return tot;
+}
+
+// Proposal: the four members A, X2 (at u) and B, Y2 (at v) around the new
+// edge, P matrices of the five final lengths as pairs (Ph/Pl [5][C*16]: central,
+// A, B, C, D; mbr = each member's branch); L_p across the central branch.
+template <int C>
+__device__ __noinline__ double propose_score_f2(const Src2<C>* mem, const int* mbr, const float* Ph, const float* Pl,
+                                                const double* pi, const int32_t* w, int P, double (*red)[2]) {
+    float pih[4], pil[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const F2 x = f2_of(pi[i]);
+        pih[i] = x.h;
+        pil[i] = x.l;
+    }
+    double acc = 0.0;
+    for (int p = threadIdx.x; p < P; p += blockDim.x) {
+        int kk = 0;
+#pragma unroll
+        for (int m = 0; m < 4; ++m) kk += mem[m].tip ? 0 : mem[m].scl[p];
+        F2 L{0.f, 0.f};
+        int E = 0;
+        for (int r = 0; r < C; ++r) {
+            float xh[4], xl[4], yh[4], yl[4], th[4], tl[4];
+            f2_apply_src4<C>(Ph + mbr[0] * C * 16, Pl + mbr[0] * C * 16, mem[0], p, r, xh, xl);
+            f2_apply_src4<C>(Ph + mbr[1] * C * 16, Pl + mbr[1] * C * 16, mem[1], p, r, th, tl);
+            f2_mul4(xh, xl, th, tl);
+            f2_apply_src4<C>(Ph + mbr[2] * C * 16, Pl + mbr[2] * C * 16, mem[2], p, r, yh, yl);
+            f2_apply_src4<C>(Ph + mbr[3] * C * 16, Pl + mbr[3] * C * 16, mem[3], p, r, th, tl);
+            f2_mul4(yh, yl, th, tl);
+            const int e = f2_normalise4(xh, xl) + f2_normalise4(yh, yl);
+            f2_apply4(Ph + r * 16, Pl + r * 16, yh, yl, th, tl);  // across the central branch (branch 0)
+            F2 Lr{0.f, 0.f};
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+                Lr = f2_add(Lr, f2_mul(f2_mul(F2{xh[i], xl[i]}, F2{th[i], tl[i]}), F2{pih[i], pil[i]}));
+            f2_merge(L, E, Lr, e);
+        }
+        L = F2{L.h * (1.0f / C), L.l * (1.0f / C)};  // 1/C is a power of two for C = 1, 2, 4
+        acc += (double)w[p] * f2_log(L, E - Prec<float>::kScaleExp * kk);
+    }
+    return block_sum(acc, red);
+}
+
+// Visit: a pruning pass in pairs over one tree's partials buffer.  D_v of
+// every inner node v > n bottom-up (h over the FP32 D slot of v, l in the U
+// slot of v; the FP32 vectors are no longer needed), then node n's vector
+// combined with leaf 0 across the edge of n.  The block computes each node's
+// P pairs (its two children, and n's own edge at the root) into Pf/Pfl from
+// W and lr (as NewtonSmem) at the lengths len.
+template <int C>
+__device__ __noinline__ double fullopt_score_f2(int n, const int32_t* ch, const double* len, Aln A, float* clv,
+                                                int32_t* scl, const double* W, const double* lr, float* Pf, float* Pfl,
+                                                double* exf, const double* pi, double (*red)[2]) {
+    const int NN = 2 * n - 2, P = A.P;
+    const size_t sstride = (size_t)P * 4 * C;
+    float pih[4], pil[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const F2 x = f2_of(pi[i]);
+        pih[i] = x.h;
+        pil[i] = x.l;
+    }
+    auto src = [&](int v) {
+        if (v < n) return Src2<C>{nullptr, nullptr, nullptr, A.tips + (size_t)v * P};
+        return Src2<C>{clv + (size_t)(v - n) * sstride, clv + (size_t)(n - 2 + (v - n - 1)) * sstride,
+                       scl + (size_t)(v - n) * P, nullptr};
+    };
+    double acc = 0.0;
+    for (int v = NN - 1; v >= n; --v) {
+        const int c0 = ch[2 * v], c1 = ch[2 * v + 1];
+        const int nm = v == n ? 3 : 2;  // matrices: child 0, child 1 (and n's own edge at the root)
+        __syncthreads();                // the previous node's sites are done with the matrices
+        for (int z = threadIdx.x; z < nm * 4 * C; z += blockDim.x) {
+            const int k = z / (4 * C), q = z % (4 * C);
+            exf[z] = exp(lr[q] * len[k == 0 ? c0 : k == 1 ? c1 : v]);
+        }
+        __syncthreads();
+        for (int z = threadIdx.x; z < nm * 16 * C; z += blockDim.x) {
+            const int k = z / (16 * C), q = z % (16 * C);
+            f2_pmat_entry(W, exf + k * 4 * C, q, Pf + k * 16 * C, Pfl + k * 16 * C);
+        }
+        __syncthreads();
+        const Src2<C> s0 = src(c0), s1 = src(c1);
+        for (int p = threadIdx.x; p < P; p += blockDim.x) {
+            const int kk = (s0.tip ? 0 : s0.scl[p]) + (s1.tip ? 0 : s1.scl[p]);
+            if (v > n) {
+                float dh[4 * C], dl[4 * C];
+#pragma unroll
+                for (int r = 0; r < C; ++r) {
+                    float th[4], tl[4];
+                    f2_apply_src4<C>(Pf, Pfl, s0, p, r, dh + 4 * r, dl + 4 * r);
+                    f2_apply_src4<C>(Pf + 16 * C, Pfl + 16 * C, s1, p, r, th, tl);
+                    f2_mul4(dh + 4 * r, dl + 4 * r, th, tl);
+                }
+                const int sc = f2_rescale<C>(dh, dl);
+                f2_store<C>(clv + (size_t)(v - n) * sstride, clv + (size_t)(n - 2 + (v - n - 1)) * sstride, p, dh, dl);
+                scl[(size_t)(v - n) * P + p] = kk + sc;
+            } else {
+                const int code = A.tips[p];  // leaf 0
+                F2 L{0.f, 0.f};
+                int E = 0;
+                for (int r = 0; r < C; ++r) {
+                    float dh[4], dl[4], th[4], tl[4];
+                    f2_apply_src4<C>(Pf, Pfl, s0, p, r, dh, dl);
+                    f2_apply_src4<C>(Pf + 16 * C, Pfl + 16 * C, s1, p, r, th, tl);
+                    f2_mul4(dh, dl, th, tl);
+                    const int e = f2_normalise4(dh, dl);
+                    f2_apply4(Pf + 32 * C + 16 * r, Pfl + 32 * C + 16 * r, dh, dl, th, tl);
+                    F2 Lr{0.f, 0.f};
+#pragma unroll
+                    for (int i = 0; i < 4; ++i)
+                        if (code >= 4 || code == i) Lr = f2_add(Lr, f2_mul(F2{th[i], tl[i]}, F2{pih[i], pil[i]}));
+                    f2_merge(L, E, Lr, e);
+                }
+                L = F2{L.h * (1.0f / C), L.l * (1.0f / C)};
+                acc += (double)A.w[p] * f2_log(L, E - Prec<float>::kScaleExp * kk);
+            }
+        }
+    }
+    return block_sum(acc, red);
+}
+
 // ---------------------------------------------------------------- P matrices of tree sets
 // Pm[tree][v][r][16] for v = 1..NN-1 (edge (v, up v)); row per thread.
+// Pm_lo (FP32 only, may be null): the rounding residuals, P - Pm (pairs for the scores).
 template <typename R>
-__global__ void k_pmats(Model M, TreeSet ts, int first, DCount cnt, R* Pm, const double* rates) {
+__global__ void k_pmats(Model M, TreeSet ts, int first, DCount cnt, R* Pm, const double* rates, float* Pm_lo) {
     const int n = ts.n, NN = 2 * n - 2, C = M.C;
     long long total = (long long)dcount(cnt) * NN * C * 4;
     for (long long x = blockIdx.x * (long long)blockDim.x + threadIdx.x; x < total;
@@ -1269,7 +1730,19 @@ __global__ void k_pmats(Model M, TreeSet ts, int first, DCount cnt, R* Pm, const
         int t = (int)(y / NN);
         double l = ts.len[(size_t)(first + t) * NN + v];
         const double rr = rates ? rates[(size_t)(first + t) * kMaxCat + r] : M.rates[r];
-        pmat_row<R>(M, l * rr, i, Pm + ((((size_t)t * NN + v) * C + r) * 16 + i * 4));
+        const size_t o = (((size_t)t * NN + v) * C + r) * 16 + i * 4;
+        if (Pm_lo) {
+            double row[4];
+            pmat_row<double>(M, l * rr, i, row);
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const F2 x = f2_of(row[j]);
+                Pm[o + j] = (R)x.h;
+                Pm_lo[o + j] = x.l;
+            }
+        } else {
+            pmat_row<R>(M, l * rr, i, Pm + o);
+        }
     }
 }
 
@@ -1331,6 +1804,58 @@ __global__ void k_partials(Model M, Aln A, TreeSet ts, int first, DCount cnt, Cl
     }
 }
 
+// Partials of the mixed path as pairs (see F2): every D_v and U_v of a tree
+// with its h part in g.clv (what the FP32 Newton iterations read) and its l
+// part in g.clv_lo; grid and layout as k_partials.  P matrices: pairs from
+// k_pmats (Pm_all h, Pm_lo l).
+template <int C>
+__global__ void k_partials_f2(Model M, Aln A, TreeSet ts, int first, DCount cnt, ClvGroup g,
+                              const float* __restrict__ Pm_all, const float* __restrict__ Pm_lo, int with_up) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    const int n = ts.n, NN = 2 * n - 2, P = A.P;
+    float* Ph = reinterpret_cast<float*>(smraw);
+    float* Pl = Ph + (size_t)NN * C * 16;
+    const int gi = blockIdx.x, tree = first + gi;
+    if (gi >= dcount(cnt)) return;  // uniform over the block
+    for (int x = threadIdx.x; x < NN * C * 16; x += blockDim.x) {
+        Ph[x] = Pm_all[(size_t)gi * NN * C * 16 + x];
+        Pl[x] = Pm_lo[(size_t)gi * NN * C * 16 + x];
+    }
+    __syncthreads();
+    const int p = blockIdx.y * blockDim.x + threadIdx.x;
+    if (p >= P) return;
+    const int32_t* up = ts.up + (size_t)tree * NN;
+    const int32_t* ch = ts.ch + (size_t)tree * NN * 2;
+    float* clv = reinterpret_cast<float*>(g.clv) + (size_t)gi * g.tree_stride;
+    float* clo = reinterpret_cast<float*>(g.clv_lo) + (size_t)gi * g.tree_stride;
+    int32_t* scl = g.scl + (size_t)gi * g.scl_stride;
+    const size_t sstride = (size_t)P * 4 * C;
+    auto slot_src = [&](int slot) {
+        return Src2<C>{clv + (size_t)slot * sstride, clo + (size_t)slot * sstride, scl + (size_t)slot * P, nullptr};
+    };
+    auto srcD = [&](int v) {
+        return v < n ? Src2<C>{nullptr, nullptr, nullptr, A.tips + (size_t)v * P} : slot_src(v - n);
+    };
+    auto make = [&](int slot, int a, const Src2<C>& sa, int b, const Src2<C>& sb) {
+        float yh[4 * C], yl[4 * C], zh[4 * C], zl[4 * C];
+        int ka, kb;
+        f2_apply_src<C>(Ph + (size_t)a * C * 16, Pl + (size_t)a * C * 16, sa, p, yh, yl, ka);
+        f2_apply_src<C>(Ph + (size_t)b * C * 16, Pl + (size_t)b * C * 16, sb, p, zh, zl, kb);
+        f2_mul_vec<C>(yh, yl, zh, zl);
+        const int sc = f2_rescale<C>(yh, yl);
+        f2_store<C>(clv + (size_t)slot * sstride, clo + (size_t)slot * sstride, p, yh, yl);
+        scl[(size_t)slot * P + p] = ka + kb + sc;
+    };
+    for (int v = NN - 1; v >= n; --v) make(v - n, ch[2 * v], srcD(ch[2 * v]), ch[2 * v + 1], srcD(ch[2 * v + 1]));
+    if (!with_up) return;
+    for (int v = n + 1; v < NN; ++v) {
+        const int u = up[v];
+        const int sib = ch[2 * u] == v ? ch[2 * u + 1] : ch[2 * u];
+        const Src2<C> above = u == n ? Src2<C>{nullptr, nullptr, nullptr, A.tips} : slot_src(n - 2 + u - n - 1);
+        make(n - 2 + (v - n - 1), sib, srcD(sib), u, above);
+    }
+}
+
 // ---------------------------------------------------------------- proposal optimisation (K4)
 // One CTA per NNI neighbour (persistent loop).  The quartet around internal
 // edge (u, v): A = the side of u towards leaf 0 (U_u, or leaf 0 itself when u
@@ -1350,6 +1875,8 @@ struct ProposeSmem {
     double ex5[5][4 * C];
     int warm[5];         // branch b starts from a learned length (its P matrices are recomputed)
     int next, grp;       // work item taken from the counter, its group
+    const float* mlo[4]; // members' FP32 residual partials (mixed precision scores), or null
+    float Plo[5][C * 16];// residuals of the five P matrices at the final lengths (pairs with Pm)
     NewtonSmem<R, C> ns;
 };
 
@@ -1409,19 +1936,24 @@ __global__ void __launch_bounds__(512) k_propose(const PropGroup* __restrict__ g
             const int node[4] = {u, it.swap == 0 ? c0 : c1, sib, it.swap == 0 ? c1 : c0};
             const int brn[4] = {1, it.swap == 0 ? 3 : 4, 2, it.swap == 0 ? 4 : 3};
             sm.bmem[0] = -1;
+            const float* clo = reinterpret_cast<const float*>(G.g.clv_lo);
+            if (clo) clo += (size_t)gi * G.g.tree_stride;
             for (int m = 0; m < 4; ++m) {
                 Src<R, C> y;
+                int slot = -1;
                 if (m == 0) {
                     if (u == n) { y.clv = nullptr; y.scl = nullptr; y.tip = G.A.tips; }
                     else {
-                        const int slot = n - 2 + (u - n - 1);
+                        slot = n - 2 + (u - n - 1);
                         y.clv = clv + (size_t)slot * sstride; y.scl = scl + (size_t)slot * P; y.tip = nullptr;
                     }
                 } else if (node[m] < n) {
                     y.clv = nullptr; y.scl = nullptr; y.tip = G.A.tips + (size_t)node[m] * P;
                 } else {
-                    y.clv = clv + (size_t)(node[m] - n) * sstride; y.scl = scl + (size_t)(node[m] - n) * P; y.tip = nullptr;
+                    slot = node[m] - n;
+                    y.clv = clv + (size_t)slot * sstride; y.scl = scl + (size_t)slot * P; y.tip = nullptr;
                 }
+                sm.mlo[m] = (clo && slot >= 0) ? clo + (size_t)slot * sstride : nullptr;
                 sm.msrc[m] = y;
                 sm.mbr[m] = brn[m];
                 sm.bmem[brn[m]] = m;
@@ -1517,8 +2049,35 @@ __global__ void __launch_bounds__(512) k_propose(const PropGroup* __restrict__ g
             }
             if (moved <= cfg.sweep_tol) break;
         }
-        // exact lnL at the final lengths: the last sum-table at its new length
-        double f1 = eval_lnl<R, C>(M, st, P, tlast, sm.ns);
+        // exact lnL at the final lengths: the last sum-table at its new length, or,
+        // in mixed precision, the pair form of the four members around the new edge
+        double f1;
+        if constexpr (sizeof(R) == 4) {
+            if (G.g.clv_lo) {
+                __syncthreads();  // the last solve is done with sm.Pm
+                for (int z = threadIdx.x; z < 5 * 4 * C; z += blockDim.x) {
+                    const int b = z / (4 * C), q = z % (4 * C);
+                    sm.ex5[b][q] = exp(sm.ns.lr[q] * sm.T[b]);
+                }
+                __syncthreads();
+                for (int z = threadIdx.x; z < 5 * 16 * C; z += blockDim.x) {
+                    const int b = z / (16 * C), q = z % (16 * C);
+                    f2_pmat_entry(sm.ns.W, sm.ex5[b], q, reinterpret_cast<float*>(sm.Pm[b]), sm.Plo[b]);
+                }
+                __syncthreads();
+                Src2<C> mem[4];
+#pragma unroll
+                for (int m = 0; m < 4; ++m)
+                    mem[m] = Src2<C>{reinterpret_cast<const float*>(sm.msrc[m].clv), sm.mlo[m], sm.msrc[m].scl,
+                                     sm.msrc[m].tip};
+                f1 = propose_score_f2<C>(mem, sm.mbr, reinterpret_cast<const float*>(sm.Pm), &sm.Plo[0][0], M.pi,
+                                         G.A.w, P, sm.ns.red);
+            } else {
+                f1 = eval_lnl<R, C>(M, st, P, tlast, sm.ns);
+            }
+        } else {
+            f1 = eval_lnl<R, C>(M, st, P, tlast, sm.ns);
+        }
         sweeps_total += sweeps;
         if (threadIdx.x == 0) {
             if (__double_as_longlong(cfg.prior_rate) != 0) {  // MAP: log prior of the neighbour's lengths
@@ -1537,9 +2096,11 @@ __global__ void __launch_bounds__(512) k_propose(const PropGroup* __restrict__ g
             }
             const int k = f1 >= *G.lmax - G.thr;
             G.kept[o] = k;
-            Slot* sl = &G.tab[it.slot];
-            sl->lnl = f1;
-            sl->tag = ((unsigned long long)dround(G.round) << 48) | (unsigned long long)(k ? 4 : 1);
+            if (G.tab) {  // no table: a hill-climb's neighbourhood scoring
+                Slot* sl = &G.tab[it.slot];
+                sl->lnl = f1;
+                sl->tag = ((unsigned long long)dround(G.round) << 48) | (unsigned long long)(k ? 4 : 1);
+            }
         }
     }
     if (threadIdx.x == 0) {
@@ -1559,6 +2120,8 @@ struct FullSmem {
     R Mt[16];
     R pi[4];
     int next, grp;
+    float Pf[3][C * 16], Pfl[3][C * 16];  // pair P matrices of the score pass (two children, the node)
+    double exf[3][4 * C];
     NewtonSmem<R, C> ns;
 };
 
@@ -1711,12 +2274,16 @@ __global__ void __launch_bounds__(512) k_fullopt(const FullGroup* __restrict__ g
             }
             if (op >= n) slot(op - n);
         };
+        // mixed precision scores every tree with the pair pass below, so an
+        // evaluation at fixed lengths needs no FP32 partials at all
+        const bool pair_score = sizeof(R) == 4;
         // bottom-up D pass
-        for (int v = NN - 1; v >= n; --v) refreshD(v);
+        if (!(pair_score && G.max_sweeps == 0))
+            for (int v = NN - 1; v >= n; --v) refreshD(v);
         int sweeps = 0, last = n;
         double tlast = 0.0;
         const int nsched = 3 * n - 5;
-        if (G.max_sweeps == 0) visit_build(n);
+        if (G.max_sweeps == 0 && !pair_score) visit_build(n);
         for (int sw = 0; sw < G.max_sweeps; ++sw) {
             ++sweeps;
             double moved = 0.0;
@@ -1744,8 +2311,17 @@ __global__ void __launch_bounds__(512) k_fullopt(const FullGroup* __restrict__ g
             }
             if (moved <= cfg.sweep_tol) break;
         }
-        // exact lnL at the final lengths (the last visited edge's sum-table)
-        double f1 = eval_lnl<R, C>(M, st, P, G.max_sweeps == 0 ? len[n] : tlast, sm.ns);
+        // exact lnL at the final lengths: the last visited edge's sum-table (FP64),
+        // or, in mixed precision, a pruning pass in pair arithmetic: D_v of every
+        // inner node bottom-up (h over the FP32 D slot, l in the U slot of v,
+        // free after the sweeps), the first inner node's combined at the root
+        double f1;
+        if constexpr (sizeof(R) == 4) {
+            f1 = fullopt_score_f2<C>(n, ch, len, A, reinterpret_cast<float*>(clv), scl, sm.ns.W, sm.ns.lr,
+                                     &sm.Pf[0][0], &sm.Pfl[0][0], &sm.exf[0][0], M.pi, sm.ns.red);
+        } else {
+            f1 = eval_lnl<R, C>(M, st, P, G.max_sweeps == 0 ? len[n] : tlast, sm.ns);
+        }
         sweeps_total += sweeps;
         __syncthreads();
         for (int v = threadIdx.x; v < NN; v += blockDim.x) glen[v] = len[v];
@@ -1845,6 +2421,18 @@ void launch_make_items(cudaStream_t s, int ncand, const int32_t* flag, const int
 void launch_compact_idx(cudaStream_t s, int N, const int32_t* flag, const int32_t* pos, int32_t* idx) {
     if (N <= 0) return;
     k_compact_idx<<<blocks_for(N, 256), 256, 0, s>>>(N, flag, pos, idx);
+    ++g_launches;
+}
+
+void launch_fill_i32(cudaStream_t s, int N, int32_t* a, int32_t va, int32_t* b, int32_t vb) {
+    if (N <= 0) return;
+    k_fill_i32<<<blocks_for(N, 256), 256, 0, s>>>(N, a, va, b, vb);
+    ++g_launches;
+}
+
+void launch_climb_best(cudaStream_t s, int F, int m, const double* lnl, const uint64_t* ikey, int32_t* best) {
+    if (F <= 0 || m <= 0) return;
+    k_climb_best<<<blocks_for(F, 8), 256, 0, s>>>(F, m, lnl, ikey, best);
     ++g_launches;
 }
 
@@ -2000,8 +2588,22 @@ void partials_t(cudaStream_t s, const Model& M, Aln A, TreeSet ts, int first, DC
                 int threads, R* pm, const double* rates) {
     const int NN = 2 * ts.n - 2;
     long long rows = (long long)count.cap * NN * C * 4;
-    k_pmats<R><<<(int)std::min<long long>(blocks_for(rows, 256), 8192), 256, 0, s>>>(M, ts, first, count, pm, rates);
+    // mixed precision: P pairs (residuals after the FP32 matrices of all trees) and pair partials
+    float* lo = sizeof(R) == 4 ? reinterpret_cast<float*>(pm) + (size_t)count.cap * NN * C * 16 : nullptr;
+    k_pmats<R><<<(int)std::min<long long>(blocks_for(rows, 256), 8192), 256, 0, s>>>(M, ts, first, count, pm, rates,
+                                                                                   lo);
     ++g_launches;
+    if constexpr (sizeof(R) == 4) {
+        if (g.clv_lo) {
+            const size_t sm2 = (size_t)NN * C * 16 * 8;
+            cudaFuncSetAttribute(k_partials_f2<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm2);
+            dim3 grid(count.cap, blocks_for(A.P, threads));
+            k_partials_f2<C><<<grid, threads, sm2, s>>>(M, A, ts, first, count, g, reinterpret_cast<float*>(pm), lo,
+                                                        with_up ? 1 : 0);
+            ++g_launches;
+            return;
+        }
+    }
     size_t smem = (size_t)NN * C * 16 * sizeof(R);
     cudaFuncSetAttribute(k_partials<R, C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     dim3 grid(count.cap, blocks_for(A.P, threads));
@@ -2011,7 +2613,8 @@ void partials_t(cudaStream_t s, const Model& M, Aln A, TreeSet ts, int first, DC
 }  // namespace
 
 size_t pmat_bytes(int prec, int C, int n, int count) {
-    return (size_t)count * (2 * n - 2) * C * 16 * (prec == 0 ? 8 : 4);
+    // FP32: the matrices, then their FP32 rounding residuals (pairs for the scores)
+    return (size_t)count * (2 * n - 2) * C * 16 * 8;
 }
 
 void launch_partials(cudaStream_t s, int prec, const Model& M, Aln A, TreeSet ts, int first, DCount count, ClvGroup g,

@@ -80,10 +80,9 @@ extern "C" pt_status pt_score_topologies_noalloc(int n_taxa, int n_patterns, con
     if (!base) return PT_ERR_CUDA;
 
     const int n = n_taxa, NN = 2 * n - 2, E = 2 * n - 3, P = n_patterns, prec = cfg.precision;
-    const size_t rs = prec == PT_PREC_FP64 ? 8 : 4;
     const int threads = cfg.threads > 0 ? cfg.threads : (P <= 128 ? 128 : 256);
     const bool smem_tab = fullopt_smem_bytes(prec, M.C, n, P, true, threads) <= (size_t)optin;
-    // layout: flags | stats | canonical trees | partials of a group of trees | sum-tables
+    // layout: flags | stats | canonical trees | launch table | per-CTA partials slabs | per-CTA sum-tables
     size_t off = 0;
     auto take = [&](size_t bytes) { size_t o = off; off += up256(bytes); return o; };
     const size_t o_err = take(sizeof(int32_t) * kErrWords);
@@ -92,24 +91,17 @@ extern "C" pt_status pt_score_topologies_noalloc(int n_taxa, int n_patterns, con
     const size_t o_up = take(4 * T * NN), o_ch = take(8 * T * NN), o_len = take(8 * T * NN),
                  o_bits = take(16 * T * NN), o_erank = take(4 * T * NN), o_sched = take(4 * T * 3 * n),
                  o_key = take(16 * T), o_emap = take(4 * T * E);
-    const size_t slots = (size_t)(2 * n - 5);
-    const size_t per_tree = up256(slots * P * 4 * M.C * rs) + up256(slots * P * 4);
+    const size_t o_grp = take(sizeof(FullGroup) + 3 * sizeof(int));
+    // each persistent CTA reuses one partials slab (and, when it does not fit in
+    // shared memory, one sum-table) tree after tree: the grid is what fits
+    const size_t slab = fullopt_slab_bytes(prec, M.C, n, P);
     const size_t spc = smem_tab ? 0 : up256(sumtable_bytes(prec, M.C, P));
     if (off > kNoAllocScratchBytes) return PT_ERR_INVALID_ARG;
-    size_t room = kNoAllocScratchBytes - off;
-    // largest group G with G partial buffers + min(G, 2 SMs) sum-tables
-    size_t G = 0;
-    for (size_t g = std::min<size_t>(T, 1 << 16); g >= 1; g = g / 2) {
-        size_t need = g * per_tree + std::min<size_t>(g, 2 * (size_t)nsm) * spc;
-        if (need <= room) { G = g; break; }
-        if (g == 1) break;
-    }
-    if (G == 0) return PT_ERR_INVALID_ARG;  // one tree does not fit: beyond the stated maximum
-    const size_t grid_max = std::min<size_t>(G, 2 * (size_t)nsm);
-    const size_t o_clv = take(G * up256(slots * P * 4 * M.C * rs));
-    const size_t o_scl = take(G * up256(slots * P * 4));
-    const size_t o_tab = take(grid_max * spc);
-    const size_t o_grp = take(sizeof(FullGroup) + 3 * sizeof(int));
+    const size_t fit = (kNoAllocScratchBytes - off) / (slab + spc);
+    if (fit == 0) return PT_ERR_INVALID_ARG;  // one tree's partials do not fit: beyond the stated maximum
+    const int grid = (int)std::min<size_t>(std::min<size_t>(T, 2 * (size_t)nsm), fit);
+    const size_t o_slab = take((size_t)grid * slab);
+    const size_t o_tab = take((size_t)grid * spc);
     if (off > kNoAllocScratchBytes) return PT_ERR_INVALID_ARG;
 
     int32_t* err = reinterpret_cast<int32_t*>(base + o_err);
@@ -125,12 +117,6 @@ extern "C" pt_status pt_score_topologies_noalloc(int n_taxa, int n_patterns, con
     ts.sched = reinterpret_cast<int32_t*>(base + o_sched);
     ts.key = reinterpret_cast<uint64_t*>(base + o_key);
     ts.emap = reinterpret_cast<int32_t*>(base + o_emap);
-    ClvGroup g;
-    g.clv = base + o_clv;
-    g.scl = reinterpret_cast<int32_t*>(base + o_scl);
-    g.tree_stride = up256(slots * P * 4 * M.C * rs) / rs;
-    g.scl_stride = up256(slots * P * 4) / 4;
-
     // the flags and counters must start at zero: the array keeps the last call's contents
     const size_t zero_bytes = o_stats + sizeof(unsigned long long) * kStWords;  // flags and counters
     if (cudaMemsetAsync(base + o_err, 0, zero_bytes, stream) != cudaSuccess) {
@@ -144,7 +130,7 @@ extern "C" pt_status pt_score_topologies_noalloc(int n_taxa, int n_patterns, con
         cudaGetLastError();
         return PT_ERR_CUDA;
     }
-    if (herr[kErrTree]) return PT_ERR_INVALID_ARG;
+    if (herr[kErrTree] || herr[kErrLen]) return PT_ERR_INVALID_ARG;
     Cfg k;
     k.tmin = cfg.tmin;
     k.tmax = cfg.tmax;
@@ -160,29 +146,25 @@ extern "C" pt_status pt_score_topologies_noalloc(int n_taxa, int n_patterns, con
     FullGroup* d_group = reinterpret_cast<FullGroup*>(base + o_grp);
     int* d_gstart = reinterpret_cast<int*>(base + o_grp + sizeof(FullGroup));
     int* d_counter = d_gstart + 2;
-    for (size_t f0 = 0; f0 < T; f0 += G) {
-        const int cnt = (int)std::min(G, T - f0);
-        const int grid = (int)std::min<size_t>((size_t)cnt, grid_max);
-        FullGroup gp;  // one group per chunk, written into the array (stream-ordered, staged copy)
-        gp.M = M;
-        gp.A = A;
-        gp.ts = ts;
-        gp.first = (int)f0;
-        gp.g = g;
-        gp.max_sweeps = mode == PT_SCORE_FULL ? cfg.full_max_sweeps : 0;
-        gp.lnl_out = lnl_out_dev + f0;
-        gp.rates = nullptr;
-        gp.order = nullptr;
-        const int gs[2] = {0, cnt};
-        if (cudaMemcpyAsync(d_group, &gp, sizeof gp, cudaMemcpyHostToDevice, stream) != cudaSuccess ||
-            cudaMemcpyAsync(d_gstart, gs, sizeof gs, cudaMemcpyHostToDevice, stream) != cudaSuccess ||
-            cudaMemsetAsync(d_counter, 0, sizeof(int), stream) != cudaSuccess) {
-            cudaGetLastError();
-            return PT_ERR_CUDA;
-        }
-        launch_fullopt(stream, prec, M.C, d_group, d_gstart, 1, d_counter, n, P, k, stats, threads, grid,
-                       smem_tab ? nullptr : base + o_tab, spc);
+    FullGroup gp;  // all trees in one persistent launch (the table is staged into the array)
+    gp.M = M;
+    gp.A = A;
+    gp.ts = ts;
+    gp.first = 0;
+    gp.g = ClvGroup{nullptr, nullptr, 0, 0, nullptr};  // partials live in the per-CTA slabs
+    gp.max_sweeps = mode == PT_SCORE_FULL ? cfg.full_max_sweeps : 0;
+    gp.lnl_out = lnl_out_dev;
+    gp.rates = nullptr;
+    gp.order = nullptr;
+    const int gs[2] = {0, n_trees};
+    if (cudaMemcpyAsync(d_group, &gp, sizeof gp, cudaMemcpyHostToDevice, stream) != cudaSuccess ||
+        cudaMemcpyAsync(d_gstart, gs, sizeof gs, cudaMemcpyHostToDevice, stream) != cudaSuccess ||
+        cudaMemsetAsync(d_counter, 0, sizeof(int), stream) != cudaSuccess) {
+        cudaGetLastError();
+        return PT_ERR_CUDA;
     }
+    launch_fullopt(stream, prec, M.C, d_group, d_gstart, 1, d_counter, n, P, k, stats, threads, grid,
+                   smem_tab ? nullptr : base + o_tab, spc, base + o_slab, slab);
     launch_lengths_to_input(stream, n, n_trees, ts, lengths_out_dev);
     if (cudaGetLastError() != cudaSuccess) return PT_ERR_CUDA;
     return PT_OK;

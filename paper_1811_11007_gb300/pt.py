@@ -29,7 +29,7 @@ EXPORTS = ["pt_config_default", "pt_create", "pt_destroy", "pt_last_error", "pt_
            "pt_mlp_loss_grad", "pt_mlp_train", "pt_mlp_enable", "pt_mlp_judge", "pt_training_log", "pt_training_pairs",
            "pt_expand_batch", "pt_expand_batch_dev", "pt_autotune", "pt_autotune_report", "pt_graph_create",
            "pt_graph_frontier_dev", "pt_graph_set_frontier", "pt_graph_run", "pt_graph_next_dev", "pt_graph_get_next",
-           "pt_graph_advance", "pt_graph_destroy", "pt_split_frequencies", "pt_last_alphas"]
+           "pt_graph_advance", "pt_graph_destroy", "pt_split_frequencies", "pt_last_alphas", "pt_hill_climb"]
 MLP_PARAMS, MLP_IN, MLP_OUT = 27912, 69, 5
 _f32p = np.ctypeslib.ndpointer(np.float32, flags="C_CONTIGUOUS")
 
@@ -116,6 +116,7 @@ def lib():
             L.pt_expand_frontier_dev.argtypes = [_vp, C.c_int, C.c_int, _vp, _vp, C.c_double,
                                                  C.POINTER(C.c_double), C.c_int, _vp, _vp, _vp, _vp,
                                                  C.POINTER(C.c_int)]
+            L.pt_hill_climb.argtypes = [_vp, C.c_int, C.c_int, _i32p, _f64p, C.c_int, _vp, _vp, _vp, _vp, _vp]
             L.pt_visited.argtypes = [_vp, C.c_int, C.c_size_t, _vp, _vp, _vp, C.POINTER(C.c_size_t)]
             L.pt_reset_visited.argtypes = [_vp, C.c_int]
             L.pt_stats.argtypes = [_vp, C.POINTER(C.c_int64), C.c_int]
@@ -307,6 +308,21 @@ class Context:
                                 C.byref(lmax), cap, _ptr(fe), _ptr(fl), _ptr(fn), _ptr(fk), C.byref(cnt)))
         k = cnt.value
         return lmax.value, {"edges": fe[:k], "lengths": fl[:k], "lnl": fn[:k], "keys": fk[:k]}
+
+    def hill_climb(self, aln: int, edges, lengths, max_moves: int = 1 << 20):
+        """Hill-climbs from each start tree (pt_hill_climb): final canonical
+        trees, lengths, lnL, keys and move counts, in input order."""
+        e = np.ascontiguousarray(edges, np.int32)
+        l = np.ascontiguousarray(lengths, np.float64)
+        T, E = l.shape
+        oe = np.zeros((T, E, 2), np.int32)
+        ol = np.zeros((T, E), np.float64)
+        on = np.zeros(T, np.float64)
+        ok = np.zeros((T, 2), np.uint64)
+        om = np.zeros(T, np.int32)
+        self._ck(lib().pt_hill_climb(self._h, aln, T, e.reshape(-1), l.reshape(-1), int(max_moves), _ptr(oe),
+                                     _ptr(ol), _ptr(on), _ptr(ok), _ptr(om)))
+        return {"edges": oe, "lengths": ol, "lnl": on, "keys": ok, "moves": om}
 
     def expand(self, aln: int, edges, lengths, threshold: float, lmax: float, cap: int | None = None):
         """One PT round on a host frontier; returns (lmax, next frontier)."""

@@ -144,6 +144,29 @@ def compress_patterns(codes: np.ndarray):
     return np.ascontiguousarray(cols.T, np.uint8), counts.astype(np.float64)
 
 
+def reinsert_leaves(edges: np.ndarray, n: int, k: int, rng: np.random.Generator) -> np.ndarray:
+    """A perturbed copy of a topology: k distinct random leaves are pruned and
+    each is reinserted on an edge chosen uniformly, as the stepwise insertion
+    of random_topology does (its inner node keeps its label).  Used for
+    starting trees near a given one."""
+    e = [[int(a), int(b)] for a, b in np.asarray(edges).reshape(-1, 2)]
+    for leaf in rng.choice(n, size=min(k, n), replace=False):
+        leaf = int(leaf)
+        i = next(j for j, (a, b) in enumerate(e) if leaf in (a, b))
+        w = e[i][1] if e[i][0] == leaf else e[i][0]
+        others = [j for j, (a, b) in enumerate(e) if j != i and w in (a, b)]
+        x, y = [next(v for v in e[j] if v != w) for j in others]
+        for j in sorted([i] + others, reverse=True):
+            del e[j]
+        e.append([x, y])
+        j = int(rng.integers(len(e)))
+        c, d = e[j]
+        e[j] = [c, w]
+        e.append([w, d])
+        e.append([leaf, w])
+    return np.asarray(e, np.int32)
+
+
 def random_trees(n: int, count: int, seed: int, init_length: float = 0.1):
     """`count` uniform random topologies with all lengths = init_length."""
     rng = np.random.default_rng(seed)

@@ -34,7 +34,7 @@ def test_clock_summary_without_samples():
 
 
 def test_default_steps(monkeypatch):
-    for argv, steps in ([[], 50], [["--workload", "batch16"], 5], [["--impl", "reference"], 3],
-                        [["--steps", "7"], 7]):
+    for argv, steps in ([[], 5], [["--workload", "pt27"], 50], [["--workload", "batch16"], 5],
+                        [["--impl", "reference"], 3], [["--steps", "7"], 7]):
         monkeypatch.setattr(sys, "argv", ["bench.py"] + argv)
         assert bench.parse().steps == steps

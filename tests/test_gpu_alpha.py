@@ -14,7 +14,7 @@ ATOL = {"fp64": 1e-5, "mixed": 2e-2}  # relative tolerance on the shape
 
 
 def _tol(prec, x):
-    return TOL[prec] + (1e-12 * abs(x) if prec == "fp64" else 0.0)
+    return TOL[prec]
 
 
 @pytest.fixture(scope="module", autouse=True)

@@ -2,8 +2,11 @@
 (oracle/mlp.py), and what the trained network gains in a PT search.
 
 BF16 weights, inputs and activations with FP32 accumulation: outputs and
-gradients agree with the FP64 reference evaluated at the same BF16-rounded
-weights and inputs to a few parts in 10^2 (8-bit mantissas).
+gradients agree element by element, to 1e-3 of each tensor's largest entry,
+with the FP64 reference evaluated at the same BF16-rounded weights and
+inputs and rounding its activations and back-propagated gradients to BF16
+where the kernels store them (the remaining difference is the FP32 rounding
+of the kernels' sums, plus the rare BF16 rounding that this flips).
 """
 import numpy as np
 import pytest
@@ -38,9 +41,12 @@ def test_forward_matches_reference():
         ctx.mlp_set_weights(w)
         y = ctx.mlp_forward(x)
         np.testing.assert_array_equal(ctx.mlp_get_weights(), w)
-    yo, _ = mlp.forward(mlp.to_bf16(w), mlp.to_bf16(x))
-    scale = max(1.0, float(np.abs(yo).max()))
-    assert np.abs(y - yo).max() <= 3e-2 * scale
+    yo, _ = mlp.forward(mlp.to_bf16(w), mlp.to_bf16(x), bf16=True)
+    scale = float(np.abs(yo).max())
+    np.testing.assert_allclose(y, yo, rtol=0, atol=1e-3 * scale)
+    # the unrounded FP64 network is only close: the BF16 activations matter
+    yf, _ = mlp.forward(mlp.to_bf16(w), mlp.to_bf16(x))
+    assert np.abs(yf - yo).max() > np.abs(y - yo).max()
 
 
 def test_gradients_match_reference():
@@ -56,14 +62,12 @@ def test_gradients_match_reference():
     with pt.Context() as ctx:
         ctx.mlp_set_weights(w)
         loss, g = ctx.mlp_loss_grad(x, t)
-    lo, go = mlp.loss_grad(mlp.to_bf16(w), mlp.to_bf16(x), t)
-    assert loss == pytest.approx(lo, rel=2e-2)
+    lo, go = mlp.loss_grad(mlp.to_bf16(w), mlp.to_bf16(x), t, bf16=True)
+    assert loss == pytest.approx(lo, rel=1e-4)
     gp, gop = mlp.unpack(g), mlp.unpack(go)
     for name, _ in mlp.SIZES:
-        a, b = gp[name].ravel(), gop[name].ravel()
-        rel = np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-30)
-        cos = float(a @ b / max(np.linalg.norm(a) * np.linalg.norm(b), 1e-30))
-        assert rel < 6e-2 and cos > 0.998, (name, rel, cos)
+        a, b = gp[name], gop[name]
+        np.testing.assert_allclose(a, b, rtol=0, atol=1e-3 * float(np.abs(b).max()), err_msg=name)
     # padding rows / columns carry no gradient
     assert np.all(gp["W1"][mlp.IN:] == 0) and np.all(gp["W3"][:, mlp.OUT:] == 0)
 

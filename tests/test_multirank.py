@@ -25,7 +25,7 @@ def _rank(rank, world, port, out):
     dist.init_process_group("gloo", rank=rank, world_size=world)
     import bench
     ms, units = bench.reduce_over_ranks([12.5, 30.0][rank], [1000.0, 3000.0][rank], world, device="cpu")
-    a, starts = bench.workload(rank)
+    a, starts = bench.workload(bench.WORKLOADS["pt128"], rank)
     out.put((rank, ms, units, int(a.codes[:, :50].sum()), int(starts[0].sum())))
     dist.barrier()
     dist.destroy_process_group()

@@ -61,3 +61,21 @@ def test_gtr_joint_distribution():
         assert _within(np.mean(a.codes[2] == i), pi[i], N)  # stationary composition
         for j in range(4):
             assert _within(counts[i, j] / N, joint[i, j], N), (i, j, counts[i, j] / N, joint[i, j])
+
+
+def test_reinsert_leaves_gives_binary_trees_near_the_original():
+    import oracle
+    rng = np.random.default_rng(5)
+    n = 40
+    e = synth.random_topology(n, rng)
+    base = {int(s[0]) | (int(s[1]) << 64) for s in oracle.tree_splits(n, e)}
+    assert oracle.tree_key(n, synth.reinsert_leaves(e, n, 0, rng)) == oracle.tree_key(n, e)
+    moved = 0
+    for k in (1, 3):
+        for _ in range(10):
+            p = synth.reinsert_leaves(e, n, k, rng)
+            deg = np.bincount(p.reshape(-1), minlength=2 * n - 2)
+            assert p.shape == (2 * n - 3, 2) and np.all(deg[:n] == 1) and np.all(deg[n:] == 3)
+            sp = {int(s[0]) | (int(s[1]) << 64) for s in oracle.tree_splits(n, p)}  # raises if not a tree
+            moved += sp != base
+    assert moved >= 15
