@@ -85,7 +85,8 @@ typedef struct {
     int full_max_sweeps;  /* cap on sweeps of the full optimisation */
     int prop_max_sweeps;  /* cap on sweeps of the proposal optimisation */
     int threads;          /* threads per CTA for the site loops (0 = automatic) */
-    size_t mem_budget;    /* device bytes for partial-likelihood buffers per launch group (0 = automatic) */
+    size_t mem_budget;    /* device bytes for partial-likelihood buffers per launch group (0 = automatic:
+                           * 40% of the free device memory when the context is created, at most 96 GB) */
     double branch_prior_rate; /* 0: maximum likelihood (default).  > 0: MAP objective ("Phylogenetic
                                * Topographer", its optional exponential branch-length prior): every length
                                * has an Exponential(rate) prior, each Newton step maximises lnL - rate t,

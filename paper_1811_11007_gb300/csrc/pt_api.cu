@@ -76,9 +76,12 @@ struct Ctx {
     // autotuned CTA sizes of the persistent kernels, per problem bucket
     struct Tune {
         int prop_threads = 0, full_threads = 0;
+        int prop_cluster = 0;  // CTAs per proposal (sites split over a thread-block cluster); 0: the default rule
+        int full_cluster = 0;  // CTAs per tree of the full optimisation; 0: one
         double prop_ms = 0, full_ms = 0;
         int prop_items = 0, full_items = 0;  // size of the launch each was tuned on
-        std::vector<std::pair<int, double>> prop_trials, full_trials;  // (threads, ms) of the tuning runs
+        std::vector<std::pair<int, double>> prop_trials, full_trials;  // (threads, ms) of the tuning runs;
+                                                                        // proposals: threads * 16 + cluster
     };
     bool autotune = false;
     std::string tune_path;
@@ -433,6 +436,21 @@ std::string tune_key(int prec, int C, int n, int P) {
 }
 
 const int kTuneThreads[] = {64, 96, 128, 192, 256, 384, 512};
+const int kTuneClusterThreads[] = {128, 256, 512};
+const int kClusters[] = {2, 4, 8};
+
+// CTAs per proposal when not tuned: one while the whole sum-table fits in a
+// CTA's shared memory; else the smallest cluster whose share leaves room for
+// two CTAs per SM (the sum-table would otherwise stream through L2/HBM at
+// every Newton evaluation).
+int default_cluster(const Ctx& c, int prec, int C, int P, int threads) {
+    if (propose_smem_bytes(prec, C, P, true, threads) <= c.smem_optin) return 1;
+    for (int K : kClusters)
+        if (propose_cluster_ok(prec, C, K) && propose_smem_bytes(prec, C, (P + K - 1) / K + 4, true, threads) <= 110 * 1024 &&
+            propose_cluster_grid(prec, C, K, threads, P) > 0)
+            return K;
+    return 1;
+}
 
 void save_tune(Ctx& c) {
     if (c.tune_path.empty()) return;
@@ -443,10 +461,11 @@ void save_tune(Ctx& c) {
     size_t i = 0;
     for (auto& kv : c.tune) {
         fprintf(f,
-                "  \"%s\": {\"prop_threads\": %d, \"full_threads\": %d, \"prop_ms\": %.4f, \"full_ms\": %.4f, "
-                "\"prop_items\": %d, \"full_items\": %d}%s\n",
-                kv.first.c_str(), kv.second.prop_threads, kv.second.full_threads, kv.second.prop_ms, kv.second.full_ms,
-                kv.second.prop_items, kv.second.full_items, ++i < c.tune.size() ? "," : "");
+                "  \"%s\": {\"prop_threads\": %d, \"prop_cluster\": %d, \"full_threads\": %d, \"full_cluster\": %d, "
+                "\"prop_ms\": %.4f, \"full_ms\": %.4f, \"prop_items\": %d, \"full_items\": %d}%s\n",
+                kv.first.c_str(), kv.second.prop_threads, kv.second.prop_cluster, kv.second.full_threads,
+                kv.second.full_cluster, kv.second.prop_ms, kv.second.full_ms, kv.second.prop_items,
+                kv.second.full_items, ++i < c.tune.size() ? "," : "");
     }
     fprintf(f, "}\n");
     fclose(f);
@@ -478,6 +497,8 @@ void load_tune(Ctx& c) {
         };
         double v;
         if (num("prop_threads", &v)) t.prop_threads = (int)v;
+        if (num("prop_cluster", &v)) t.prop_cluster = (int)v == 2 || (int)v == 4 || (int)v == 8 ? (int)v : 1;
+        if (num("full_cluster", &v)) t.full_cluster = (int)v == 2 || (int)v == 4 || (int)v == 8 ? (int)v : 1;
         if (num("full_threads", &v)) t.full_threads = (int)v;
         if (num("prop_ms", &v)) t.prop_ms = v;
         if (num("full_ms", &v)) t.full_ms = v;
@@ -563,22 +584,35 @@ void run_full_jobs(Ctx& c, std::vector<FullJob> jobs, bool allow_tune = true) {
         const int* gstart;
         int* counter;
         const FullGroup* dg = upload_groups(c, "full", groups, counts, &gstart, &counter);
-        // one launch at a given CTA size; returns its device time when timed
-        auto run = [&](int threads, unsigned long long* stats, bool timed) {
+        // one launch at a given CTA size and number of CTAs per tree (a cluster
+        // of K shares each tree's sites); returns its device time when timed
+        auto run = [&](int threads, int K, unsigned long long* stats, bool timed) {
             const bool smem_tab = fullopt_smem_bytes(prec, C, maxN, maxP, true, threads) <= c.smem_optin;
-            const int bps = std::max(1, fullopt_blocks_per_sm(prec, C, threads, smem_tab, maxN, maxP));
-            const int grid = std::min(total, bps * c.sm_count);
+            int grid = 0;
             void* scratch = nullptr;
-            size_t spc = 0;
-            if (!smem_tab) {
-                spc = (sumtable_bytes(prec, C, maxP) + 255) & ~size_t(255);
-                scratch = buf<unsigned char>(c, "full.scratch", spc * grid);
+            size_t spc = 0, sl = slab_stride;
+            if (K > 1) {
+                const int cgr = fullopt_cluster_grid(prec, C, K, threads, maxN, maxP);
+                grid = std::min(total * K, cgr) / K * K;
+                if (grid == 0) K = 1;
+                sl = 0;
+                for (const FullJob& j : jobs)
+                    sl = std::max(sl, fullopt_slab_bytes(prec, C, j.a->n, cluster_sites(j.a->P, K)));
             }
-            unsigned char* slab = buf<unsigned char>(c, "full.slab", slab_stride * grid);
+            if (K == 1) {
+                sl = slab_stride;
+                const int bps = std::max(1, fullopt_blocks_per_sm(prec, C, threads, smem_tab, maxN, maxP));
+                grid = std::min(total, bps * c.sm_count);
+                if (!smem_tab) {
+                    spc = (sumtable_bytes(prec, C, maxP) + 255) & ~size_t(255);
+                    scratch = buf<unsigned char>(c, "full.scratch", spc * grid);
+                }
+            }
+            unsigned char* slab = buf<unsigned char>(c, "full.slab", sl * grid);
             ck(c, cudaMemsetAsync(counter, 0, sizeof(int), c.stream), "counter");
             size_t e0 = timed ? ev_record(c) : 0;
             launch_fullopt(c.stream, prec, C, dg, gstart, (int)groups.size(), counter, maxN, maxP, kcfg(c), stats,
-                           threads, grid, scratch, spc, slab, slab_stride);
+                           threads, grid, scratch, spc, slab, sl, K);
             ck(c, cudaGetLastError(), "full optimisation launch");
             float ms = 0.f;
             if (timed) {
@@ -589,10 +623,13 @@ void run_full_jobs(Ctx& c, std::vector<FullJob> jobs, bool allow_tune = true) {
             return (double)ms;
         };
         const std::string key = tune_key(prec, C, maxN, maxP);
-        int threads = threads_for(c, maxP);
+        int threads = threads_for(c, maxP), K = 1;
         auto it = c.tune.find(key);
         const bool have = it != c.tune.end() && it->second.full_threads;
-        if (have) threads = it->second.full_threads;
+        if (have) {
+            threads = it->second.full_threads;
+            if (it->second.full_cluster) K = it->second.full_cluster;
+        }
         // tune on launches with enough trees to fill the GPU, and again when a
         // launch is much larger than the one the bucket was tuned on
         const bool big = total >= 2 * c.sm_count && (!have || total >= 4 * it->second.full_items);
@@ -618,28 +655,39 @@ void run_full_jobs(Ctx& c, std::vector<FullJob> jobs, bool allow_tune = true) {
             unsigned long long* tstats = buf<unsigned long long>(c, "tune.stats", kStWords);
             double best = 1e30;
             std::vector<std::pair<int, double>> trials;
-            for (int cand : kTuneThreads) {
+            // candidates: CTA sizes with one CTA per tree, and clusters of K CTAs per tree
+            std::vector<std::pair<int, int>> cands;
+            for (int t : kTuneThreads) cands.push_back({t, 1});
+            for (int k : kClusters)
+                if (propose_cluster_ok(prec, C, k) && (maxP + k - 1) / k >= 64)
+                    for (int t : kTuneClusterThreads)
+                        if (fullopt_cluster_grid(prec, C, k, t, maxN, maxP) > 0) cands.push_back({t, k});
+            int bt = threads, bK = K;
+            for (auto [ct, kc] : cands) {
                 double ms = 1e30;
                 for (int rep = 0; rep < 2; ++rep) {  // best of two: single trials are noisy
-                    const double x = run(cand, tstats, true);
+                    const double x = run(ct, kc, tstats, true);
                     copy(false);
                     if (x > 0) ms = std::min(ms, x);
                 }
-                trials.push_back({cand, ms});
-                if (ms < best) { best = ms; threads = cand; }
+                trials.push_back({kc > 1 ? ct * 16 + kc : ct, ms});
+                if (ms < best) { best = ms; bt = ct; bK = kc; }
             }
             // keep the default unless a candidate is clearly (>= 5%) faster
             const int dflt = threads_for(c, maxP);
             for (auto& tr : trials)
-                if (tr.first == dflt && tr.second <= best * 1.05) { threads = dflt; best = tr.second; }
+                if (tr.first == dflt && tr.second <= best * 1.05) { bt = dflt; bK = 1; best = tr.second; }
+            threads = bt;
+            K = bK;
             c.tune[key].full_trials = trials;
             c.tune[key].full_threads = threads;
+            c.tune[key].full_cluster = K;
             c.tune[key].full_ms = best;
             c.tune[key].full_items = total;
             save_tune(c);
         }
         Span sp(c, 6);
-        run(threads, c.d_stats, false);
+        run(threads, K, c.d_stats, false);
         sp.end();
     }
 }
@@ -1084,20 +1132,28 @@ void expand_batch(Ctx& c, const std::vector<RoundIn>& ins, std::vector<RoundOut>
         const int* gstart;
         int* counter;
         const PropGroup* dg = upload_groups(c, "prop", groups, counts, &gstart, &counter);
-        auto run = [&](int threads, unsigned long long* stats, bool timed) {
+        auto run = [&](int threads, int K, unsigned long long* stats, bool timed) {
             const bool smem_tab = propose_smem_bytes(prec, C, maxP, true, threads) <= c.smem_optin;
-            const int bps = std::max(1, propose_blocks_per_sm(prec, C, threads, smem_tab, maxP));
-            const int grid = std::min(tot, bps * c.sm_count);
+            int grid = 0;
             void* scratch = nullptr;
             size_t spc = 0;
-            if (!smem_tab) {
-                spc = (sumtable_bytes(prec, C, maxP) + 255) & ~size_t(255);
-                scratch = buf<unsigned char>(c, "prop.scratch", spc * grid);
+            if (K > 1) {  // clusters of K CTAs, each CTA a share of the sites
+                const int cgr = propose_cluster_grid(prec, C, K, threads, maxP);
+                grid = std::min(tot * K, cgr) / K * K;
+                if (grid == 0) K = 1;
+            }
+            if (K == 1) {
+                const int bps = std::max(1, propose_blocks_per_sm(prec, C, threads, smem_tab, maxP));
+                grid = std::min(tot, bps * c.sm_count);
+                if (!smem_tab) {
+                    spc = (sumtable_bytes(prec, C, maxP) + 255) & ~size_t(255);
+                    scratch = buf<unsigned char>(c, "prop.scratch", spc * grid);
+                }
             }
             ck(c, cudaMemsetAsync(counter, 0, sizeof(int), c.stream), "counter");
             size_t e0 = timed ? ev_record(c) : 0;
             launch_propose(c.stream, prec, C, dg, gstart, (int)groups.size(), counter, kcfg(c), stats, threads, grid,
-                           scratch, spc, maxP);
+                           scratch, spc, maxP, K);
             ck(c, cudaGetLastError(), "propose launch");
             float ms = 0.f;
             if (timed) {
@@ -1109,34 +1165,54 @@ void expand_batch(Ctx& c, const std::vector<RoundIn>& ins, std::vector<RoundOut>
         };
         const std::string key = tune_key(prec, C, maxN, maxP);
         int threads = threads_for(c, maxP);
+        int K = default_cluster(c, prec, C, maxP, threads);
         auto tt = c.tune.find(key);
         const bool have = tt != c.tune.end() && tt->second.prop_threads;
-        if (have) threads = tt->second.prop_threads;
+        if (have) {
+            threads = tt->second.prop_threads;
+            if (tt->second.prop_cluster) K = tt->second.prop_cluster;
+        }
         const bool big = tot >= 4 * c.sm_count && (!have || tot >= 4 * tt->second.prop_items);
         if (c.autotune && big) {  // trials rewrite the same outputs; inputs are not modified
             unsigned long long* tstats = buf<unsigned long long>(c, "tune.stats", kStWords);
             double best = 1e30;
             std::vector<std::pair<int, double>> trials;
-            for (int cand : kTuneThreads) {
+            // candidates: CTA sizes x sites per CTA (the whole alignment, or a 1/K share
+            // in a cluster of K CTAs); single CTAs whose sum-table does not fit in shared
+            // memory are tried at the default size only
+            std::vector<std::pair<int, int>> cands;
+            const bool fits = propose_smem_bytes(prec, C, maxP, true, threads_for(c, maxP)) <= c.smem_optin;
+            if (fits) for (int t : kTuneThreads) cands.push_back({t, 1});
+            else cands.push_back({threads_for(c, maxP), 1});
+            for (int k : kClusters)
+                if (propose_cluster_ok(prec, C, k) && (maxP + k - 1) / k >= 64)
+                    for (int t : kTuneClusterThreads) cands.push_back({t, k});
+            const int dK = default_cluster(c, prec, C, maxP, threads_for(c, maxP));
+            int bt = threads, bK = K;
+            for (auto [ct, kc] : cands) {
                 double ms = 1e30;
                 for (int rep = 0; rep < 2; ++rep) {  // best of two: single trials are noisy
-                    const double x = run(cand, tstats, true);
+                    const double x = run(ct, kc, tstats, true);
                     if (x > 0) ms = std::min(ms, x);
                 }
-                trials.push_back({cand, ms});
-                if (ms < best) { best = ms; threads = cand; }
+                trials.push_back({ct * 16 + kc, ms});
+                if (ms < best) { best = ms; bt = ct; bK = kc; }
             }
+            // keep the default unless a candidate is clearly (>= 5%) faster
             const int dflt = threads_for(c, maxP);
             for (auto& tr : trials)
-                if (tr.first == dflt && tr.second <= best * 1.05) { threads = dflt; best = tr.second; }
+                if (tr.first == dflt * 16 + dK && tr.second <= best * 1.05) { bt = dflt; bK = dK; best = tr.second; }
+            threads = bt;
+            K = bK;
             c.tune[key].prop_trials = trials;
             c.tune[key].prop_threads = threads;
+            c.tune[key].prop_cluster = K;
             c.tune[key].prop_ms = best;
             c.tune[key].prop_items = tot;
             save_tune(c);
         }
         Span sp3(c, 3);
-        run(threads, c.d_stats, false);
+        run(threads, K, c.d_stats, false);
         sp3.end();
         if (c.log_on)
             for (size_t q = ci; q < ce; ++q) {
@@ -1441,7 +1517,7 @@ struct GraphRound {
     cudaGraphExec_t exec = nullptr;
     long long kernels = 0;      // kernel nodes per replay
     bool mlp = false;
-    int prop_threads = 0, full_threads = 0;
+    int prop_threads = 0, full_threads = 0, prop_cluster = 1, full_cluster = 1;
     // di layout: F [na], m [na], ncand [na], W [na], K [na], G [na], round [na],
     // gstart (proposal) [na + 1], gstart (full optimisation) [na + 1], two counters,
     // perm [na] (group order of the persistent launches: larger problems first)
@@ -1550,7 +1626,7 @@ void graph_record(Ctx& c, GraphRound& g, cudaStream_t s, int C, int maxN, int ma
     launch_prefix_counts(s, na, di + g.oW(), di + g.oPerm(), di + g.oGSP());
     cudaMemsetAsync(di + g.oCP(), 0, sizeof(int), s);
     launch_propose(s, prec, C, g.dpg, di + g.oGSP(), na, di + g.oCP(), kcfg(c), c.d_stats, g.prop_threads, pgrid,
-                   g.prop_scratch, pspc, maxP);
+                   g.prop_scratch, pspc, maxP, g.prop_cluster);
     if (g.mlp)  // the judges take this round's proposals
         for (int k = 0; k < na; ++k) {
             GraphAln& x = g.a[k];
@@ -1569,7 +1645,7 @@ void graph_record(Ctx& c, GraphRound& g, cudaStream_t s, int C, int maxN, int ma
     launch_prefix_counts(s, na, di + g.oK(), di + g.oPerm(), di + g.oGSF());
     cudaMemsetAsync(di + g.oCF(), 0, sizeof(int), s);
     launch_fullopt(s, prec, C, g.dfg, di + g.oGSF(), na, di + g.oCF(), maxN, maxP, kcfg(c), c.d_stats,
-                   g.full_threads, fgrid, g.full_scratch, fspc, g.slab, slab_stride);
+                   g.full_threads, fgrid, g.full_scratch, fspc, g.slab, slab_stride, g.full_cluster);
     for (int k = 0; k < na; ++k) {
         GraphAln& x = g.a[k];
         AlnState& A = c.alns[x.aln];
@@ -1627,17 +1703,44 @@ GraphRound* graph_create(Ctx& c, const std::vector<int>& ids, const std::vector<
     // CTA sizes: the autotuned ones of this problem bucket when known
     const std::string key = tune_key(prec, C, maxN, maxP);
     g.prop_threads = g.full_threads = threads_for(c, maxP);
+    g.prop_cluster = default_cluster(c, prec, C, maxP, g.prop_threads);
     auto tt = c.tune.find(key);
     if (tt != c.tune.end()) {
         if (tt->second.prop_threads) g.prop_threads = tt->second.prop_threads;
+        if (tt->second.prop_cluster) g.prop_cluster = tt->second.prop_cluster;
         if (tt->second.full_threads) g.full_threads = tt->second.full_threads;
+        if (tt->second.full_cluster) g.full_cluster = tt->second.full_cluster;
     }
-    const bool ptab = propose_smem_bytes(prec, C, maxP, true, g.prop_threads) <= c.smem_optin;
+    bool ptab = propose_smem_bytes(prec, C, maxP, true, g.prop_threads) <= c.smem_optin;
     const bool ftab = fullopt_smem_bytes(prec, C, maxN, maxP, true, g.full_threads) <= c.smem_optin;
-    const int pgrid = std::max(1, propose_blocks_per_sm(prec, C, g.prop_threads, ptab, maxP)) * c.sm_count;
-    const int fgrid = std::max(1, fullopt_blocks_per_sm(prec, C, g.full_threads, ftab, maxN, maxP)) * c.sm_count;
+    int pgrid = std::max(1, propose_blocks_per_sm(prec, C, g.prop_threads, ptab, maxP)) * c.sm_count;
+    if (g.prop_cluster > 1) {  // clusters: every CTA's sum-table share in shared memory
+        const int cgrid = propose_cluster_grid(prec, C, g.prop_cluster, g.prop_threads, maxP);
+        if (cgrid > 0) {
+            pgrid = cgrid;
+            ptab = true;
+        } else {
+            g.prop_cluster = 1;
+        }
+    }
+    int fgrid = std::max(1, fullopt_blocks_per_sm(prec, C, g.full_threads, ftab, maxN, maxP)) * c.sm_count;
+    bool ftab2 = ftab;
+    if (g.full_cluster > 1) {  // the tuned cluster form of the visits, as pt_expand_batch runs them
+        const int cgrid = fullopt_cluster_grid(prec, C, g.full_cluster, g.full_threads, maxN, maxP);
+        if (cgrid > 0) {
+            fgrid = cgrid;
+            ftab2 = true;
+            slab_stride = 0;
+            for (int k = 0; k < na; ++k) {
+                const AlnState& A = c.alns[ids[k]];
+                slab_stride = std::max(slab_stride, fullopt_slab_bytes(prec, C, A.n, cluster_sites(A.P, g.full_cluster)));
+            }
+        } else {
+            g.full_cluster = 1;
+        }
+    }
     const size_t tabb = (sumtable_bytes(prec, C, maxP) + 255) & ~size_t(255);
-    const size_t pspc = ptab ? 0 : tabb, fspc = ftab ? 0 : tabb;
+    const size_t pspc = ptab ? 0 : tabb, fspc = ftab2 ? 0 : tabb;
     Arena ar;
     for (GraphAln& x : g.a) {
         const int n = x.n, E = x.E, cap = x.cap, F = x.F_cap;
@@ -1902,7 +2005,9 @@ pt_status pt_create(pt_ctx** out, const pt_config* cfg) {
         ck(c, cudaMemset(c.d_err, 0, sizeof(int32_t) * kErrWords), "memset");
         size_t fr, tot;
         ck(c, cudaMemGetInfo(&fr, &tot), "cudaMemGetInfo");
-        c.budget = c.cfg.mem_budget ? c.cfg.mem_budget : std::min<size_t>(fr / 4, (size_t)24 << 30);
+        // frontier partials of one proposal wave: 40% of the free memory at creation, at
+        // most 96 GB (a 256-tree frontier of 128 taxa x 6000 patterns takes ~50 GB: one wave)
+        c.budget = c.cfg.mem_budget ? c.cfg.mem_budget : std::min<size_t>(fr / 5 * 2, (size_t)96 << 30);
     } catch (const Fail& e) {
         pt_destroy(ctx);
         return e.st;
@@ -2459,16 +2564,21 @@ pt_status pt_autotune_report(pt_ctx* ctx, char* out, size_t cap, size_t* len) {
         for (auto& kv : c.tune) {
             char b[256];
             snprintf(b, sizeof b,
-                     "\"%s\": {\"prop_threads\": %d, \"full_threads\": %d, \"prop_ms\": %.4f, \"full_ms\": %.4f, "
-                     "\"prop_items\": %d, \"full_items\": %d",
-                     kv.first.c_str(), kv.second.prop_threads, kv.second.full_threads, kv.second.prop_ms,
-                     kv.second.full_ms, kv.second.prop_items, kv.second.full_items);
+                     "\"%s\": {\"prop_threads\": %d, \"prop_cluster\": %d, \"full_threads\": %d, "
+                     "\"full_cluster\": %d, \"prop_ms\": %.4f, \"full_ms\": %.4f, \"prop_items\": %d, \"full_items\": %d",
+                     kv.first.c_str(), kv.second.prop_threads, kv.second.prop_cluster, kv.second.full_threads,
+                     kv.second.full_cluster, kv.second.prop_ms, kv.second.full_ms, kv.second.prop_items,
+                     kv.second.full_items);
             txt += b;
             for (int w = 0; w < 2; ++w) {
                 const auto& tr = w == 0 ? kv.second.prop_trials : kv.second.full_trials;
                 txt += w == 0 ? ", \"prop_trials\": {" : ", \"full_trials\": {";
                 for (size_t j = 0; j < tr.size(); ++j) {
-                    snprintf(b, sizeof b, "%s\"%d\": %.4f", j ? ", " : "", tr[j].first, tr[j].second);
+                    if (w == 0 || tr[j].first >= 1024)  // "threads x CTAs per item (tree)"
+                        snprintf(b, sizeof b, "%s\"%dx%d\": %.4f", j ? ", " : "", tr[j].first / 16, tr[j].first % 16,
+                                 tr[j].second);
+                    else
+                        snprintf(b, sizeof b, "%s\"%d\": %.4f", j ? ", " : "", tr[j].first, tr[j].second);
                     txt += b;
                 }
                 txt += "}";

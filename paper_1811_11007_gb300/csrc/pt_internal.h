@@ -271,12 +271,27 @@ struct FullGroup {
 // Batched launches over groups: gstart [ngroups + 1] is the prefix sum of the
 // groups' item (tree) counts (device); counter (device, zeroed) hands out the
 // items dynamically, in order, to the persistent CTAs.
+// cluster > 1 (FP32, 4 categories; 2, 4 or 8): thread-block clusters of that many CTAs
+// share each item, each CTA a contiguous share of the sites with its sum-table in
+// shared memory (scratch unused); grid is then a multiple of cluster.
 void launch_propose(cudaStream_t s, int prec, int C, const PropGroup* groups, const int* gstart, int ngroups,
                     int* counter, Cfg cfg, unsigned long long* stats, int threads, int grid, void* scratch,
-                    size_t scratch_per_cta, int maxP);
+                    size_t scratch_per_cta, int maxP, int cluster = 1);
+// Whether the proposal kernel has a cluster form for (precision, categories, cluster size).
+bool propose_cluster_ok(int prec, int C, int K);
+// Resident CTAs of the cluster form on the whole GPU (a multiple of K; 0 when it cannot run).
+int propose_cluster_grid(int prec, int C, int K, int threads, int maxP);
+// cluster > 1 (slab mode, FP32, 4 categories): clusters of that many CTAs share each tree,
+// each CTA a share of the sites (cluster_sites(P, cluster)) with its own slab of
+// slab_per_cta = fullopt_slab_bytes of the share; grid a multiple of cluster.
 void launch_fullopt(cudaStream_t s, int prec, int C, const FullGroup* groups, const int* gstart, int ngroups,
                     int* counter, int maxN, int maxP, Cfg cfg, unsigned long long* stats, int threads, int grid,
-                    void* scratch, size_t scratch_per_cta, void* slab = nullptr, size_t slab_per_cta = 0);
+                    void* scratch, size_t scratch_per_cta, void* slab = nullptr, size_t slab_per_cta = 0,
+                    int cluster = 1);
+// Resident CTAs of the full optimisation's cluster form (a multiple of K; 0: cannot run).
+int fullopt_cluster_grid(int prec, int C, int K, int threads, int maxN, int maxP);
+// Sites per CTA when K CTAs share P sites (a multiple of 4).
+inline int cluster_sites(int P, int K) { return K > 1 ? ((P + K - 1) / K + 3) & ~3 : P; }
 // Bytes of one CTA's partials slab for trees of n taxa and P patterns (a multiple of 256).
 size_t fullopt_slab_bytes(int prec, int C, int n, int P);
 

@@ -15,6 +15,7 @@
 #include "pt_internal.h"
 #include "pt_gamma.h"
 
+#include <cooperative_groups.h>
 #include <cuda_runtime.h>
 
 #include <atomic>
@@ -1283,7 +1284,40 @@ struct NewtonSmem {
     double tb;             // broadcast of the current length
     int done;
     int leader;            // the warp that takes the Newton steps
+    double cx[2][3];       // cluster exchange: this CTA's partial sums, two alternating slots
 };
+
+// Sums of up to three values held by one thread (`writer`) of each CTA of a
+// thread-block cluster of K CTAs, returned to every thread of every CTA.  The
+// K partials are added in rank order, so every CTA gets the same bits (the
+// CTAs of a cluster then take identical Newton steps).  Every thread of every
+// CTA must call it the same number of times; `seq` (a per-thread count,
+// equal in all threads) alternates the slot, so a CTA writes a slot only
+// after every CTA has passed the barrier of the exchange that last read it.
+template <int K>
+__device__ __forceinline__ void cluster_sum(bool writer, double (*cx)[3], int& seq, double& a, double& b, double& c) {
+    namespace cg = cooperative_groups;
+    cg::cluster_group cl = cg::this_cluster();
+    const int s = seq & 1;
+    ++seq;
+    if (writer) {
+        cx[s][0] = a;
+        cx[s][1] = b;
+        cx[s][2] = c;
+    }
+    cl.sync();
+    double x = 0.0, y = 0.0, z = 0.0;
+#pragma unroll
+    for (int r = 0; r < K; ++r) {
+        const double* q = cl.map_shared_rank(&cx[s][0], r);
+        x += q[0];
+        y += q[1];
+        z += q[2];
+    }
+    a = x;
+    b = y;
+    c = z;
+}
 
 __device__ __forceinline__ double warp_sum(double x) {
     for (int o = 16; o; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
@@ -1419,8 +1453,10 @@ __device__ __forceinline__ bool newton_step(double& t, double& lo, double& hi, d
 __device__ __forceinline__ double log_split(double x) { return log(x); }
 
 // lnL of the current sum-table at length t: sum_p w_p (ln L_p + E_p ln 2), FP64 accumulation.
-template <typename R, int C>
-__device__ double eval_lnl(const Model& M, const STab<R, C>& st, int P, double t, NewtonSmem<R, C>& ns) {
+// K > 1: the CTA's sites are its share of a cluster's; the result is the cluster's sum.
+template <typename R, int C, int K = 1>
+__device__ double eval_lnl(const Model& M, const STab<R, C>& st, int P, double t, NewtonSmem<R, C>& ns,
+                           int* cseq = nullptr) {
     put_egh<R, C>(M, t, ns, true);
     __syncthreads();
     R e[4 * C];
@@ -1470,6 +1506,10 @@ __device__ double eval_lnl(const Model& M, const STab<R, C>& st, int P, double t
     double tot = 0.0;
     for (int i = 0; i < nw; ++i) tot += ns.red[i][0];
     __syncthreads();
+    if constexpr (K > 1) {
+        double b = 0.0, c = 0.0;
+        cluster_sum<K>(threadIdx.x == 0, ns.cx, *cseq, tot, b, c);
+    }
     return tot;
 }
 
@@ -1479,9 +1519,12 @@ __device__ double eval_lnl(const Model& M, const STab<R, C>& st, int P, double t
 // of the next length; after the last step warp 0 also writes P_r(t) of the
 // final length into Pdst [C][16] (visible when the call returns).  Returns
 // the final length (in every thread).
-template <typename R, int C>
+// K > 1: the sum-table holds this CTA's share of a cluster's sites; each
+// evaluation's derivative sums are reduced over the cluster (cluster_sum), and
+// every CTA takes the same step.
+template <typename R, int C, int K = 1>
 __device__ double newton_solve(const Model& M, const Cfg& cfg, const STab<R, C>& st, int P, double t0,
-                               NewtonSmem<R, C>& ns, int& evals, bool& converged, R* Pdst) {
+                               NewtonSmem<R, C>& ns, int& evals, bool& converged, R* Pdst, int* cseq = nullptr) {
     double lo = cfg.tmin, hi = cfg.tmax;
     double t = fmin(fmax(t0, lo), hi);
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = (blockDim.x + 31) >> 5;
@@ -1526,6 +1569,8 @@ __device__ double newton_solve(const Model& M, const Cfg& cfg, const STab<R, C>&
         }
         __syncthreads();
         ++evals;
+        double D1 = 0.0, D2 = 0.0;
+        float D2f = 0.f;
         if (w == ld) {
             // Both derivative sums in one FP64 butterfly: lane j < nw holds warp j's
             // d1 partial, lane 16 + j its d2 partial; offsets below 16 keep the halves
@@ -1547,10 +1592,17 @@ __device__ double newton_solve(const Model& M, const Cfg& cfg, const STab<R, C>&
                 D += __shfl_xor_sync(0xffffffffu, D, o);
                 Df += __shfl_xor_sync(0xffffffffu, Df, o);
             }
-            double D1 = __shfl_sync(0xffffffffu, D, 0);
-            const double D2 = __shfl_sync(0xffffffffu, D, 16);
+            D1 = __shfl_sync(0xffffffffu, D, 0);
+            D2 = __shfl_sync(0xffffffffu, D, 16);
+            D2f = __shfl_sync(0xffffffffu, Df, 16);
+        }
+        if constexpr (K > 1) {  // the cluster's sums (every thread takes part in the exchange)
+            double d2f = D2f;
+            cluster_sum<K>(w == ld && lane == 0, ns.cx, *cseq, D1, D2, d2f);
+            D2f = (float)d2f;
+        }
+        if (w == ld) {
             if (prior) D1 -= cfg.prior_rate;  // MAP: the prior's slope
-            const float D2f = __shfl_sync(0xffffffffu, Df, 16);
             const bool done = newton_step(t, lo, hi, D1, D2, D2f, cfg.newton_tol);
             const bool last = done || it + 1 == cfg.newton_maxit;
             if (!last) put_egh<R, C>(M, t, ns, false, lane);
@@ -1595,9 +1647,10 @@ __device__ __forceinline__ double block_sum(double acc, double (*red)[2]) {
 // Proposal: the four members A, X2 (at u) and B, Y2 (at v) around the new
 // edge, P matrices of the five final lengths as pairs (Ph/Pl [5][C*16]: central,
 // A, B, C, D; mbr = each member's branch); L_p across the central branch.
-template <int C>
+template <int C, int K = 1>
 __device__ __noinline__ double propose_score_f2(const Src2<C>* mem, const int* mbr, const float* Ph, const float* Pl,
-                                                const double* pi, const int32_t* w, int P, double (*red)[2]) {
+                                                const double* pi, const int32_t* w, int p0, int p1, double (*red)[2],
+                                                double (*cx)[3], int* cseq) {
     float pih[4], pil[4];
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
@@ -1606,7 +1659,7 @@ __device__ __noinline__ double propose_score_f2(const Src2<C>* mem, const int* m
         pil[i] = x.l;
     }
     double acc = 0.0;
-    for (int p = threadIdx.x; p < P; p += blockDim.x) {
+    for (int p = p0 + threadIdx.x; p < p1; p += blockDim.x) {
         int kk = 0;
 #pragma unroll
         for (int m = 0; m < 4; ++m) kk += mem[m].tip ? 0 : mem[m].scl[p];
@@ -1631,7 +1684,12 @@ __device__ __noinline__ double propose_score_f2(const Src2<C>* mem, const int* m
         L = F2{L.h * (1.0f / C), L.l * (1.0f / C)};  // 1/C is a power of two for C = 1, 2, 4
         acc += (double)w[p] * f2_log(L, E - Prec<float>::kScaleExp * kk);
     }
-    return block_sum(acc, red);
+    double tot = block_sum(acc, red);
+    if constexpr (K > 1) {
+        double b = 0.0, c = 0.0;
+        cluster_sum<K>(threadIdx.x == 0, cx, *cseq, tot, b, c);
+    }
+    return tot;
 }
 
 // Visit: a pruning pass in pairs over one tree's partials buffer.  D_v of
@@ -1640,12 +1698,16 @@ __device__ __noinline__ double propose_score_f2(const Src2<C>* mem, const int* m
 // combined with leaf 0 across the edge of n.  The block computes each node's
 // P pairs (its two children, and n's own edge at the root) into Pf/Pfl from
 // W and lr (as NewtonSmem) at the lengths len.
-template <int C>
-__device__ __noinline__ double fullopt_score_f2(int n, const int32_t* ch, const double* len, Aln A, float* clv,
-                                                int32_t* scl, const double* W, const double* lr, float* Pf, float* Pfl,
-                                                double* exf, const double* pi, double (*red)[2]) {
+// Sites: tips0 / w0 are the alignment's tip rows (row stride A.P) and weights
+// offset to this CTA's first site, Pl sites of them, stored vectors of Ps
+// sites per slot; with K > 1 the result is summed over the cluster.
+template <int C, int K = 1>
+__device__ __noinline__ double fullopt_score_f2(int n, const int32_t* ch, const double* len, Aln A, const uint8_t* tips0,
+                                                const int32_t* w0, int Pl, int Ps, float* clv, int32_t* scl,
+                                                const double* W, const double* lr, float* Pf, float* Pfl, double* exf,
+                                                const double* pi, double (*red)[2], double (*cx)[3], int* cseq) {
     const int NN = 2 * n - 2, P = A.P;
-    const size_t sstride = (size_t)P * 4 * C;
+    const size_t sstride = (size_t)Ps * 4 * C;
     float pih[4], pil[4];
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
@@ -1654,9 +1716,9 @@ __device__ __noinline__ double fullopt_score_f2(int n, const int32_t* ch, const 
         pil[i] = x.l;
     }
     auto src = [&](int v) {
-        if (v < n) return Src2<C>{nullptr, nullptr, nullptr, A.tips + (size_t)v * P};
+        if (v < n) return Src2<C>{nullptr, nullptr, nullptr, tips0 + (size_t)v * P};
         return Src2<C>{clv + (size_t)(v - n) * sstride, clv + (size_t)(n - 2 + (v - n - 1)) * sstride,
-                       scl + (size_t)(v - n) * P, nullptr};
+                       scl + (size_t)(v - n) * Ps, nullptr};
     };
     double acc = 0.0;
     for (int v = NN - 1; v >= n; --v) {
@@ -1674,7 +1736,7 @@ __device__ __noinline__ double fullopt_score_f2(int n, const int32_t* ch, const 
         }
         __syncthreads();
         const Src2<C> s0 = src(c0), s1 = src(c1);
-        for (int p = threadIdx.x; p < P; p += blockDim.x) {
+        for (int p = threadIdx.x; p < Pl; p += blockDim.x) {
             const int kk = (s0.tip ? 0 : s0.scl[p]) + (s1.tip ? 0 : s1.scl[p]);
             if (v > n) {
                 float dh[4 * C], dl[4 * C];
@@ -1687,9 +1749,9 @@ __device__ __noinline__ double fullopt_score_f2(int n, const int32_t* ch, const 
                 }
                 const int sc = f2_rescale<C>(dh, dl);
                 f2_store<C>(clv + (size_t)(v - n) * sstride, clv + (size_t)(n - 2 + (v - n - 1)) * sstride, p, dh, dl);
-                scl[(size_t)(v - n) * P + p] = kk + sc;
+                scl[(size_t)(v - n) * Ps + p] = kk + sc;
             } else {
-                const int code = A.tips[p];  // leaf 0
+                const int code = tips0[p];  // leaf 0
                 F2 L{0.f, 0.f};
                 int E = 0;
                 for (int r = 0; r < C; ++r) {
@@ -1706,11 +1768,16 @@ __device__ __noinline__ double fullopt_score_f2(int n, const int32_t* ch, const 
                     f2_merge(L, E, Lr, e);
                 }
                 L = F2{L.h * (1.0f / C), L.l * (1.0f / C)};
-                acc += (double)A.w[p] * f2_log(L, E - Prec<float>::kScaleExp * kk);
+                acc += (double)w0[p] * f2_log(L, E - Prec<float>::kScaleExp * kk);
             }
         }
     }
-    return block_sum(acc, red);
+    double tot = block_sum(acc, red);
+    if constexpr (K > 1) {
+        double b = 0.0, c = 0.0;
+        cluster_sum<K>(threadIdx.x == 0, cx, *cseq, tot, b, c);
+    }
+    return tot;
 }
 
 // ---------------------------------------------------------------- P matrices of tree sets
@@ -1880,7 +1947,10 @@ struct ProposeSmem {
     NewtonSmem<R, C> ns;
 };
 
-template <typename R, int C, bool kSmemTab>
+// K > 1: launched as clusters of K CTAs; the CTAs of a cluster work on the
+// same item, each on a contiguous share of the sites (its sum-table in shared
+// memory), with the Newton sums and scores reduced over the cluster.
+template <typename R, int C, bool kSmemTab, int K = 1>
 __global__ void __launch_bounds__(512) k_propose(const PropGroup* __restrict__ groups, const int* __restrict__ gstart,
                                                  int ngroups, int* counter, Cfg cfg, unsigned long long* stats,
                                                  unsigned char* scratch, size_t scratch_per_cta) {
@@ -1891,24 +1961,40 @@ __global__ void __launch_bounds__(512) k_propose(const PropGroup* __restrict__ g
     const int total = gstart[ngroups];
     const int nb = cfg.propose_mode == 1 ? 1 : 5;
     unsigned long long evals_total = 0, sweeps_total = 0, nonconv = 0;
+    int cseq = 0;  // cluster exchanges so far (equal in every thread of the cluster)
+    const int rank = K > 1 ? (int)cooperative_groups::this_cluster().block_rank() : 0;
     while (true) {
-        __syncthreads();  // previous item done with shared memory
-        if (threadIdx.x == 0) {
+        // previous item done with shared memory (in every CTA of the cluster: rank 0 writes theirs)
+        if constexpr (K > 1) cooperative_groups::this_cluster().sync();
+        else __syncthreads();
+        if (threadIdx.x == 0 && rank == 0) {
             const int x = atomicAdd(counter, 1);
             int k = 0;
             while (k + 1 < ngroups && gstart[k + 1] <= x) ++k;
-            sm.next = x;
-            sm.grp = k;
+            if constexpr (K > 1) {
+                cooperative_groups::cluster_group cl = cooperative_groups::this_cluster();
+                for (int r = 0; r < K; ++r) {
+                    *cl.map_shared_rank(&sm.next, r) = x;
+                    *cl.map_shared_rank(&sm.grp, r) = k;
+                }
+            } else {
+                sm.next = x;
+                sm.grp = k;
+            }
         }
-        __syncthreads();
+        if constexpr (K > 1) cooperative_groups::this_cluster().sync();
+        else __syncthreads();
         const int x = sm.next;
         if (x >= total) break;
         const PropGroup& G = groups[sm.grp];
         const int o = x - gstart[sm.grp];
         const Model& M = G.M;
         const int n = G.fr.n, NN = 2 * n - 2, P = G.A.P;
+        // this CTA's sites [p0, p1) (all of them when K = 1)
+        const int S = K > 1 ? (((P + K - 1) / K + 3) & ~3) : P;
+        const int p0 = min(P, rank * S), p1 = min(P, p0 + S), Pl = p1 - p0;
         STab<R, C> st;
-        st.pcap = (P + 3) & ~3;
+        st.pcap = (S + 3) & ~3;
         st.s = reinterpret_cast<R*>(tab_base);
         st.ew = st.s + (size_t)4 * C * st.pcap;
         const size_t sstride = (size_t)P * 4 * C;
@@ -2009,7 +2095,8 @@ __global__ void __launch_bounds__(512) k_propose(const PropGroup* __restrict__ g
                 const R* P1 = sm.Pm[sm.mbr[i1m]];
                 const R* P2 = sm.Pm[sm.mbr[i2m]];
                 const R* P3 = sm.Pm[sm.mbr[i3m]];
-                for (int p = threadIdx.x; p < P; p += blockDim.x) {
+                for (int pl = threadIdx.x; pl < Pl; pl += blockDim.x) {
+                    const int p = p0 + pl;
                     R X[4 * C], Y[4 * C], t0[4 * C], t1[4 * C];
                     int k0, k1, k2, k3;
                     apply_p<R, C>(P0, a0, p, t0, k0);
@@ -2033,13 +2120,13 @@ __global__ void __launch_bounds__(512) k_propose(const PropGroup* __restrict__ g
                     int ex = normalise<R, C>(X), ey = normalise<R, C>(Y);
                     R s4[4 * C];
                     sumtable<R, C>(sm.Mt, sm.pi, X, Y, s4);
-                    st.put(p, s4, (R)(ex + ey - Prec<R>::kScaleExp * (k0 + k1 + k2 + k3)), (R)G.A.w[p]);
+                    st.put(pl, s4, (R)(ex + ey - Prec<R>::kScaleExp * (k0 + k1 + k2 + k3)), (R)G.A.w[p]);
                 }
                 const double told = sm.T[b];
                 int ev;
                 bool conv;
                 // new length; the solve leaves P matrices of branch b at it in sm.Pm[b]
-                const double t = newton_solve<R, C>(M, cfg, st, P, told, sm.ns, ev, conv, sm.Pm[b]);
+                const double t = newton_solve<R, C, K>(M, cfg, st, Pl, told, sm.ns, ev, conv, sm.Pm[b], &cseq);
                 moved = fmax(moved, fabs(t - told));
                 evals_total += ev;
                 item_evals += ev;
@@ -2070,16 +2157,16 @@ __global__ void __launch_bounds__(512) k_propose(const PropGroup* __restrict__ g
                 for (int m = 0; m < 4; ++m)
                     mem[m] = Src2<C>{reinterpret_cast<const float*>(sm.msrc[m].clv), sm.mlo[m], sm.msrc[m].scl,
                                      sm.msrc[m].tip};
-                f1 = propose_score_f2<C>(mem, sm.mbr, reinterpret_cast<const float*>(sm.Pm), &sm.Plo[0][0], M.pi,
-                                         G.A.w, P, sm.ns.red);
+                f1 = propose_score_f2<C, K>(mem, sm.mbr, reinterpret_cast<const float*>(sm.Pm), &sm.Plo[0][0], M.pi,
+                                            G.A.w, p0, p1, sm.ns.red, sm.ns.cx, &cseq);
             } else {
-                f1 = eval_lnl<R, C>(M, st, P, tlast, sm.ns);
+                f1 = eval_lnl<R, C, K>(M, st, Pl, tlast, sm.ns, &cseq);
             }
         } else {
-            f1 = eval_lnl<R, C>(M, st, P, tlast, sm.ns);
+            f1 = eval_lnl<R, C, K>(M, st, Pl, tlast, sm.ns, &cseq);
         }
         sweeps_total += sweeps;
-        if (threadIdx.x == 0) {
+        if (threadIdx.x == 0 && rank == 0) {
             if (__double_as_longlong(cfg.prior_rate) != 0) {  // MAP: log prior of the neighbour's lengths
                 double sum = 0.0;
                 for (int w = 1; w < NN; ++w) sum += len[w];
@@ -2103,11 +2190,12 @@ __global__ void __launch_bounds__(512) k_propose(const PropGroup* __restrict__ g
             }
         }
     }
-    if (threadIdx.x == 0) {
+    if (threadIdx.x == 0 && rank == 0) {
         atomicAdd(&stats[kStPropEvals], evals_total);
         atomicAdd(&stats[kStPropSweeps], sweeps_total);
         atomicAdd(&stats[kStNonconv], nonconv);
     }
+    if constexpr (K > 1) cooperative_groups::this_cluster().sync();  // no CTA leaves while others may read it
 }
 
 // ---------------------------------------------------------------- full optimisation (K7)
@@ -2125,7 +2213,10 @@ struct FullSmem {
     NewtonSmem<R, C> ns;
 };
 
-template <typename R, int C, bool kSmemTab>
+// K > 1: launched as clusters of K CTAs working on the same tree, each on a
+// contiguous share of the sites (partials slab and sum-table of its share),
+// Newton sums and scores reduced over the cluster; slab mode only.
+template <typename R, int C, bool kSmemTab, int K = 1>
 __global__ void __launch_bounds__(512) k_fullopt(const FullGroup* __restrict__ groups, const int* __restrict__ gstart,
                                                  int ngroups, int* counter, int nn_max, Cfg cfg,
                                                  unsigned long long* stats, unsigned char* scratch,
@@ -2140,16 +2231,29 @@ __global__ void __launch_bounds__(512) k_fullopt(const FullGroup* __restrict__ g
     unsigned char* const tab_base = kSmemTab ? smraw + off : scratch + (size_t)blockIdx.x * scratch_per_cta;
     const int total = gstart[ngroups];
     unsigned long long evals_total = 0, sweeps_total = 0, nonconv = 0;
+    int cseq = 0;  // cluster exchanges so far (equal in every thread of the cluster)
+    const int rank = K > 1 ? (int)cooperative_groups::this_cluster().block_rank() : 0;
     while (true) {
-        __syncthreads();
-        if (threadIdx.x == 0) {
+        // previous tree done with shared memory (in every CTA of the cluster: rank 0 writes theirs)
+        if constexpr (K > 1) cooperative_groups::this_cluster().sync();
+        else __syncthreads();
+        if (threadIdx.x == 0 && rank == 0) {
             const int x = atomicAdd(counter, 1);
             int k = 0;
             while (k + 1 < ngroups && gstart[k + 1] <= x) ++k;
-            sm.next = x;
-            sm.grp = k;
+            if constexpr (K > 1) {
+                cooperative_groups::cluster_group cl = cooperative_groups::this_cluster();
+                for (int r = 0; r < K; ++r) {
+                    *cl.map_shared_rank(&sm.next, r) = x;
+                    *cl.map_shared_rank(&sm.grp, r) = k;
+                }
+            } else {
+                sm.next = x;
+                sm.grp = k;
+            }
         }
-        __syncthreads();
+        if constexpr (K > 1) cooperative_groups::this_cluster().sync();
+        else __syncthreads();
         const int x = sm.next;
         if (x >= total) break;
         const FullGroup& G = groups[sm.grp];
@@ -2157,11 +2261,17 @@ __global__ void __launch_bounds__(512) k_fullopt(const FullGroup* __restrict__ g
         const Model& M = G.M;
         const Aln& A = G.A;
         const int n = G.ts.n, NN = 2 * n - 2, P = A.P;
+        // this CTA's sites [p0, p0 + Pl) of the tree's P (all of them when K = 1); its
+        // stored vectors hold Ps sites per slot; tip rows keep the stride P
+        const int Ps = K > 1 ? (((P + K - 1) / K + 3) & ~3) : P;
+        const int p0 = min(P, rank * Ps), Pl = min(P, p0 + Ps) - p0;
+        const uint8_t* tips0 = A.tips + p0;
+        const int32_t* w0 = A.w + p0;
         STab<R, C> st;
-        st.pcap = (P + 3) & ~3;
+        st.pcap = (Ps + 3) & ~3;
         st.s = reinterpret_cast<R*>(tab_base);
         st.ew = st.s + (size_t)4 * C * st.pcap;
-        const size_t sstride = (size_t)P * 4 * C;
+        const size_t sstride = (size_t)Ps * 4 * C;
         const int tree = G.first + gi;
         const int32_t* up = G.ts.up + (size_t)tree * NN;
         const int32_t* ch = G.ts.ch + (size_t)tree * NN * 2;
@@ -2172,7 +2282,7 @@ __global__ void __launch_bounds__(512) k_fullopt(const FullGroup* __restrict__ g
         if (slab) {  // this CTA's own partials, reused tree after tree
             unsigned char* b = slab + (size_t)blockIdx.x * slab_per_cta;
             clv = reinterpret_cast<R*>(b);
-            scl = reinterpret_cast<int32_t*>(b + (((size_t)(2 * n - 5) * P * 4 * C * sizeof(R) + 255) & ~size_t(255)));
+            scl = reinterpret_cast<int32_t*>(b + (((size_t)(2 * n - 5) * Ps * 4 * C * sizeof(R) + 255) & ~size_t(255)));
         } else {
             clv = reinterpret_cast<R*>(G.g.clv) + (size_t)gi * G.g.tree_stride;
             scl = G.g.scl + (size_t)gi * G.g.scl_stride;
@@ -2194,19 +2304,19 @@ __global__ void __launch_bounds__(512) k_fullopt(const FullGroup* __restrict__ g
         __syncthreads();
         auto srcD = [&](int v) {
             Src<R, C> y;
-            if (v < n) { y.clv = nullptr; y.scl = nullptr; y.tip = A.tips + (size_t)v * P; }
-            else { y.clv = clv + (size_t)(v - n) * sstride; y.scl = scl + (size_t)(v - n) * P; y.tip = nullptr; }
+            if (v < n) { y.clv = nullptr; y.scl = nullptr; y.tip = tips0 + (size_t)v * P; }
+            else { y.clv = clv + (size_t)(v - n) * sstride; y.scl = scl + (size_t)(v - n) * Ps; y.tip = nullptr; }
             return y;
         };
         auto srcU = [&](int v) {  // the vector at up[v] without v's subtree, for inner v != n
             Src<R, C> y;
             const int slot = n - 2 + (v - n - 1);
-            y.clv = clv + (size_t)slot * sstride; y.scl = scl + (size_t)slot * P; y.tip = nullptr;
+            y.clv = clv + (size_t)slot * sstride; y.scl = scl + (size_t)slot * Ps; y.tip = nullptr;
             return y;
         };
         auto refreshD = [&](int v) {
             const int c0 = ch[2 * v], c1 = ch[2 * v + 1];
-            for (int p = threadIdx.x; p < P; p += blockDim.x) {
+            for (int p = threadIdx.x; p < Pl; p += blockDim.x) {
                 R y0[4 * C], y1[4 * C];
                 int k0, k1;
                 apply_p<R, C>(Pm + (size_t)c0 * C * 16, srcD(c0), p, y0, k0);
@@ -2215,13 +2325,13 @@ __global__ void __launch_bounds__(512) k_fullopt(const FullGroup* __restrict__ g
                 for (int q = 0; q < 4 * C; ++q) y0[q] *= y1[q];
                 const int sc = rescale<R, C>(y0);
                 store_vec<R, C>(clv + (size_t)(v - n) * sstride, p, y0);
-                scl[(size_t)(v - n) * P + p] = k0 + k1 + sc;
+                scl[(size_t)(v - n) * Ps + p] = k0 + k1 + sc;
             }
         };
         // builds the sum-table of edge (v, up v), storing U_v for inner v
         auto visit_build = [&](int v) {
-            const Src<R, C> tip0 = {nullptr, nullptr, A.tips};
-            for (int p = threadIdx.x; p < P; p += blockDim.x) {
+            const Src<R, C> tip0 = {nullptr, nullptr, tips0};
+            for (int p = threadIdx.x; p < Pl; p += blockDim.x) {
                 R X[4 * C], Y[4 * C];
                 int cx, cy;
                 // D_v first: its load then overlaps the two below instead of waiting
@@ -2243,22 +2353,22 @@ __global__ void __launch_bounds__(512) k_fullopt(const FullGroup* __restrict__ g
                     if (v >= n) {
                         const int slot = n - 2 + (v - n - 1);
                         store_vec<R, C>(clv + (size_t)slot * sstride, p, X);
-                        scl[(size_t)slot * P + p] = cx;
+                        scl[(size_t)slot * Ps + p] = cx;
                     }
                 }
                 const int ex = normalise<R, C>(X), ey = normalise<R, C>(Y);
                 R s4[4 * C];
                 sumtable<R, C>(sm.Mt, sm.pi, X, Y, s4);
-                st.put(p, s4, (R)(ex + ey - Prec<R>::kScaleExp * (cx + cy)), (R)A.w[p]);
+                st.put(p, s4, (R)(ex + ey - Prec<R>::kScaleExp * (cx + cy)), (R)w0[p]);
             }
         };
         // the stored vectors an operation of the schedule reads, requested into L2
         // while the operation before it runs (its Newton iterations touch no HBM)
         auto prefetch_op = [&](int op) {
-            const size_t vb = (size_t)P * 4 * C * sizeof(R);
+            const size_t vb = (size_t)Pl * 4 * C * sizeof(R);
             auto slot = [&](int sl) {
                 prefetch_l2(clv + (size_t)sl * sstride, vb);
-                prefetch_l2(scl + (size_t)sl * P, (size_t)P * 4);
+                prefetch_l2(scl + (size_t)sl * Ps, (size_t)Pl * 4);
             };
             if (op & kUpd) {
                 const int w = op & (kUpd - 1);
@@ -2301,7 +2411,8 @@ __global__ void __launch_bounds__(512) k_fullopt(const FullGroup* __restrict__ g
                 int ev;
                 bool conv;
                 // the solve leaves the P matrices of edge v at its new length in Pm
-                const double t = newton_solve<R, C>(M, cfg, st, P, told, sm.ns, ev, conv, Pm + (size_t)v * C * 16);
+                const double t = newton_solve<R, C, K>(M, cfg, st, Pl, told, sm.ns, ev, conv, Pm + (size_t)v * C * 16,
+                                                       &cseq);
                 moved = fmax(moved, fabs(t - told));
                 evals_total += ev;
                 if (!conv) ++nonconv;
@@ -2317,15 +2428,17 @@ __global__ void __launch_bounds__(512) k_fullopt(const FullGroup* __restrict__ g
         // free after the sweeps), the first inner node's combined at the root
         double f1;
         if constexpr (sizeof(R) == 4) {
-            f1 = fullopt_score_f2<C>(n, ch, len, A, reinterpret_cast<float*>(clv), scl, sm.ns.W, sm.ns.lr,
-                                     &sm.Pf[0][0], &sm.Pfl[0][0], &sm.exf[0][0], M.pi, sm.ns.red);
+            f1 = fullopt_score_f2<C, K>(n, ch, len, A, tips0, w0, Pl, Ps, reinterpret_cast<float*>(clv), scl, sm.ns.W,
+                                        sm.ns.lr, &sm.Pf[0][0], &sm.Pfl[0][0], &sm.exf[0][0], M.pi, sm.ns.red,
+                                        sm.ns.cx, &cseq);
         } else {
-            f1 = eval_lnl<R, C>(M, st, P, G.max_sweeps == 0 ? len[n] : tlast, sm.ns);
+            f1 = eval_lnl<R, C, K>(M, st, Pl, G.max_sweeps == 0 ? len[n] : tlast, sm.ns, &cseq);
         }
         sweeps_total += sweeps;
         __syncthreads();
-        for (int v = threadIdx.x; v < NN; v += blockDim.x) glen[v] = len[v];
-        if (threadIdx.x == 0) {
+        if (rank == 0)
+            for (int v = threadIdx.x; v < NN; v += blockDim.x) glen[v] = len[v];
+        if (threadIdx.x == 0 && rank == 0) {
             if (__double_as_longlong(cfg.prior_rate) != 0) {  // MAP: log prior of the lengths
                 double sum = 0.0;
                 for (int w = 1; w < NN; ++w) sum += len[w];
@@ -2334,11 +2447,12 @@ __global__ void __launch_bounds__(512) k_fullopt(const FullGroup* __restrict__ g
             G.lnl_out[gi] = f1;
         }
     }
-    if (threadIdx.x == 0) {
+    if (threadIdx.x == 0 && rank == 0) {
         atomicAdd(&stats[kStFullEvals], evals_total);
         atomicAdd(&stats[kStFullSweeps], sweeps_total);
         atomicAdd(&stats[kStNonconv], nonconv);
     }
+    if constexpr (K > 1) cooperative_groups::this_cluster().sync();  // no CTA leaves while others may read it
 }
 
 inline int blocks_for(long long n, int t) { return (int)((n + t - 1) / t); }
@@ -2648,6 +2762,67 @@ void propose_t(cudaStream_t s, const PropGroup* groups, const int* gstart, int n
     }
     ++g_launches;
 }
+// Sites per CTA of a cluster of K CTAs sharing P sites (a multiple of 4).
+inline int cluster_share(int P, int K) { return ((P + K - 1) / K + 3) & ~3; }
+
+// The proposal kernel as clusters of K (2, 4 or 8) CTAs, FP32 partials, 4
+// categories, sum-tables of maxP / K sites in shared memory.  grid: a multiple
+// of K.  Returns false when the configuration cannot be launched.
+template <int K>
+bool propose_cluster_t(cudaStream_t s, const PropGroup* groups, const int* gstart, int ngroups, int* counter, Cfg cfg,
+                       unsigned long long* stats, int threads, int grid, int maxP) {
+    const size_t smem = propose_smem_bytes(1, 4, cluster_share(maxP, K), true, threads);
+    auto kern = k_propose<float, 4, true, K>;
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    cudaLaunchConfig_t lc = {};
+    lc.gridDim = dim3((grid / K) * K);
+    lc.blockDim = dim3(threads);
+    lc.dynamicSmemBytes = smem;
+    lc.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = K;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    lc.attrs = at;
+    lc.numAttrs = 1;
+    const cudaError_t e = cudaLaunchKernelEx(&lc, kern, groups, gstart, ngroups, counter, cfg, stats,
+                                             (unsigned char*)nullptr, (size_t)0);
+    ++g_launches;
+    return e == cudaSuccess;
+}
+
+// Resident clusters of K CTAs of the proposal kernel on the whole GPU (0: cannot run).
+template <int K>
+int propose_cluster_occ(int threads, int maxP) {
+    const size_t smem = propose_smem_bytes(1, 4, cluster_share(maxP, K), true, threads);
+    auto kern = k_propose<float, 4, true, K>;
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    cudaLaunchConfig_t lc = {};
+    lc.gridDim = dim3(K * 1024);
+    lc.blockDim = dim3(threads);
+    lc.dynamicSmemBytes = smem;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = K;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    lc.attrs = at;
+    lc.numAttrs = 1;
+    int nc = 0;
+    if (cudaOccupancyMaxActiveClusters(&nc, kern, &lc) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    return nc;
+}
+
 template <typename R, int C>
 void fullopt_t(cudaStream_t s, const FullGroup* groups, const int* gstart, int ngroups, int* counter, int maxN,
                int maxP, Cfg cfg, unsigned long long* stats, int threads, int grid, void* scratch, size_t spc,
@@ -2687,6 +2862,67 @@ int prop_occ(int threads, bool smem_tab, int maxP) {
     cudaGetLastError();
     return nb;
 }
+// The full optimisation as clusters of K CTAs (FP32, 4 categories): each CTA
+// a 1/K share of the sites, sum-table share in shared memory, its own slab of
+// slab_per_cta bytes (fullopt_slab_bytes of the share).  Returns false when
+// the configuration cannot be launched.
+template <int K>
+bool fullopt_cluster_t(cudaStream_t s, const FullGroup* groups, const int* gstart, int ngroups, int* counter, int maxN,
+                       int maxP, Cfg cfg, unsigned long long* stats, int threads, int grid, void* slab,
+                       size_t slab_per_cta) {
+    const size_t smem = fullopt_smem_bytes(1, 4, maxN, cluster_share(maxP, K), true, threads);
+    auto kern = k_fullopt<float, 4, true, K>;
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    cudaLaunchConfig_t lc = {};
+    lc.gridDim = dim3((grid / K) * K);
+    lc.blockDim = dim3(threads);
+    lc.dynamicSmemBytes = smem;
+    lc.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = K;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    lc.attrs = at;
+    lc.numAttrs = 1;
+    const cudaError_t e = cudaLaunchKernelEx(&lc, kern, groups, gstart, ngroups, counter, 2 * maxN - 2, cfg, stats,
+                                             (unsigned char*)nullptr, (size_t)0,
+                                             reinterpret_cast<unsigned char*>(slab), slab_per_cta);
+    ++g_launches;
+    return e == cudaSuccess;
+}
+
+template <int K>
+int fullopt_cluster_occ(int threads, int maxN, int maxP) {
+    const size_t smem = fullopt_smem_bytes(1, 4, maxN, cluster_share(maxP, K), true, threads);
+    auto kern = k_fullopt<float, 4, true, K>;
+    if (smem > 227 * 1024 ||
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    cudaLaunchConfig_t lc = {};
+    lc.gridDim = dim3(K * 1024);
+    lc.blockDim = dim3(threads);
+    lc.dynamicSmemBytes = smem;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = K;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    lc.attrs = at;
+    lc.numAttrs = 1;
+    int nc = 0;
+    if (cudaOccupancyMaxActiveClusters(&nc, kern, &lc) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    return nc;
+}
+
 template <typename R, int C>
 int full_occ(int threads, bool smem_tab, int maxN, int maxP) {
     const int prec = sizeof(R) == 8 ? 0 : 1;
@@ -2715,9 +2951,25 @@ int fullopt_blocks_per_sm(int prec, int C, int threads, bool smem_tab, int maxN,
     return C == 1 ? full_occ<float, 1>(threads, smem_tab, maxN, maxP) : full_occ<float, 4>(threads, smem_tab, maxN, maxP);
 }
 
+bool propose_cluster_ok(int prec, int C, int K) { return prec == 1 && C == 4 && (K == 2 || K == 4 || K == 8); }
+
+int propose_cluster_grid(int prec, int C, int K, int threads, int maxP) {
+    if (!propose_cluster_ok(prec, C, K)) return 0;
+    const int nc = K == 2 ? propose_cluster_occ<2>(threads, maxP)
+                          : K == 4 ? propose_cluster_occ<4>(threads, maxP) : propose_cluster_occ<8>(threads, maxP);
+    return nc * K;
+}
+
 void launch_propose(cudaStream_t s, int prec, int C, const PropGroup* groups, const int* gstart, int ngroups,
                     int* counter, Cfg cfg, unsigned long long* stats, int threads, int grid, void* scratch,
-                    size_t scratch_per_cta, int maxP) {
+                    size_t scratch_per_cta, int maxP, int cluster) {
+    if (cluster > 1 && propose_cluster_ok(prec, C, cluster)) {
+        const bool ok = cluster == 2 ? propose_cluster_t<2>(s, groups, gstart, ngroups, counter, cfg, stats, threads, grid, maxP)
+                        : cluster == 4 ? propose_cluster_t<4>(s, groups, gstart, ngroups, counter, cfg, stats, threads, grid, maxP)
+                                       : propose_cluster_t<8>(s, groups, gstart, ngroups, counter, cfg, stats, threads, grid, maxP);
+        if (ok) return;
+        cudaGetLastError();  // not launchable here: the single-CTA form below
+    }
     if (prec == 0) {
         if (C == 1) propose_t<double, 1>(s, groups, gstart, ngroups, counter, cfg, stats, threads, grid, scratch, scratch_per_cta, maxP);
         else propose_t<double, 4>(s, groups, gstart, ngroups, counter, cfg, stats, threads, grid, scratch, scratch_per_cta, maxP);
@@ -2727,9 +2979,24 @@ void launch_propose(cudaStream_t s, int prec, int C, const PropGroup* groups, co
     }
 }
 
+int fullopt_cluster_grid(int prec, int C, int K, int threads, int maxN, int maxP) {
+    if (!propose_cluster_ok(prec, C, K)) return 0;
+    const int nc = K == 2 ? fullopt_cluster_occ<2>(threads, maxN, maxP)
+                          : K == 4 ? fullopt_cluster_occ<4>(threads, maxN, maxP) : fullopt_cluster_occ<8>(threads, maxN, maxP);
+    return nc * K;
+}
+
 void launch_fullopt(cudaStream_t s, int prec, int C, const FullGroup* groups, const int* gstart, int ngroups,
                     int* counter, int maxN, int maxP, Cfg cfg, unsigned long long* stats, int threads, int grid,
-                    void* scratch, size_t scratch_per_cta, void* slab, size_t slab_per_cta) {
+                    void* scratch, size_t scratch_per_cta, void* slab, size_t slab_per_cta, int cluster) {
+    if (cluster > 1 && slab && propose_cluster_ok(prec, C, cluster)) {
+        const bool ok =
+            cluster == 2 ? fullopt_cluster_t<2>(s, groups, gstart, ngroups, counter, maxN, maxP, cfg, stats, threads, grid, slab, slab_per_cta)
+            : cluster == 4 ? fullopt_cluster_t<4>(s, groups, gstart, ngroups, counter, maxN, maxP, cfg, stats, threads, grid, slab, slab_per_cta)
+                           : fullopt_cluster_t<8>(s, groups, gstart, ngroups, counter, maxN, maxP, cfg, stats, threads, grid, slab, slab_per_cta);
+        if (ok) return;
+        cudaGetLastError();  // not launchable here: the single-CTA form below
+    }
     if (prec == 0) {
         if (C == 1) fullopt_t<double, 1>(s, groups, gstart, ngroups, counter, maxN, maxP, cfg, stats, threads, grid, scratch, scratch_per_cta, slab, slab_per_cta);
         else fullopt_t<double, 4>(s, groups, gstart, ngroups, counter, maxN, maxP, cfg, stats, threads, grid, scratch, scratch_per_cta, slab, slab_per_cta);
