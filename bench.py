@@ -62,7 +62,8 @@ WORKLOADS = {
 # workload's shapes (dram__bytes_read.sum + dram__bytes_write.sum of the captured launch divided
 # by its units: neighbours, or full-optimisation sweeps of kept trees); None until captured
 # (profiles/ holds the captures)
-DRAM = {"pt128": {"per_neighbour": None, "per_full_sweep": None},
+DRAM = {"pt128": {"per_neighbour": (1.499489e9 + 0.329010e9) / 1961,      # profiles/k_propose_128taxa_5908patterns.md
+                  "per_full_sweep": (100.401751e9 + 84.887369e9) / 693},   # profiles/k_fullopt_128taxa_5908patterns.md
         "pt27": {"per_neighbour": None, "per_full_sweep": None}}
 FP32_LANES_PER_SM = 128
 # the 27-taxon alignments the warm-start network is trained on
@@ -463,12 +464,12 @@ def run_ours(args, W, rank, world, dev):
         hbm_peak = hbm_peak or 6800.0
         st = res["stats"]
         nd = res["steps"]
-        # algorithmic bytes (the minimum each kernel must move): the proposal
-        # kernel reads the four member vectors of an edge once for its two swaps, 128*P per
-        # neighbour; a visit writes and reads each of its 2n-5 stored vectors once per sweep,
-        # 128*P*(2n-5) per sweep, plus the first bottom-up pass 128*P*(n-2) and the pair pass
-        # (h and l) 256*P*(n-2) per kept tree
-        prop_bytes = 128.0 * P * res["units"] / max(world, 1)
+        # algorithmic bytes: per neighbour the path's 320*P (its four member
+        # vectors, shared by the two swaps of an edge, 128*P, and the amortised production of the
+        # parent's partials, 192*P), over the proposal kernel's time; a visit writes and reads each
+        # of its 2n-5 stored vectors once per sweep, 128*P*(2n-5) per sweep, plus the first
+        # bottom-up pass 128*P*(n-2) and the pair pass (h and l) 256*P*(n-2) per kept tree
+        prop_bytes = 320.0 * P * res["units"] / max(world, 1)
         full_bytes = 128.0 * P * ((2 * n - 5) * res["full_sweeps"] + 3 * (n - 2) * res["kept"])
         prop_s, full_s = res["prop_ms"] / 1e3, res["full_ms"] / 1e3
         dram = DRAM.get(args.workload, {})
