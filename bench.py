@@ -27,6 +27,10 @@ error: the timed round against the plain FP64 GPU round (every proposal and
 --workload batch16: 16 alignments (taxa ~ U[20,100], sites ~ U[300,5000]),
        256 frontier trees each (random topologies with optimised lengths),
        one graph round over all of them per step.
+--workload warm64: the warm-start network trained on about 1 M logged pairs,
+       then 4-round searches on fresh 64-taxon x 1500-site alignments from
+       hill-climbed starts, plain against learned start (Newton evaluations
+       saved, identical decisions).
 --impl reference: the FP64 CPU oracle, timed on this host's cores on a
 bounded sample of the same step.
 """
@@ -66,8 +70,11 @@ DRAM = {"pt128": {"per_neighbour": (1.499489e9 + 0.329010e9) / 1961,      # prof
                   "per_full_sweep": (100.401751e9 + 84.887369e9) / 693},   # profiles/k_fullopt_128taxa_5908patterns.md
         "pt27": {"per_neighbour": None, "per_full_sweep": None}}
 FP32_LANES_PER_SM = 128
-# the 27-taxon alignments the warm-start network is trained on
-TRAIN_TAXA, TRAIN_SITES, TRAIN_THRESH = 27, 2000, 10.0
+# warm-start training runs (log_training_runs): 27-taxon x 2000-site searches from 8 hill-climbs
+# (threshold 10, up to 8 rounds) and 7-taxon JC69 exhaustive searches; TRAIN_RUNS runs log about
+# 0.2 M pairs (--workload warm64 logs about 1 M)
+TRAIN_TAXA, TRAIN_SITES, TRAIN_THRESH, TRAIN_STARTS, TRAIN_ROUNDS = 27, 2000, 10.0, 8, 8
+TRAIN_RUNS, TRAIN_STEPS, TRAIN_LOG_CAP = 30, 4000, 1 << 21
 BATCH_THRESH = 10.0  # --workload batch16
 
 
@@ -86,10 +93,11 @@ def parse():
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--cpu-sample", type=int, default=0, help="frontier trees in the CPU baseline sample (0: one per thread)")
     p.add_argument("--cpu-threads", type=int, default=0, help="threads of the CPU baseline (0: all cores)")
-    p.add_argument("--workload", default="pt128", choices=["pt128", "pt27", "batch16"])
+    p.add_argument("--workload", default="pt128", choices=["pt128", "pt27", "batch16", "warm64"])
     args = p.parse_args()
     if args.steps is None:  # a few seconds of timed GPU work; the oracle's steps take a few seconds each
         args.steps = 3 if args.impl == "reference" else (5 if args.workload == "batch16" else
+                                                          3 if args.workload == "warm64" else
                                                           WORKLOADS[args.workload]["steps"])
     return args
 
@@ -203,40 +211,83 @@ def reduce_over_ranks(ms: float, units: float, world: int, device="cuda"):
     return float(t.item()), float(u.item())
 
 
-def train_warm_start(ctx, rank):
-    """Trains the warm-start network on proposals logged from PT searches on
-    other (27-taxon x 2000-site) alignments (untimed set-up), then enables it."""
+def log_training_runs(ctx, rank, n_runs, seed0=5000):
+    """Logs (features, optimised lengths) pairs of the plain start's proposals
+    from PT runs on fresh seeded alignments shaped like the two small
+    workloads: every 5th run a 7-taxon x 500-site JC69 search with an infinite
+    threshold (all 945 topologies), the others 27-taxon x 2000-site GTR+G4
+    searches from 8 hill-climbs (threshold 10, frontier capped at 256 trees, up
+    to 8 rounds).  The climbs are not logged.  Returns the runs' shapes."""
     from paper_1811_11007_gb300 import synth
-    for j in range(3):
-        seed = synth.SEED_BASE + 40 + j + 1000 * rank
-        a = synth.simulate(TRAIN_TAXA, TRAIN_SITES, seed, model="gtr", alpha=0.5, mean_branch=0.05)
-        aid = ctx.load_alignment(a.codes)
-        ctx.set_model(aid, a.exch, a.freqs, 0.5, 4)
-        # a search (threshold 10) until the frontier is large, then log the proposals of the next rounds
-        e, l = synth.random_trees(TRAIN_TAXA, 8, seed + 1)
-        lmax, front, _ = build_frontier(ctx, aid, e, l, 256, TRAIN_THRESH)
-        ctx.reset_visited(aid)  # score the saved frontier's neighbours afresh, as a benchmark step does
-        ctx.training_log(True, 1 << 20)
-        for _ in range(3):
+    ctx.mlp_enable(False)
+    runs = {"jc7_exhaustive": 0, "gtr27_climbed": 0}
+    for j in range(n_runs):
+        seed = synth.SEED_BASE + seed0 + j + 100000 * rank
+        if j % 5 == 4:
+            a = synth.simulate(7, 500, seed, model="jc", alpha=None, mean_branch=0.1)
+            aid = ctx.load_alignment(a.codes)
+            ctx.set_model(aid, a.exch, a.freqs, 1.0, 1)
+            e, l = synth.random_trees(7, 1, seed + 1)
+            thr, cap, rounds = math.inf, 1024, 16
+            runs["jc7_exhaustive"] += 1
+        else:
+            a = synth.simulate(TRAIN_TAXA, TRAIN_SITES, seed, model="gtr", alpha=0.5, mean_branch=0.05)
+            aid = ctx.load_alignment(a.codes)
+            ctx.set_model(aid, a.exch, a.freqs, 0.5, 4)
+            hc = ctx.hill_climb(aid, *synth.random_trees(TRAIN_TAXA, TRAIN_STARTS, seed + 1))
+            e, l = hc["edges"], hc["lengths"]
+            thr, cap, rounds = TRAIN_THRESH, 256, TRAIN_ROUNDS
+            runs["gtr27_climbed"] += 1
+        ctx.training_log(True, TRAIN_LOG_CAP)
+        lmax, front = ctx.begin(aid, e, l, thr)
+        for _ in range(rounds):
             if not len(front["edges"]):
                 break
-            lmax, front = ctx.expand(aid, front["edges"][:256], front["lengths"][:256], TRAIN_THRESH, lmax)
+            lmax, front = ctx.expand(aid, front["edges"][:cap], front["lengths"][:cap], thr, lmax)
         ctx.training_log(False)
-    x, t = ctx.training_pairs()
+    return runs
+
+
+def mlp_init_weights():
+    """He-normal hidden layers, a small output layer; padding rows and columns zero."""
+    from paper_1811_11007_gb300 import synth
     rng = np.random.default_rng(synth.SEED_BASE + 99)
     w = np.zeros(27912, np.float32)
-    # He-normal hidden layers, small output layer; padding rows/columns zero
     w[0:69 * 128] = rng.normal(0, np.sqrt(2 / 69), 69 * 128)
     w[80 * 128 + 128:80 * 128 + 128 + 128 * 128] = rng.normal(0, np.sqrt(2 / 128), 128 * 128)
     w3 = rng.normal(0, 0.1 * np.sqrt(1 / 128), (128, 8))
     w3[:, 5:] = 0
     o3 = 80 * 128 + 128 + 128 * 128 + 128
     w[o3:o3 + 1024] = w3.ravel()
+    return w
+
+
+def warm_start_weights(rank, n_runs=None):
+    """The warm-start network's weights, trained (untimed set-up) on pairs
+    logged from other alignments' PT runs (log_training_runs, in a context of
+    its own with small visited tables) by the library's own kernels."""
+    from paper_1811_11007_gb300 import pt, synth
+    t0 = time.time()
+    with pt.Context(precision="mixed", table_log2=18) as tc:
+        runs = log_training_runs(tc, rank, TRAIN_RUNS if n_runs is None else n_runs)
+        x, t = tc.training_pairs()
+        t_log = time.time() - t0
+        tc.mlp_set_weights(mlp_init_weights())
+        loss = tc.mlp_train(TRAIN_STEPS, batch=2048, lr=2e-3, seed=synth.SEED_BASE + 7)
+        w = tc.mlp_get_weights()
+    return w, {"train_pairs": int(len(x)), "runs": runs, "steps": TRAIN_STEPS, "batch": 2048,
+               "final_batch_loss": loss,
+               "zero_prediction_loss": float(np.mean(np.asarray(t, np.float64) ** 2)) if len(t) else None,
+               "log_s": t_log, "train_s": time.time() - t0 - t_log}
+
+
+def train_warm_start(ctx, rank, n_runs=None):
+    """Trains the warm-start network (warm_start_weights), loads it into ctx
+    and enables it there."""
+    w, info = warm_start_weights(rank, n_runs)
     ctx.mlp_set_weights(w)
-    loss = ctx.mlp_train(2000, batch=1024, lr=2e-3, seed=synth.SEED_BASE + 7)
     ctx.mlp_enable(True)
-    return {"train_pairs": int(len(x)), "final_batch_loss": loss,
-            "zero_prediction_loss": float(np.mean(np.asarray(t, np.float64) ** 2)) if len(t) else None}
+    return info
 
 
 def _keys(k):
@@ -650,6 +701,93 @@ def run_batch16(args, rank, world, dev):
     }
 
 
+WARM64_RUNS = 150  # --workload warm64: about 1 M logged pairs
+
+
+def run_warm64(args, rank, world, dev):
+    """The learned warm start at its stated scale: the network trained on about
+    1 M pairs (WARM64_RUNS runs of log_training_runs), then PT on fresh
+    64-taxon x 1500-site GTR+G4 alignments (Exp(0.05) branches) from 8
+    hill-climbs, threshold 10, 4 rounds with the frontier capped at 256 trees,
+    once from the plain start (untimed; the comparison) and once from the
+    learned start (one timed step per alignment, its visited table reset).
+    Decisions must be identical; the Newton evaluations saved are reported."""
+    import torch
+    from paper_1811_11007_gb300 import pt, synth
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.current_stream()
+    t0 = time.time()
+    w, info = warm_start_weights(rank, WARM64_RUNS)
+    setup_s = time.time() - t0
+    n, sites, T, R = 64, 1500, 10.0, 4
+    ctx = pt.Context(precision="mixed", table_log2=20, stream=stream)
+    ctx.mlp_set_weights(w)
+    res = []
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def search(aid, lmax, front, on):
+        ctx.mlp_enable(on)
+        ctx.reset_visited(aid)
+        lm, f = lmax, front
+        ev, sc, nl, fronts = 0, 0, 0, []
+        e0.record(stream)
+        for _ in range(R):
+            if not len(f["edges"]):
+                break
+            lm, f = ctx.expand(aid, f["edges"][:256], f["lengths"][:256], T, lm)
+            st = ctx.stats()
+            ev += st["prop_evals"]
+            sc += st["scored"]
+            nl += st["launches"]
+            fronts.append((lm, _keys(f["keys"])))
+        e1.record(stream)
+        torch.cuda.synchronize()
+        v = ctx.visited(aid)
+        return {"ms": e0.elapsed_time(e1), "evals": ev, "scored": sc, "launches": nl, "fronts": fronts,
+                "visited": dict(zip(_keys(v["keys"]), v["status"]))}
+
+    steps = args.steps
+    with ClockSampler(dev) as clk:
+        for k in range(steps):
+            seed = synth.SEED_BASE + 640 + k + 1000 * rank
+            a = synth.simulate(n, sites, seed, model="gtr", alpha=0.5, mean_branch=0.05)
+            aid = ctx.load_alignment(a.codes)
+            ctx.set_model(aid, a.exch, a.freqs, 0.5, 4)
+            ctx.mlp_enable(False)
+            hc = ctx.hill_climb(aid, *synth.random_trees(n, 8, seed + 1))
+            lmax, front = ctx.begin(aid, hc["edges"], hc["lengths"], T)
+            p = search(aid, lmax, front, False)
+            q = search(aid, lmax, front, True)
+            same = (p["visited"] == q["visited"] and [x[1] for x in p["fronts"]] == [x[1] for x in q["fronts"]]
+                    and all(abs(x[0] - y[0]) <= 1e-3 for x, y in zip(p["fronts"], q["fronts"])))
+            res.append({"seed": seed, "patterns": ctx.alignment_info(aid)[1], "scored": q["scored"],
+                        "visited": len(q["visited"]), "plain_evals": p["evals"], "learned_evals": q["evals"],
+                        "plain_ms": p["ms"], "learned_ms": q["ms"], "launches": q["launches"],
+                        "identical_decisions": bool(same),
+                        "judge": ctx.mlp_judge(aid)})
+    ms = sum(r["learned_ms"] for r in res)
+    units = sum(r["scored"] for r in res)
+    ms, units = reduce_over_ranks(ms, units, world, device=f"cuda:{dev}")
+    if rank != 0:
+        return None
+    pe, le = sum(r["plain_evals"] for r in res), sum(r["learned_evals"] for r in res)
+    return {
+        "metric": "branch-optimised topologies/sec (unique NNI neighbours scored per PT round)",
+        "value": units / (ms / 1e3), "unit": "topologies/s", "n_gpus": world, "steps": steps, "warmup": 0,
+        "ms_per_step": ms / steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32 partials + f64 reductions", "data": "synthetic (seeded simulation)",
+        "config": {"workload": f"learned warm start: fresh {n}-taxon x {sites}-site GTR+G4 alignments, 8 hill-climbs, "
+                               f"threshold {T}, {R} rounds (frontier <= 256); one step = the learned-start search "
+                               f"on one alignment (the plain-start search on it untimed)",
+                   "parallelism": f"replicas x{world}", "l2": "per-step working set below L2 (searches, not repeats)"},
+        "plain_start_value": sum(r["scored"] for r in res) / (sum(r["plain_ms"] for r in res) / 1e3),
+        "newton_evals_saved": 1 - le / pe, "prop_evals_per_neighbour": {"plain": pe / units, "learned": le / units},
+        "identical_decisions": all(r["identical_decisions"] for r in res),
+        "alignments": res, "learned_warm_start": info, "setup_s": setup_s, "clocks": clk.summary(),
+        "gpu_launches": sum(r["launches"] for r in res),
+    }
+
+
 def _oracle_problem(a):
     import oracle
     from paper_1811_11007_gb300 import synth
@@ -793,8 +931,8 @@ def main():
         build.build()
     if world > 1:
         torch.distributed.barrier()
-    if args.workload == "batch16":
-        out = run_batch16(args, rank, world, local)
+    if args.workload in ("batch16", "warm64"):
+        out = (run_batch16 if args.workload == "batch16" else run_warm64)(args, rank, world, local)
         if rank == 0:
             print(json.dumps(out))
         if world > 1:

@@ -255,8 +255,7 @@ struct PropGroup {
     const double* rates;     // per-frontier-tree category rates [tree][kMaxCat] (shape re-optimisation), or null
 };
 // One group of a batched full-optimisation launch: trees [first, first + n) of ts.
-// Partials: g (tree i of the group at g.clv + i * tree_stride), or, when the
-// launch passes a slab, the launching CTA's own part of it (g unused).
+// Partials: the launching CTA's own slab (g is not used by the kernel).
 struct FullGroup {
     Model M;
     Aln A;
@@ -292,7 +291,8 @@ void launch_fullopt(cudaStream_t s, int prec, int C, const FullGroup* groups, co
 int fullopt_cluster_grid(int prec, int C, int K, int threads, int maxN, int maxP);
 // Sites per CTA when K CTAs share P sites (a multiple of 4).
 inline int cluster_sites(int P, int K) { return K > 1 ? ((P + K - 1) / K + 3) & ~3 : P; }
-// Bytes of one CTA's partials slab for trees of n taxa and P patterns (a multiple of 256).
+// Bytes of one CTA's slab for trees of n taxa and P patterns (a multiple of 256): partials,
+// scalers and the P matrices of every edge.  Every full-optimisation launch passes slabs.
 size_t fullopt_slab_bytes(int prec, int C, int n, int P);
 
 // GTR+Gamma model set-up on the host (pt_api.cu); false on invalid parameters.

@@ -1285,6 +1285,8 @@ struct NewtonSmem {
     int done;
     int leader;            // the warp that takes the Newton steps
     double cx[2][3];       // cluster exchange: this CTA's partial sums, two alternating slots
+    alignas(16) float cxf[2][4];  // the same for FP32 pairs (d1 hi, lo, d2 hi, lo), read as float4
+    alignas(16) float cxw[2][16][4];  // per-warp FP32 pairs of the Newton sums, published to the cluster
 };
 
 // Sums of up to three values held by one thread (`writer`) of each CTA of a
@@ -1317,6 +1319,38 @@ __device__ __forceinline__ void cluster_sum(bool writer, double (*cx)[3], int& s
     a = x;
     b = y;
     c = z;
+}
+
+// cluster_sum for two values held as FP32 pairs (h, l): the K CTAs' pairs are
+// added in rank order with two-sums (every CTA gets the same bits).
+template <int K>
+__device__ __forceinline__ void cluster_sum_f2(bool writer, float (*cx)[4], int& seq, float& ah, float& al, float& bh,
+                                               float& bl) {
+    namespace cg = cooperative_groups;
+    cg::cluster_group cl = cg::this_cluster();
+    const int s = seq & 1;
+    ++seq;
+    if (writer) {
+        cx[s][0] = ah;
+        cx[s][1] = al;
+        cx[s][2] = bh;
+        cx[s][3] = bl;
+    }
+    cl.sync();
+    float xh = 0.f, xl = 0.f, yh = 0.f, yl = 0.f;
+#pragma unroll
+    for (int r = 0; r < K; ++r) {
+        const float4 q = *reinterpret_cast<const float4*>(cl.map_shared_rank(&cx[s][0], r));
+        const F2 u = f2_two_sum(xh, q.x), v = f2_two_sum(yh, q.z);
+        xh = u.h;
+        xl = __fadd_rn(__fadd_rn(xl, q.y), u.l);
+        yh = v.h;
+        yl = __fadd_rn(__fadd_rn(yl, q.w), v.l);
+    }
+    ah = xh;
+    al = xl;
+    bh = yh;
+    bl = yl;
 }
 
 __device__ __forceinline__ double warp_sum(double x) {
@@ -1399,6 +1433,23 @@ __device__ __forceinline__ void put_egh(const Model& M, double t, NewtonSmem<R, 
     }
 }
 
+// put_egh's FP32 branch for a length given as FP32 (no FP64 instruction).
+template <typename R, int C>
+__device__ __forceinline__ void put_egh_f(float t, NewtonSmem<R, C>& ns, int q) {
+    if (q < 4 * C) {
+        if ((q & 3) == 0) {
+            ns.egh[0][q] = (R)(1.0f / C);
+            ns.egh[1][q] = R(0);
+            ns.egh[2][q] = R(0);
+        } else {
+            const float l = ns.lrf[q], x = l * t, e = expf(x) * (1.0f / C);
+            ns.egh[0][q] = (R)(expm1f(x) * (1.0f / C));
+            ns.egh[1][q] = (R)(l * e);
+            ns.egh[2][q] = (R)(l * l * e);
+        }
+    }
+}
+
 // Safeguarded Newton step: bracket [lo, hi]; Newton point when d2 < 0 and
 // strictly inside, else sqrt(lo*hi).  Returns true when converged.
 //
@@ -1445,6 +1496,47 @@ __device__ __forceinline__ bool newton_step(double& t, double& lo, double& hi, d
     }
     const double tm = sqrt(lo * hi);
     const bool conv = (__double_as_longlong(tm - t) & 0x7fffffffffffffffLL) <= __double_as_longlong(tol);
+    t = tm;
+    return conv;
+}
+
+// The same safeguarded step on FP32 pairs (F2): the mixed path's derivative
+// sums arrive as pairs, and t, lo, hi are carried as pairs (~48 bits), so the
+// step needs no FP64 instruction (a dependent FP64 operation costs 64 cycles on
+// this part).  Quotient: one reciprocal seed, refined once (q = q0 + (d1 -
+// q0 d2) / d2); square root of the bisection: sqrtf refined by one Heron step.
+__device__ __forceinline__ bool f2_lt(F2 a, F2 b) { return a.h < b.h || (a.h == b.h && a.l < b.l); }
+__device__ __forceinline__ F2 f2_abs(F2 a) { return a.h < 0.f ? F2{-a.h, -a.l} : a; }
+__device__ __forceinline__ F2 f2_sub(F2 a, F2 b) {
+    const F2 d = f2_two_sum(a.h, -b.h);
+    return f2_norm(d.h, __fadd_rn(d.l, __fsub_rn(a.l, b.l)));
+}
+__device__ __forceinline__ F2 f2_div(F2 a, F2 b) {
+    const float rc = __frcp_rn(b.h);
+    const float q0 = __fmul_rn(a.h, rc);
+    const float p = __fmul_rn(q0, b.h), pe = __fmaf_rn(q0, b.h, -p);
+    // a - q0 b: a.h - p is exact (p lies within a factor 2 of a.h)
+    const float r = __fadd_rn(__fsub_rn(__fsub_rn(a.h, p), pe), __fsub_rn(a.l, __fmul_rn(q0, b.l)));
+    return f2_norm(q0, __fmul_rn(r, rc));
+}
+__device__ __forceinline__ F2 f2_sqrt(F2 x) {
+    const float s0 = sqrtf(x.h);
+    if (!(s0 > 0.f)) return F2{s0, 0.f};
+    const float p = __fmul_rn(s0, s0), pe = __fmaf_rn(s0, s0, -p);
+    const float r = __fadd_rn(__fsub_rn(__fsub_rn(x.h, p), pe), x.l);
+    return f2_norm(s0, __fmul_rn(r, __fmul_rn(0.5f, __frcp_rn(s0))));
+}
+__device__ __forceinline__ bool newton_step_f2(F2& t, F2& lo, F2& hi, F2 d1, F2 d2, F2 tol) {
+    if (d1.h == 0.f) return true;  // d1 == 0 (a pair is zero iff its high part is)
+    if (d1.h > 0.f) lo = t; else hi = t;
+    const F2 q = f2_div(d1, d2);
+    const F2 tn = f2_sub(t, q);
+    if (d2.h < 0.f && f2_lt(lo, tn) && f2_lt(tn, hi)) {  // NaN fails the bracket test
+        t = tn;
+        return !f2_lt(tol, f2_abs(q));
+    }
+    const F2 tm = f2_sqrt(f2_mul(lo, hi));
+    const bool conv = !f2_lt(tol, f2_abs(f2_sub(tm, t)));
     t = tm;
     return conv;
 }
@@ -1536,6 +1628,15 @@ __device__ double newton_solve(const Model& M, const Cfg& cfg, const STab<R, C>&
     const int ld = ns.leader;
     converged = false;
     evals = 0;
+    // mixed precision: the leader's step on pairs (t, bracket, tolerance, prior slope)
+    F2 tp{0.f, 0.f}, lop{0.f, 0.f}, hip{0.f, 0.f}, tolp{0.f, 0.f}, prp{0.f, 0.f};
+    if (sizeof(R) == 4 && w == ld) {
+        tp = f2_of(t);
+        lop = f2_of(lo);
+        hip = f2_of(hi);
+        tolp = f2_of(cfg.newton_tol);
+        prp = f2_of(cfg.prior_rate);
+    }
     for (int it = 0; it < cfg.newton_maxit; ++it) {
         R e[4 * C], g[4 * C], h[4 * C];
 #pragma unroll
@@ -1560,48 +1661,126 @@ __device__ double newton_solve(const Model& M, const Cfg& cfg, const STab<R, C>&
             a1 = fma(wt, a, a1);
             a2 = fma(wt, b - a * a, a2);
         }
+        // the per-warp sums: to this CTA's shared memory, or (FP32 pairs in a cluster)
+        // straight to the cluster exchange, whose barrier then serves both levels
+        bool pub = false;  // published to the cluster exchange (slot cs)
+        int cs = 0;
         if constexpr (sizeof(R) == 4) {
             const float2 d1 = warp_sum_comp(a1), d2 = warp_sum_comp(a2);
-            if (lane == 0) { ns.redf[w][0] = d1.x; ns.redf[w][1] = d1.y; ns.redf[w][2] = d2.x; ns.redf[w][3] = d2.y; }
+            if constexpr (K > 1) {
+                cs = *cseq & 1;
+                ++*cseq;
+                if (lane == 0)
+                    *reinterpret_cast<float4*>(&ns.cxw[cs][w][0]) = make_float4(d1.x, d1.y, d2.x, d2.y);
+                cooperative_groups::this_cluster().sync();
+                pub = true;
+            } else if (lane == 0) {
+                ns.redf[w][0] = d1.x; ns.redf[w][1] = d1.y; ns.redf[w][2] = d2.x; ns.redf[w][3] = d2.y;
+            }
         } else {
             const double d1 = warp_sum(a1), d2 = warp_sum(a2);
             if (lane == 0) { ns.red[w][0] = d1; ns.red[w][1] = d2; }
         }
-        __syncthreads();
+        if (!pub) __syncthreads();
         ++evals;
         double D1 = 0.0, D2 = 0.0;
         float D2f = 0.f;
-        if (w == ld) {
-            // Both derivative sums in one FP64 butterfly: lane j < nw holds warp j's
-            // d1 partial, lane 16 + j its d2 partial; offsets below 16 keep the halves
-            // apart.  An FP32 sum of the same words runs alongside (reciprocal seed).
-            const int src = lane & 15, half = lane >> 4;
-            double D = 0.0;
-            float Df = 0.f;
-            if (src < nw) {
-                if constexpr (sizeof(R) == 4) {
-                    const float h = ns.redf[src][2 * half], l = ns.redf[src][2 * half + 1];
-                    D = (double)h + (double)l;
-                    Df = h;
+        if constexpr (sizeof(R) == 4) {
+            // Both derivative sums as FP32 pairs in one compensated butterfly: lane
+            // j < nw holds warp j's d1 pair, lane 16 + j its d2 pair; offsets below 16
+            // keep the halves apart.  Two-sums carry the pairs exactly enough (~48
+            // bits) that FP64 is needed only to convert the totals for the step.
+            float h = 0.f, l = 0.f;
+            if constexpr (K > 1) {
+                if (w == ld) {
+                    // the cluster's K x nw warp pairs: lane j takes pairs j, j + 32, ...
+                    // (CTA j / nw, warp j % nw) in a fixed order, then a 32-lane
+                    // butterfly: every CTA adds the same numbers in the same order
+                    namespace cg = cooperative_groups;
+                    cg::cluster_group cl = cg::this_cluster();
+                    float h2 = 0.f, l2 = 0.f;
+                    for (int j = lane; j < K * nw; j += 32) {
+                        const float4 q = *reinterpret_cast<const float4*>(cl.map_shared_rank(&ns.cxw[cs][j % nw][0], j / nw));
+                        const F2 u = f2_two_sum(h, q.x), v = f2_two_sum(h2, q.z);
+                        h = u.h;
+                        l = __fadd_rn(__fadd_rn(l, q.y), u.l);
+                        h2 = v.h;
+                        l2 = __fadd_rn(__fadd_rn(l2, q.w), v.l);
+                    }
+                    for (int o = 16; o; o >>= 1) {
+                        const float oh = __shfl_xor_sync(0xffffffffu, h, o), ol = __shfl_xor_sync(0xffffffffu, l, o);
+                        const float oh2 = __shfl_xor_sync(0xffffffffu, h2, o), ol2 = __shfl_xor_sync(0xffffffffu, l2, o);
+                        const F2 u = f2_two_sum(h, oh), v = f2_two_sum(h2, oh2);
+                        h = u.h;
+                        l = __fadd_rn(__fadd_rn(l, ol), u.l);
+                        h2 = v.h;
+                        l2 = __fadd_rn(__fadd_rn(l2, ol2), v.l);
+                    }
+                    if (lane >= 16) {  // lanes < 16: d1, the others d2 (as below)
+                        h = h2;
+                        l = l2;
+                    }
+                }
+            } else if (w == ld) {
+                const int src = lane & 15, half = lane >> 4;
+                if (src < nw) {
+                    h = ns.redf[src][2 * half];
+                    l = ns.redf[src][2 * half + 1];
+                }
+                for (int o = top; o; o >>= 1) {
+                    const float oh = __shfl_xor_sync(0xffffffffu, h, o), ol = __shfl_xor_sync(0xffffffffu, l, o);
+                    const F2 t2 = f2_two_sum(h, oh);
+                    h = t2.h;
+                    l = __fadd_rn(__fadd_rn(l, ol), t2.l);
+                }
+            }
+            if (w == ld) {  // lanes < 16 hold d1, the others d2
+                // the butterfly leaves (h, l) unnormalised (l can reach a sizeable
+                // fraction of h after cancellation): renormalise, so that the
+                // quotient's reciprocal seed is taken from the rounded total
+                F2 d1p = f2_two_sum(__shfl_sync(0xffffffffu, h, 0), __shfl_sync(0xffffffffu, l, 0));
+                const F2 d2p = f2_two_sum(__shfl_sync(0xffffffffu, h, 16), __shfl_sync(0xffffffffu, l, 16));
+                if (prior) d1p = f2_sub(d1p, prp);  // MAP: the prior's slope
+                const bool done = newton_step_f2(tp, lop, hip, d1p, d2p, tolp);
+                const bool last = done || it + 1 == cfg.newton_maxit;
+                if (!last) {
+                    put_egh_f<R, C>(tp.h, ns, lane);
                 } else {
+                    t = (double)tp.h + (double)tp.l;
+                    if (lane < 4 * C) ns.ex[lane] = exp(ns.lr[lane] * t);  // for the P matrices below
+                }
+                if (lane == 0) {
+                    if (last) ns.tb = t;
+                    ns.done = last ? (done ? 1 : 2) : 0;
+                }
+            }
+        } else {
+            if (w == ld) {
+                // Both derivative sums in one FP64 butterfly: lane j < nw holds warp j's
+                // d1 partial, lane 16 + j its d2 partial; offsets below 16 keep the halves
+                // apart.  An FP32 sum of the same words runs alongside (reciprocal seed).
+                const int src = lane & 15, half = lane >> 4;
+                double D = 0.0;
+                float Df = 0.f;
+                if (src < nw) {
                     D = ns.red[src][half];
                     Df = (float)D;
                 }
+                for (int o = top; o; o >>= 1) {
+                    D += __shfl_xor_sync(0xffffffffu, D, o);
+                    Df += __shfl_xor_sync(0xffffffffu, Df, o);
+                }
+                D1 = __shfl_sync(0xffffffffu, D, 0);
+                D2 = __shfl_sync(0xffffffffu, D, 16);
+                D2f = __shfl_sync(0xffffffffu, Df, 16);
             }
-            for (int o = top; o; o >>= 1) {
-                D += __shfl_xor_sync(0xffffffffu, D, o);
-                Df += __shfl_xor_sync(0xffffffffu, Df, o);
+            if constexpr (K > 1) {  // the cluster's sums (every thread takes part in the exchange)
+                double d2f = D2f;
+                cluster_sum<K>(w == ld && lane == 0, ns.cx, *cseq, D1, D2, d2f);
+                D2f = (float)d2f;
             }
-            D1 = __shfl_sync(0xffffffffu, D, 0);
-            D2 = __shfl_sync(0xffffffffu, D, 16);
-            D2f = __shfl_sync(0xffffffffu, Df, 16);
         }
-        if constexpr (K > 1) {  // the cluster's sums (every thread takes part in the exchange)
-            double d2f = D2f;
-            cluster_sum<K>(w == ld && lane == 0, ns.cx, *cseq, D1, D2, d2f);
-            D2f = (float)d2f;
-        }
-        if (w == ld) {
+        if (sizeof(R) == 8 && w == ld) {
             if (prior) D1 -= cfg.prior_rate;  // MAP: the prior's slope
             const bool done = newton_step(t, lo, hi, D1, D2, D2f, cfg.newton_tol);
             const bool last = done || it + 1 == cfg.newton_maxit;
@@ -2220,14 +2399,15 @@ template <typename R, int C, bool kSmemTab, int K = 1>
 __global__ void __launch_bounds__(512) k_fullopt(const FullGroup* __restrict__ groups, const int* __restrict__ gstart,
                                                  int ngroups, int* counter, int nn_max, Cfg cfg,
                                                  unsigned long long* stats, unsigned char* scratch,
-                                                 size_t scratch_per_cta, unsigned char* slab, size_t slab_per_cta) {
+                                                 size_t scratch_per_cta, unsigned char* slab, size_t slab_per_cta,
+                                                 int p_smem) {
     extern __shared__ __align__(16) unsigned char smraw[];
     FullSmem<R, C>& sm = *reinterpret_cast<FullSmem<R, C>*>(smraw);
     size_t off = (sizeof(FullSmem<R, C>) + 15) & ~size_t(15);
     double* len = reinterpret_cast<double*>(smraw + off);
     off += ((size_t)nn_max * sizeof(double) + 15) & ~size_t(15);
-    R* Pm = reinterpret_cast<R*>(smraw + off);
-    off += ((size_t)nn_max * C * 16 * sizeof(R) + 15) & ~size_t(15);
+    R* const Psm = reinterpret_cast<R*>(smraw + off);  // P matrices here when p_smem
+    if (p_smem) off += ((size_t)nn_max * C * 16 * sizeof(R) + 15) & ~size_t(15);
     unsigned char* const tab_base = kSmemTab ? smraw + off : scratch + (size_t)blockIdx.x * scratch_per_cta;
     const int total = gstart[ngroups];
     unsigned long long evals_total = 0, sweeps_total = 0, nonconv = 0;
@@ -2277,16 +2457,16 @@ __global__ void __launch_bounds__(512) k_fullopt(const FullGroup* __restrict__ g
         const int32_t* ch = G.ts.ch + (size_t)tree * NN * 2;
         const int32_t* sched = G.ts.sched + (size_t)tree * 3 * n;
         double* glen = G.ts.len + (size_t)tree * NN;
-        R* clv;
-        int32_t* scl;
-        if (slab) {  // this CTA's own partials, reused tree after tree
-            unsigned char* b = slab + (size_t)blockIdx.x * slab_per_cta;
-            clv = reinterpret_cast<R*>(b);
-            scl = reinterpret_cast<int32_t*>(b + (((size_t)(2 * n - 5) * Ps * 4 * C * sizeof(R) + 255) & ~size_t(255)));
-        } else {
-            clv = reinterpret_cast<R*>(G.g.clv) + (size_t)gi * G.g.tree_stride;
-            scl = G.g.scl + (size_t)gi * G.g.scl_stride;
-        }
+        // this CTA's own slab, reused tree after tree: partials, scalers and the P
+        // matrices of every edge; the P matrices move to shared memory when the
+        // launch shape leaves it free (p_smem, see full_p_smem), else they are read
+        // from the slab through L1 and the shared memory holds the sum-table share
+        unsigned char* const b = slab + (size_t)blockIdx.x * slab_per_cta;
+        const size_t clv_bytes = ((size_t)(2 * n - 5) * Ps * 4 * C * sizeof(R) + 255) & ~size_t(255);
+        const size_t scl_bytes = ((size_t)(2 * n - 5) * Ps * 4 + 255) & ~size_t(255);
+        R* const clv = reinterpret_cast<R*>(b);
+        int32_t* const scl = reinterpret_cast<int32_t*>(b + clv_bytes);
+        R* const Pm = p_smem ? Psm : reinterpret_cast<R*>(b + clv_bytes + scl_bytes);
         if (threadIdx.x < 16) {
             const int i = threadIdx.x >> 2, k = threadIdx.x & 3;
             sm.Mt[threadIdx.x] = (R)(M.sqpi[i] * M.R[i * 4 + k]);
@@ -2677,8 +2857,7 @@ size_t propose_fixed() { return (sizeof(ProposeSmem<R, C>) + 15) & ~size_t(15); 
 template <typename R, int C>
 size_t full_fixed(int n) {
     const int NN = 2 * n - 2;
-    return ((sizeof(FullSmem<R, C>) + 15) & ~size_t(15)) + (((size_t)NN * 8 + 15) & ~size_t(15)) +
-           (((size_t)NN * C * 16 * sizeof(R) + 15) & ~size_t(15));
+    return ((sizeof(FullSmem<R, C>) + 15) & ~size_t(15)) + (((size_t)NN * 8 + 15) & ~size_t(15));
 }
 }  // namespace
 
@@ -2689,11 +2868,26 @@ size_t propose_smem_bytes(int prec, int C, int P, bool table_in_smem, int thread
     return f + (table_in_smem ? sumtable_bytes(prec, C, P) : 0);
 }
 
+// Where a full optimisation keeps the P matrices of a tree's edges: in shared
+// memory when the CTA already takes the SM's whole register file (512 threads x
+// 128 registers, so one CTA per SM and no other taker for the shared memory) and
+// they fit beside the rest; otherwise in the CTA's slab, read through L1, which
+// leaves the shared memory to the sum-table share so that two smaller CTAs fit.
+static bool full_p_smem(int prec, int C, int n, int P, bool table_in_smem, int threads) {
+    const size_t f = (prec == 0 ? (C == 1 ? full_fixed<double, 1>(n) : full_fixed<double, 4>(n))
+                                : (C == 1 ? full_fixed<float, 1>(n) : full_fixed<float, 4>(n))) +
+                     (table_in_smem ? sumtable_bytes(prec, C, P) : 0);
+    const size_t pb = ((size_t)(2 * n - 2) * C * 16 * (prec == 0 ? 8 : 4) + 15) & ~size_t(15);
+    return threads >= 512 && f + pb <= (size_t)227 * 1024;
+}
+
 size_t fullopt_smem_bytes(int prec, int C, int n, int P, bool table_in_smem, int threads) {
-    (void)threads;
     size_t f = prec == 0 ? (C == 1 ? full_fixed<double, 1>(n) : full_fixed<double, 4>(n))
                          : (C == 1 ? full_fixed<float, 1>(n) : full_fixed<float, 4>(n));
-    return f + (table_in_smem ? sumtable_bytes(prec, C, P) : 0);
+    f += table_in_smem ? sumtable_bytes(prec, C, P) : 0;
+    if (full_p_smem(prec, C, n, P, table_in_smem, threads))
+        f += ((size_t)(2 * n - 2) * C * 16 * (prec == 0 ? 8 : 4) + 15) & ~size_t(15);
+    return f;
 }
 
 namespace {
@@ -2832,15 +3026,17 @@ void fullopt_t(cudaStream_t s, const FullGroup* groups, const int* gstart, int n
     unsigned char* sl = reinterpret_cast<unsigned char*>(slab);
     if (scratch) {
         const size_t smem = fullopt_smem_bytes(prec, C, maxN, maxP, false, threads);
+        const int ps = full_p_smem(prec, C, maxN, maxP, false, threads);
         cudaFuncSetAttribute(k_fullopt<R, C, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         k_fullopt<R, C, false><<<grid, threads, smem, s>>>(groups, gstart, ngroups, counter, nn, cfg, stats,
                                                            reinterpret_cast<unsigned char*>(scratch), spc, sl,
-                                                           slab_per_cta);
+                                                           slab_per_cta, ps);
     } else {
         const size_t smem = fullopt_smem_bytes(prec, C, maxN, maxP, true, threads);
+        const int ps = full_p_smem(prec, C, maxN, maxP, true, threads);
         cudaFuncSetAttribute(k_fullopt<R, C, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         k_fullopt<R, C, true><<<grid, threads, smem, s>>>(groups, gstart, ngroups, counter, nn, cfg, stats, nullptr, 0,
-                                                          sl, slab_per_cta);
+                                                          sl, slab_per_cta, ps);
     }
     ++g_launches;
 }
@@ -2871,6 +3067,7 @@ bool fullopt_cluster_t(cudaStream_t s, const FullGroup* groups, const int* gstar
                        int maxP, Cfg cfg, unsigned long long* stats, int threads, int grid, void* slab,
                        size_t slab_per_cta) {
     const size_t smem = fullopt_smem_bytes(1, 4, maxN, cluster_share(maxP, K), true, threads);
+    const int ps = full_p_smem(1, 4, maxN, cluster_share(maxP, K), true, threads);
     auto kern = k_fullopt<float, 4, true, K>;
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
         cudaGetLastError();
@@ -2890,7 +3087,7 @@ bool fullopt_cluster_t(cudaStream_t s, const FullGroup* groups, const int* gstar
     lc.numAttrs = 1;
     const cudaError_t e = cudaLaunchKernelEx(&lc, kern, groups, gstart, ngroups, counter, 2 * maxN - 2, cfg, stats,
                                              (unsigned char*)nullptr, (size_t)0,
-                                             reinterpret_cast<unsigned char*>(slab), slab_per_cta);
+                                             reinterpret_cast<unsigned char*>(slab), slab_per_cta, ps);
     ++g_launches;
     return e == cudaSuccess;
 }
@@ -3008,7 +3205,8 @@ void launch_fullopt(cudaStream_t s, int prec, int C, const FullGroup* groups, co
 
 size_t fullopt_slab_bytes(int prec, int C, int n, int P) {
     const size_t slots = (size_t)(2 * n - 5), rs = prec == 0 ? 8 : 4;
-    return ((slots * P * 4 * C * rs + 255) & ~size_t(255)) + ((slots * P * 4 + 255) & ~size_t(255));
+    return ((slots * P * 4 * C * rs + 255) & ~size_t(255)) + ((slots * P * 4 + 255) & ~size_t(255)) +
+           (((size_t)(2 * n - 2) * C * 16 * rs + 255) & ~size_t(255));
 }
 
 }  // namespace pt

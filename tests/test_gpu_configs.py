@@ -1,9 +1,10 @@
 """Two workload configurations beyond the benchmarked round, as GPU parity cases:
 
 * learned warm start on fresh 64-taxon x 1500-site GTR+G4 alignments: a
-  network trained on PT rounds of other (27-taxon) alignments, a multi-round
-  search from the plain and from the learned start deciding identically
-  (next frontiers, statuses), with the Newton evaluations it saves printed;
+  network trained on PT runs of other (27-taxon and 7-taxon) alignments, a
+  multi-round search from 8 hill-climbed starts run from the plain and from
+  the learned start, deciding identically (next frontiers, statuses), the
+  learned start needing fewer Newton evaluations (the saving is printed);
 * PT at scale: 128 taxa x 10000 sites (~6000 patterns), Exp(0.02) branches,
   32 random starts, threshold 15, a 2^24-slot visited table; the learned +
   mixed-precision round against the plain FP64 GPU path on the same frontier
@@ -42,54 +43,62 @@ def _round(ctx, aid, front, T, lmax):
     return lm, nxt, ctx.last_proposals(), ctx.stats()
 
 
-def test_learned_start_on_fresh_64_taxa():
-    import bench
+def test_learned_start_on_fresh_64_taxa(warm_weights):
+    """Fresh 64-taxon x 1500-site alignments, searched as PT searches them: 8
+    hill-climbs from random trees give the starts, threshold 10, four rounds
+    (frontier capped at 256 trees) from the plain and from the learned start.
+    The learned start must decide identically and need fewer proposal Newton
+    evaluations; the saving is printed."""
     n, sites, T = 64, 1500, 10.0
-    seed = synth.SEED_BASE + 640
+    saved = []
     with pt.Context(precision="mixed", table_log2=20) as ctx:
-        bench.train_warm_start(ctx, 0)  # trained on rounds of 27-taxon alignments
-        a = synth.simulate(n, sites, seed, model="gtr", alpha=0.5, mean_branch=0.05)
-        aid = ctx.load_alignment(a.codes)
-        ctx.set_model(aid, a.exch, a.freqs, 0.5, 4)
-        e, l = synth.random_trees(n, 8, seed + 1)
-        ctx.mlp_enable(False)
-        lmax, front = ctx.begin(aid, e, l, T)
-        trails = {}
-        for on in (False, True):
-            ctx.mlp_enable(on)
-            ctx.reset_visited(aid)
-            lm, f = lmax, front
-            fronts, evals = [], np.zeros(2, np.int64)
-            for _ in range(4):
-                if not len(f["edges"]):
-                    break
-                lm, f = ctx.expand(aid, f["edges"], f["lengths"], T, lm)
-                st = ctx.stats()
-                evals += (st["prop_evals"], st["full_evals"])
-                fronts.append((lm, f))
-            v = ctx.visited(aid)
-            trails[on] = (fronts, evals, dict(zip(_keys(v["keys"]), zip(v["status"], v["lnl"]))))
-    (f0, ev0, v0), (f1, ev1, v1) = trails[False], trails[True]
-    assert len(f0) == len(f1) >= 2
-    for (lm0, a0), (lm1, a1) in zip(f0, f1):
-        assert abs(lm0 - lm1) <= TOL
-        assert _keys(a0["keys"]) == _keys(a1["keys"])
-        np.testing.assert_allclose(a0["lnl"], a1["lnl"], rtol=0, atol=TOL)
-    assert set(v0) == set(v1)
-    assert all(v0[k][0] == v1[k][0] for k in v0)  # every status (kept / rejected / frontier) identical
-    print(f"64 taxa x {sites} sites, {len(v0)} topologies visited: proposal Newton evaluations plain {ev0[0]}, "
-          f"learned {ev1[0]} ({100 * (1 - ev1[0] / ev0[0]):.1f}% saved); visit evaluations plain {ev0[1]}, "
-          f"learned {ev1[1]}")
+        ctx.mlp_set_weights(warm_weights)  # trained on runs of 27-taxon and 7-taxon alignments
+        for seed in (synth.SEED_BASE + 640, synth.SEED_BASE + 641):
+            a = synth.simulate(n, sites, seed, model="gtr", alpha=0.5, mean_branch=0.05)
+            aid = ctx.load_alignment(a.codes)
+            ctx.set_model(aid, a.exch, a.freqs, 0.5, 4)
+            ctx.mlp_enable(False)
+            hc = ctx.hill_climb(aid, *synth.random_trees(n, 8, seed + 1))
+            lmax, front = ctx.begin(aid, hc["edges"], hc["lengths"], T)
+            trails = {}
+            for on in (False, True):
+                ctx.mlp_enable(on)
+                ctx.reset_visited(aid)
+                lm, f = lmax, front
+                fronts, evals, scored = [], np.zeros(2, np.int64), 0
+                for _ in range(4):
+                    if not len(f["edges"]):
+                        break
+                    lm, f = ctx.expand(aid, f["edges"][:256], f["lengths"][:256], T, lm)
+                    st = ctx.stats()
+                    evals += (st["prop_evals"], st["full_evals"])
+                    scored += st["scored"]
+                    fronts.append((lm, f))
+                v = ctx.visited(aid)
+                trails[on] = (fronts, evals, scored, dict(zip(_keys(v["keys"]), zip(v["status"], v["lnl"]))))
+            (f0, ev0, s0, v0), (f1, ev1, s1, v1) = trails[False], trails[True]
+            assert len(f0) == len(f1) >= 2 and s0 == s1
+            for (lm0, a0), (lm1, a1) in zip(f0, f1):
+                assert abs(lm0 - lm1) <= TOL
+                assert _keys(a0["keys"]) == _keys(a1["keys"])
+                np.testing.assert_allclose(a0["lnl"], a1["lnl"], rtol=0, atol=TOL)
+            assert set(v0) == set(v1)
+            assert all(v0[k][0] == v1[k][0] for k in v0)  # every status (kept / rejected / frontier) identical
+            saved.append(1 - ev1[0] / ev0[0])
+            print(f"64 taxa x {sites} sites (seed {seed}), {len(v0)} topologies visited, {s0} proposals: "
+                  f"proposal Newton evaluations plain {ev0[0]} ({ev0[0] / s0:.1f} per proposal), learned {ev1[0]} "
+                  f"({ev1[0] / s1:.1f}; {100 * saved[-1]:.1f}% saved); visit evaluations plain {ev0[1]}, "
+                  f"learned {ev1[1]}; judge {ctx.mlp_judge(aid)}")
+    assert all(x > 0 for x in saved)  # the network pays on every fresh alignment
 
 
-def test_scale_128_taxa_learned_mixed_vs_plain_fp64():
-    import bench
+def test_scale_128_taxa_learned_mixed_vs_plain_fp64(warm_weights):
     n, sites, T = 128, 10000, 15.0
     seed = synth.SEED_BASE + 1280
     a = synth.simulate(n, sites, seed, model="gtr", alpha=0.5, mean_branch=0.02)
     e, l = synth.random_trees(n, 32, seed + 1)
     with pt.Context(precision="mixed", table_log2=24) as mx, pt.Context(precision="fp64", table_log2=20) as dp:
-        bench.train_warm_start(mx, 0)
+        mx.mlp_set_weights(warm_weights)
         am = mx.load_alignment(a.codes)
         mx.set_model(am, a.exch, a.freqs, 0.5, 4)
         ad = dp.load_alignment(a.codes)

@@ -1,6 +1,6 @@
 """The benchmarked PT round at its full size and in its launch configuration:
 27 taxa x 2000 sites GTR+G4 (alpha 0.5), the frontier (up to 256 trees) a
-threshold-10 search reaches from 8 random starts, learned warm start,
+threshold-10 search reaches from 8 hill-climbed starts, learned warm start,
 autotuned CTA sizes, replayed as a CUDA graph.  Checked against the FP64
 oracle on sampled outputs (proposals one by one, visits of kept trees) and by
 properties that hold at any size (the scored key set equals the oracle's NNI
@@ -32,25 +32,35 @@ def built():
     build.build()
 
 
-def test_benchmark_round_full_size():
+def test_benchmark_round_full_size(warm_weights):
     import bench
-    n, T = bench.N_TAXA, bench.THRESH
-    a, starts = bench.workload(0)
+    W = bench.WORKLOADS["pt27"]
+    n, T = W["taxa"], W["thresh"]
+    a, starts = bench.workload(W, 0)
     tips, w = synth.compress_patterns(a.codes)
     pb = oracle.Problem(tips, w, a.exch, a.freqs, 0.5, 4)
     with pt.Context(precision="mixed", table_log2=22) as ctx:
-        bench.train_warm_start(ctx, 0)
         aid = ctx.load_alignment(a.codes)
         ctx.set_model(aid, a.exch, a.freqs, 0.5, 4)
-        lmax0, front, _ = bench.build_frontier(ctx, aid, starts, 256)
+        hc = ctx.hill_climb(aid, *starts)
+        lmax0, front, _ = bench.build_frontier(ctx, aid, hc["edges"], hc["lengths"], W["frontier"], T)
+        ctx.mlp_set_weights(warm_weights)
+        ctx.mlp_enable(True)
         F = len(front["edges"])
         assert F >= 64
         ctx.autotune(True)
+        # a first round tunes the launch shapes and lets the judge take its first
+        # decision (which thins its sample of the other start from every 4th
+        # proposal to every 16th); the compared rounds then share both
+        ctx.reset_visited(aid)
+        ctx.expand(aid, front["edges"], front["lengths"], T, lmax0)
+        assert ctx.autotune_report()  # the round was large enough to tune its CTA sizes
+        state = ctx.mlp_judge(aid)["state"]
         ctx.reset_visited(aid)
         lm_d, nxt_d = ctx.expand(aid, front["edges"], front["lengths"], T, lmax0)
         props = ctx.last_proposals()
         st = ctx.stats()
-        assert ctx.autotune_report()  # the round was large enough to tune its CTA sizes
+        assert ctx.mlp_judge(aid)["state"] == state
         # the headline launch: the same round recorded as a CUDA graph, at the tuned sizes
         g = ctx.graph([aid], [F], [T])
         try:

@@ -37,15 +37,17 @@ def _decides_like(lm, nxt, lm_p, nx_p):
     np.testing.assert_allclose(nxt["lnl"], nx_p["lnl"], rtol=0, atol=1e-3)
 
 
-def test_judge_keeps_a_helpful_network_and_drops_a_harmful_one():
+def test_judge_keeps_a_helpful_network_and_drops_a_harmful_one(warm_weights):
     import bench
-    T = bench.THRESH
-    a, starts = bench.workload(0)
+    W = bench.WORKLOADS["pt27"]
+    T = W["thresh"]
+    a, starts = bench.workload(W, 0)
     with pt.Context(precision="mixed", table_log2=22) as ctx:
-        bench.train_warm_start(ctx, 0)
         aid = ctx.load_alignment(a.codes)
         ctx.set_model(aid, a.exch, a.freqs, 0.5, 4)
-        lmax0, front, _ = bench.build_frontier(ctx, aid, starts, 256)
+        hc = ctx.hill_climb(aid, *starts)
+        lmax0, front, _ = bench.build_frontier(ctx, aid, hc["edges"], hc["lengths"], W["frontier"], T)
+        ctx.mlp_set_weights(warm_weights)
         trained = np.array(ctx.mlp_get_weights(), np.float32)
         ctx.mlp_enable(False)
         lm_p, nx_p, st_p, sc_p, _ = _round(ctx, aid, front, T, lmax0)
