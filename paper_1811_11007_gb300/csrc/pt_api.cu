@@ -276,6 +276,7 @@ void end_stats(Ctx& c, const int64_t* host_counts) {
     ck(c, cudaStreamSynchronize(c.stream), "stream sync");
     for (int i = 0; i < kStWords; ++i) c.stats[i] = (int64_t)h[i];
     c.stats[kStLaunches] = launch_count() - c.launches0;
+    if (h[kStTimeout]) fail(c, PT_ERR_TIMEOUT, "%llu CTAs gave up waiting for their cluster's Newton sums", h[kStTimeout]);
     if (host_counts)
         for (int i : {kStCand, kStScored, kStKept}) c.stats[i] = host_counts[i];
 }
@@ -1186,7 +1187,8 @@ void expand_batch(Ctx& c, const std::vector<RoundIn>& ins, std::vector<RoundOut>
             else cands.push_back({threads_for(c, maxP), 1});
             for (int k : kClusters)
                 if (propose_cluster_ok(prec, C, k) && (maxP + k - 1) / k >= 64)
-                    for (int t : kTuneClusterThreads) cands.push_back({t, k});
+                    for (int t : kTuneClusterThreads)
+                        if (propose_cluster_grid(prec, C, k, t, maxP) > 0) cands.push_back({t, k});
             const int dK = default_cluster(c, prec, C, maxP, threads_for(c, maxP));
             int bt = threads, bK = K;
             for (auto [ct, kc] : cands) {

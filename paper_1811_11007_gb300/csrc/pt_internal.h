@@ -90,7 +90,9 @@ enum { kErrTree = 0, kErrTable = 1, kErrKey = 2, kErrNumeric = 3, kErrLen = 4, k
 // Device counters (int64 words), match pt_stats.
 enum {
     kStCand = 0, kStDup = 1, kStScored = 2, kStKept = 3, kStGood = 4, kStPropEvals = 5, kStFullEvals = 6,
-    kStNonconv = 7, kStPropSweeps = 8, kStFullSweeps = 9, kStLaunches = 10, kStWords = 16
+    kStNonconv = 7, kStPropSweeps = 8, kStFullSweeps = 9, kStLaunches = 10,
+    kStTimeout = 11,  // CTAs whose wait for their cluster's Newton sums ran out (PT_ERR_TIMEOUT)
+    kStWords = 16
 };
 
 // A group of trees sharing one partial-likelihood buffer: tree g's vectors

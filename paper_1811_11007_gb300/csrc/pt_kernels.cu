@@ -822,6 +822,35 @@ __device__ __forceinline__ void load_raw(const Src<R, C>& s, int p, R* x, int& c
     }
 }
 
+// Row i of P_r from a [C][16] row-major block as one 16-byte load (FP32) or two
+// (FP64); every P block starts on a 16-byte boundary.
+template <typename R>
+__device__ __forceinline__ void pm_row(const R* Pm, int r, int i, R* w) {
+    if constexpr (sizeof(R) == 4) {
+        const float4 v = reinterpret_cast<const float4*>(Pm)[r * 4 + i];
+        w[0] = v.x; w[1] = v.y; w[2] = v.z; w[3] = v.w;
+    } else {
+        const double2 a = reinterpret_cast<const double2*>(Pm)[(r * 4 + i) * 2];
+        const double2 b = reinterpret_cast<const double2*>(Pm)[(r * 4 + i) * 2 + 1];
+        w[0] = a.x; w[1] = a.y; w[2] = b.x; w[3] = b.y;
+    }
+}
+
+template <typename R, int C>
+__device__ __forceinline__ void apply_p_reg(const R* Pm, const R* x, R* y) {
+#pragma unroll
+    for (int r = 0; r < C; ++r)
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            R w[4];
+            pm_row<R>(Pm, r, i, w);
+            R acc = w[0] * x[r * 4];
+#pragma unroll
+            for (int j = 1; j < 4; ++j) acc = fma(w[j], x[r * 4 + j], acc);
+            y[r * 4 + i] = acc;
+        }
+}
+
 // y_r = P_r x_r (Pm: [C][16] row-major); for a tip the product is a column
 // of P (or all ones for a gap).
 template <typename R, int C>
@@ -842,28 +871,7 @@ __device__ __forceinline__ void apply_p(const R* Pm, const Src<R, C>& s, int p, 
     }
     R x[4 * C];
     load_raw<R, C>(s, p, x, cnt);
-#pragma unroll
-    for (int r = 0; r < C; ++r)
-#pragma unroll
-        for (int i = 0; i < 4; ++i) {
-            R acc = Pm[r * 16 + i * 4] * x[r * 4];
-#pragma unroll
-            for (int j = 1; j < 4; ++j) acc = fma(Pm[r * 16 + i * 4 + j], x[r * 4 + j], acc);
-            y[r * 4 + i] = acc;
-        }
-}
-
-template <typename R, int C>
-__device__ __forceinline__ void apply_p_reg(const R* Pm, const R* x, R* y) {
-#pragma unroll
-    for (int r = 0; r < C; ++r)
-#pragma unroll
-        for (int i = 0; i < 4; ++i) {
-            R acc = Pm[r * 16 + i * 4] * x[r * 4];
-#pragma unroll
-            for (int j = 1; j < 4; ++j) acc = fma(Pm[r * 16 + i * 4 + j], x[r * 4 + j], acc);
-            y[r * 4 + i] = acc;
-        }
+    apply_p_reg<R, C>(Pm, x, y);
 }
 
 template <typename R, int C>
@@ -1271,6 +1279,72 @@ struct STab {
     }
 };
 
+// Warps of one thread-block cluster whose Newton sums one CTA receives (K x warps
+// per CTA); launch shapes above it are not offered.
+constexpr int kMaxClusterWarps = 64;
+// A CTA gives up waiting for its cluster's Newton sums after this many cycles
+// (about 2 s); the kernel then reports PT_ERR_TIMEOUT through its statistics.
+constexpr long long kExchangeWaitCycles = 1ll << 32;
+
+// mbarrier and cluster-push primitives (PTX).  A push st.async's 16 bytes into
+// the same variable of another CTA `rank` of the cluster and completes 16 bytes
+// of the transaction count of that CTA's barrier; a CTA's own warps store their
+// entries locally and arrive on the barrier; the receiver arms its barrier with
+// the bytes it expects from the other CTAs and waits on the phase parity.
+__device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void mbar_init(unsigned long long* bar, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_fence_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+__device__ __forceinline__ void mbar_arrive_expect(unsigned long long* bar, unsigned bytes) {
+    asm volatile(
+        "{\n\t.reg .b64 st;\n\t"
+        "mbarrier.arrive.expect_tx.release.cta.shared::cta.b64 st, [%0], %1;\n\t}" ::"r"(smem_addr(bar)),
+        "r"(bytes)
+        : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(unsigned long long* bar) {
+    asm volatile(
+        "{\n\t.reg .b64 st;\n\t"
+        "mbarrier.arrive.release.cta.shared::cta.b64 st, [%0];\n\t}" ::"r"(smem_addr(bar))
+        : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, unsigned parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+__device__ __forceinline__ void cluster_push16(float* dst, unsigned long long* bar, unsigned rank, float4 v) {
+    uint32_t d, b;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(d) : "r"(smem_addr(dst)), "r"(rank));
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(b) : "r"(smem_addr(bar)), "r"(rank));
+    asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.v4.f32 [%0], {%1, %2, %3, %4}, [%5];" ::"r"(d),
+                 "f"(v.x), "f"(v.y), "f"(v.z), "f"(v.w), "r"(b)
+                 : "memory");
+}
+__device__ __forceinline__ unsigned cluster_rank() {
+    unsigned r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+// Sets up the two exchange barriers of a cluster CTA (once per launch, before its
+// first cluster barrier; thread 0): each phase takes one arrival per warp of the
+// CTA (its local entry) and one from the leader, which arms the remote bytes.
+template <typename NS>
+__device__ __forceinline__ void cluster_exchange_init(NS& ns) {
+    const unsigned nw = (blockDim.x + 31) >> 5;
+    mbar_init(&ns.mbx[0], nw + 1);
+    mbar_init(&ns.mbx[1], nw + 1);
+    ns.abort_ = 0;
+    mbar_fence_init();
+}
+
 // Block-wide context for the Newton machinery.
 template <typename R, int C>
 struct NewtonSmem {
@@ -1286,7 +1360,12 @@ struct NewtonSmem {
     int leader;            // the warp that takes the Newton steps
     double cx[2][3];       // cluster exchange: this CTA's partial sums, two alternating slots
     alignas(16) float cxf[2][4];  // the same for FP32 pairs (d1 hi, lo, d2 hi, lo), read as float4
-    alignas(16) float cxw[2][16][4];  // per-warp FP32 pairs of the Newton sums, published to the cluster
+    // Newton sums of a cluster (K > 1, FP32 pairs): every warp of every CTA pushes its
+    // (d1 h, l, d2 h, l) into entry rank * nw + warp of every CTA's slot, two
+    // alternating slots, each with an mbarrier that counts the bytes it received
+    alignas(16) float cxr[2][kMaxClusterWarps][4];
+    alignas(8) unsigned long long mbx[2];
+    int abort_;            // a wait on mbx ran out: later waits are skipped (reported by the kernel)
 };
 
 // Sums of up to three values held by one thread (`writer`) of each CTA of a
@@ -1605,6 +1684,29 @@ __device__ double eval_lnl(const Model& M, const STab<R, C>& st, int P, double t
     return tot;
 }
 
+// One site's terms of the Newton sums: a = L'/L, b = L''/L and the site weight,
+// from the sum-table at the coefficients e, g, h (the stationary slots, k = 0,
+// have zero derivative coefficients).
+template <typename R, int C>
+__device__ __forceinline__ void newton_site(const STab<R, C>& st, int p, const R* e, const R* g, const R* h, R& a, R& b,
+                                            R& wt) {
+    R s[4 * C];
+    st.get(p, s);
+    R L = e[0] * s[0], L1 = g[1] * s[1], L2 = h[1] * s[1];
+#pragma unroll
+    for (int q = 1; q < 4 * C; ++q) {
+        L = fma(e[q], s[q], L);
+        if ((q & 3) != 0 && q != 1) {
+            L1 = fma(g[q], s[q], L1);
+            L2 = fma(h[q], s[q], L2);
+        }
+    }
+    const R inv = Prec<R>::rcp(L);
+    a = L1 * inv;
+    b = L2 * inv;
+    wt = st.ew[st.pcap + p];
+}
+
 // Newton solve on the current sum-table from t0.  Per evaluation: every
 // thread sums w L'/L and w (L''/L - (L'/L)^2) over its sites, the warps
 // reduce, and warp 0 alone takes the FP64 step and writes the coefficients
@@ -1616,7 +1718,8 @@ __device__ double eval_lnl(const Model& M, const STab<R, C>& st, int P, double t
 // every CTA takes the same step.
 template <typename R, int C, int K = 1>
 __device__ double newton_solve(const Model& M, const Cfg& cfg, const STab<R, C>& st, int P, double t0,
-                               NewtonSmem<R, C>& ns, int& evals, bool& converged, R* Pdst, int* cseq = nullptr) {
+                               NewtonSmem<R, C>& ns, int& evals, bool& converged, R* Pdst, int* cseq = nullptr,
+                               int* nseq = nullptr) {
     double lo = cfg.tmin, hi = cfg.tmax;
     double t = fmin(fmax(t0, lo), hi);
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = (blockDim.x + 31) >> 5;
@@ -1642,38 +1745,48 @@ __device__ double newton_solve(const Model& M, const Cfg& cfg, const STab<R, C>&
 #pragma unroll
         for (int q = 0; q < 4 * C; ++q) { e[q] = ns.egh[0][q]; g[q] = ns.egh[1][q]; h[q] = ns.egh[2][q]; }
         R a1 = R(0), a2 = R(0);
-        for (int p = threadIdx.x; p < P; p += blockDim.x) {
-            R s[4 * C];
-            st.get(p, s);
-            // the stationary slots (k = 0) have zero derivative coefficients
-            R L = e[0] * s[0], L1 = g[1] * s[1], L2 = h[1] * s[1];
-#pragma unroll
-            for (int q = 1; q < 4 * C; ++q) {
-                L = fma(e[q], s[q], L);
-                if ((q & 3) != 0 && q != 1) {
-                    L1 = fma(g[q], s[q], L1);
-                    L2 = fma(h[q], s[q], L2);
-                }
-            }
-            R inv = Prec<R>::rcp(L);
-            R a = L1 * inv, b = L2 * inv;
-            R wt = st.ew[st.pcap + p];
+        // two sites per pass (their chains interleave), added in site order
+        const int bd = blockDim.x;
+        int p = threadIdx.x;
+        for (; p + bd < P; p += 2 * bd) {
+            R a, b, wt, a_, b_, wt_;
+            newton_site<R, C>(st, p, e, g, h, a, b, wt);
+            newton_site<R, C>(st, p + bd, e, g, h, a_, b_, wt_);
+            a1 = fma(wt, a, a1);
+            a2 = fma(wt, b - a * a, a2);
+            a1 = fma(wt_, a_, a1);
+            a2 = fma(wt_, b_ - a_ * a_, a2);
+        }
+        if (p < P) {
+            R a, b, wt;
+            newton_site<R, C>(st, p, e, g, h, a, b, wt);
             a1 = fma(wt, a, a1);
             a2 = fma(wt, b - a * a, a2);
         }
         // the per-warp sums: to this CTA's shared memory, or (FP32 pairs in a cluster)
-        // straight to the cluster exchange, whose barrier then serves both levels
-        bool pub = false;  // published to the cluster exchange (slot cs)
-        int cs = 0;
+        // pushed into every CTA of the cluster, where the leader waits for them
+        bool pub = false;  // pushed to the cluster (slot cs of exchange xe)
+        int cs = 0, xe = 0;
         if constexpr (sizeof(R) == 4) {
             const float2 d1 = warp_sum_comp(a1), d2 = warp_sum_comp(a2);
             if constexpr (K > 1) {
-                cs = *cseq & 1;
-                ++*cseq;
-                if (lane == 0)
-                    *reinterpret_cast<float4*>(&ns.cxw[cs][w][0]) = make_float4(d1.x, d1.y, d2.x, d2.y);
-                cooperative_groups::this_cluster().sync();
-                pub = true;
+                // Slot cs is free in every CTA: a warp pushes exchange xe only after its
+                // CTA's leader received all of exchange xe - 1, which every CTA pushed
+                // after its own leader had read exchange xe - 2 (the last use of cs).
+                xe = *nseq;
+                cs = xe & 1;
+                ++*nseq;
+                if (lane == 0) {
+                    const float4 v = make_float4(d1.x, d1.y, d2.x, d2.y);
+                    const unsigned me = cluster_rank();
+                    float* slot = &ns.cxr[cs][me * nw + w][0];
+#pragma unroll
+                    for (int r = 0; r < K; ++r)
+                        if ((unsigned)r != me) cluster_push16(slot, &ns.mbx[cs], (unsigned)r, v);
+                    *reinterpret_cast<float4*>(slot) = v;  // this CTA's own copy
+                    mbar_arrive(&ns.mbx[cs]);
+                }
+                pub = true;  // no block barrier here: only the leader needs the sums
             } else if (lane == 0) {
                 ns.redf[w][0] = d1.x; ns.redf[w][1] = d1.y; ns.redf[w][2] = d2.x; ns.redf[w][3] = d2.y;
             }
@@ -1693,14 +1806,21 @@ __device__ double newton_solve(const Model& M, const Cfg& cfg, const STab<R, C>&
             float h = 0.f, l = 0.f;
             if constexpr (K > 1) {
                 if (w == ld) {
+                    // wait (bounded) until the slot holds all K x nw pushes of this exchange
+                    if (lane == 0) mbar_arrive_expect(&ns.mbx[cs], (unsigned)((K - 1) * nw * 16));
+                    bool ok = ns.abort_ != 0;  // after a wait ran out, none is waited for again
+                    const long long tw = clock64();
+                    while (!ok) {
+                        ok = mbar_try_wait(&ns.mbx[cs], (unsigned)(xe >> 1) & 1u);
+                        if (!ok && clock64() - tw > kExchangeWaitCycles) break;
+                    }
+                    if (__any_sync(0xffffffffu, !ok) && lane == 0) ns.abort_ = 1;
                     // the cluster's K x nw warp pairs: lane j takes pairs j, j + 32, ...
                     // (CTA j / nw, warp j % nw) in a fixed order, then a 32-lane
                     // butterfly: every CTA adds the same numbers in the same order
-                    namespace cg = cooperative_groups;
-                    cg::cluster_group cl = cg::this_cluster();
                     float h2 = 0.f, l2 = 0.f;
                     for (int j = lane; j < K * nw; j += 32) {
-                        const float4 q = *reinterpret_cast<const float4*>(cl.map_shared_rank(&ns.cxw[cs][j % nw][0], j / nw));
+                        const float4 q = *reinterpret_cast<const float4*>(&ns.cxr[cs][j][0]);
                         const F2 u = f2_two_sum(h, q.x), v = f2_two_sum(h2, q.z);
                         h = u.h;
                         l = __fadd_rn(__fadd_rn(l, q.y), u.l);
@@ -2141,7 +2261,9 @@ __global__ void __launch_bounds__(512) k_propose(const PropGroup* __restrict__ g
     const int nb = cfg.propose_mode == 1 ? 1 : 5;
     unsigned long long evals_total = 0, sweeps_total = 0, nonconv = 0;
     int cseq = 0;  // cluster exchanges so far (equal in every thread of the cluster)
+    int nseq = 0;  // pushed Newton exchanges so far (the same)
     const int rank = K > 1 ? (int)cooperative_groups::this_cluster().block_rank() : 0;
+    if (K > 1 && threadIdx.x == 0) cluster_exchange_init(sm.ns);  // before the first cluster barrier
     while (true) {
         // previous item done with shared memory (in every CTA of the cluster: rank 0 writes theirs)
         if constexpr (K > 1) cooperative_groups::this_cluster().sync();
@@ -2305,7 +2427,7 @@ __global__ void __launch_bounds__(512) k_propose(const PropGroup* __restrict__ g
                 int ev;
                 bool conv;
                 // new length; the solve leaves P matrices of branch b at it in sm.Pm[b]
-                const double t = newton_solve<R, C, K>(M, cfg, st, Pl, told, sm.ns, ev, conv, sm.Pm[b], &cseq);
+                const double t = newton_solve<R, C, K>(M, cfg, st, Pl, told, sm.ns, ev, conv, sm.Pm[b], &cseq, &nseq);
                 moved = fmax(moved, fabs(t - told));
                 evals_total += ev;
                 item_evals += ev;
@@ -2374,6 +2496,7 @@ __global__ void __launch_bounds__(512) k_propose(const PropGroup* __restrict__ g
         atomicAdd(&stats[kStPropSweeps], sweeps_total);
         atomicAdd(&stats[kStNonconv], nonconv);
     }
+    if (K > 1 && threadIdx.x == 0 && sm.ns.abort_) atomicAdd(&stats[kStTimeout], 1ull);
     if constexpr (K > 1) cooperative_groups::this_cluster().sync();  // no CTA leaves while others may read it
 }
 
@@ -2412,7 +2535,9 @@ __global__ void __launch_bounds__(512) k_fullopt(const FullGroup* __restrict__ g
     const int total = gstart[ngroups];
     unsigned long long evals_total = 0, sweeps_total = 0, nonconv = 0;
     int cseq = 0;  // cluster exchanges so far (equal in every thread of the cluster)
+    int nseq = 0;  // pushed Newton exchanges so far (the same)
     const int rank = K > 1 ? (int)cooperative_groups::this_cluster().block_rank() : 0;
+    if (K > 1 && threadIdx.x == 0) cluster_exchange_init(sm.ns);  // before the first cluster barrier
     while (true) {
         // previous tree done with shared memory (in every CTA of the cluster: rank 0 writes theirs)
         if constexpr (K > 1) cooperative_groups::this_cluster().sync();
@@ -2592,7 +2717,7 @@ __global__ void __launch_bounds__(512) k_fullopt(const FullGroup* __restrict__ g
                 bool conv;
                 // the solve leaves the P matrices of edge v at its new length in Pm
                 const double t = newton_solve<R, C, K>(M, cfg, st, Pl, told, sm.ns, ev, conv, Pm + (size_t)v * C * 16,
-                                                       &cseq);
+                                                       &cseq, &nseq);
                 moved = fmax(moved, fabs(t - told));
                 evals_total += ev;
                 if (!conv) ++nonconv;
@@ -2632,6 +2757,7 @@ __global__ void __launch_bounds__(512) k_fullopt(const FullGroup* __restrict__ g
         atomicAdd(&stats[kStFullSweeps], sweeps_total);
         atomicAdd(&stats[kStNonconv], nonconv);
     }
+    if (K > 1 && threadIdx.x == 0 && sm.ns.abort_) atomicAdd(&stats[kStTimeout], 1ull);
     if constexpr (K > 1) cooperative_groups::this_cluster().sync();  // no CTA leaves while others may read it
 }
 
@@ -2965,6 +3091,7 @@ inline int cluster_share(int P, int K) { return ((P + K - 1) / K + 3) & ~3; }
 template <int K>
 bool propose_cluster_t(cudaStream_t s, const PropGroup* groups, const int* gstart, int ngroups, int* counter, Cfg cfg,
                        unsigned long long* stats, int threads, int grid, int maxP) {
+    if (K * ((threads + 31) / 32) > kMaxClusterWarps) return false;
     const size_t smem = propose_smem_bytes(1, 4, cluster_share(maxP, K), true, threads);
     auto kern = k_propose<float, 4, true, K>;
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
@@ -2992,6 +3119,7 @@ bool propose_cluster_t(cudaStream_t s, const PropGroup* groups, const int* gstar
 // Resident clusters of K CTAs of the proposal kernel on the whole GPU (0: cannot run).
 template <int K>
 int propose_cluster_occ(int threads, int maxP) {
+    if (K * ((threads + 31) / 32) > kMaxClusterWarps) return 0;
     const size_t smem = propose_smem_bytes(1, 4, cluster_share(maxP, K), true, threads);
     auto kern = k_propose<float, 4, true, K>;
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
@@ -3066,6 +3194,7 @@ template <int K>
 bool fullopt_cluster_t(cudaStream_t s, const FullGroup* groups, const int* gstart, int ngroups, int* counter, int maxN,
                        int maxP, Cfg cfg, unsigned long long* stats, int threads, int grid, void* slab,
                        size_t slab_per_cta) {
+    if (K * ((threads + 31) / 32) > kMaxClusterWarps) return false;
     const size_t smem = fullopt_smem_bytes(1, 4, maxN, cluster_share(maxP, K), true, threads);
     const int ps = full_p_smem(1, 4, maxN, cluster_share(maxP, K), true, threads);
     auto kern = k_fullopt<float, 4, true, K>;
@@ -3094,6 +3223,7 @@ bool fullopt_cluster_t(cudaStream_t s, const FullGroup* groups, const int* gstar
 
 template <int K>
 int fullopt_cluster_occ(int threads, int maxN, int maxP) {
+    if (K * ((threads + 31) / 32) > kMaxClusterWarps) return 0;
     const size_t smem = fullopt_smem_bytes(1, 4, maxN, cluster_share(maxP, K), true, threads);
     auto kern = k_fullopt<float, 4, true, K>;
     if (smem > 227 * 1024 ||
