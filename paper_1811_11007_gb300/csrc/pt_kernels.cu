@@ -2418,7 +2418,11 @@ __global__ void __launch_bounds__(512) k_propose(const PropGroup* __restrict__ g
                         for (int q = 0; q < 4 * C; ++q) Y[q] = t1[q] * X[q];
                         load_raw<R, C>(a3, p, X, k3);
                     }
-                    int ex = normalise<R, C>(X), ey = normalise<R, C>(Y);
+                    // b > 0: X is the member's stored vector (kept above 2^-kScaleExp by the
+                    // rescaling) or a tip, so it needs no normalisation: its scale multiplies
+                    // the site's sum-table row by a power of two, exactly, which the Newton
+                    // ratios L'/L, L''/L do not see and the row's exponent field records
+                    int ex = b == 0 ? normalise<R, C>(X) : 0, ey = normalise<R, C>(Y);
                     R s4[4 * C];
                     sumtable<R, C>(sm.Mt, sm.pi, X, Y, s4);
                     st.put(pl, s4, (R)(ex + ey - Prec<R>::kScaleExp * (k0 + k1 + k2 + k3)), (R)G.A.w[p]);
@@ -2661,7 +2665,9 @@ __global__ void __launch_bounds__(512) k_fullopt(const FullGroup* __restrict__ g
                         scl[(size_t)slot * Ps + p] = cx;
                     }
                 }
-                const int ex = normalise<R, C>(X), ey = normalise<R, C>(Y);
+                // Y is D_v as stored (kept above 2^-kScaleExp by the rescaling) or a tip:
+                // no normalisation needed (an exact power-of-two scale of the row)
+                const int ex = normalise<R, C>(X), ey = 0;
                 R s4[4 * C];
                 sumtable<R, C>(sm.Mt, sm.pi, X, Y, s4);
                 st.put(p, s4, (R)(ex + ey - Prec<R>::kScaleExp * (cx + cy)), (R)w0[p]);
