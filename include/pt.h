@@ -58,7 +58,9 @@ typedef enum {
     PT_ERR_TABLE_FULL = 3,       /* visited table probe limit reached */
     PT_ERR_BUFFER_TOO_SMALL = 4, /* output capacity below the required count */
     PT_ERR_CUDA = 5,             /* a CUDA runtime call failed */
-    PT_ERR_TIMEOUT = 6,          /* a bounded device wait ran out */
+    PT_ERR_TIMEOUT = 6,          /* a bounded device wait ran out: a CTA of a thread-block
+                                    cluster waited about 2 s for its cluster's Newton sums
+                                    (the call's results are then not valid) */
     PT_ERR_STATE = 7             /* call out of order (no alignment / model) */
 } pt_status;
 
