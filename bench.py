@@ -67,7 +67,7 @@ WORKLOADS = {
 # by its units: neighbours, or full-optimisation sweeps of kept trees); None until captured
 # (profiles/ holds the captures)
 DRAM = {"pt128": {"per_neighbour": (1.492012e9 + 0.312236e9) / 1961,      # profiles/k_propose_128taxa_5908patterns.md
-                  "per_full_sweep": (145.852160e9 + 84.913132e9) / 692},   # profiles/k_fullopt_128taxa_5908patterns.md
+                  "per_full_sweep": (145.843998e9 + 84.912576e9) / 692},   # profiles/k_fullopt_128taxa_5908patterns.md
         "pt27": {"per_neighbour": None, "per_full_sweep": None}}
 FP32_LANES_PER_SM = 128
 # warm-start training runs (log_training_runs): 27-taxon x 2000-site searches from 8 hill-climbs

@@ -2542,12 +2542,20 @@ __global__ void __launch_bounds__(512) k_fullopt(const FullGroup* __restrict__ g
     int nseq = 0;  // pushed Newton exchanges so far (the same)
     const int rank = K > 1 ? (int)cooperative_groups::this_cluster().block_rank() : 0;
     if (K > 1 && threadIdx.x == 0) cluster_exchange_init(sm.ns);  // before the first cluster barrier
+    bool first = true;  // thread 0: this CTA (cluster) has not taken a tree yet
     while (true) {
         // previous tree done with shared memory (in every CTA of the cluster: rank 0 writes theirs)
         if constexpr (K > 1) cooperative_groups::this_cluster().sync();
         else __syncthreads();
         if (threadIdx.x == 0 && rank == 0) {
-            const int x = atomicAdd(counter, 1);
+            // Cluster c's first tree is tree c (the costliest trees come first, and clusters
+            // in launch order are spread over the SMs), later ones come from the counter
+            // after the grid's first trees.  With fewer trees than clusters, taking the
+            // first trees from the counter let two CTAs of one SM win trees while other SMs
+            // stayed idle (a capacity-sized graph launch).
+            const int nclus = (int)(gridDim.x / K);
+            const int x = first ? (int)(blockIdx.x / K) : nclus + atomicAdd(counter, 1);
+            first = false;
             int k = 0;
             while (k + 1 < ngroups && gstart[k + 1] <= x) ++k;
             if constexpr (K > 1) {
