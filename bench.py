@@ -515,7 +515,7 @@ def run_ours(args, W, rank, world, dev):
         hbm_peak = hbm_peak or 6800.0
         st = res["stats"]
         nd = res["steps"]
-        # algorithmic bytes (DESIGN.md section 6): per neighbour the path's 320*P (its four member
+        # algorithmic bytes: per neighbour the path's 320*P (its four member
         # vectors, shared by the two swaps of an edge, 128*P, and the amortised production of the
         # parent's partials, 192*P), over the proposal kernel's time; a visit writes and reads each
         # of its 2n-5 stored vectors once per sweep, 128*P*(2n-5) per sweep, plus the first
