@@ -444,13 +444,30 @@ const int kClusters[] = {2, 4, 8};
 // CTA's shared memory; else the smallest cluster whose share leaves room for
 // two CTAs per SM (the sum-table would otherwise stream through L2/HBM at
 // every Newton evaluation).
+// Default CTAs per item of an untuned launch: one CTA when its sum-table fits in
+// shared memory; else the smallest thread-block cluster whose shares leave room
+// for two CTAs per SM (a resident grid of at least 1.9 x the SMs), the shape
+// the tuner picks at 128 taxa x 5908 patterns; failing that, the smallest
+// cluster that launches at all.
+template <typename Grid>
+int pick_cluster(const Ctx& c, int prec, int C, Grid grid) {
+    int any = 0;
+    for (int K : kClusters) {
+        if (!propose_cluster_ok(prec, C, K)) continue;
+        const int g = grid(K);
+        if (g <= 0) continue;
+        if (!any) any = K;
+        if (10 * g >= 19 * c.sm_count) return K;
+    }
+    return any ? any : 1;
+}
 int default_cluster(const Ctx& c, int prec, int C, int P, int threads) {
     if (propose_smem_bytes(prec, C, P, true, threads) <= c.smem_optin) return 1;
-    for (int K : kClusters)
-        if (propose_cluster_ok(prec, C, K) && propose_smem_bytes(prec, C, (P + K - 1) / K + 4, true, threads) <= 110 * 1024 &&
-            propose_cluster_grid(prec, C, K, threads, P) > 0)
-            return K;
-    return 1;
+    return pick_cluster(c, prec, C, [&](int K) { return propose_cluster_grid(prec, C, K, threads, P); });
+}
+int default_full_cluster(const Ctx& c, int prec, int C, int maxN, int P, int threads) {
+    if (fullopt_smem_bytes(prec, C, maxN, P, true, threads) <= c.smem_optin) return 1;
+    return pick_cluster(c, prec, C, [&](int K) { return fullopt_cluster_grid(prec, C, K, threads, maxN, P); });
 }
 
 void save_tune(Ctx& c) {
@@ -624,7 +641,8 @@ void run_full_jobs(Ctx& c, std::vector<FullJob> jobs, bool allow_tune = true) {
             return (double)ms;
         };
         const std::string key = tune_key(prec, C, maxN, maxP);
-        int threads = threads_for(c, maxP), K = 1;
+        int threads = threads_for(c, maxP), K = default_full_cluster(c, prec, C, maxN, maxP, threads_for(c, maxP));
+        const int dK = K;
         auto it = c.tune.find(key);
         const bool have = it != c.tune.end() && it->second.full_threads;
         if (have) {
@@ -677,7 +695,11 @@ void run_full_jobs(Ctx& c, std::vector<FullJob> jobs, bool allow_tune = true) {
             // keep the default unless a candidate is clearly (>= 5%) faster
             const int dflt = threads_for(c, maxP);
             for (auto& tr : trials)
-                if (tr.first == dflt && tr.second <= best * 1.05) { bt = dflt; bK = 1; best = tr.second; }
+                if (tr.first == (dK > 1 ? dflt * 16 + dK : dflt) && tr.second <= best * 1.05) {
+                    bt = dflt;
+                    bK = dK;
+                    best = tr.second;
+                }
             threads = bt;
             K = bK;
             c.tune[key].full_trials = trials;
@@ -1706,6 +1728,7 @@ GraphRound* graph_create(Ctx& c, const std::vector<int>& ids, const std::vector<
     const std::string key = tune_key(prec, C, maxN, maxP);
     g.prop_threads = g.full_threads = threads_for(c, maxP);
     g.prop_cluster = default_cluster(c, prec, C, maxP, g.prop_threads);
+    g.full_cluster = default_full_cluster(c, prec, C, maxN, maxP, g.full_threads);
     auto tt = c.tune.find(key);
     if (tt != c.tune.end()) {
         if (tt->second.prop_threads) g.prop_threads = tt->second.prop_threads;
