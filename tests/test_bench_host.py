@@ -1,6 +1,8 @@
 """Host logic of bench.py that needs no GPU: the clock record built from
 nvidia-smi rows (median SM clock, maximum, throttle reasons seen, malformed
-rows skipped) and the per-workload default step counts."""
+rows skipped), the per-workload default step counts, and the protocol of the
+warm-start training runs (driven through a recording stand-in for the
+context)."""
 import sys
 
 import bench
@@ -38,3 +40,61 @@ def test_default_steps(monkeypatch):
                         [["--impl", "reference"], 3], [["--steps", "7"], 7]):
         monkeypatch.setattr(sys, "argv", ["bench.py"] + argv)
         assert bench.parse().steps == steps
+
+
+def test_default_steps_warm64(monkeypatch):
+    monkeypatch.setattr(sys, "argv", ["bench.py", "--workload", "warm64"])
+    assert bench.parse().steps == 3
+
+
+class _FakeCtx:
+    """Records the calls the warm-start training runs make (no GPU)."""
+
+    def __init__(self):
+        self.calls, self.logging, self.alns = [], False, []
+
+    def mlp_enable(self, on):
+        self.calls.append(("mlp", on))
+
+    def load_alignment(self, codes):
+        self.alns.append(codes.shape)
+        return len(self.alns) - 1
+
+    def set_model(self, aid, exch, freqs, alpha, ncat):
+        self.calls.append(("model", aid, ncat))
+
+    def hill_climb(self, aid, edges, lengths):
+        self.calls.append(("climb", aid, len(edges), self.logging))
+        return {"edges": edges, "lengths": lengths}
+
+    def training_log(self, on, capacity=0):
+        self.logging = on
+
+    def begin(self, aid, edges, lengths, thr):
+        self.calls.append(("begin", aid, len(edges), thr, self.logging))
+        return 0.0, {"edges": edges[:1], "lengths": lengths[:1]}
+
+    def expand(self, aid, edges, lengths, thr, lmax):
+        self.calls.append(("expand", aid, len(edges), thr, self.logging))
+        return lmax, {"edges": edges[:0], "lengths": lengths[:0]}  # the search ends
+
+
+def test_training_runs_protocol():
+    """Every 5th logged run is a 7-taxon x 500-site JC69 search (one category,
+    infinite threshold, one random start); the others are 27-taxon x 2000-site
+    GTR+G4 searches (4 categories, threshold 10) from 8 hill-climbs, which are
+    not logged; the network stays off; every round is logged."""
+    ctx = _FakeCtx()
+    runs = bench.log_training_runs(ctx, 0, 5)
+    assert runs == {"jc7_exhaustive": 1, "gtr27_climbed": 4}
+    assert ctx.calls[0] == ("mlp", False)
+    assert [s[0] for s in ctx.alns] == [27, 27, 27, 27, 7]
+    climbs = [c for c in ctx.calls if c[0] == "climb"]
+    assert [c[1] for c in climbs] == [0, 1, 2, 3] and all(c[2] == 8 and not c[3] for c in climbs)
+    models = {c[1]: c[2] for c in ctx.calls if c[0] == "model"}
+    assert models == {0: 4, 1: 4, 2: 4, 3: 4, 4: 1}
+    searches = [c for c in ctx.calls if c[0] in ("begin", "expand")]
+    assert all(c[4] for c in searches)  # logged
+    assert {c[3] for c in searches if c[1] < 4} == {bench.TRAIN_THRESH}
+    assert {c[3] for c in searches if c[1] == 4} == {float("inf")}
+    assert not ctx.logging
